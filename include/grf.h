@@ -1,0 +1,182 @@
+/*
+ * grf.h -- C ABI of the GB300 (sm_103a) sampler of Matern-type Gaussian random
+ * fields on metric graphs: lumped-mass FEM white noise, sinc quadrature of the
+ * Balakrishnan integral, and a non-overlapping edge/vertex domain decomposition
+ * of every shifted system (Kovacs, Molnar, Szaraz, "Efficient generation of
+ * Gaussian random fields on metric graphs via domain decomposition and mass
+ * matrix lumping").
+ *
+ * Conventions used below.
+ *   M_L  lumped mass: h_e at an interior node of edge e, sum_{e at v} h_e/2 at
+ *        vertex v (Sec. 3, Phase 2, lumped case).
+ *   G    P1 stiffness (Sec. 3, Phase 2);  K = kappa^2 M_L + G (the operator
+ *        kappa^2 - Delta of Eq. 1).
+ *   b    white noise M_L^{1/2} xi, xi ~ N(0, I) (Eq. wh_def, Sec. 2.5).
+ *   Quadrature (Eq. 4 and the limits of Sec. 4.1), 0 < beta < 1:
+ *        y_l = l k, l = -K^-..K^+, K^- = ceil(pi^2/(4k^2 beta)),
+ *        K^+ = ceil(pi^2/(4k^2(1-beta))), t_l = e^{2 y_l},
+ *        w_l = (2k sin(pi beta)/pi) e^{2 beta y_l};
+ *        U = sum_l w_l (M_L + t_l K)^{-1} b   (= sum_l (c_I M_L + c_L K)^{-1} b).
+ *   beta >= 1: beta = n + f; U = (K^{-1} M_L)^n U_f (f > 0) or
+ *        (K^{-1} M_L)^{n-1} K^{-1} b (f = 0).
+ *   DOF order: kept vertices (degree-0 vertices are dropped) in increasing
+ *        input id, then the interior nodes edge by edge, each edge from
+ *        edge_u towards edge_v (Sec. 3, Phase 1 mesh).
+ *   Field buffers are sample-major: element (s, j) at s * n_dofs + j.
+ *
+ * Ownership: input host arrays are copied; a grf_graph is owned by the library
+ * until grf_graph_destroy; output buffers and streams belong to the caller.
+ * The library allocates and caches device memory per graph (graph arrays and
+ * workspace), freed by grf_graph_destroy.
+ *
+ * Errors: every entry point returns GRF_OK (0) or a negative code; the
+ * message of the last failure on the calling thread is in grf_last_error().
+ * Device pointers must be on the device that is current when the call is made.
+ * All device work is enqueued on `stream` (NULL = legacy default stream);
+ * calls that return statistics synchronise that stream before returning.
+ */
+#ifndef GRF_H
+#define GRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GRF_OK 0
+#define GRF_EINVAL (-1)   /* invalid argument */
+#define GRF_ENOMEM (-2)   /* device or host allocation failed */
+#define GRF_ENOCONV (-3)  /* some vertex PCG did not reach rtol in max_iter; output written */
+#define GRF_ECUDA (-4)    /* CUDA runtime error */
+#define GRF_ENOTSUP (-5)  /* option not supported */
+#define GRF_ENUMERIC (-6) /* NaN/Inf or loss of positive definiteness detected */
+
+#define GRF_FP64 0        /* every step in FP64 */
+#define GRF_MIXED 1       /* FP32 edge sweeps; FP64 Schur blocks, PCG, quadrature sum */
+
+#define GRF_PRECOND_JACOBI 0
+
+#define GRF_OUT_F64 0
+#define GRF_OUT_F32 1
+
+typedef struct grf_graph grf_graph;
+
+typedef struct grf_options {
+  int32_t precision;   /* GRF_FP64 or GRF_MIXED */
+  int32_t precond;     /* GRF_PRECOND_JACOBI */
+  int32_t out_dtype;   /* GRF_OUT_F64 or GRF_OUT_F32 */
+  int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
+  double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */
+  int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms) */
+  int32_t reserved;
+} grf_options;
+
+typedef struct grf_stats {
+  int64_t n_dofs;          /* N = |V_kept| + sum_e (n_e - 1) */
+  int64_t n_nodes;         /* quadrature nodes solved (plus 1 per integer power) */
+  int64_t n_systems;       /* vertex systems solved: nodes x samples */
+  int64_t pcg_iters_total; /* sum of PCG iterations over all systems */
+  int32_t pcg_iters_max;
+  int32_t n_unconverged;   /* systems that hit max_iter */
+  int32_t numeric_flag;    /* nonzero: NaN/Inf or p.Sp <= 0 met */
+  int32_t kernel_launches; /* kernels this call launched */
+  /* with grf_options.timing: device milliseconds per phase, measured with CUDA
+   * events on the call's stream: [0] noise, [1] Schur blocks, [2] condensed
+   * right-hand side, [3] vertex PCG, [4] recovery + quadrature sum,
+   * [5] layout/mass scaling between stages; zero otherwise */
+  double phase_ms[6];
+} grf_stats;
+
+/* Build a metric graph and its uniform mesh (Sec. 2.1 graph; Sec. 3, Phase 1
+ * mesh: n_e = ceil(l_e / h), h_e = l_e / n_e).
+ *   n_vertices >= 1, n_edges >= 1; edge_u/edge_v: host int64 [n_edges], ids in
+ *   [0, n_vertices), no self-loops (parallel edges are allowed); lengths: host
+ *   double [n_edges], finite and > 0; n_elems: host int32 [n_edges] with every
+ *   entry >= 1, or NULL to use ceil(l_e / h) with h > 0.
+ *   Degree-0 vertices are dropped (their lumped mass is 0).
+ *   On success *out holds a new handle. Host-only; no device work. */
+int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
+                     const int64_t* edge_v, const double* lengths,
+                     const int32_t* n_elems, double h, grf_graph** out);
+
+/* Release the handle and all device memory it cached. NULL is accepted. */
+int grf_graph_destroy(grf_graph* g);
+
+/* Sizes of the mesh (Sec. 3, Phase 1). Any output pointer may be NULL.
+ *   vertex_map: host int64 [n_vertices input], input id -> kept id or -1.
+ *   interior_offsets: host int64 [n_edges + 1]; the interior nodes of edge e
+ *   are DOFs n_kept + interior_offsets[e] .. n_kept + interior_offsets[e+1]-1. */
+int grf_graph_info(const grf_graph* g, int64_t* n_dofs, int64_t* n_kept_vertices,
+                   int64_t* n_interior, int64_t* vertex_map, int64_t* interior_offsets);
+
+/* Draw n_samples fields of (kappa^2 - Delta)^beta u = W (Eq. 1) by the
+ * lumped-mass, domain-decomposed sinc quadrature (Eq. 4, Eq. spde_approx_fem,
+ * Sec. 3 Phases 2-5).
+ *   kappa > 0; beta > 0; k_step > 0 (quadrature step); seed: Philox key.
+ *   out: device buffer [n_samples][n_dofs] of double (GRF_OUT_F64) or float.
+ *   opts: NULL for defaults. stream: cudaStream_t or NULL.
+ *   stats: host, may be NULL. The call synchronises `stream` before returning.
+ * Returns GRF_ENOCONV if some PCG hit max_iter (output still written),
+ * GRF_ENUMERIC on NaN/Inf. */
+int grf_sample(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
+               int64_t n_samples, void* out, const grf_options* opts, void* stream,
+               grf_stats* stats);
+
+/* The same through host memory: out_host is a host buffer of the layout above;
+ * the call copies the field device -> host. For callers without device buffers. */
+int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
+                    int64_t n_samples, void* out_host, const grf_options* opts,
+                    void* stream, grf_stats* stats);
+
+/* White noise only (Eq. wh_def with the lumped factor, Sec. 2.5):
+ *   raw_words != 0: out is uint32 [n_samples][n_dofs], word j of sample s =
+ *     word (j mod 4) of Philox4x32-10(key = (seed lo32, seed hi32),
+ *     counter = (q lo32, q hi32, s, 0)), q = j div 4;
+ *   raw_words == 0: out is double [n_samples][n_dofs], b = sqrt(M_L) xi with
+ *     u = (word + 1/2) 2^-32 and Box-Muller on the word pairs (0,1), (2,3):
+ *     xi_a = sqrt(-2 ln u_a) cos(2 pi u_b), xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
+ * Asynchronous on `stream`. */
+int grf_noise(grf_graph* g, uint64_t seed, int64_t n_samples, void* out, int32_t raw_words,
+              void* stream);
+
+/* General right-hand side: out = sum_l weight[l] (alpha[l] M_L + gamma[l] K)^{-1} rhs
+ * through the same domain decomposition (Sec. 2.7 and Sec. 3, Phases 3-5).
+ *   alpha >= 0, gamma > 0, weight: host double [n_nodes];
+ *   rhs: device double [n_rhs][n_dofs]; out: device [n_rhs][n_dofs] per opts->out_dtype.
+ *   Synchronises `stream`. */
+int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
+              const double* gamma, const double* weight, int64_t n_rhs, const double* rhs,
+              void* out, const grf_options* opts, void* stream, grf_stats* stats);
+
+/* Vertex Schur system of one shifted matrix A = alpha M_L + gamma K (Eq.
+ * global_schur, Eq. local_reduced_schur): S = sum_e S^(e) assembled from
+ * per-edge 2x2 blocks.
+ *   diag: device double [n_kept]   (S_vv);
+ *   offdiag: device double [n_edges] (the coupling S_uv contributed by edge e).
+ * Asynchronous on `stream`. */
+int grf_schur(grf_graph* g, double kappa, double alpha, double gamma, double* diag,
+              double* offdiag, void* stream);
+
+/* Condensed right-hand side and vertex solution of one shifted system
+ * (Eq. global_schur, Eq. local_reduced_schur, Phase 4 PCG):
+ *   g_out[s][v] = rhs_v - sum_e A_vI^(e) (A_II^(e))^{-1} rhs_I^(e),
+ *   u_out[s][v] solves S u = g by Jacobi-PCG.
+ *   rhs: device double [n_rhs][n_dofs]; g_out, u_out: device double [n_rhs][n_kept].
+ *   Synchronises `stream`. */
+int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int64_t n_rhs,
+                     const double* rhs, double* g_out, double* u_out,
+                     const grf_options* opts, void* stream, grf_stats* stats);
+
+/* Bytes of device workspace grf_sample would cache for this graph and size. */
+int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t n_samples,
+                        const grf_options* opts, size_t* bytes);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* grf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRF_H */

@@ -1,0 +1,310 @@
+"""Python binding of the GB300 metric-graph Gaussian random field sampler.
+
+Argument marshalling only: every step of the sampler runs in the CUDA kernels
+of libgrf.so (built from csrc/ by build.py) behind the C ABI declared in
+include/grf.h. PyTorch supplies device memory and streams. There is no CPU
+path: if the library is missing, importing this package raises.
+
+The functions carry the C names (grf_graph_create, grf_sample, ...); the
+`Graph` class wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgrf.so")
+
+GRF_OK, GRF_EINVAL, GRF_ENOMEM, GRF_ENOCONV, GRF_ECUDA, GRF_ENOTSUP, GRF_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+GRF_FP64, GRF_MIXED = 0, 1
+GRF_PRECOND_JACOBI = 0
+GRF_OUT_F64, GRF_OUT_F32 = 0, 1
+
+C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
+             "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
+             "grf_workspace_bytes", "grf_last_error")
+
+
+class GrfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"grf error {code}: {msg}")
+        self.code = code
+
+
+class grf_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("out_dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class grf_stats(ctypes.Structure):
+    _fields_ = [("n_dofs", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("n_systems", ctypes.c_int64), ("pcg_iters_total", ctypes.c_int64),
+                ("pcg_iters_max", ctypes.c_int32), ("n_unconverged", ctypes.c_int32),
+                ("numeric_flag", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
+                ("phase_ms", ctypes.c_double * 6)]
+
+    PHASES = ("noise", "schur", "condense", "pcg", "recover", "layout")
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
+        return d
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2605_02670_gb300.build "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, I32, D, U64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_uint64
+    sig = {
+        "grf_graph_create": [I64, I64, P, P, P, P, D, ctypes.POINTER(P)],
+        "grf_graph_destroy": [P],
+        "grf_graph_info": [P, P, P, P, P, P],
+        "grf_sample": [P, D, D, D, U64, I64, P, P, P, P],
+        "grf_sample_host": [P, D, D, D, U64, I64, P, P, P, P],
+        "grf_noise": [P, U64, I64, P, I32, P],
+        "grf_apply": [P, D, I64, P, P, P, I64, P, P, P, P, P],
+        "grf_schur": [P, D, D, D, P, P, P],
+        "grf_vertex_solve": [P, D, D, D, I64, P, P, P, P, P, P],
+        "grf_workspace_bytes": [P, D, D, I64, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.grf_last_error.argtypes = []
+    lib.grf_last_error.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(code: int, allow=(GRF_OK,)) -> int:
+    if code not in allow:
+        raise GrfError(code, _lib.grf_last_error().decode())
+    return code
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
+                 timing=False) -> grf_options:
+    prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
+    if out_dtype is None:
+        out_dtype = "f64" if prec == GRF_FP64 else "f32"
+    od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
+    return grf_options(prec, GRF_PRECOND_JACOBI, od, int(max_iter), float(rtol),
+                       1 if timing else 0, 0)
+
+
+# ------------------------------------------------------------ C-named functions
+
+
+def grf_graph_create(edge_u, edge_v, lengths, n_vertices: int, h: float | None = None,
+                     n_elems=None) -> ctypes.c_void_p:
+    eu = np.ascontiguousarray(edge_u, dtype=np.int64)
+    ev = np.ascontiguousarray(edge_v, dtype=np.int64)
+    ln = np.ascontiguousarray(lengths, dtype=np.float64)
+    ne_ptr = None
+    if n_elems is not None:
+        ne = np.ascontiguousarray(n_elems, dtype=np.int32)
+        ne_ptr = _ptr(ne)
+    handle = ctypes.c_void_p()
+    _check(_lib.grf_graph_create(int(n_vertices), int(eu.shape[0]), _ptr(eu), _ptr(ev), _ptr(ln),
+                                 ne_ptr, float(h) if h is not None else 0.0, ctypes.byref(handle)))
+    return handle
+
+
+def grf_graph_destroy(handle) -> None:
+    _check(_lib.grf_graph_destroy(handle))
+
+
+def grf_graph_info(handle, n_vertices_in: int, n_edges: int) -> dict:
+    n, nk, ni = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    vmap = np.empty(n_vertices_in, np.int64)
+    offs = np.empty(n_edges + 1, np.int64)
+    _check(_lib.grf_graph_info(handle, ctypes.byref(n), ctypes.byref(nk), ctypes.byref(ni),
+                               _ptr(vmap), _ptr(offs)))
+    return {"n_dofs": n.value, "n_kept_vertices": nk.value, "n_interior": ni.value,
+            "vertex_map": vmap, "interior_offsets": offs}
+
+
+def grf_sample(handle, kappa, beta, k_step, seed, n_samples, out_ptr: int, opts: grf_options,
+               stream=None, allow_noconv=False) -> dict:
+    st = grf_stats()
+    allow = (GRF_OK, GRF_ENOCONV) if allow_noconv else (GRF_OK,)
+    _check(_lib.grf_sample(handle, float(kappa), float(beta), float(k_step), int(seed),
+                           int(n_samples), ctypes.c_void_p(out_ptr), ctypes.byref(opts),
+                           _stream(stream), ctypes.byref(st)), allow)
+    return st.as_dict()
+
+
+def grf_sample_host(handle, kappa, beta, k_step, seed, n_samples, out: np.ndarray,
+                    opts: grf_options, stream=None) -> dict:
+    st = grf_stats()
+    _check(_lib.grf_sample_host(handle, float(kappa), float(beta), float(k_step), int(seed),
+                                int(n_samples), _ptr(out), ctypes.byref(opts), _stream(stream),
+                                ctypes.byref(st)))
+    return st.as_dict()
+
+
+def grf_noise(handle, seed, n_samples, out_ptr: int, raw_words: bool, stream=None) -> None:
+    _check(_lib.grf_noise(handle, int(seed), int(n_samples), ctypes.c_void_p(out_ptr),
+                          1 if raw_words else 0, _stream(stream)))
+
+
+def grf_apply(handle, kappa, alpha, gamma, weight, n_rhs, rhs_ptr: int, out_ptr: int,
+              opts: grf_options, stream=None) -> dict:
+    a = np.ascontiguousarray(alpha, np.float64)
+    g = np.ascontiguousarray(gamma, np.float64)
+    w = np.ascontiguousarray(weight, np.float64)
+    st = grf_stats()
+    _check(_lib.grf_apply(handle, float(kappa), int(a.shape[0]), _ptr(a), _ptr(g), _ptr(w),
+                          int(n_rhs), ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(out_ptr),
+                          ctypes.byref(opts), _stream(stream), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def grf_schur(handle, kappa, alpha, gamma, diag_ptr: int, off_ptr: int, stream=None) -> None:
+    _check(_lib.grf_schur(handle, float(kappa), float(alpha), float(gamma),
+                          ctypes.c_void_p(diag_ptr), ctypes.c_void_p(off_ptr), _stream(stream)))
+
+
+def grf_vertex_solve(handle, kappa, alpha, gamma, n_rhs, rhs_ptr: int, g_ptr: int, u_ptr: int,
+                     opts: grf_options, stream=None) -> dict:
+    st = grf_stats()
+    _check(_lib.grf_vertex_solve(handle, float(kappa), float(alpha), float(gamma), int(n_rhs),
+                                 ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(g_ptr),
+                                 ctypes.c_void_p(u_ptr), ctypes.byref(opts), _stream(stream),
+                                 ctypes.byref(st)))
+    return st.as_dict()
+
+
+def grf_workspace_bytes(handle, beta, k_step, n_samples, opts: grf_options) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.grf_workspace_bytes(handle, float(beta), float(k_step), int(n_samples),
+                                    ctypes.byref(opts), ctypes.byref(b)))
+    return b.value
+
+
+# ------------------------------------------------------------ convenience wrapper
+
+
+class Graph:
+    """A metric graph handle with torch-tensor helpers (device memory only)."""
+
+    def __init__(self, edge_u, edge_v, lengths, n_vertices: int, h: float | None = None,
+                 n_elems=None):
+        self.n_vertices_in = int(n_vertices)
+        self.n_edges = int(np.asarray(edge_u).shape[0])
+        self.handle = grf_graph_create(edge_u, edge_v, lengths, n_vertices, h, n_elems)
+        info = grf_graph_info(self.handle, self.n_vertices_in, self.n_edges)
+        self.n_dofs = info["n_dofs"]
+        self.n_kept = info["n_kept_vertices"]
+        self.n_interior = info["n_interior"]
+        self.vertex_map = info["vertex_map"]
+        self.interior_offsets = info["interior_offsets"]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            grf_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
+               rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False):
+        import torch
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing)
+        dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
+        if out is None:
+            out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
+        assert out.dtype == dt and out.is_cuda and out.is_contiguous()
+        assert tuple(out.shape) == (n_samples, self.n_dofs)
+        stats = grf_sample(self.handle, kappa, beta, k_step, seed, n_samples, out.data_ptr(),
+                           opts, stream, allow_noconv)
+        return out, stats
+
+    def sample_host(self, kappa, beta, k_step, seed, n_samples, precision="fp64",
+                    out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False):
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing)
+        dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
+        if out is None:
+            out = np.empty((n_samples, self.n_dofs), dtype=dt)
+        stats = grf_sample_host(self.handle, kappa, beta, k_step, seed, n_samples, out, opts,
+                                stream)
+        return out, stats
+
+    def noise(self, seed, n_samples, raw=False, stream=None):
+        import torch
+        dt = torch.int32 if raw else torch.float64
+        out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
+        grf_noise(self.handle, seed, n_samples, out.data_ptr(), raw, stream)
+        return out
+
+    def apply(self, kappa, alpha, gamma, weight, rhs, precision="fp64", out_dtype=None,
+              rtol=0.0, max_iter=0, stream=None):
+        import torch
+        opts = make_options(precision, out_dtype, rtol, max_iter)
+        rhs = rhs.to(dtype=torch.float64).contiguous()
+        dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
+        out = torch.empty(tuple(rhs.shape), dtype=dt, device="cuda")
+        stats = grf_apply(self.handle, kappa, alpha, gamma, weight, rhs.shape[0], rhs.data_ptr(),
+                          out.data_ptr(), opts, stream)
+        return out, stats
+
+    def schur(self, kappa, alpha, gamma, stream=None):
+        import torch
+        diag = torch.empty(self.n_kept, dtype=torch.float64, device="cuda")
+        off = torch.empty(self.n_edges, dtype=torch.float64, device="cuda")
+        grf_schur(self.handle, kappa, alpha, gamma, diag.data_ptr(), off.data_ptr(), stream)
+        return diag, off
+
+    def vertex_solve(self, kappa, alpha, gamma, rhs, precision="fp64", rtol=0.0, max_iter=0,
+                     stream=None):
+        import torch
+        opts = make_options(precision, None, rtol, max_iter)
+        rhs = rhs.to(dtype=torch.float64).contiguous()
+        g = torch.empty((rhs.shape[0], self.n_kept), dtype=torch.float64, device="cuda")
+        u = torch.empty_like(g)
+        stats = grf_vertex_solve(self.handle, kappa, alpha, gamma, rhs.shape[0], rhs.data_ptr(),
+                                 g.data_ptr(), u.data_ptr(), opts, stream)
+        return g, u, stats
+
+    def workspace_bytes(self, beta, k_step, n_samples, precision="fp64") -> int:
+        return grf_workspace_bytes(self.handle, beta, k_step, n_samples, make_options(precision))
+
+
+def mesh_elements(lengths, h: float, clip=None) -> np.ndarray:
+    """Per-edge element counts n_e = ceil(l_e / h) (Sec. 3, Phase 1), optionally
+    clipped to [lo, hi], as int32 for grf_graph_create."""
+    n = np.ceil(np.asarray(lengths, np.float64) / h)
+    if clip is not None:
+        n = np.clip(n, clip[0], clip[1])
+    return np.maximum(n, 1).astype(np.int32)

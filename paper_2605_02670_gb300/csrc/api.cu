@@ -1,0 +1,758 @@
+// C ABI of the sampler (include/grf.h): graph building, quadrature nodes,
+// workspace management and the launch sequence of one sample call.
+//
+// Launch sequence of grf_sample (Sec. 3, Phases 2-5):
+//   noise (Phase 2) -> per node l: 2x2 edge Schur blocks and vertex diagonal
+//   -> condensed right-hand side g (Phase 3) -> Jacobi-PCG per (l, s)
+//   (Phase 4) -> vertex quadrature sum and fused interior recovery +
+//   quadrature sum (Phase 5). All nodes and samples are batched in each launch.
+#include <cmath>
+#include <cstdarg>
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/grf.h"
+#include "grf_internal.h"
+
+using namespace grf;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return fail(_e == cudaErrorMemoryAllocation ? GRF_ENOMEM : GRF_ECUDA, "%s: %s (%s:%d)", \
+                  #expr, cudaGetErrorString(_e), __FILE__, __LINE__);                    \
+  } while (0)
+
+#define GRF_TRY(expr)       \
+  do {                      \
+    int _r = (expr);        \
+    if (_r != GRF_OK) return _r; \
+  } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bump allocator over one cached device block.
+struct Carve {
+  char* base;
+  size_t off = 0;
+  bool dry;
+  explicit Carve(void* b) : base((char*)b), dry(b == nullptr) {}
+  template <typename T>
+  T* take(size_t count) {
+    size_t o = off;
+    off += align_up(count * sizeof(T));
+    return dry ? nullptr : reinterpret_cast<T*>(base + o);
+  }
+};
+
+}  // namespace
+
+struct grf_graph {
+  int64_t nv_in = 0;
+  int32_t nv = 0;
+  int32_t ne = 0;
+  int64_t ni = 0;
+  int64_t n = 0;
+  std::vector<int64_t> vertex_map;
+  std::vector<int32_t> eu, ev, nel, vptr, adj_edge, adj_nbr;
+  std::vector<double> he;
+  std::vector<int64_t> ioff;
+  std::vector<double> ml_vertex;  // lumped mass at kept vertices
+
+  int device = -1;
+  void* dev_block = nullptr;
+  DevGraph d{};
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+
+  ~grf_graph() {
+    if (device >= 0) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(device);
+      if (dev_block) cudaFree(dev_block);
+      if (ws) cudaFree(ws);
+      cudaSetDevice(cur);
+    }
+  }
+};
+
+namespace {
+
+__global__ void sqrt_ml_kernel(DevGraph g, const double* mlv, double* out) {
+  const int64_t total = g.n;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    if (j < g.nv) {
+      out[j] = sqrt(mlv[j]);
+    } else {
+      // interior DOF: find its edge by bisection over the interior offsets
+      const int64_t i = j - g.nv;
+      int32_t lo = 0, hi = g.ne - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (g.ioff[mid] <= i) lo = mid; else hi = mid - 1;
+      }
+      out[j] = sqrt(g.he[lo]);
+    }
+  }
+}
+
+int ensure_device(grf_graph* g) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (g->device == dev && g->dev_block) return GRF_OK;
+  if (g->device >= 0 && g->device != dev)
+    return fail(GRF_EINVAL, "graph was first used on device %d, now on device %d", g->device, dev);
+  const size_t E = (size_t)g->ne, V = (size_t)g->nv;
+  Carve c(nullptr);
+  c.take<int32_t>(E); c.take<int32_t>(E); c.take<int32_t>(E); c.take<double>(E);
+  c.take<int64_t>(E + 1); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
+  c.take<double>((size_t)g->n); c.take<double>(V);
+  void* blk = nullptr;
+  CUDA_TRY(cudaMalloc(&blk, c.off));
+  g->device = dev;
+  g->dev_block = blk;
+  Carve k(blk);
+  int32_t* eu = k.take<int32_t>(E);
+  int32_t* ev = k.take<int32_t>(E);
+  int32_t* nel = k.take<int32_t>(E);
+  double* he = k.take<double>(E);
+  int64_t* ioff = k.take<int64_t>(E + 1);
+  int32_t* vptr = k.take<int32_t>(V + 1);
+  int32_t* ae = k.take<int32_t>(2 * E);
+  int32_t* an = k.take<int32_t>(2 * E);
+  double* sml = k.take<double>((size_t)g->n);
+  double* mlv = k.take<double>(V);
+  CUDA_TRY(cudaMemcpy(eu, g->eu.data(), E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(ev, g->ev.data(), E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(nel, g->nel.data(), E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(he, g->he.data(), E * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(ioff, g->ioff.data(), (E + 1) * 8, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(vptr, g->vptr.data(), (V + 1) * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(ae, g->adj_edge.data(), 2 * E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(an, g->adj_nbr.data(), 2 * E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(mlv, g->ml_vertex.data(), V * 8, cudaMemcpyHostToDevice));
+  DevGraph& d = g->d;
+  d.nv = g->nv; d.ne = g->ne; d.ni = g->ni; d.n = g->n;
+  d.eu = eu; d.ev = ev; d.nel = nel; d.he = he; d.ioff = ioff;
+  d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.sqrt_ml = sml;
+  int64_t blocks = (g->n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  return GRF_OK;
+}
+
+int ensure_ws(grf_graph* g, size_t bytes) {
+  if (g->ws && g->ws_bytes >= bytes) return GRF_OK;
+  if (g->ws) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaFree(g->ws));
+    g->ws = nullptr;
+    g->ws_bytes = 0;
+  }
+  CUDA_TRY(cudaMalloc(&g->ws, bytes));
+  g->ws_bytes = bytes;
+  return GRF_OK;
+}
+
+struct HostNodes {
+  std::vector<double> alpha, gamma, weight;
+  int32_t L() const { return (int32_t)alpha.size(); }
+};
+
+// Sinc quadrature nodes of Eq. 4 with the limits of Sec. 4.1, 0 < f < 1:
+// y_l = l k, l = -K^- .. K^+; A_l = M_L + t_l K with t_l = e^{2 y_l};
+// weight w_l = (2 k sin(pi f) / pi) e^{2 f y_l}.
+HostNodes quadrature_nodes(double f, double k) {
+  const double pi = 3.14159265358979323846;
+  const long km = (long)std::ceil(pi * pi / (4.0 * k * k * f));
+  const long kp = (long)std::ceil(pi * pi / (4.0 * k * k * (1.0 - f)));
+  HostNodes h;
+  const double c = 2.0 * k * std::sin(pi * f) / pi;
+  for (long l = -km; l <= kp; ++l) {
+    const double y = (double)l * k;
+    h.alpha.push_back(1.0);
+    h.gamma.push_back(std::exp(2.0 * y));
+    h.weight.push_back(c * std::exp(2.0 * f * y));
+  }
+  return h;
+}
+
+HostNodes stiffness_node() {
+  HostNodes h;
+  h.alpha.push_back(0.0);
+  h.gamma.push_back(1.0);
+  h.weight.push_back(1.0);
+  return h;
+}
+
+struct Opts {
+  int precision, precond, out_dtype, max_iter;
+  double rtol;
+  bool timing;
+};
+
+int read_opts(const grf_options* o, Opts* r) {
+  r->timing = o && o->timing != 0;
+  r->precision = o ? o->precision : GRF_FP64;
+  r->precond = o ? o->precond : GRF_PRECOND_JACOBI;
+  r->out_dtype = o ? o->out_dtype : GRF_OUT_F64;
+  r->max_iter = (o && o->max_iter > 0) ? o->max_iter : 1000;
+  r->rtol = (o && o->rtol > 0) ? o->rtol : (r->precision == GRF_FP64 ? 1e-12 : 1e-9);
+  if (r->precision != GRF_FP64 && r->precision != GRF_MIXED)
+    return fail(GRF_EINVAL, "unknown precision %d", r->precision);
+  if (r->precond != GRF_PRECOND_JACOBI)
+    return fail(GRF_ENOTSUP, "preconditioner %d not available", r->precond);
+  if (r->out_dtype != GRF_OUT_F64 && r->out_dtype != GRF_OUT_F32)
+    return fail(GRF_EINVAL, "unknown out_dtype %d", r->out_dtype);
+  return GRF_OK;
+}
+
+// Device workspace of one domain-decomposed apply with L nodes and S right-hand sides.
+struct ApplyWs {
+  double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv, *gvec, *x, *r, *p, *q, *acc;
+  void *yscr, *rpscr;
+  int32_t* iters;
+  PcgStatus* status;
+};
+
+void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w) {
+  const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
+  const size_t nsg = (Ss + recover_sample_group() - 1) / recover_sample_group();
+  w->alpha = c.take<double>(Ls);
+  w->gamma = c.take<double>(Ls);
+  w->weight = c.take<double>(Ls);
+  w->saa = c.take<double>(Ls * E);
+  w->sab = c.take<double>(Ls * E);
+  w->diag = c.take<double>(Ls * V);
+  w->offv = c.take<double>(Ls * 2 * E);
+  w->gvec = c.take<double>(Ls * Ss * V);
+  w->x = c.take<double>(Ls * Ss * V);
+  w->r = c.take<double>(Ls * Ss * V);
+  w->p = c.take<double>(Ls * Ss * V);
+  w->q = c.take<double>(Ls * Ss * V);
+  w->acc = c.take<double>((size_t)g->ni * Ss);
+  w->yscr = c.take<char>((size_t)g->ni * Ss * tsize);
+  w->rpscr = c.take<char>((size_t)g->ni * nsg * tsize);
+  w->iters = c.take<int32_t>(Ls * Ss);
+  w->status = c.take<PcgStatus>(1);
+}
+
+// Per-call statistics, kernel-launch count and (optional) CUDA-event phase timing.
+struct RunStats {
+  int64_t nodes = 0, systems = 0, iters_total = 0;
+  int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0;
+  bool timing = false;
+  struct Span {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Span> spans;
+  cudaEvent_t open = nullptr;
+  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+
+  void begin(cudaStream_t st) {
+    if (!timing) return;
+    cudaEventCreate(&open);
+    cudaEventRecord(open, st);
+  }
+  void end(int phase, cudaStream_t st) {
+    if (!timing || !open) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, st);
+    spans.push_back({phase, open, b});
+    open = nullptr;
+  }
+  // after the stream has been synchronised
+  void settle() {
+    for (auto& s : spans) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s.a, s.b) == cudaSuccess) phase_ms[s.phase] += ms;
+      cudaEventDestroy(s.a);
+      cudaEventDestroy(s.b);
+    }
+    spans.clear();
+  }
+  ~RunStats() { settle(); }
+};
+
+DevNodes dev_nodes(const ApplyWs& w, int32_t L) {
+  DevNodes d;
+  d.L = L;
+  d.alpha = w.alpha;
+  d.gamma = w.gamma;
+  d.weight = w.weight;
+  return d;
+}
+
+int upload_nodes(const HostNodes& h, const ApplyWs& w, cudaStream_t st) {
+  const size_t b = sizeof(double) * h.alpha.size();
+  CUDA_TRY(cudaMemcpyAsync(w.alpha, h.alpha.data(), b, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(w.gamma, h.gamma.data(), b, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(w.weight, h.weight.data(), b, cudaMemcpyHostToDevice, st));
+  return GRF_OK;
+}
+
+int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* rs) {
+  PcgStatus h{};
+  CUDA_TRY(cudaMemcpyAsync(&h, w.status, sizeof h, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  rs->settle();
+  rs->nodes += L;
+  rs->systems += (int64_t)L * S;
+  rs->iters_total += (int64_t)h.iters_total;
+  if (h.iters_max > rs->iters_max) rs->iters_max = h.iters_max;
+  rs->unconverged += h.n_unconverged;
+  rs->numeric += h.numeric_flag;
+  return GRF_OK;
+}
+
+// Schur blocks + condensation + PCG for the nodes already uploaded to w.
+template <typename T>
+int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64_t S,
+                 const T* b, double* gvec, double* xv, const Opts& o, cudaStream_t st,
+                 RunStats* rs) {
+  const DevNodes nd = dev_nodes(w, L);
+  rs->begin(st);
+  launch_schur(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, st);
+  rs->end(1, st);
+  rs->begin(st);
+  launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
+  rs->end(2, st);
+  CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
+  rs->begin(st);
+  launch_pcg_jacobi(g->d, L, S, w.diag, w.offv, gvec, xv, w.r, w.p, w.q, o.rtol, o.max_iter,
+                    w.iters, w.status, st);
+  rs->end(3, st);
+  rs->launches += 5;
+  CUDA_TRY(cudaGetLastError());
+  return GRF_OK;
+}
+
+// out = sum_l w_l A_l^{-1} b with b sample-minor [n][S] in precision T.
+template <typename T, typename OutT>
+int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T* b, OutT* out,
+             const Opts& o, cudaStream_t st, void* ws_tail, RunStats* rs) {
+  Carve c(ws_tail);
+  ApplyWs w;
+  carve_apply(c, g, hn.L(), S, sizeof(T), &w);
+  const double k2 = kappa * kappa;
+  GRF_TRY(upload_nodes(hn, w, st));
+  GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
+  rs->begin(st);
+  launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out, w.acc, (T*)w.yscr,
+                          (T*)w.rpscr, st);
+  rs->end(4, st);
+  rs->launches += g->ni > 0 ? 2 : 1;
+  CUDA_TRY(cudaGetLastError());
+  return collect(w, st, hn.L(), S, rs);
+}
+
+size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize) {
+  Carve c(nullptr);
+  ApplyWs w;
+  carve_apply(c, g, L, S, tsize, &w);
+  return c.off;
+}
+
+int finish(const RunStats& rs, grf_graph* g, grf_stats* stats) {
+  if (stats) {
+    stats->n_dofs = g->n;
+    stats->n_nodes = rs.nodes;
+    stats->n_systems = rs.systems;
+    stats->pcg_iters_total = rs.iters_total;
+    stats->pcg_iters_max = rs.iters_max;
+    stats->n_unconverged = rs.unconverged;
+    stats->numeric_flag = rs.numeric;
+    stats->kernel_launches = rs.launches;
+    for (int i = 0; i < 6; ++i) stats->phase_ms[i] = rs.phase_ms[i];
+  }
+  if (rs.numeric) return fail(GRF_ENUMERIC, "NaN/Inf or non-positive p.Sp in %d PCG systems", rs.numeric);
+  if (rs.unconverged)
+    return fail(GRF_ENOCONV, "%d PCG systems did not converge", rs.unconverged);
+  return GRF_OK;
+}
+
+int check_params(double kappa, double beta, double k_step) {
+  if (!(kappa > 0) || !std::isfinite(kappa)) return fail(GRF_EINVAL, "kappa must be > 0");
+  if (!(beta > 0) || !std::isfinite(beta) || beta > 64) return fail(GRF_EINVAL, "beta must be in (0, 64]");
+  if (!(k_step > 0) || !std::isfinite(k_step)) return fail(GRF_EINVAL, "k_step must be > 0");
+  return GRF_OK;
+}
+
+// Stages: the fractional part (or the first stiffness solve) then the integer powers.
+void plan(double beta, double k_step, std::vector<HostNodes>* stages) {
+  const double n_int = std::floor(beta);
+  const double f = beta - n_int;
+  if (f > 1e-12) {
+    stages->push_back(quadrature_nodes(f, k_step));
+    for (int i = 0; i < (int)n_int; ++i) stages->push_back(stiffness_node());
+  } else {
+    for (int i = 0; i < (int)n_int; ++i) stages->push_back(stiffness_node());
+  }
+}
+
+template <typename T, typename OutT>
+int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed, int64_t S,
+                OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
+  std::vector<HostNodes> stages;
+  plan(beta, k_step, &stages);
+  size_t need = align_up((size_t)g->n * S * sizeof(T));
+  size_t tail = 0;
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, sizeof(T)));
+  const bool multi = stages.size() > 1;
+  if (multi) need += align_up((size_t)g->n * S * sizeof(double));
+  GRF_TRY(ensure_ws(g, need + tail));
+  Carve c(g->ws);
+  T* b = c.take<T>((size_t)g->n * S);
+  double* tmp = multi ? c.take<double>((size_t)g->n * S) : nullptr;
+  void* ws_tail = g->ws ? (char*)g->ws + c.off : nullptr;
+  rs->begin(st);
+  launch_noise_minor<T>(g->d, seed, S, b, st);
+  rs->end(0, st);
+  rs->launches += 1;
+  CUDA_TRY(cudaGetLastError());
+  for (size_t i = 0; i < stages.size(); ++i) {
+    const bool last = i + 1 == stages.size();
+    if (i > 0) {
+      rs->begin(st);
+      launch_to_minor<T>(g->d, S, tmp, b, true, st);
+      rs->end(5, st);
+      rs->launches += 1;
+    }
+    if (last) {
+      GRF_TRY((dd_apply<T, OutT>(g, stages[i], kappa, S, b, out, o, st, ws_tail, rs)));
+    } else {
+      GRF_TRY((dd_apply<T, double>(g, stages[i], kappa, S, b, tmp, o, st, ws_tail, rs)));
+    }
+  }
+  return GRF_OK;
+}
+
+int check_graph(const grf_graph* g) {
+  if (!g) return fail(GRF_EINVAL, "null graph");
+  return GRF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grf_last_error(void) { return g_last_error.c_str(); }
+
+int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
+                     const int64_t* edge_v, const double* lengths, const int32_t* n_elems,
+                     double h, grf_graph** out) {
+  if (!out) return fail(GRF_EINVAL, "out is null");
+  *out = nullptr;
+  if (n_vertices < 1 || n_edges < 1) return fail(GRF_EINVAL, "need at least one vertex and edge");
+  if (n_edges > (int64_t)1 << 29 || n_vertices > (int64_t)1 << 30)
+    return fail(GRF_EINVAL, "graph too large");
+  if (!edge_u || !edge_v || !lengths) return fail(GRF_EINVAL, "null edge arrays");
+  if (!n_elems && !(h > 0 && std::isfinite(h))) return fail(GRF_EINVAL, "need n_elems or h > 0");
+  grf_graph* g = new (std::nothrow) grf_graph();
+  if (!g) return fail(GRF_ENOMEM, "host allocation failed");
+  const int64_t E = n_edges;
+  std::vector<int64_t> deg(n_vertices, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t a = edge_u[e], b = edge_v[e];
+    if (a < 0 || a >= n_vertices || b < 0 || b >= n_vertices) {
+      delete g;
+      return fail(GRF_EINVAL, "edge %lld has an endpoint out of range", (long long)e);
+    }
+    if (a == b) {
+      delete g;
+      return fail(GRF_EINVAL, "edge %lld is a self-loop", (long long)e);
+    }
+    if (!(lengths[e] > 0) || !std::isfinite(lengths[e])) {
+      delete g;
+      return fail(GRF_EINVAL, "edge %lld has a non-positive or non-finite length", (long long)e);
+    }
+    deg[a]++;
+    deg[b]++;
+  }
+  g->nv_in = n_vertices;
+  g->vertex_map.assign(n_vertices, -1);
+  int32_t nv = 0;
+  for (int64_t v = 0; v < n_vertices; ++v)
+    if (deg[v] > 0) g->vertex_map[v] = nv++;
+  g->nv = nv;
+  g->ne = (int32_t)E;
+  g->eu.resize(E);
+  g->ev.resize(E);
+  g->nel.resize(E);
+  g->he.resize(E);
+  g->ioff.assign(E + 1, 0);
+  g->ml_vertex.assign(nv, 0.0);
+  for (int64_t e = 0; e < E; ++e) {
+    double ne_d;
+    if (n_elems) {
+      if (n_elems[e] < 1) {
+        delete g;
+        return fail(GRF_EINVAL, "edge %lld has n_elems < 1", (long long)e);
+      }
+      ne_d = n_elems[e];
+    } else {
+      ne_d = std::ceil(lengths[e] / h);
+      if (ne_d < 1) ne_d = 1;
+      if (ne_d > 1e9) {
+        delete g;
+        return fail(GRF_EINVAL, "edge %lld needs too many elements", (long long)e);
+      }
+    }
+    g->nel[e] = (int32_t)ne_d;
+    g->he[e] = lengths[e] / ne_d;
+    g->eu[e] = (int32_t)g->vertex_map[edge_u[e]];
+    g->ev[e] = (int32_t)g->vertex_map[edge_v[e]];
+    g->ioff[e + 1] = g->ioff[e] + (g->nel[e] - 1);
+    g->ml_vertex[g->eu[e]] += 0.5 * g->he[e];
+    g->ml_vertex[g->ev[e]] += 0.5 * g->he[e];
+  }
+  g->ni = g->ioff[E];
+  g->n = nv + g->ni;
+  // vertex incidence lists (CSR), edges in increasing id per vertex
+  g->vptr.assign(nv + 1, 0);
+  for (int64_t e = 0; e < E; ++e) {
+    g->vptr[g->eu[e] + 1]++;
+    g->vptr[g->ev[e] + 1]++;
+  }
+  for (int32_t v = 0; v < nv; ++v) g->vptr[v + 1] += g->vptr[v];
+  g->adj_edge.resize(2 * E);
+  g->adj_nbr.resize(2 * E);
+  std::vector<int32_t> fill(g->vptr.begin(), g->vptr.end() - 1);
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t a = g->eu[e], b = g->ev[e];
+    g->adj_edge[fill[a]] = (int32_t)e;
+    g->adj_nbr[fill[a]++] = b;
+    g->adj_edge[fill[b]] = (int32_t)e;
+    g->adj_nbr[fill[b]++] = a;
+  }
+  *out = g;
+  return GRF_OK;
+}
+
+int grf_graph_destroy(grf_graph* g) {
+  delete g;
+  return GRF_OK;
+}
+
+int grf_graph_info(const grf_graph* g, int64_t* n_dofs, int64_t* n_kept_vertices,
+                   int64_t* n_interior, int64_t* vertex_map, int64_t* interior_offsets) {
+  GRF_TRY(check_graph(g));
+  if (n_dofs) *n_dofs = g->n;
+  if (n_kept_vertices) *n_kept_vertices = g->nv;
+  if (n_interior) *n_interior = g->ni;
+  if (vertex_map) std::memcpy(vertex_map, g->vertex_map.data(), sizeof(int64_t) * g->nv_in);
+  if (interior_offsets)
+    std::memcpy(interior_offsets, g->ioff.data(), sizeof(int64_t) * (g->ne + 1));
+  return GRF_OK;
+}
+
+int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t n_samples,
+                        const grf_options* opts, size_t* bytes) {
+  GRF_TRY(check_graph(g));
+  if (!bytes) return fail(GRF_EINVAL, "bytes is null");
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  GRF_TRY(check_params(1.0, beta, k_step));
+  const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
+  std::vector<HostNodes> stages;
+  plan(beta, k_step, &stages);
+  size_t need = align_up((size_t)g->n * n_samples * ts);
+  if (stages.size() > 1) need += align_up((size_t)g->n * n_samples * 8);
+  size_t tail = 0;
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), n_samples, ts));
+  *bytes = need + tail;
+  return GRF_OK;
+}
+
+int grf_sample(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
+               int64_t n_samples, void* out, const grf_options* opts, void* stream,
+               grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  GRF_TRY(check_params(kappa, beta, k_step));
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  if (n_samples < 0 || n_samples > (int64_t)1 << 24) return fail(GRF_EINVAL, "bad n_samples");
+  if (n_samples == 0) return finish(RunStats{}, g, stats);
+  if (!out) return fail(GRF_EINVAL, "out is null");
+  GRF_TRY(ensure_device(g));
+  cudaStream_t st = (cudaStream_t)stream;
+  RunStats rs;
+  rs.timing = o.timing;
+  int r;
+  if (o.precision == GRF_FP64) {
+    r = o.out_dtype == GRF_OUT_F64
+            ? sample_impl<double, double>(g, kappa, beta, k_step, seed, n_samples, (double*)out, o, st, &rs)
+            : sample_impl<double, float>(g, kappa, beta, k_step, seed, n_samples, (float*)out, o, st, &rs);
+  } else {
+    r = o.out_dtype == GRF_OUT_F64
+            ? sample_impl<float, double>(g, kappa, beta, k_step, seed, n_samples, (double*)out, o, st, &rs)
+            : sample_impl<float, float>(g, kappa, beta, k_step, seed, n_samples, (float*)out, o, st, &rs);
+  }
+  if (r != GRF_OK) return r;
+  return finish(rs, g, stats);
+}
+
+int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
+                    int64_t n_samples, void* out_host, const grf_options* opts, void* stream,
+                    grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  if (!out_host) return fail(GRF_EINVAL, "out_host is null");
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  GRF_TRY(ensure_device(g));
+  const size_t bytes = (size_t)g->n * (size_t)n_samples * (o.out_dtype == GRF_OUT_F64 ? 8 : 4);
+  void* dout = nullptr;
+  CUDA_TRY(cudaMallocAsync(&dout, bytes ? bytes : 1, (cudaStream_t)stream));
+  int r = grf_sample(g, kappa, beta, k_step, seed, n_samples, dout, opts, stream, stats);
+  if (r == GRF_OK || r == GRF_ENOCONV) {
+    cudaError_t e = cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) r = fail(GRF_ECUDA, "copy to host: %s", cudaGetErrorString(e));
+  }
+  cudaFreeAsync(dout, (cudaStream_t)stream);
+  return r;
+}
+
+int grf_noise(grf_graph* g, uint64_t seed, int64_t n_samples, void* out, int32_t raw_words,
+              void* stream) {
+  GRF_TRY(check_graph(g));
+  if (n_samples < 0) return fail(GRF_EINVAL, "bad n_samples");
+  if (n_samples == 0) return GRF_OK;
+  if (!out) return fail(GRF_EINVAL, "out is null");
+  GRF_TRY(ensure_device(g));
+  launch_noise_major(g->d, seed, n_samples, out, raw_words != 0, (cudaStream_t)stream);
+  CUDA_TRY(cudaGetLastError());
+  return GRF_OK;
+}
+
+int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
+              const double* gamma, const double* weight, int64_t n_rhs, const double* rhs,
+              void* out, const grf_options* opts, void* stream, grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  if (!(kappa > 0)) return fail(GRF_EINVAL, "kappa must be > 0");
+  if (n_nodes < 1 || n_nodes > 100000 || !alpha || !gamma || !weight)
+    return fail(GRF_EINVAL, "bad node list");
+  for (int64_t l = 0; l < n_nodes; ++l)
+    if (!(alpha[l] >= 0) || !(gamma[l] > 0) || !std::isfinite(alpha[l]) ||
+        !std::isfinite(gamma[l]) || !std::isfinite(weight[l]))
+      return fail(GRF_EINVAL, "node %lld needs alpha >= 0, gamma > 0", (long long)l);
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  if (n_rhs < 0) return fail(GRF_EINVAL, "bad n_rhs");
+  if (n_rhs == 0) return finish(RunStats{}, g, stats);
+  if (!rhs || !out) return fail(GRF_EINVAL, "null buffer");
+  GRF_TRY(ensure_device(g));
+  HostNodes hn;
+  hn.alpha.assign(alpha, alpha + n_nodes);
+  hn.gamma.assign(gamma, gamma + n_nodes);
+  hn.weight.assign(weight, weight + n_nodes);
+  const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
+  const size_t head = align_up((size_t)g->n * n_rhs * ts);
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts)));
+  cudaStream_t st = (cudaStream_t)stream;
+  RunStats rs;
+  rs.timing = o.timing;
+  void* tail = (char*)g->ws + head;
+  int r;
+  if (o.precision == GRF_FP64) {
+    double* b = (double*)g->ws;
+    launch_to_minor<double>(g->d, n_rhs, rhs, b, false, st);
+    r = o.out_dtype == GRF_OUT_F64 ? dd_apply<double, double>(g, hn, kappa, n_rhs, b, (double*)out, o, st, tail, &rs)
+                                   : dd_apply<double, float>(g, hn, kappa, n_rhs, b, (float*)out, o, st, tail, &rs);
+  } else {
+    float* b = (float*)g->ws;
+    launch_to_minor<float>(g->d, n_rhs, rhs, b, false, st);
+    r = o.out_dtype == GRF_OUT_F64 ? dd_apply<float, double>(g, hn, kappa, n_rhs, b, (double*)out, o, st, tail, &rs)
+                                   : dd_apply<float, float>(g, hn, kappa, n_rhs, b, (float*)out, o, st, tail, &rs);
+  }
+  if (r != GRF_OK) return r;
+  return finish(rs, g, stats);
+}
+
+int grf_schur(grf_graph* g, double kappa, double alpha, double gamma, double* diag,
+              double* offdiag, void* stream) {
+  GRF_TRY(check_graph(g));
+  if (!(kappa > 0) || !(alpha >= 0) || !(gamma > 0)) return fail(GRF_EINVAL, "bad parameters");
+  if (!diag || !offdiag) return fail(GRF_EINVAL, "null buffer");
+  GRF_TRY(ensure_device(g));
+  HostNodes hn;
+  hn.alpha = {alpha};
+  hn.gamma = {gamma};
+  hn.weight = {1.0};
+  GRF_TRY(ensure_ws(g, apply_bytes(g, 1, 1, 8)));
+  Carve c(g->ws);
+  ApplyWs w;
+  carve_apply(c, g, 1, 1, 8, &w);
+  cudaStream_t st = (cudaStream_t)stream;
+  GRF_TRY(upload_nodes(hn, w, st));
+  launch_schur(g->d, dev_nodes(w, 1), kappa * kappa, w.saa, offdiag, diag, w.offv, st);
+  CUDA_TRY(cudaGetLastError());
+  return GRF_OK;
+}
+
+int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int64_t n_rhs,
+                     const double* rhs, double* g_out, double* u_out, const grf_options* opts,
+                     void* stream, grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  if (!(kappa > 0) || !(alpha >= 0) || !(gamma > 0)) return fail(GRF_EINVAL, "bad parameters");
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  if (n_rhs < 0) return fail(GRF_EINVAL, "bad n_rhs");
+  if (n_rhs == 0) return finish(RunStats{}, g, stats);
+  if (!rhs || !g_out || !u_out) return fail(GRF_EINVAL, "null buffer");
+  GRF_TRY(ensure_device(g));
+  HostNodes hn;
+  hn.alpha = {alpha};
+  hn.gamma = {gamma};
+  hn.weight = {1.0};
+  const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
+  const size_t head = align_up((size_t)g->n * n_rhs * ts);
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts)));
+  Carve c((char*)g->ws + head);
+  ApplyWs w;
+  carve_apply(c, g, 1, n_rhs, ts, &w);
+  cudaStream_t st = (cudaStream_t)stream;
+  GRF_TRY(upload_nodes(hn, w, st));
+  const double k2 = kappa * kappa;
+  RunStats rs;
+  rs.timing = o.timing;
+  rs.launches += 1;
+  if (o.precision == GRF_FP64) {
+    double* b = (double*)g->ws;
+    launch_to_minor<double>(g->d, n_rhs, rhs, b, false, st);
+    GRF_TRY(vertex_phase<double>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
+  } else {
+    float* b = (float*)g->ws;
+    launch_to_minor<float>(g->d, n_rhs, rhs, b, false, st);
+    GRF_TRY(vertex_phase<float>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
+  }
+  GRF_TRY(collect(w, st, 1, n_rhs, &rs));
+  return finish(rs, g, stats);
+}
+
+}  // extern "C"

@@ -1,0 +1,126 @@
+// Lumped-mass white noise b = M_L^{1/2} xi (Eq. wh_def with the diagonal
+// factor of Sec. 2.5): O(N), one Philox4x32-10 block per four DOFs.
+//
+// Philox4x32-10 follows its published definition (Salmon et al., SC'11):
+// ten rounds of two 32x32->64 multiplies with M0 = 0xD2511F53 and
+// M1 = 0xCD9E8D57, the key bumped by (0x9E3779B9, 0xBB67AE85) between rounds.
+// Key = (seed lo32, seed hi32); counter = (q lo32, q hi32, s, 0) for DOFs
+// 4q..4q+3 of sample s. Uniform u = (word + 1/2) 2^-32; Box-Muller on word
+// pairs (0,1) and (2,3).
+//
+// HBM-bound: each thread writes four values and reads four mass factors.
+#include "grf_internal.h"
+
+namespace grf {
+namespace {
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 noise_block(uint64_t seed, uint64_t q, uint32_t s) {
+  return philox4x32_10(make_uint4((uint32_t)q, (uint32_t)(q >> 32), s, 0u), (uint32_t)seed,
+                       (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& n0, double& n1) {
+  const double ua = ((double)xa + 0.5) * 0x1p-32;
+  const double ub = ((double)xb + 0.5) * 0x1p-32;
+  const double r = sqrt(-2.0 * log(ua));
+  double sn, cs;
+  sincospi(2.0 * ub, &sn, &cs);
+  n0 = r * cs;
+  n1 = r * sn;
+}
+
+__device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& n0, float& n1) {
+  const float ua = fmaf((float)xa, 0x1p-32f, 0x1p-33f);
+  const float ub = fmaf((float)xb, 0x1p-32f, 0x1p-33f);
+  const float r = sqrtf(-2.0f * logf(ua));
+  float sn, cs;
+  sincospif(2.0f * ub, &sn, &cs);
+  n0 = r * cs;
+  n1 = r * sn;
+}
+
+// thread -> (q, s) with s fastest: a warp writes whole rows b[j][s0..s0+31]
+template <typename T>
+__global__ void noise_minor_kernel(DevGraph g, uint64_t seed, int64_t S, T* __restrict__ b) {
+  const int64_t nq = (g.n + 3) / 4;
+  const int64_t total = nq * S;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t / S;
+    const int64_t s = t - q * S;
+    const uint4 w = noise_block(seed, (uint64_t)q, (uint32_t)s);
+    T n[4];
+    box_muller(w.x, w.y, n[0], n[1]);
+    box_muller(w.z, w.w, n[2], n[3]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = 4 * q + k;
+      if (j < g.n) b[j * S + s] = (T)g.sqrt_ml[j] * n[k];
+    }
+  }
+}
+
+__global__ void noise_major_kernel(DevGraph g, uint64_t seed, int64_t S, void* out, int raw) {
+  const int64_t nq = (g.n + 3) / 4;
+  const int64_t total = nq * S;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / nq;
+    const int64_t q = t - s * nq;
+    const uint4 w = noise_block(seed, (uint64_t)q, (uint32_t)s);
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+    double n[4];
+    if (!raw) {
+      box_muller(w.x, w.y, n[0], n[1]);
+      box_muller(w.z, w.w, n[2], n[3]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t j = 4 * q + k;
+      if (j >= g.n) break;
+      if (raw)
+        static_cast<uint32_t*>(out)[s * g.n + j] = words[k];
+      else
+        static_cast<double*>(out)[s * g.n + j] = g.sqrt_ml[j] * n[k];
+    }
+  }
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+}  // namespace
+
+template <typename T>
+void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st) {
+  const int64_t total = ((g.n + 3) / 4) * S;
+  noise_minor_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(g, seed, S, b);
+}
+template void launch_noise_minor<float>(const DevGraph&, uint64_t, int64_t, float*, cudaStream_t);
+template void launch_noise_minor<double>(const DevGraph&, uint64_t, int64_t, double*,
+                                         cudaStream_t);
+
+void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
+                        cudaStream_t st) {
+  const int64_t total = ((g.n + 3) / 4) * S;
+  noise_major_kernel<<<grid_for(total, 256), 256, 0, st>>>(g, seed, S, out, raw ? 1 : 0);
+}
+
+}  // namespace grf

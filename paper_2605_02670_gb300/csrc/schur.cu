@@ -1,0 +1,79 @@
+// Per-edge 2x2 Schur blocks of A = alpha M_L + gamma K (Eq. local_reduced_schur)
+// and the vertex Schur diagonal (Eq. global_schur), in FP64.
+//
+// On edge e (h = h_e, n = n_e elements, m = n - 1 interior nodes) the interior
+// block is A_II = c T with c = gamma / h and T = tridiag(-1, 2 + delta, -1),
+// delta = (alpha / gamma + kappa^2) h^2; the vertex-interior couplings are -c and
+// the edge's share of A_vv is c (1 + delta / 2). With 2 + delta = 2 cosh(theta),
+// the inverse of T has (T^{-1})_11 = sinh(m theta) / sinh(n theta) and
+// (T^{-1})_1m = sinh(theta) / sinh(n theta), so the Schur block is
+//   S^(e) = c sinh(theta) [[coth(n theta), -csch(n theta)],
+//                          [-csch(n theta), coth(n theta)]]
+// (the first entry uses cosh(theta) sinh(n theta) - sinh(m theta) =
+// cosh(n theta) sinh(theta)). This is the matrix the paper applies
+// matrix-free through one Thomas solve per edge in every PCG iteration
+// (Eq. matrix_free_local); it has rank-2 coupling, so the block is exact and
+// costs O(1) per (node, edge) instead of O(n_e). sinh(theta) =
+// sqrt(delta (1 + delta / 4)) and theta = 2 asinh(sqrt(delta) / 2) avoid
+// cancellation for small delta; exp / expm1 keep large n theta finite.
+#include "grf_internal.h"
+
+namespace grf {
+namespace {
+
+__global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, double* __restrict__ saa,
+                                   double* __restrict__ sab) {
+  const int64_t total = (int64_t)nd.L * g.ne;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / g.ne;
+    const int32_t e = (int32_t)(t - l * g.ne);
+    const double h = g.he[e];
+    const double gam = nd.gamma[l];
+    const double c = gam / h;
+    const double delta = (nd.alpha[l] / gam + kappa2) * h * h;
+    const double sh = sqrt(delta * (1.0 + 0.25 * delta));
+    const double theta = 2.0 * asinh(0.5 * sqrt(delta));
+    const double nth = (double)g.nel[e] * theta;
+    const double e1 = exp(-nth);
+    const double e2 = -expm1(-2.0 * nth);  // 1 - exp(-2 n theta)
+    saa[t] = c * sh * ((2.0 - e2) / e2);
+    sab[t] = -c * sh * (2.0 * e1 / e2);
+  }
+}
+
+__global__ void vertex_diag_kernel(DevGraph g, int32_t L, const double* __restrict__ saa,
+                                   const double* __restrict__ sab, double* __restrict__ diag,
+                                   double* __restrict__ offv) {
+  const int64_t total = (int64_t)L * g.nv;
+  const int64_t nadj = 2 * (int64_t)g.ne;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / g.nv;
+    const int32_t v = (int32_t)(t - l * g.nv);
+    double d = 0.0;
+    for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
+      const int64_t i = l * g.ne + g.adj_edge[k];
+      d += saa[i];
+      offv[l * nadj + k] = sab[i];
+    }
+    diag[t] = d;
+  }
+}
+
+int grid_for(int64_t total, int threads) {
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+}  // namespace
+
+void launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa, double* sab,
+                  double* diag, double* offv, cudaStream_t st) {
+  edge_blocks_kernel<<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(g, nd, kappa2, saa, sab);
+  vertex_diag_kernel<<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, saa, sab, diag,
+                                                                          offv);
+}
+
+}  // namespace grf

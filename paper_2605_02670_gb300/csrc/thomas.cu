@@ -1,0 +1,267 @@
+// Edge-interior sweeps of the domain decomposition (Sec. 3, Phases 3 and 5).
+//
+// On edge e the interior block of A_l = alpha_l M_L + gamma_l K is c T with
+// c = gamma_l / h_e and T = tridiag(-1, 2 + delta, -1), delta =
+// (alpha_l / gamma_l + kappa^2) h_e^2. Thomas elimination of T (Eq.
+// thomas_coefficients) has pivots p_i = 1 + q_i with the excess recurrence
+//   q_1 = 1 + delta,  q_{i+1} = delta + q_i / (1 + q_i),
+// which never subtracts, so it keeps full relative accuracy of delta even in
+// FP32 where 2 + delta would round delta away. Forward substitution is
+// y_i = r_i + y_{i-1} / p_{i-1}, back substitution x_i = (y_i + x_{i+1}) / p_i.
+//
+// condense: g_v = b_v + sum_{e at v} (T^{-1} b_I^(e))_{node next to v}
+//   (Eq. local_reduced_schur: -A_vI A_II^{-1} = c T^{-1} / c). The end value
+//   next to edge_v is one forward elimination from edge_u's side; by symmetry
+//   of the constant-coefficient T the end value next to edge_u is the same
+//   elimination run from edge_v's side. Both run in one pass over b_I.
+// recover: U_I = sum_l w_l T^{-1} (b_I / c + u_a e_1 + u_b e_m) (Eq.
+//   internal_recovery) with the quadrature sum (Phase 5) fused: the weight is
+//   folded into the right-hand side and the sum over nodes is kept in FP64.
+#include "grf_internal.h"
+
+namespace grf {
+namespace {
+
+constexpr int kSG = 4;  // samples per thread: pivots are shared across them
+
+int grid_for(int64_t total, int threads) {
+  int64_t blocks = (total + threads - 1) / threads;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+template <typename T>
+__global__ void gvec_init_kernel(DevGraph g, int32_t L, int64_t S, const T* __restrict__ b,
+                                 double* __restrict__ gvec) {
+  const int64_t total = (int64_t)L * S * g.nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t % g.nv;
+    const int64_t s = (t / g.nv) % S;
+    gvec[t] = (double)b[v * S + s];
+  }
+}
+
+// thread -> (e, l, sample group); lanes of one warp share e, so their b loads
+// coincide across l.
+template <typename T>
+__global__ void condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
+                                const T* __restrict__ b, double* __restrict__ gvec) {
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  const int64_t total = (int64_t)g.ne * nd.L * nsg;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = t % nsg;
+    const int64_t r = t / nsg;
+    const int32_t l = (int32_t)(r % nd.L);
+    const int32_t e = (int32_t)(r / nd.L);
+    const int32_t m = g.nel[e] - 1;
+    if (m <= 0) continue;
+    const double h = g.he[e];
+    const T delta = (T)((nd.alpha[l] / nd.gamma[l] + kappa2) * h * h);
+    const T* bI = b + (g.nv + g.ioff[e]) * S;
+    const int64_t s0 = sg * kSG;
+    T yf[kSG], yr[kSG];
+#pragma unroll
+    for (int k = 0; k < kSG; ++k) {
+      const bool ok = s0 + k < S;
+      yf[k] = ok ? bI[s0 + k] : (T)0;
+      yr[k] = ok ? bI[(int64_t)(m - 1) * S + s0 + k] : (T)0;
+    }
+    T q = (T)1 + delta;
+    T rp = (T)1 / ((T)1 + q);
+    for (int32_t i = 1; i < m; ++i) {
+      const T* rowf = bI + (int64_t)i * S + s0;
+      const T* rowr = bI + (int64_t)(m - 1 - i) * S + s0;
+#pragma unroll
+      for (int k = 0; k < kSG; ++k) {
+        if (s0 + k < S) {
+          yf[k] = rowf[k] + rp * yf[k];
+          yr[k] = rowr[k] + rp * yr[k];
+        }
+      }
+      q = delta + q * rp;
+      rp = (T)1 / ((T)1 + q);
+    }
+    double* gl = gvec + (int64_t)l * S * g.nv;
+    const int32_t a = g.eu[e], bv = g.ev[e];
+#pragma unroll
+    for (int k = 0; k < kSG; ++k) {
+      if (s0 + k < S) {
+        atomicAdd(gl + (s0 + k) * g.nv + bv, (double)(yf[k] * rp));
+        atomicAdd(gl + (s0 + k) * g.nv + a, (double)(yr[k] * rp));
+      }
+    }
+  }
+}
+
+template <typename OutT>
+__global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
+                                    OutT* __restrict__ out) {
+  const int64_t total = S * g.nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / g.nv;
+    const int64_t v = t - s * g.nv;
+    double acc = 0.0;
+    for (int32_t l = 0; l < nd.L; ++l) acc += nd.weight[l] * xv[((int64_t)l * S + s) * g.nv + v];
+    out[s * g.n + v] = (OutT)acc;
+  }
+}
+
+// thread -> (e, sample group); loops over all nodes l, keeping the FP64 sum
+// of w_l x^(l) in acc. yscr / rpscr hold the forward sweep for the back sweep.
+template <typename T, typename OutT>
+__global__ void recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
+                               const T* __restrict__ b, const double* __restrict__ xv,
+                               OutT* __restrict__ out, double* __restrict__ acc,
+                               T* __restrict__ yscr, T* __restrict__ rpscr) {
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  const int64_t total = (int64_t)g.ne * nsg;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sg = t % nsg;
+    const int32_t e = (int32_t)(t / nsg);
+    const int32_t m = g.nel[e] - 1;
+    if (m <= 0) continue;
+    const int64_t off = g.ioff[e];
+    const int64_t s0 = sg * kSG;
+    const T* bI = b + (g.nv + off) * S;
+    double* aI = acc + off * S;
+    T* yI = yscr + off * S;
+    T* rI = rpscr + off * nsg + sg;
+    const double h = g.he[e];
+    const int32_t va = g.eu[e], vb = g.ev[e];
+    for (int32_t l = 0; l < nd.L; ++l) {
+      const double gam = nd.gamma[l];
+      const double w = nd.weight[l];
+      const T delta = (T)((nd.alpha[l] / gam + kappa2) * h * h);
+      const T sc = (T)(w * h / gam);  // w_l / c
+      T xa[kSG], xb[kSG], y[kSG];
+#pragma unroll
+      for (int k = 0; k < kSG; ++k) {
+        const bool ok = s0 + k < S;
+        const int64_t base = ((int64_t)l * S + (ok ? s0 + k : 0)) * g.nv;
+        xa[k] = ok ? (T)(w * xv[base + va]) : (T)0;
+        xb[k] = ok ? (T)(w * xv[base + vb]) : (T)0;
+        y[k] = ok ? bI[s0 + k] * sc + xa[k] + (m == 1 ? xb[k] : (T)0) : (T)0;
+        if (ok) yI[s0 + k] = y[k];
+      }
+      T q = (T)1 + delta;
+      T rp = (T)1 / ((T)1 + q);
+      rI[0] = rp;
+      for (int32_t i = 1; i < m; ++i) {
+        const T* row = bI + (int64_t)i * S + s0;
+        T* yrow = yI + (int64_t)i * S + s0;
+        const bool last = (i == m - 1);
+#pragma unroll
+        for (int k = 0; k < kSG; ++k) {
+          if (s0 + k < S) {
+            y[k] = row[k] * sc + (last ? xb[k] : (T)0) + rp * y[k];
+            yrow[k] = y[k];
+          }
+        }
+        q = delta + q * rp;
+        rp = (T)1 / ((T)1 + q);
+        rI[(int64_t)i * nsg] = rp;
+      }
+      // back substitution, accumulating w_l x^(l) in FP64
+      T x[kSG];
+#pragma unroll
+      for (int k = 0; k < kSG; ++k) {
+        if (s0 + k < S) {
+          x[k] = y[k] * rp;
+          aI[(int64_t)(m - 1) * S + s0 + k] += (double)x[k];
+        }
+      }
+      for (int32_t i = m - 2; i >= 0; --i) {
+        const T rpi = rI[(int64_t)i * nsg];
+        const T* yrow = yI + (int64_t)i * S + s0;
+        double* arow = aI + (int64_t)i * S + s0;
+#pragma unroll
+        for (int k = 0; k < kSG; ++k) {
+          if (s0 + k < S) {
+            x[k] = (yrow[k] + x[k]) * rpi;
+            arow[k] += (double)x[k];
+          }
+        }
+      }
+    }
+    for (int32_t i = 0; i < m; ++i) {
+#pragma unroll
+      for (int k = 0; k < kSG; ++k) {
+        if (s0 + k < S) out[(s0 + k) * g.n + g.nv + off + i] = (OutT)aI[(int64_t)i * S + s0 + k];
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void to_minor_kernel(DevGraph g, int64_t S, const double* __restrict__ src,
+                                T* __restrict__ dst, int mass_scale) {
+  const int64_t total = S * g.n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / S;
+    const int64_t s = t - j * S;
+    double v = src[s * g.n + j];
+    if (mass_scale) {
+      const double r = g.sqrt_ml[j];
+      v *= r * r;
+    }
+    dst[t] = (T)v;
+  }
+}
+
+}  // namespace
+
+int recover_sample_group() { return kSG; }
+
+template <typename T>
+void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
+                     double* gvec, cudaStream_t st) {
+  gvec_init_kernel<T><<<grid_for((int64_t)nd.L * S * g.nv, 256), 256, 0, st>>>(g, nd.L, S, b, gvec);
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  condense_kernel<T><<<grid_for((int64_t)g.ne * nd.L * nsg, 128), 128, 0, st>>>(g, nd, kappa2, S, b,
+                                                                               gvec);
+}
+
+template <typename T, typename OutT>
+void launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
+                    const double* xv, OutT* out, double* acc, T* yscr, T* rpscr, cudaStream_t st) {
+  vertex_accum_kernel<OutT><<<grid_for(S * g.nv, 256), 256, 0, st>>>(g, nd, S, xv, out);
+  if (g.ni == 0) return;
+  cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)g.ni * (size_t)S, st);
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  recover_kernel<T, OutT><<<grid_for((int64_t)g.ne * nsg, 128), 128, 0, st>>>(
+      g, nd, kappa2, S, b, xv, out, acc, yscr, rpscr);
+}
+
+template <typename T>
+void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bool mass_scale,
+                     cudaStream_t st) {
+  to_minor_kernel<T><<<grid_for(S * g.n, 256), 256, 0, st>>>(g, S, src, dst, mass_scale ? 1 : 0);
+}
+
+template void launch_condense<float>(const DevGraph&, const DevNodes&, double, int64_t,
+                                     const float*, double*, cudaStream_t);
+template void launch_condense<double>(const DevGraph&, const DevNodes&, double, int64_t,
+                                      const double*, double*, cudaStream_t);
+template void launch_recover<float, float>(const DevGraph&, const DevNodes&, double, int64_t,
+                                           const float*, const double*, float*, double*, float*,
+                                           float*, cudaStream_t);
+template void launch_recover<float, double>(const DevGraph&, const DevNodes&, double, int64_t,
+                                            const float*, const double*, double*, double*, float*,
+                                            float*, cudaStream_t);
+template void launch_recover<double, double>(const DevGraph&, const DevNodes&, double, int64_t,
+                                             const double*, const double*, double*, double*,
+                                             double*, double*, cudaStream_t);
+template void launch_recover<double, float>(const DevGraph&, const DevNodes&, double, int64_t,
+                                            const double*, const double*, float*, double*,
+                                            double*, double*, cudaStream_t);
+template void launch_to_minor<float>(const DevGraph&, int64_t, const double*, float*, bool,
+                                     cudaStream_t);
+template void launch_to_minor<double>(const DevGraph&, int64_t, const double*, double*, bool,
+                                      cudaStream_t);
+
+}  // namespace grf

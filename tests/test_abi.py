@@ -1,0 +1,92 @@
+"""The C ABI library loads, exports every symbol include/grf.h declares, and its
+host-side graph logic (validation, mesh, DOF map) agrees with the oracle's.
+No device work: runs without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import grf_inputs as gi
+import paper_2605_02670_gb300 as grf
+from oracle import fem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "grf.h")).read()
+    return sorted(set(re.findall(r"^\S.*?\b(grf_\w+)\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert "grf_sample" in names and "grf_graph_create" in names
+    lib = ctypes.CDLL(grf.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(grf.C_SYMBOLS)
+
+
+@pytest.mark.parametrize("name", ["square5", "rgg_small", "grid_small", "ba_small"])
+def test_mesh_and_dof_map_match_oracle(name):
+    if name == "square5":
+        g, h, clip = gi.square_diagonal(0), 2.0 ** -7, None
+    elif name == "rgg_small":
+        g, h, clip = gi.random_geometric(300, 0.07, seed=2), 2.0 ** -6, None
+    elif name == "grid_small":
+        g, h, clip = gi.grid_deleted(20, 20, 0.15, seed=7), 2.0 ** -4, None
+    else:
+        g, h, clip = gi.barabasi_albert(500, 3, seed=1), 2.0 ** -5, (2, 64)
+    ne = grf.mesh_elements(g.lengths, h, clip)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, n_elems=ne)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h, clip=clip)
+    assert G.n_dofs == m.n_dofs and G.n_kept == m.n_vertices and G.n_interior == m.n_interior
+    np.testing.assert_array_equal(G.vertex_map, m.vertex_map)
+    np.testing.assert_array_equal(G.interior_offsets, m.interior_offsets)
+    G2 = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h)
+    if clip is None:
+        assert G2.n_dofs == m.n_dofs
+
+
+@pytest.mark.parametrize("case,msg", [
+    (([0], [0], [1.0], 2, 0.1), "self-loop"),
+    (([0], [5], [1.0], 2, 0.1), "out of range"),
+    (([0], [1], [-1.0], 2, 0.1), "length"),
+    (([0], [1], [np.nan], 2, 0.1), "length"),
+    (([0], [1], [1.0], 2, 0.0), "h > 0"),
+])
+def test_invalid_graphs_rejected(case, msg):
+    with pytest.raises(grf.GrfError) as ei:
+        grf.Graph(*case[:4], h=case[4])
+    assert ei.value.code == grf.GRF_EINVAL and msg in str(ei.value)
+
+
+def test_invalid_element_counts_rejected():
+    with pytest.raises(grf.GrfError):
+        grf.Graph([0], [1], [1.0], 2, n_elems=[0])
+
+
+def test_invalid_sampling_parameters_rejected_before_device_work():
+    G = grf.Graph([0, 1], [1, 2], [1.0, 0.5], 3, h=0.1)
+    opts = grf.make_options("fp64")
+    for kappa, beta, k in [(0.0, 0.5, 0.3), (1.0, 0.0, 0.3), (1.0, 0.5, 0.0), (np.nan, 0.5, 0.3)]:
+        with pytest.raises(grf.GrfError) as ei:
+            grf.grf_sample(G.handle, kappa, beta, k, 1, 2, 0, opts, stream=0)
+        assert ei.value.code == grf.GRF_EINVAL
+    bad = grf.grf_options(7, 0, 0, 0, 0.0)
+    with pytest.raises(grf.GrfError):
+        grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad, stream=0)
+    unsupported = grf.grf_options(0, 3, 0, 0, 0.0)
+    with pytest.raises(grf.GrfError) as ei:
+        grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, unsupported, stream=0)
+    assert ei.value.code == grf.GRF_ENOTSUP
+
+
+def test_workspace_query_is_host_only():
+    G = grf.Graph([0, 1], [1, 2], [1.0, 0.5], 3, h=0.1)
+    b1 = G.workspace_bytes(0.75, 0.5, 4)
+    b2 = G.workspace_bytes(0.75, 0.5, 8)
+    b3 = G.workspace_bytes(1.75, 0.5, 8)
+    assert 0 < b1 < b2 < b3

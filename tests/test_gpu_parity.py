@@ -1,0 +1,263 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the noise words are bit-exact; FP64 normals agree to a few ulp
+(device and host math libraries differ in the last bits); fields agree within a
+relative M_L-weighted L2 error of 1e-6 in FP64 mode and 1e-4 in mixed mode
+(FP32 edge sweeps). The per-kernel FP64 checks are tighter (1e-9): what is
+left there is the PCG tolerance (rtol 1e-12) times the Schur condition number."""
+import math
+
+import numpy as np
+import pytest
+
+import grf_inputs as gi
+from oracle import fem, noise, philox, quadrature, sampler
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+grf = pytest.importorskip("paper_2605_02670_gb300")
+
+TOL = {"fp64": 1e-6, "mixed": 1e-4}
+
+
+def rel_l2(u, ref, ml):
+    u = np.atleast_2d(u)
+    ref = np.atleast_2d(ref)
+    num = np.sqrt((ml[None, :] * (u - ref) ** 2).sum(axis=1))
+    den = np.sqrt((ml[None, :] * ref ** 2).sum(axis=1))
+    return float((num / den).max())
+
+
+def make(g, h=None, n_elems=None, clip=None):
+    if n_elems is None and clip is not None:
+        n_elems = grf.mesh_elements(g.lengths, h, clip)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h, n_elems=n_elems)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h, n_elems=n_elems,
+                       clip=None)
+    return G, m
+
+
+GRAPHS = {
+    "square5": lambda: (gi.square_diagonal(0), 2.0 ** -7),
+    "interval": lambda: (gi.interval(1.3), 0.05),
+    "random12": lambda: (gi.random_small_graph(12, 20, 3), 0.07),
+    "short_edges": lambda: (gi.Graph(5, np.array([0, 1, 2, 3, 0, 1]), np.array([1, 2, 3, 4, 2, 0]),
+                                     np.array([0.05, 0.11, 0.2, 0.9, 0.15, 0.33])), 0.1),
+    "isolated": lambda: (gi.Graph(6, np.array([0, 2, 2]), np.array([2, 4, 5]),
+                                  np.array([0.7, 1.2, 0.4])), 0.03),
+}
+
+
+# ---------------------------------------------------------------- noise
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("seed", [1, 0xDEADBEEF12345678])
+def test_noise_words_bit_exact(name, seed):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    words = G.noise(seed, 5, raw=True).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(words, philox.noise_words(seed, m.n_dofs, 5))
+
+
+@pytest.mark.parametrize("name", ["square5", "random12", "isolated"])
+def test_noise_values(name):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    b = G.noise(7, 6).cpu().numpy()
+    ref = noise.white_noise(fem.lumped_mass(m), 7, 6)
+    np.testing.assert_allclose(b, ref, rtol=1e-13, atol=1e-14)
+
+
+def test_noise_large_counter_range():
+    # more than 2^32 / 4 ... only the counter split matters; use a large DOF count
+    g = gi.Graph(2, np.array([0]), np.array([1]), np.array([1.0]))
+    G, m = make(g, n_elems=[3_000_001])
+    words = G.noise(3, 2, raw=True).cpu().numpy().view(np.uint32)
+    ref = philox.noise_words(3, m.n_dofs, 2)
+    np.testing.assert_array_equal(words[:, -1000:], ref[:, -1000:])
+    np.testing.assert_array_equal(words[:, :1000], ref[:, :1000])
+
+
+# ---------------------------------------------------------------- Schur blocks
+
+
+@pytest.mark.parametrize("name", ["square5", "random12", "short_edges", "isolated"])
+@pytest.mark.parametrize("alpha,gamma", [(1.0, 1e-25), (1.0, 1e-3), (1.0, 0.7), (1.0, 4e9),
+                                         (0.0, 1.0)])
+def test_schur_blocks(name, alpha, gamma):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    kappa = 2.3
+    diag, off = G.schur(kappa, alpha, gamma)
+    ml, _, kmat = sampler.assemble(m, kappa)
+    s = sampler.vertex_schur_dense(m, ml, kmat, gamma, alpha=alpha)
+    np.testing.assert_allclose(diag.cpu().numpy(), np.diag(s), rtol=1e-11)
+    # off-diagonal: the oracle's S_uv sums over parallel edges
+    offs = off.cpu().numpy()
+    dense = np.zeros_like(s)
+    for e in range(g.n_edges):
+        a, b = m.edge_u[e], m.edge_v[e]
+        dense[a, b] += offs[e]
+        dense[b, a] += offs[e]
+    mask = ~np.eye(s.shape[0], dtype=bool)
+    np.testing.assert_allclose(dense[mask], s[mask], rtol=1e-10,
+                               atol=1e-13 * np.abs(np.diag(s)).max())
+
+
+# ---------------------------------------------------------------- condensation + PCG
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("gamma", [1e-12, 0.05, 3.0, 1e7])
+def test_vertex_condensation_and_pcg(precision, gamma):
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    kappa = 1.7
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = noise.white_noise(ml, 4, 5)
+    gv, uv, st = G.vertex_solve(kappa, 1.0, gamma, torch.tensor(rhs, device="cuda"),
+                                precision=precision)
+    g_ref, u_ref = sampler.vertex_condensation(m, ml, kmat, gamma, rhs)
+    tol = 1e-10 if precision == "fp64" else 1e-5
+    for got, ref in ((gv, g_ref), (uv, u_ref)):
+        got = got.cpu().numpy()
+        err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() < tol, err
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
+# ---------------------------------------------------------------- general right-hand side
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_apply_matches_oracle(precision, name):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    kappa = 3.1
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rng = np.random.default_rng(5)
+    rhs = rng.standard_normal((3, m.n_dofs))
+    t = np.array([1e-9, 0.01, 1.0, 30.0, 1e6])
+    w = np.array([0.3, 1.0, 2.0, 0.5, 1e-3])
+    alpha = np.ones_like(t)
+    out, st = G.apply(kappa, alpha, t, w, torch.tensor(rhs, device="cuda"), precision=precision,
+                      out_dtype="f64")
+    ref = sampler.shifted_sum(ml, kmat, rhs, t, w)
+    assert rel_l2(out.cpu().numpy(), ref, ml) < TOL[precision] / 10
+    # the stiffness node (alpha = 0) used for the integer part of beta
+    out0, _ = G.apply(kappa, [0.0], [1.0], [1.0], torch.tensor(rhs, device="cuda"),
+                      precision=precision, out_dtype="f64")
+    ref0 = sampler.stiff_solve(kmat, rhs)
+    assert rel_l2(out0.cpu().numpy(), ref0, ml) < TOL[precision] / 10
+
+
+# ---------------------------------------------------------------- whole sampler
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("beta", [0.3, 0.75])
+def test_sample_matches_oracle(precision, name, beta):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    kappa, k, seed, S = 4.0, 0.45, 11, 5
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
+    ml = fem.lumped_mass(m)
+    assert rel_l2(u.cpu().numpy(), ref, ml) < TOL[precision]
+    km, kp = quadrature.limits(beta, k)
+    assert st["n_nodes"] == km + kp + 1 and st["n_systems"] == (km + kp + 1) * S
+    assert st["n_unconverged"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("beta", [1.0, 1.25, 2.0, 2.6])
+def test_sample_integer_powers(precision, beta):
+    g, h = GRAPHS["square5"]()
+    G, m = make(g, 2.0 ** -5)
+    kappa, k, seed, S = 2.0, 0.5, 3, 2
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=2.0 ** -5)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
+
+
+def test_sample_square5_workload_fp64_and_f32_output():
+    w = gi.WORKLOADS["square5"]
+    g = w.graph()
+    G, m = make(g, w.h)
+    _, ref, _ = sampler.sample(g, w.kappa, w.beta, w.k_step, w.seed, 1, h=w.h)
+    ml = fem.lumped_mass(m)
+    u, _ = G.sample(w.kappa, w.beta, w.k_step, w.seed, 1, precision="fp64")
+    assert rel_l2(u.cpu().numpy(), ref, ml) < 1e-6
+    u32, _ = G.sample(w.kappa, w.beta, w.k_step, w.seed, 1, precision="fp64", out_dtype="f32")
+    assert u32.dtype == torch.float32
+    assert rel_l2(u32.double().cpu().numpy(), ref, ml) < 1e-6
+    uh, _ = G.sample_host(w.kappa, w.beta, w.k_step, w.seed, 1, precision="fp64")
+    np.testing.assert_array_equal(uh, u.cpu().numpy())
+
+
+def test_sample_is_deterministic_in_seed_and_sample_index():
+    g, h = GRAPHS["random12"]()
+    G, _ = make(g, h)
+    a, _ = G.sample(2.0, 0.6, 0.5, 99, 6, precision="mixed")
+    b, _ = G.sample(2.0, 0.6, 0.5, 99, 3, precision="mixed")
+    # sample s depends only on (seed, s): the first three rows agree
+    np.testing.assert_allclose(a[:3].cpu().numpy(), b.cpu().numpy(), rtol=1e-5, atol=1e-7)
+    c, _ = G.sample(2.0, 0.6, 0.5, 100, 3, precision="mixed")
+    assert not np.allclose(c.cpu().numpy(), b.cpu().numpy())
+
+
+def test_zero_samples_and_max_iter_flag():
+    g, h = GRAPHS["random12"]()
+    G, _ = make(g, h)
+    out, st = G.sample(2.0, 0.6, 0.5, 1, 0)
+    assert out.shape == (0, G.n_dofs) and st["n_systems"] == 0
+    with pytest.raises(grf.GrfError) as ei:
+        G.sample(0.3, 0.6, 0.5, 1, 2, max_iter=1, rtol=1e-14)
+    assert ei.value.code == grf.GRF_ENOCONV
+    u, st = G.sample(0.3, 0.6, 0.5, 1, 2, max_iter=1, rtol=1e-14, allow_noconv=True)
+    assert st["n_unconverged"] > 0 and np.isfinite(u.cpu().numpy()).all()
+
+
+# ---------------------------------------------------------------- bench-size workloads
+
+
+def _sampled_node_check(wname, nodes_t, S, precision):
+    """Full-size graph, bench launch configuration, single shifted nodes:
+    the oracle factorises one node at a time."""
+    w = gi.WORKLOADS[wname]
+    g = w.graph()
+    ne = grf.mesh_elements(g.lengths, w.h, w.clip)
+    G, m = make(g, n_elems=ne)
+    ml, _, kmat = sampler.assemble(m, w.kappa)
+    b = noise.white_noise(ml, w.seed, S)
+    bt = torch.tensor(b, device="cuda")
+    for t in nodes_t:
+        out, _ = G.apply(w.kappa, [1.0], [t], [1.0], bt, precision=precision, out_dtype="f64")
+        ref = sampler.shifted_sum(ml, kmat, b, [t], [1.0])
+        assert rel_l2(out.cpu().numpy(), ref, ml) < TOL[precision], t
+
+
+def test_rgg2000_full_size_sampled_nodes():
+    w = gi.WORKLOADS["rgg2000"]
+    t, _ = quadrature.nodes(w.beta, w.k_step)
+    _sampled_node_check("rgg2000", [t[0], t[len(t) // 2], t[-1]], 4, "mixed")
+
+
+def test_rgg2000_full_size_sample_properties():
+    """Whole sampler at full size: finite, the vertex values of a mixed and an
+    FP64 run agree, and the sample mean / variance of the noise-driven field
+    behave (mean ~ 0 over DOFs)."""
+    w = gi.WORKLOADS["rgg2000"]
+    g = w.graph()
+    G, m = make(g, w.h)
+    u32, st = G.sample(w.kappa, w.beta, w.k_step, w.seed, w.n_samples, precision="mixed",
+                       out_dtype="f64")
+    u64, _ = G.sample(w.kappa, w.beta, w.k_step, w.seed, 2, precision="fp64")
+    ml = fem.lumped_mass(m)
+    a = u32.cpu().numpy()
+    assert np.isfinite(a).all() and st["n_unconverged"] == 0
+    assert rel_l2(a[:2], u64.cpu().numpy(), ml) < TOL["mixed"]
