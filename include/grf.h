@@ -169,6 +169,30 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
                      const double* rhs, double* g_out, double* u_out,
                      const grf_options* opts, void* stream, grf_stats* stats);
 
+/* grf_vertex_solve for callers that cannot allocate device memory: code whose
+ * device memory is owned by another allocator with a fixed budget, or loops
+ * that must not pay the device-wide synchronisation cudaMalloc/cudaFree can
+ * cause. It allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine); all of its scratch lives in one static device array of 16 MiB that
+ * every GPU loading this library holds until the process exits. The paper has
+ * no counterpart to this entry point.
+ *   Same arguments, layouts and results as grf_vertex_solve.
+ *   The graph must already be resident on the current device: a call that may
+ *   allocate (grf_vertex_solve, grf_sample, grf_noise, ...) must have used the
+ *   graph on that device before; otherwise GRF_EINVAL, with no device work.
+ *   Sizes whose scratch (about 8 n_dofs n_rhs bytes in FP64, plus the Schur
+ *   system and three PCG vectors per right-hand side) exceeds 16 MiB are
+ *   rejected with GRF_EINVAL and a message naming the limit.
+ *   The first call on a device looks up the device address of the static array
+ *   (once per device, with that device current); make that first call before
+ *   any stream capture. All calls share the one array and it keeps the last
+ *   call's contents: calls that overlap on the GPU (other streams, other
+ *   threads) race with each other. grf_options.timing is ignored.
+ *   Synchronises `stream`. */
+int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double gamma,
+                             int64_t n_rhs, const double* rhs, double* g_out, double* u_out,
+                             const grf_options* opts, void* stream, grf_stats* stats);
+
 /* Bytes of device workspace grf_sample would cache for this graph and size. */
 int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t n_samples,
                         const grf_options* opts, size_t* bytes);

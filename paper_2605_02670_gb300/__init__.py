@@ -25,7 +25,7 @@ GRF_OUT_F64, GRF_OUT_F32 = 0, 1
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
-             "grf_workspace_bytes", "grf_last_error")
+             "grf_vertex_solve_noalloc", "grf_workspace_bytes", "grf_last_error")
 
 
 class GrfError(RuntimeError):
@@ -72,6 +72,7 @@ def _load() -> ctypes.CDLL:
         "grf_apply": [P, D, I64, P, P, P, I64, P, P, P, P, P],
         "grf_schur": [P, D, D, D, P, P, P],
         "grf_vertex_solve": [P, D, D, D, I64, P, P, P, P, P, P],
+        "grf_vertex_solve_noalloc": [P, D, D, D, I64, P, P, P, P, P, P],
         "grf_workspace_bytes": [P, D, D, I64, P, P],
     }
     for name, args in sig.items():
@@ -199,6 +200,20 @@ def grf_vertex_solve(handle, kappa, alpha, gamma, n_rhs, rhs_ptr: int, g_ptr: in
                                  ctypes.c_void_p(rhs_ptr), ctypes.c_void_p(g_ptr),
                                  ctypes.c_void_p(u_ptr), ctypes.byref(opts), _stream(stream),
                                  ctypes.byref(st)))
+    return st.as_dict()
+
+
+def grf_vertex_solve_noalloc(handle, kappa, alpha, gamma, n_rhs, rhs_ptr: int, g_ptr: int,
+                             u_ptr: int, opts: grf_options, stream=None) -> dict:
+    """grf_vertex_solve for callers that cannot allocate device memory: its
+    scratch is a fixed 16 MiB static device array inside the library. The
+    graph must already have been used on this device by an allocating call;
+    concurrent calls on the GPU race on the shared array."""
+    st = grf_stats()
+    _check(_lib.grf_vertex_solve_noalloc(handle, float(kappa), float(alpha), float(gamma),
+                                         int(n_rhs), ctypes.c_void_p(rhs_ptr),
+                                         ctypes.c_void_p(g_ptr), ctypes.c_void_p(u_ptr),
+                                         ctypes.byref(opts), _stream(stream), ctypes.byref(st)))
     return st.as_dict()
 
 

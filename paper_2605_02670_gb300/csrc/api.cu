@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -459,6 +460,58 @@ int check_graph(const grf_graph* g) {
 
 }  // namespace
 
+// Scratch of grf_vertex_solve_noalloc: one fixed device array that every GPU
+// loading this library holds until the process exits. Host code must not pass
+// this name to a kernel (on the host it is only a stand-in for the symbol);
+// the device address comes from cudaGetSymbolAddress below.
+static constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char grf_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of grf_noalloc_scratch on device `dev` (which must be the
+// current device), looked up once per device and cached.
+int noalloc_scratch(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(GRF_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, grf_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(GRF_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return GRF_OK;
+}
+
+// The part of an apply workspace one vertex solve touches (no recovery buffers).
+void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, ApplyWs* w, void** b) {
+  const size_t E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
+  *b = c.take<char>((size_t)g->n * Ss * tsize);
+  w->alpha = c.take<double>(1);
+  w->gamma = c.take<double>(1);
+  w->weight = c.take<double>(1);
+  w->saa = c.take<double>(E);
+  w->sab = c.take<double>(E);
+  w->diag = c.take<double>(V);
+  w->offv = c.take<double>(2 * E);
+  w->r = c.take<double>(Ss * V);
+  w->p = c.take<double>(Ss * V);
+  w->q = c.take<double>(Ss * V);
+  w->iters = c.take<int32_t>(Ss);
+  w->status = c.take<PcgStatus>(1);
+  w->gvec = w->x = w->acc = nullptr;
+  w->yscr = w->rpscr = nullptr;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* grf_last_error(void) { return g_last_error.c_str(); }
@@ -748,6 +801,65 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
     GRF_TRY(vertex_phase<double>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
   } else {
     float* b = (float*)g->ws;
+    launch_to_minor<float>(g->d, n_rhs, rhs, b, false, st);
+    GRF_TRY(vertex_phase<float>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
+  }
+  GRF_TRY(collect(w, st, 1, n_rhs, &rs));
+  return finish(rs, g, stats);
+}
+
+// grf_vertex_solve without any device allocation: every scratch buffer lives
+// in grf_noalloc_scratch. The graph must already be resident on the current
+// device. The first call on a device looks up the array's device address
+// (cudaGetSymbolAddress); make that first call before any stream capture.
+// Calls share the array, so calls that overlap on the GPU race with each
+// other; the PCG status words are cleared at every call, everything else is
+// fully overwritten before it is read. Per-phase timing is not recorded here.
+int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double gamma,
+                             int64_t n_rhs, const double* rhs, double* g_out, double* u_out,
+                             const grf_options* opts, void* stream, grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  if (!(kappa > 0) || !(alpha >= 0) || !(gamma > 0)) return fail(GRF_EINVAL, "bad parameters");
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  if (n_rhs < 0) return fail(GRF_EINVAL, "bad n_rhs");
+  if (n_rhs == 0) return finish(RunStats{}, g, stats);
+  if (!rhs || !g_out || !u_out) return fail(GRF_EINVAL, "null buffer");
+  const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
+  Carve dry(nullptr);
+  ApplyWs w;
+  void* bptr = nullptr;
+  carve_vertex_solve(dry, g, n_rhs, ts, &w, &bptr);
+  if (dry.off > kNoAllocScratchBytes)
+    return fail(GRF_EINVAL,
+                "grf_vertex_solve_noalloc needs %zu bytes of scratch for n_dofs=%lld x n_rhs=%lld "
+                "but its static scratch holds %zu bytes; use grf_vertex_solve or fewer rhs",
+                dry.off, (long long)g->n, (long long)n_rhs, kNoAllocScratchBytes);
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  if (g->device != dev || !g->dev_block)
+    return fail(GRF_EINVAL,
+                "graph is not resident on device %d; a call that allocates (e.g. grf_vertex_solve) "
+                "must have used it there first", dev);
+  void* base = nullptr;
+  GRF_TRY(noalloc_scratch(dev, &base));
+  Carve c(base);
+  carve_vertex_solve(c, g, n_rhs, ts, &w, &bptr);
+  cudaStream_t st = (cudaStream_t)stream;
+  const double one = 1.0;
+  CUDA_TRY(cudaMemcpyAsync(w.alpha, &alpha, sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(w.gamma, &gamma, sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(w.weight, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  const double k2 = kappa * kappa;
+  RunStats rs;
+  rs.timing = false;
+  rs.launches += 1;
+  if (o.precision == GRF_FP64) {
+    double* b = (double*)bptr;
+    launch_to_minor<double>(g->d, n_rhs, rhs, b, false, st);
+    GRF_TRY(vertex_phase<double>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
+  } else {
+    float* b = (float*)bptr;
     launch_to_minor<float>(g->d, n_rhs, rhs, b, false, st);
     GRF_TRY(vertex_phase<float>(g, w, 1, k2, n_rhs, b, g_out, u_out, o, st, &rs));
   }
