@@ -78,6 +78,14 @@ struct grf_graph {
   std::vector<double> he;
   std::vector<int64_t> ioff;
   std::vector<double> ml_vertex;  // lumped mass at kept vertices
+  // recovery edge bins per precision ([0] FP32 sweeps, [1] FP64): edge ids
+  // grouped by bin, the count per bin, and last the edges beyond every bin
+  std::vector<int32_t> bin_edges[2];
+  int32_t bin_count[2][kMaxBins + 1] = {};
+  int32_t n_bins[2] = {0, 0};
+  const int32_t* d_bin_edges[2] = {nullptr, nullptr};
+
+  int64_t long_edges(bool fp64) const { return bin_count[fp64 ? 1 : 0][n_bins[fp64 ? 1 : 0]]; }
 
   int device = -1;
   void* dev_block = nullptr;
@@ -129,6 +137,7 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(E); c.take<int32_t>(E); c.take<int32_t>(E); c.take<double>(E);
   c.take<int64_t>(E + 1); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   c.take<double>((size_t)g->n); c.take<double>(V);
+  c.take<int32_t>(E + 1); c.take<int32_t>(E + 1);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -144,6 +153,13 @@ int ensure_device(grf_graph* g) {
   int32_t* an = k.take<int32_t>(2 * E);
   double* sml = k.take<double>((size_t)g->n);
   double* mlv = k.take<double>(V);
+  for (int p = 0; p < 2; ++p) {
+    int32_t* be = k.take<int32_t>(E + 1);
+    if (!g->bin_edges[p].empty())
+      CUDA_TRY(cudaMemcpy(be, g->bin_edges[p].data(), g->bin_edges[p].size() * 4,
+                          cudaMemcpyHostToDevice));
+    g->d_bin_edges[p] = be;
+  }
   CUDA_TRY(cudaMemcpy(eu, g->eu.data(), E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(ev, g->ev.data(), E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(nel, g->nel.data(), E * 4, cudaMemcpyHostToDevice));
@@ -233,8 +249,13 @@ int read_opts(const grf_options* o, Opts* r) {
 
 // Device workspace of one domain-decomposed apply with L nodes and S right-hand sides.
 struct ApplyWs {
-  double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv, *gvec, *x, *r, *p, *q, *acc;
+  double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv, *gvec, *x, *acc;
+  void *r, *p, *q, *d;  // PCG vectors in the sweep precision T [L][S][V]
+  void* dscale;         // T [L][V]
+  void* offv_t;         // float [L][2E] (mixed precision only)
   void *yscr, *rpscr;
+  void* prm;  // SweepParams<T> [L][E]
+  void* xw;   // T [L][S][V]
   int32_t* iters;
   PcgStatus* status;
 };
@@ -251,12 +272,19 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->offv = c.take<double>(Ls * 2 * E);
   w->gvec = c.take<double>(Ls * Ss * V);
   w->x = c.take<double>(Ls * Ss * V);
-  w->r = c.take<double>(Ls * Ss * V);
-  w->p = c.take<double>(Ls * Ss * V);
-  w->q = c.take<double>(Ls * Ss * V);
-  w->acc = c.take<double>((size_t)g->ni * Ss);
-  w->yscr = c.take<char>((size_t)g->ni * Ss * tsize);
-  w->rpscr = c.take<char>((size_t)g->ni * nsg * tsize);
+  w->r = c.take<char>(Ls * Ss * V * tsize);
+  w->p = c.take<char>(Ls * Ss * V * tsize);
+  w->q = c.take<char>(Ls * Ss * V * tsize);
+  w->d = c.take<char>(Ls * Ss * V * tsize);
+  w->dscale = c.take<char>(Ls * V * tsize);
+  w->offv_t = tsize == 4 ? c.take<char>(Ls * 2 * E * 4) : nullptr;
+  // scratch of the sequential recovery, only for edges longer than every bin
+  const size_t ni_long = g->long_edges(tsize == 8) > 0 ? (size_t)g->ni : 0;
+  w->acc = c.take<double>(ni_long * Ss);
+  w->yscr = c.take<char>(ni_long * Ss * tsize);
+  w->rpscr = c.take<char>(ni_long * nsg * tsize);
+  w->prm = c.take<char>(Ls * E * 4 * tsize);
+  w->xw = c.take<char>(Ls * Ss * V * tsize);
   w->iters = c.take<int32_t>(Ls * Ss);
   w->status = c.take<PcgStatus>(1);
 }
@@ -338,17 +366,20 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                  RunStats* rs) {
   const DevNodes nd = dev_nodes(w, L);
   rs->begin(st);
-  launch_schur(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, st);
+  rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv,
+                                  (SweepParams<T>*)w.prm, (T*)w.dscale, (T*)w.offv_t, st);
   rs->end(1, st);
   rs->begin(st);
   launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
   rs->end(2, st);
   CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
+  // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
+  const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
   rs->begin(st);
-  launch_pcg_jacobi(g->d, L, S, w.diag, w.offv, gvec, xv, w.r, w.p, w.q, o.rtol, o.max_iter,
-                    w.iters, w.status, st);
+  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, gvec, xv, (T*)w.d,
+                (T*)w.r, (T*)w.p, (T*)w.q, o.rtol, o.max_iter, w.iters, w.status, st);
   rs->end(3, st);
-  rs->launches += 5;
+  rs->launches += 3;
   CUDA_TRY(cudaGetLastError());
   return GRF_OK;
 }
@@ -363,11 +394,13 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   const double k2 = kappa * kappa;
   GRF_TRY(upload_nodes(hn, w, st));
   GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
+  const int p = sizeof(T) == 8 ? 1 : 0;
   rs->begin(st);
-  launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out, w.acc, (T*)w.yscr,
-                          (T*)w.rpscr, st);
+  rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
+                                          (const SweepParams<T>*)w.prm, (T*)w.xw,
+                                          g->d_bin_edges[p], g->bin_count[p], g->n_bins[p], w.acc,
+                                          (T*)w.yscr, (T*)w.rpscr, st);
   rs->end(4, st);
-  rs->launches += g->ni > 0 ? 2 : 1;
   CUDA_TRY(cudaGetLastError());
   return collect(w, st, hn.L(), S, rs);
 }
@@ -501,13 +534,17 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->sab = c.take<double>(E);
   w->diag = c.take<double>(V);
   w->offv = c.take<double>(2 * E);
-  w->r = c.take<double>(Ss * V);
-  w->p = c.take<double>(Ss * V);
-  w->q = c.take<double>(Ss * V);
+  w->r = c.take<char>(Ss * V * tsize);
+  w->p = c.take<char>(Ss * V * tsize);
+  w->q = c.take<char>(Ss * V * tsize);
+  w->d = c.take<char>(Ss * V * tsize);
+  w->dscale = c.take<char>(V * tsize);
+  w->offv_t = tsize == 4 ? c.take<char>(2 * E * 4) : nullptr;
   w->iters = c.take<int32_t>(Ss);
   w->status = c.take<PcgStatus>(1);
   w->gvec = w->x = w->acc = nullptr;
   w->yscr = w->rpscr = nullptr;
+  w->prm = w->xw = nullptr;
 }
 
 }  // namespace
@@ -585,6 +622,28 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
     g->ml_vertex[g->ev[e]] += 0.5 * g->he[e];
   }
   g->ni = g->ioff[E];
+  // recovery bins: smallest bin whose 32 * NW * B lanes x nodes hold the interior
+  for (int p = 0; p < 2; ++p) {
+    int32_t Bs[kMaxBins], NWs[kMaxBins];
+    const int nb = recover_bins(p == 1, Bs, NWs);
+    g->n_bins[p] = nb;
+    std::vector<std::vector<int32_t>> lists(nb + 1);
+    for (int64_t e = 0; e < E; ++e) {
+      const int64_t m = g->nel[e] - 1;
+      if (m <= 0) continue;
+      int bin = nb;
+      for (int i = 0; i < nb; ++i)
+        if (m <= (int64_t)32 * NWs[i] * Bs[i]) {
+          bin = i;
+          break;
+        }
+      lists[bin].push_back((int32_t)e);
+    }
+    for (int i = 0; i <= nb; ++i) {
+      g->bin_count[p][i] = (int32_t)lists[i].size();
+      g->bin_edges[p].insert(g->bin_edges[p].end(), lists[i].begin(), lists[i].end());
+    }
+  }
   g->n = nv + g->ni;
   // vertex incidence lists (CSR), edges in increasing id per vertex
   g->vptr.assign(nv + 1, 0);
@@ -763,7 +822,8 @@ int grf_schur(grf_graph* g, double kappa, double alpha, double gamma, double* di
   carve_apply(c, g, 1, 1, 8, &w);
   cudaStream_t st = (cudaStream_t)stream;
   GRF_TRY(upload_nodes(hn, w, st));
-  launch_schur(g->d, dev_nodes(w, 1), kappa * kappa, w.saa, offdiag, diag, w.offv, st);
+  launch_schur<double>(g->d, dev_nodes(w, 1), kappa * kappa, w.saa, offdiag, diag, w.offv,
+                       nullptr, nullptr, nullptr, st);
   CUDA_TRY(cudaGetLastError());
   return GRF_OK;
 }

@@ -47,12 +47,26 @@ void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaS
 void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
                         cudaStream_t st);
 
+// Per-(node, edge) constants of the interior sweeps in the sweep precision T:
+// delta, w_l h_e / gamma_l (= w_l / c), sinh(theta), theta with
+// 2 + delta = 2 cosh(theta).
+template <typename T>
+struct alignas(4 * sizeof(T)) SweepParams {
+  T delta, sc, sh, theta;
+};
+
 // ---- schur.cu
 // Per-(l, e) 2x2 Schur blocks and vertex diagonal:
 //   saa[l][e], sab[l][e];  diag[l][v] = sum_{e at v} saa[l][e];
-//   offv[l][k] = sab[l][adj_edge[k]] in vertex-incidence order.
-void launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa,
-                  double* sab, double* diag, double* offv, cudaStream_t st);
+//   offv[l][k] = sab[l][adj_edge[k]] in vertex-incidence order;
+//   prm[l][e] (if not null): the sweep constants above;
+//   dscale[l][v] (if not null): 1 / S_vv (T = double) or 1 / sqrt(S_vv) (T = float);
+//   offv_t (T = float, if not null): offv / sqrt(S_vv S_ww).
+// Returns the number of kernels launched.
+template <typename T>
+int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa,
+                 double* sab, double* diag, double* offv, SweepParams<T>* prm, T* dscale,
+                 T* offv_t, cudaStream_t st);
 
 // ---- thomas.cu
 // rhs (sample-minor [n][S], T) -> condensed right-hand side gvec[l][s][v] (double)
@@ -60,11 +74,18 @@ template <typename T>
 void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                      const T* b, double* gvec, cudaStream_t st);
 // Vertex accumulation out[s][v] = sum_l w_l x[l][s][v], and fused interior
-// recovery + quadrature sum for the interior DOFs.
+// recovery + quadrature sum for the interior DOFs: binned register-resident
+// kernels (recover.cu) for edges up to the largest bin, the sequential kernel
+// for longer ones (bin_count[n_bins] of them, listed last in bin_edges; they
+// need acc/yscr/rpscr, sized [n_interior][S]). bin_count is a host array.
+// Returns the number of kernels launched.
+// prm: sweep constants from launch_schur; xw: [L][S][nv] scratch that receives
+// w_l u_v^(l) in precision T.
 template <typename T, typename OutT>
-void launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                    const T* b, const double* xv, OutT* out, double* acc, T* yscr, T* rpscr,
-                    cudaStream_t st);
+int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                   const T* b, const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
+                   const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins,
+                   double* acc, T* yscr, T* rpscr, cudaStream_t st);
 // [S][n] double -> [n][S] T, each DOF j scaled by scale[j] (or 1 when scale is null
 // and mass_scale is false; by M_L,j = sqrt_ml[j]^2 when mass_scale is true)
 template <typename T>
@@ -72,11 +93,30 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
                      cudaStream_t st);
 
 // ---- pcg.cu
-void launch_pcg_jacobi(const DevGraph& g, int32_t L, int64_t S, const double* diag,
-                       const double* offv, const double* gvec, double* x, double* r, double* p,
-                       double* q, double rtol, int32_t max_iter, int32_t* iters,
-                       PcgStatus* status, cudaStream_t st);
+// Vertex PCG for all L x S systems; x[l][s][v] (FP64) receives the solution.
+// VT = double: FP64 Jacobi-PCG (dscale = 1 / D, offv_t = offv).
+// VT = float: FP32 Jacobi-scaled CG inside FP64 refinement (dscale = 1 / sqrt(D),
+// offv_t = scaled blocks). d, r, p, q: [L][S][nv] scratch used when a system's
+// vectors do not fit in shared memory.
+template <typename VT>
+void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
+                const VT* dscale_t, const VT* offv_t, const double* gvec, double* x, VT* d,
+                VT* r, VT* p, VT* q, double rtol, int32_t max_iter, int32_t* iters,
+                PcgStatus* status, cudaStream_t st);
 
 int recover_sample_group();
+
+// ---- recover.cu
+// Edge bins of the register-resident recovery: bin i takes edges with
+// m <= 32 * NW[i] * B[i] interior nodes. Returns the number of bins.
+constexpr int kMaxBins = 8;
+int recover_bins(bool fp64, int32_t* B, int32_t* NW);
+// bin_edges: edge ids grouped by bin (bin_count[i] each, bins in order);
+// prm[l][e] sweep constants, xw[l][s][v] = w_l u_v^(l) in precision T.
+// Returns the number of kernels launched.
+template <typename T, typename OutT>
+int launch_recover_bins(const DevGraph& g, int32_t L, int64_t S, const T* b,
+                        const SweepParams<T>* prm, const T* xw, OutT* out,
+                        const int32_t* bin_edges, const int32_t* bin_count, cudaStream_t st);
 
 }  // namespace grf

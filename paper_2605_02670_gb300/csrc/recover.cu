@@ -1,0 +1,349 @@
+// Fused interior recovery + quadrature sum (Eq. internal_recovery, Sec. 3
+// Phase 5) with the edge interior held in registers.
+//
+// For every node l the interior values of edge e solve
+//   T_l x = (w_l / c_l) b_I + w_l u_a e_1 + w_l u_b e_m,
+//   T_l = tridiag(-1, 2 + delta_l, -1),  c_l = gamma_l / h_e,
+// and U_I = sum_l x^(l). A unit of work is (edge, group of kSG samples). The
+// unit's m interior nodes are split into contiguous segments of B nodes, one
+// per lane of NW warps, and stay in registers for all L nodes: the noise is
+// read once and the field written once.
+//
+// Thomas forward elimination y_K = r_K + y_{K-1} / p_{K-1} and back
+// substitution x_K = (y_K + x_{K+1}) / p_K are first-order affine recurrences;
+// each lane runs them on its segment from a zero carry, the carries are found
+// by a scan of the composed affine maps across lanes (warp shuffles, shared
+// memory across warps), and each lane then adds carry x (product of 1/p) to its
+// values.
+//
+// Pivots p_K = 1 + q_K: with 2 + delta = 2 cosh(theta) the elimination pivots
+// of T are p_K = sinh((K+1) theta) / sinh(K theta), so
+//   q_K = delta / 2 + sinh(theta) coth(K theta)
+// with no subtraction. A lane evaluates this once at the start of its segment
+// and continues with q_{K+1} = delta + q_K / (1 + q_K) (the same excess
+// recurrence the sequential sweep uses), which is contracting, so the start
+// error does not grow.
+//
+// The sum over nodes: FP32 partial sums over `group` consecutive nodes, added
+// into an FP64 accumulator held in shared memory.
+#include "grf_internal.h"
+
+namespace grf {
+namespace {
+
+constexpr int kSG = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
+__device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
+
+// Inclusive composition of affine maps y -> R + A y across the lanes of a warp.
+// forward: lane i ends with f_i o f_{i-1} o ... o f_0;
+// backward: lane i ends with f_i o f_{i+1} o ... o f_31.
+template <typename T, bool kForward>
+__device__ __forceinline__ void warp_scan(T& a, T (&r)[kSG], int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    T ap, rp[kSG];
+    if (kForward) {
+      ap = __shfl_up_sync(kFull, a, d);
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) rp[s] = __shfl_up_sync(kFull, r[s], d);
+    } else {
+      ap = __shfl_down_sync(kFull, a, d);
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) rp[s] = __shfl_down_sync(kFull, r[s], d);
+    }
+    const bool take = kForward ? (lane >= d) : (lane + d < 32);
+    if (take) {
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) r[s] = fma(a, rp[s], r[s]);
+      a = a * ap;
+    }
+  }
+}
+
+// Carry into this lane: the value at the end of the previous lane (forward) or
+// at the start of the next lane (backward), given the lane's own map (a, r).
+// NW > 1 combines warp totals through shared memory.
+template <typename T, bool kForward, int NW>
+__device__ __forceinline__ void lane_carry(T a, const T (&r)[kSG], int lane, int wi,
+                                           T (*sh_a)[NW], T (*sh_r)[NW][kSG], T (&carry)[kSG]) {
+  T ia = a, ir[kSG];
+#pragma unroll
+  for (int s = 0; s < kSG; ++s) ir[s] = r[s];
+  warp_scan<T, kForward>(ia, ir, lane);
+  // exclusive: neighbour's inclusive result
+  const int src = kForward ? lane - 1 : lane + 1;
+  const bool edge_lane = kForward ? (lane == 0) : (lane == 31);
+  T ea = kForward ? __shfl_up_sync(kFull, ia, 1) : __shfl_down_sync(kFull, ia, 1);
+  T er[kSG];
+#pragma unroll
+  for (int s = 0; s < kSG; ++s)
+    er[s] = kForward ? __shfl_up_sync(kFull, ir[s], 1) : __shfl_down_sync(kFull, ir[s], 1);
+  (void)src;
+  if (edge_lane) {
+    ea = (T)1;
+#pragma unroll
+    for (int s = 0; s < kSG; ++s) er[s] = (T)0;
+  }
+  T win[kSG];
+#pragma unroll
+  for (int s = 0; s < kSG; ++s) win[s] = (T)0;
+  if (NW > 1) {
+    const int tot_lane = kForward ? 31 : 0;
+    const int dir = kForward ? 0 : 1;
+    if (lane == tot_lane) {
+      sh_a[dir][wi] = ia;
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) sh_r[dir][wi][s] = ir[s];
+    }
+    __syncthreads();
+    if (kForward) {
+      for (int j = 0; j < wi; ++j) {
+#pragma unroll
+        for (int s = 0; s < kSG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
+      }
+    } else {
+      for (int j = NW - 1; j > wi; --j) {
+#pragma unroll
+        for (int s = 0; s < kSG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < kSG; ++s) carry[s] = fma(ea, win[s], er[s]);
+}
+
+// Dynamic shared memory per CTA: the FP64 node sums [warp][B*kSG][32], and for
+// kRbSmem the unit's noise [warp][B][32][kSG].
+template <typename T, int B, int NW, int UPC, bool kRbSmem>
+constexpr size_t seg_smem_bytes() {
+  return (size_t)UPC * NW * B * kSG * 32 * (sizeof(double) + (kRbSmem ? sizeof(T) : 0));
+}
+
+template <typename T, typename OutT, int B, int NW, int UPC, bool kRbSmem>
+__global__ void __launch_bounds__(32 * NW * UPC)
+    recover_seg_kernel(DevGraph g, int32_t L, int64_t S, const int32_t* __restrict__ edges,
+                       int32_t n_edges, const T* __restrict__ b,
+                       const SweepParams<T>* __restrict__ prm, const T* __restrict__ xw,
+                       OutT* __restrict__ out, int group) {
+  __shared__ T sh_a[2][NW];
+  __shared__ T sh_r[2][NW][kSG];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ul = warp / NW, wi = warp % NW;
+  double(*acc)[32] = reinterpret_cast<double(*)[32]>(dyn) + (size_t)warp * B * kSG;
+  T* rbs = reinterpret_cast<T*>(dyn + (size_t)UPC * NW * B * kSG * 32 * sizeof(double)) +
+           (size_t)warp * B * 32 * kSG;
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  const int64_t n_units = (int64_t)n_edges * nsg;
+  // all warps of a CTA take the same number of trips (NW > 1 uses __syncthreads)
+  const int64_t trips = (n_units + (int64_t)gridDim.x * UPC - 1) / ((int64_t)gridDim.x * UPC);
+  for (int64_t trip = 0; trip < trips; ++trip) {
+    const int64_t unit = (trip * gridDim.x + blockIdx.x) * UPC + ul;
+    const bool live = unit < n_units;
+    const int32_t e = live ? edges[unit / nsg] : 0;
+    const int64_t s0 = live ? (unit % nsg) * kSG : 0;
+    const int32_t m = live ? g.nel[e] - 1 : 0;
+    const int64_t off = live ? g.ioff[e] : 0;
+    const int32_t va = live ? g.eu[e] : 0, vb = live ? g.ev[e] : 0;
+    const int K0 = (wi * 32 + lane) * B + 1;  // 1-based first node of this lane
+    T rb[kRbSmem ? 1 : B][kSG];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) {
+        const bool ok = (K0 + k <= m) && (s0 + s < S);
+        const T v = ok ? b[(g.nv + off + K0 + k - 1) * S + s0 + s] : (T)0;
+        if (kRbSmem)
+          rbs[(k * 32 + lane) * kSG + s] = v;
+        else
+          rb[kRbSmem ? 0 : k][s] = v;
+        acc[k * kSG + s][lane] = 0.0;
+      }
+    }
+    T accf[B][kSG];
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) accf[k][s] = (T)0;
+
+    for (int32_t l = 0; l < L; ++l) {
+      const SweepParams<T> pr = prm[(int64_t)l * g.ne + e];
+      const T dl = pr.delta, sc = pr.sc, shv = pr.sh, th = pr.theta;
+      T xa[kSG], xb[kSG];
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) {
+        const bool ok = live && (s0 + s < S);
+        const int64_t base = ((int64_t)l * S + (ok ? s0 + s : 0)) * g.nv;
+        xa[s] = ok ? xw[base + va] : (T)0;
+        xb[s] = ok ? xw[base + vb] : (T)0;
+      }
+      // pivots of this lane's nodes (rp[k] = 1 / p_{K0+k}) and of the node before
+      T q, rp_prev;
+      if (K0 >= 2) {
+        q = (T)0.5 * dl + shv / tanh_t((T)(K0 - 1) * th);
+        rp_prev = rcp((T)1 + q);
+        q = dl + q * rp_prev;
+      } else {
+        rp_prev = (T)0;
+        q = (T)1 + dl;
+      }
+      T rp[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        const T r_ = rcp((T)1 + q);
+        rp[k] = (K0 + k <= m) ? r_ : (T)0;
+        q = dl + q * r_;
+      }
+      if (K0 > m) rp_prev = (T)0;
+      // right-hand side and forward elimination from a zero carry
+      T y[B][kSG];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        const int K = K0 + k;
+#pragma unroll
+        for (int s = 0; s < kSG; ++s) {
+          const T bv = kRbSmem ? rbs[(k * 32 + lane) * kSG + s] : rb[kRbSmem ? 0 : k][s];
+          T r = bv * sc;
+          if (K == 1) r += xa[s];
+          if (K == m) r += xb[s];
+          y[k][s] = (k == 0) ? r : fma(rp[k - 1], y[k - 1][s], r);
+        }
+      }
+      T af = rp_prev;
+#pragma unroll
+      for (int k = 0; k < B - 1; ++k) af *= rp[k];
+      T yin[kSG];
+      lane_carry<T, true, NW>(af, y[B - 1], lane, wi, sh_a, sh_r, yin);
+      {
+        T c = rp_prev;
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          if (k > 0) c *= rp[k - 1];
+#pragma unroll
+          for (int s = 0; s < kSG; ++s) y[k][s] = fma(c, yin[s], y[k][s]);
+        }
+      }
+      // back substitution from a zero carry: x_K = y_K / p_K + x_{K+1} / p_K
+#pragma unroll
+      for (int k = B - 1; k >= 0; --k) {
+#pragma unroll
+        for (int s = 0; s < kSG; ++s) {
+          const T u = y[k][s] * rp[k];
+          y[k][s] = (k == B - 1) ? u : fma(rp[k], y[k + 1][s], u);
+        }
+      }
+      T ab = (T)1;
+#pragma unroll
+      for (int k = 0; k < B; ++k) ab *= rp[k];
+      T xin[kSG];
+      lane_carry<T, false, NW>(ab, y[0], lane, wi, sh_a, sh_r, xin);
+      {
+        T c = (T)1;
+#pragma unroll
+        for (int k = B - 1; k >= 0; --k) {
+          c *= rp[k];
+#pragma unroll
+          for (int s = 0; s < kSG; ++s) accf[k][s] += fma(c, xin[s], y[k][s]);
+        }
+      }
+      if ((l + 1) % group == 0 || l + 1 == L) {
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+#pragma unroll
+          for (int s = 0; s < kSG; ++s) {
+            acc[k * kSG + s][lane] += (double)accf[k][s];
+            accf[k][s] = (T)0;
+          }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int K = K0 + k;
+#pragma unroll
+      for (int s = 0; s < kSG; ++s) {
+        if (live && K <= m && s0 + s < S)
+          out[(s0 + s) * g.n + g.nv + off + K - 1] = (OutT)acc[k * kSG + s][lane];
+      }
+    }
+  }
+}
+
+int grid_for(int64_t units, int upc) {
+  int64_t blocks = (units + upc - 1) / upc;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+template <typename T, typename OutT, int B, int NW>
+void launch_bin(const DevGraph& g, int32_t L, int64_t S, const int32_t* edges, int32_t n,
+                const T* b, const SweepParams<T>* prm, const T* xw, OutT* out, int group,
+                cudaStream_t st) {
+  if (n <= 0) return;
+  constexpr int UPC = NW == 1 ? 4 : 1;
+  constexpr bool kRbSmem = NW > 4;
+  constexpr size_t smem = seg_smem_bytes<T, B, NW, UPC, kRbSmem>();
+  auto kern = recover_seg_kernel<T, OutT, B, NW, UPC, kRbSmem>;
+  if (smem > 48 * 1024)  // the attribute is per device, so set it at every launch
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSG - 1) / kSG);
+  kern<<<grid_for(units, UPC), 32 * NW * UPC, smem, st>>>(g, L, S, edges, n, b, prm, xw, out,
+                                                        group);
+}
+
+}  // namespace
+
+// Bin table: bin i holds edges whose interior fits 32 * NW lanes x B nodes;
+// longer edges go to the generic sequential kernel.
+int recover_bins(bool fp64, int32_t* B_out, int32_t* NW_out) {
+  static const int32_t bf[] = {1, 2, 4, 8, 8, 8, 8, 8};
+  static const int32_t wf[] = {1, 1, 1, 1, 2, 4, 8, 16};
+  static const int32_t bd[] = {1, 2, 4, 4, 4, 4, 4};
+  static const int32_t wd[] = {1, 1, 1, 2, 4, 8, 16};
+  const int n = fp64 ? 7 : 8;
+  for (int i = 0; i < n; ++i) {
+    B_out[i] = fp64 ? bd[i] : bf[i];
+    NW_out[i] = fp64 ? wd[i] : wf[i];
+  }
+  return n;
+}
+
+template <typename T, typename OutT>
+int launch_recover_bins(const DevGraph& g, int32_t L, int64_t S, const T* b,
+                        const SweepParams<T>* prm, const T* xw, OutT* out,
+                        const int32_t* bin_edges, const int32_t* bin_count, cudaStream_t st) {
+  // FP32 partial sums over 16 consecutive nodes before each FP64 addition
+  const int group = sizeof(T) == 4 ? 16 : (1 << 30);
+  const int32_t* e = bin_edges;
+  int n = 0;
+#define GRF_BIN(i, B_, NW_)                                                               \
+  launch_bin<T, OutT, B_, NW_>(g, L, S, e, bin_count[i], b, prm, xw, out, group, st); \
+  n += bin_count[i] > 0;                                                              \
+  e += bin_count[i];
+  if constexpr (sizeof(T) == 4) {
+    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 8, 1)
+    GRF_BIN(4, 8, 2) GRF_BIN(5, 8, 4) GRF_BIN(6, 8, 8) GRF_BIN(7, 8, 16)
+  } else {
+    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 4, 2)
+    GRF_BIN(4, 4, 4) GRF_BIN(5, 4, 8) GRF_BIN(6, 4, 16)
+  }
+#undef GRF_BIN
+  return n;
+}
+
+#define GRF_INST(T, O)                                                                         \
+  template int launch_recover_bins<T, O>(const DevGraph&, int32_t, int64_t, const T*,          \
+                                         const SweepParams<T>*, const T*, O*, const int32_t*, \
+                                         const int32_t*, cudaStream_t);
+GRF_INST(float, float)
+GRF_INST(float, double)
+GRF_INST(double, double)
+GRF_INST(double, float)
+#undef GRF_INST
+
+}  // namespace grf

@@ -21,8 +21,9 @@
 namespace grf {
 namespace {
 
+template <typename T>
 __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, double* __restrict__ saa,
-                                   double* __restrict__ sab) {
+                                   double* __restrict__ sab, SweepParams<T>* __restrict__ prm) {
   const int64_t total = (int64_t)nd.L * g.ne;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -39,12 +40,23 @@ __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, doubl
     const double e2 = -expm1(-2.0 * nth);  // 1 - exp(-2 n theta)
     saa[t] = c * sh * ((2.0 - e2) / e2);
     sab[t] = -c * sh * (2.0 * e1 / e2);
+    if (prm) {
+      SweepParams<T> p;
+      p.delta = (T)delta;
+      p.sc = (T)(nd.weight[l] / c);
+      p.sh = (T)sh;
+      p.theta = (T)theta;
+      prm[t] = p;
+    }
   }
 }
 
+// diag[l][v] = S_vv, offv in incidence order, and the PCG scaling in precision
+// T: 1 / S_vv for FP64 PCG, 1 / sqrt(S_vv) for the Jacobi-scaled FP32 solve.
+template <typename T>
 __global__ void vertex_diag_kernel(DevGraph g, int32_t L, const double* __restrict__ saa,
                                    const double* __restrict__ sab, double* __restrict__ diag,
-                                   double* __restrict__ offv) {
+                                   double* __restrict__ offv, T* __restrict__ dscale) {
   const int64_t total = (int64_t)L * g.nv;
   const int64_t nadj = 2 * (int64_t)g.ne;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -58,6 +70,24 @@ __global__ void vertex_diag_kernel(DevGraph g, int32_t L, const double* __restri
       offv[l * nadj + k] = sab[i];
     }
     diag[t] = d;
+    if (dscale) dscale[t] = sizeof(T) == 8 ? (T)(1.0 / d) : (T)(1.0 / sqrt(d));
+  }
+}
+
+// offv_t[l][k] = offv[l][k] / sqrt(S_vv S_ww) in FP32 (unit-diagonal scaling)
+__global__ void scaled_offdiag_kernel(DevGraph g, int32_t L, const double* __restrict__ offv,
+                                      const float* __restrict__ dscale, float* __restrict__ offv_t) {
+  const int64_t total = (int64_t)L * g.nv;
+  const int64_t nadj = 2 * (int64_t)g.ne;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / g.nv;
+    const int32_t v = (int32_t)(t - l * g.nv);
+    const double sv = (double)dscale[t];
+    for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
+      const double sw = (double)dscale[l * g.nv + g.adj_nbr[k]];
+      offv_t[l * nadj + k] = (float)(offv[l * nadj + k] * sv * sw);
+    }
   }
 }
 
@@ -69,11 +99,28 @@ int grid_for(int64_t total, int threads) {
 
 }  // namespace
 
-void launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa, double* sab,
-                  double* diag, double* offv, cudaStream_t st) {
-  edge_blocks_kernel<<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(g, nd, kappa2, saa, sab);
-  vertex_diag_kernel<<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, saa, sab, diag,
-                                                                          offv);
+template <typename T>
+int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa, double* sab,
+                 double* diag, double* offv, SweepParams<T>* prm, T* dscale, T* offv_t,
+                 cudaStream_t st) {
+  edge_blocks_kernel<T><<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(g, nd, kappa2, saa,
+                                                                            sab, prm);
+  vertex_diag_kernel<T><<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, saa, sab,
+                                                                             diag, offv, dscale);
+  if constexpr (sizeof(T) == 4) {
+    if (dscale && offv_t) {
+      scaled_offdiag_kernel<<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, offv,
+                                                                                 dscale, offv_t);
+      return 3;
+    }
+  }
+  return 2;
 }
+template int launch_schur<float>(const DevGraph&, const DevNodes&, double, double*, double*,
+                                 double*, double*, SweepParams<float>*, float*, float*,
+                                 cudaStream_t);
+template int launch_schur<double>(const DevGraph&, const DevNodes&, double, double*, double*,
+                                  double*, double*, SweepParams<double>*, double*, double*,
+                                  cudaStream_t);
 
 }  // namespace grf

@@ -95,16 +95,23 @@ __global__ void condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t 
   }
 }
 
-template <typename OutT>
+// U_v = sum_l w_l u_v^(l) in FP64; also leaves xw = w_l u_v^(l) in the sweep
+// precision for the interior recovery.
+template <typename T, typename OutT>
 __global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
-                                    OutT* __restrict__ out) {
+                                    OutT* __restrict__ out, T* __restrict__ xw) {
   const int64_t total = S * g.nv;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = t / g.nv;
     const int64_t v = t - s * g.nv;
     double acc = 0.0;
-    for (int32_t l = 0; l < nd.L; ++l) acc += nd.weight[l] * xv[((int64_t)l * S + s) * g.nv + v];
+    for (int32_t l = 0; l < nd.L; ++l) {
+      const int64_t i = ((int64_t)l * S + s) * g.nv + v;
+      const double wx = nd.weight[l] * xv[i];
+      acc += wx;
+      xw[i] = (T)wx;
+    }
     out[s * g.n + v] = (OutT)acc;
   }
 }
@@ -113,15 +120,16 @@ __global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const do
 // of w_l x^(l) in acc. yscr / rpscr hold the forward sweep for the back sweep.
 template <typename T, typename OutT>
 __global__ void recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
+                               const int32_t* __restrict__ edges, int32_t n_edges,
                                const T* __restrict__ b, const double* __restrict__ xv,
                                OutT* __restrict__ out, double* __restrict__ acc,
                                T* __restrict__ yscr, T* __restrict__ rpscr) {
   const int64_t nsg = (S + kSG - 1) / kSG;
-  const int64_t total = (int64_t)g.ne * nsg;
+  const int64_t total = (int64_t)n_edges * nsg;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t sg = t % nsg;
-    const int32_t e = (int32_t)(t / nsg);
+    const int32_t e = edges[t / nsg];
     const int32_t m = g.nel[e] - 1;
     if (m <= 0) continue;
     const int64_t off = g.ioff[e];
@@ -227,14 +235,25 @@ void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64
 }
 
 template <typename T, typename OutT>
-void launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
-                    const double* xv, OutT* out, double* acc, T* yscr, T* rpscr, cudaStream_t st) {
-  vertex_accum_kernel<OutT><<<grid_for(S * g.nv, 256), 256, 0, st>>>(g, nd, S, xv, out);
-  if (g.ni == 0) return;
-  cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)g.ni * (size_t)S, st);
-  const int64_t nsg = (S + kSG - 1) / kSG;
-  recover_kernel<T, OutT><<<grid_for((int64_t)g.ne * nsg, 128), 128, 0, st>>>(
-      g, nd, kappa2, S, b, xv, out, acc, yscr, rpscr);
+int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
+                   const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
+                   const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins, double* acc,
+                   T* yscr, T* rpscr, cudaStream_t st) {
+  vertex_accum_kernel<T, OutT><<<grid_for(S * g.nv, 256), 256, 0, st>>>(g, nd, S, xv, out, xw);
+  int launches = 1;
+  if (g.ni == 0) return launches;
+  launches += launch_recover_bins<T, OutT>(g, nd.L, S, b, prm, xw, out, bin_edges, bin_count, st);
+  int64_t skip = 0;
+  for (int i = 0; i < n_bins; ++i) skip += bin_count[i];
+  const int32_t n_long = bin_count[n_bins];  // edges longer than the largest bin
+  if (n_long > 0) {
+    cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)g.ni * (size_t)S, st);
+    const int64_t nsg = (S + kSG - 1) / kSG;
+    recover_kernel<T, OutT><<<grid_for((int64_t)n_long * nsg, 128), 128, 0, st>>>(
+        g, nd, kappa2, S, bin_edges + skip, n_long, b, xv, out, acc, yscr, rpscr);
+    launches += 1;
+  }
+  return launches;
 }
 
 template <typename T>
@@ -247,18 +266,16 @@ template void launch_condense<float>(const DevGraph&, const DevNodes&, double, i
                                      const float*, double*, cudaStream_t);
 template void launch_condense<double>(const DevGraph&, const DevNodes&, double, int64_t,
                                       const double*, double*, cudaStream_t);
-template void launch_recover<float, float>(const DevGraph&, const DevNodes&, double, int64_t,
-                                           const float*, const double*, float*, double*, float*,
-                                           float*, cudaStream_t);
-template void launch_recover<float, double>(const DevGraph&, const DevNodes&, double, int64_t,
-                                            const float*, const double*, double*, double*, float*,
-                                            float*, cudaStream_t);
-template void launch_recover<double, double>(const DevGraph&, const DevNodes&, double, int64_t,
-                                             const double*, const double*, double*, double*,
-                                             double*, double*, cudaStream_t);
-template void launch_recover<double, float>(const DevGraph&, const DevNodes&, double, int64_t,
-                                            const double*, const double*, float*, double*,
-                                            double*, double*, cudaStream_t);
+#define GRF_INST_RECOVER(T, O)                                                                 \
+  template int launch_recover<T, O>(const DevGraph&, const DevNodes&, double, int64_t, const T*, \
+                                    const double*, O*, const SweepParams<T>*, T*,                \
+                                    const int32_t*, const int32_t*, int32_t, double*, T*, T*,    \
+                                    cudaStream_t);
+GRF_INST_RECOVER(float, float)
+GRF_INST_RECOVER(float, double)
+GRF_INST_RECOVER(double, double)
+GRF_INST_RECOVER(double, float)
+#undef GRF_INST_RECOVER
 template void launch_to_minor<float>(const DevGraph&, int64_t, const double*, float*, bool,
                                      cudaStream_t);
 template void launch_to_minor<double>(const DevGraph&, int64_t, const double*, double*, bool,

@@ -174,6 +174,24 @@ def test_sample_matches_oracle(precision, name, beta):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_every_recovery_bin(precision):
+    """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
+    recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps) and the
+    sequential kernel for edges longer than the largest bin."""
+    ne = [2, 33, 65, 129, 257, 513, 1025, 2049, 4097, 5000, 3, 31]
+    E = len(ne)
+    eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 3])
+    ev = np.array([1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 5, 8])
+    lengths = np.array(ne) * 1e-3 * np.linspace(0.8, 1.2, E)
+    g = gi.Graph(10, eu, ev, lengths)
+    G, m = make(g, n_elems=ne)
+    kappa, beta, k, seed, S = 6.0, 0.6, 0.5, 21, 6
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, n_elems=ne)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("beta", [1.0, 1.25, 2.0, 2.6])
 def test_sample_integer_powers(precision, beta):
     g, h = GRAPHS["square5"]()
