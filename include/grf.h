@@ -70,8 +70,19 @@ typedef struct grf_options {
   int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
   double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */
   int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms) */
-  int32_t reserved;
+  int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
 } grf_options;
+
+/* Vertex PCG launch layouts (same results up to rounding):
+ *   PER_SYSTEM: one CTA per (node, sample) system, Schur matrix read through
+ *     the caches, vectors in shared memory when they fit;
+ *   STAGED (mixed precision, graphs whose Schur matrix fits in shared memory):
+ *     one CTA per (node, sample group) stages the node's matrix in shared
+ *     memory and solves its samples one after another;
+ *   AUTO: the library's choice. */
+#define GRF_PCG_AUTO 0
+#define GRF_PCG_PER_SYSTEM 1
+#define GRF_PCG_STAGED 2
 
 typedef struct grf_stats {
   int64_t n_dofs;          /* N = |V_kept| + sum_e (n_e - 1) */

@@ -22,6 +22,8 @@ GRF_OK, GRF_EINVAL, GRF_ENOMEM, GRF_ENOCONV, GRF_ECUDA, GRF_ENOTSUP, GRF_ENUMERI
 GRF_FP64, GRF_MIXED = 0, 1
 GRF_PRECOND_JACOBI = 0
 GRF_OUT_F64, GRF_OUT_F32 = 0, 1
+GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED = 0, 1, 2
+PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged": GRF_PCG_STAGED}
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
@@ -38,7 +40,7 @@ class grf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("out_dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pcg_layout", ctypes.c_int32)]
 
 
 class grf_stats(ctypes.Structure):
@@ -111,13 +113,13 @@ def _stream(stream):
 
 
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
-                 timing=False) -> grf_options:
+                 timing=False, pcg_layout="auto") -> grf_options:
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, GRF_PRECOND_JACOBI, od, int(max_iter), float(rtol),
-                       1 if timing else 0, 0)
+                       1 if timing else 0, PCG_LAYOUTS[pcg_layout])
 
 
 # ------------------------------------------------------------ C-named functions
@@ -254,9 +256,10 @@ class Graph:
             pass
 
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
-               rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False):
+               rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
+               pcg_layout="auto"):
         import torch
-        opts = make_options(precision, out_dtype, rtol, max_iter, timing)
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")

@@ -229,10 +229,15 @@ struct Opts {
   int precision, precond, out_dtype, max_iter;
   double rtol;
   bool timing;
+  int pcg_layout;  // 1 per system, 2 staged
 };
 
 int read_opts(const grf_options* o, Opts* r) {
   r->timing = o && o->timing != 0;
+  const int lay = o ? o->pcg_layout : GRF_PCG_AUTO;
+  if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED)
+    return fail(GRF_EINVAL, "unknown pcg_layout %d", lay);
+  r->pcg_layout = lay == GRF_PCG_AUTO ? GRF_PCG_PER_SYSTEM : lay;
   r->precision = o ? o->precision : GRF_FP64;
   r->precond = o ? o->precond : GRF_PRECOND_JACOBI;
   r->out_dtype = o ? o->out_dtype : GRF_OUT_F64;
@@ -377,7 +382,8 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
   rs->begin(st);
   launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, gvec, xv, (T*)w.d,
-                (T*)w.r, (T*)w.p, (T*)w.q, o.rtol, o.max_iter, w.iters, w.status, st);
+                (T*)w.r, (T*)w.p, (T*)w.q, o.rtol, o.max_iter, w.iters, w.status,
+                o.pcg_layout, st);
   rs->end(3, st);
   rs->launches += 3;
   CUDA_TRY(cudaGetLastError());

@@ -97,12 +97,13 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 // VT = double: FP64 Jacobi-PCG (dscale = 1 / D, offv_t = offv).
 // VT = float: FP32 Jacobi-scaled CG inside FP64 refinement (dscale = 1 / sqrt(D),
 // offv_t = scaled blocks). d, r, p, q: [L][S][nv] scratch used when a system's
-// vectors do not fit in shared memory.
+// vectors do not fit in shared memory. layout: 1 one CTA per system, 2 staged
+// matrix per (node, sample group) when it fits (mixed only), else layout 1.
 template <typename VT>
 void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
                 const VT* dscale_t, const VT* offv_t, const double* gvec, double* x, VT* d,
                 VT* r, VT* p, VT* q, double rtol, int32_t max_iter, int32_t* iters,
-                PcgStatus* status, cudaStream_t st);
+                PcgStatus* status, int layout, cudaStream_t st);
 
 int recover_sample_group();
 

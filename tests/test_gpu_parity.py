@@ -173,6 +173,19 @@ def test_sample_matches_oracle(precision, name, beta):
     assert st["n_unconverged"] == 0
 
 
+@pytest.mark.parametrize("layout", ["per_system", "staged"])
+@pytest.mark.parametrize("name", ["square5", "random12", "isolated"])
+def test_sample_pcg_layouts(layout, name):
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    kappa, beta, k, seed, S = 4.0, 0.6, 0.45, 13, 7
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     pcg_layout=layout)
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+    assert st["n_unconverged"] == 0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_sample_every_recovery_bin(precision):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
