@@ -233,7 +233,8 @@ def run_grf(args, w, graph):
 
     def step(i, timing=True):
         return G.sample(w.kappa, w.beta, w.k_step, seed0 + i, S, precision=prec,
-                        out_dtype=out_dtype, out=out, timing=timing, pcg_layout=args.pcg_layout)
+                        out_dtype=out_dtype, out=out, timing=timing, pcg_layout=args.pcg_layout,
+                        recover_sg=args.recover_sg)
 
     for i in range(args.warmup):
         step(i)
@@ -346,6 +347,7 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged"])
+    ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
     args = ap.parse_args()
     w = gi.WORKLOADS[args.workload]
     graph = w.graph()

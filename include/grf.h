@@ -71,6 +71,9 @@ typedef struct grf_options {
   double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */
   int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms) */
   int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
+  int32_t recover_sg;  /* samples per lane in the interior recovery: 0 = auto, or 1, 2, 4
+                          (FP32 sweeps; FP64 sweeps always use 2) */
+  int32_t reserved;
 } grf_options;
 
 /* Vertex PCG launch layouts (same results up to rounding):

@@ -40,7 +40,8 @@ class grf_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("out_dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
-                ("pcg_layout", ctypes.c_int32)]
+                ("pcg_layout", ctypes.c_int32), ("recover_sg", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class grf_stats(ctypes.Structure):
@@ -113,13 +114,13 @@ def _stream(stream):
 
 
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
-                 timing=False, pcg_layout="auto") -> grf_options:
+                 timing=False, pcg_layout="auto", recover_sg=0) -> grf_options:
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, GRF_PRECOND_JACOBI, od, int(max_iter), float(rtol),
-                       1 if timing else 0, PCG_LAYOUTS[pcg_layout])
+                       1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg), 0)
 
 
 # ------------------------------------------------------------ C-named functions
@@ -257,9 +258,9 @@ class Graph:
 
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
                rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
-               pcg_layout="auto"):
+               pcg_layout="auto", recover_sg=0):
         import torch
-        opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout)
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")

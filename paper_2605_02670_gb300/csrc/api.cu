@@ -230,10 +230,15 @@ struct Opts {
   double rtol;
   bool timing;
   int pcg_layout;  // 1 per system, 2 staged
+  int recover_sg;  // 1, 2 or 4
 };
 
 int read_opts(const grf_options* o, Opts* r) {
   r->timing = o && o->timing != 0;
+  const int sg = o ? o->recover_sg : 0;
+  if (sg != 0 && sg != 1 && sg != 2 && sg != 4)
+    return fail(GRF_EINVAL, "recover_sg must be 0, 1, 2 or 4 (got %d)", sg);
+  r->recover_sg = sg == 0 ? 4 : sg;
   const int lay = o ? o->pcg_layout : GRF_PCG_AUTO;
   if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED)
     return fail(GRF_EINVAL, "unknown pcg_layout %d", lay);
@@ -405,7 +410,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
                                           (const SweepParams<T>*)w.prm, (T*)w.xw,
                                           g->d_bin_edges[p], g->bin_count[p], g->n_bins[p], w.acc,
-                                          (T*)w.yscr, (T*)w.rpscr, st);
+                                          (T*)w.yscr, (T*)w.rpscr, o.recover_sg, st);
   rs->end(4, st);
   CUDA_TRY(cudaGetLastError());
   return collect(w, st, hn.L(), S, rs);

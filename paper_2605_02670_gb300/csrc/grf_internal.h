@@ -85,7 +85,7 @@ template <typename T, typename OutT>
 int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                    const T* b, const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins,
-                   double* acc, T* yscr, T* rpscr, cudaStream_t st);
+                   double* acc, T* yscr, T* rpscr, int sg, cudaStream_t st);
 // [S][n] double -> [n][S] T, each DOF j scaled by scale[j] (or 1 when scale is null
 // and mass_scale is false; by M_L,j = sqrt_ml[j]^2 when mass_scale is true)
 template <typename T>
@@ -115,9 +115,11 @@ int recover_bins(bool fp64, int32_t* B, int32_t* NW);
 // bin_edges: edge ids grouped by bin (bin_count[i] each, bins in order);
 // prm[l][e] sweep constants, xw[l][s][v] = w_l u_v^(l) in precision T.
 // Returns the number of kernels launched.
+// sg: samples per lane (FP32 sweeps: 1, 2 or 4; FP64 sweeps use 2).
 template <typename T, typename OutT>
 int launch_recover_bins(const DevGraph& g, int32_t L, int64_t S, const T* b,
                         const SweepParams<T>* prm, const T* xw, OutT* out,
-                        const int32_t* bin_edges, const int32_t* bin_count, cudaStream_t st);
+                        const int32_t* bin_edges, const int32_t* bin_count, int sg,
+                        cudaStream_t st);
 
 }  // namespace grf

@@ -449,9 +449,9 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
   const size_t smem = (sizeof(VT) == 4 ? sizeof(double) : 0) * (size_t)g.nv +
                       4 * sizeof(VT) * (size_t)g.nv;
   if (smem <= kSmemMax - 16 * 1024) {
-    if (smem > 48 * 1024)  // per device: set at every launch
-      cudaFuncSetAttribute(pcg_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem);
+    // dynamic + static may pass the 48 KB default; per device: set at every launch
+    cudaFuncSetAttribute(pcg_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     pcg_kernel<VT, true><<<blocks, kThreadsA, smem, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
                                                           gvec, x, d, r, p, q, rtol, max_iter,
                                                           iters, status);

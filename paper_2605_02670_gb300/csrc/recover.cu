@@ -4,7 +4,7 @@
 // For every node l the interior values of edge e solve
 //   T_l x = (w_l / c_l) b_I + w_l u_a e_1 + w_l u_b e_m,
 //   T_l = tridiag(-1, 2 + delta_l, -1),  c_l = gamma_l / h_e,
-// and U_I = sum_l x^(l). A unit of work is (edge, group of kSG samples). The
+// and U_I = sum_l x^(l). A unit of work is (edge, group of SG samples). The
 // unit's m interior nodes are split into contiguous segments of B nodes, one
 // per lane of NW warps, and stay in registers for all L nodes: the noise is
 // read once and the field written once.
@@ -24,14 +24,17 @@
 // recurrence the sequential sweep uses), which is contracting, so the start
 // error does not grow.
 //
-// The sum over nodes: FP32 partial sums over `group` consecutive nodes, added
-// into an FP64 accumulator held in shared memory.
+// The sum over nodes: partial sums in the sweep precision over `group`
+// consecutive nodes, added into an FP64 accumulator held in shared memory.
+//
+// SG trades registers for shared work: pivots and the scans' multipliers are
+// computed once per lane for SG samples, while fewer samples per lane leave
+// room for more resident warps. It is a launch parameter picked by measurement.
 #include "grf_internal.h"
 
 namespace grf {
 namespace {
 
-constexpr int kSG = 4;
 constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
@@ -42,24 +45,24 @@ __device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
 // Inclusive composition of affine maps y -> R + A y across the lanes of a warp.
 // forward: lane i ends with f_i o f_{i-1} o ... o f_0;
 // backward: lane i ends with f_i o f_{i+1} o ... o f_31.
-template <typename T, bool kForward>
-__device__ __forceinline__ void warp_scan(T& a, T (&r)[kSG], int lane) {
+template <typename T, int SG, bool kForward>
+__device__ __forceinline__ void warp_scan(T& a, T (&r)[SG], int lane) {
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    T ap, rp[kSG];
+    T ap, rp[SG];
     if (kForward) {
       ap = __shfl_up_sync(kFull, a, d);
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) rp[s] = __shfl_up_sync(kFull, r[s], d);
+      for (int s = 0; s < SG; ++s) rp[s] = __shfl_up_sync(kFull, r[s], d);
     } else {
       ap = __shfl_down_sync(kFull, a, d);
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) rp[s] = __shfl_down_sync(kFull, r[s], d);
+      for (int s = 0; s < SG; ++s) rp[s] = __shfl_down_sync(kFull, r[s], d);
     }
     const bool take = kForward ? (lane >= d) : (lane + d < 32);
     if (take) {
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) r[s] = fma(a, rp[s], r[s]);
+      for (int s = 0; s < SG; ++s) r[s] = fma(a, rp[s], r[s]);
       a = a * ap;
     }
   }
@@ -68,78 +71,76 @@ __device__ __forceinline__ void warp_scan(T& a, T (&r)[kSG], int lane) {
 // Carry into this lane: the value at the end of the previous lane (forward) or
 // at the start of the next lane (backward), given the lane's own map (a, r).
 // NW > 1 combines warp totals through shared memory.
-template <typename T, bool kForward, int NW>
-__device__ __forceinline__ void lane_carry(T a, const T (&r)[kSG], int lane, int wi,
-                                           T (*sh_a)[NW], T (*sh_r)[NW][kSG], T (&carry)[kSG]) {
-  T ia = a, ir[kSG];
+template <typename T, int SG, bool kForward, int NW>
+__device__ __forceinline__ void lane_carry(T a, const T (&r)[SG], int lane, int wi,
+                                           T (*sh_a)[NW], T (*sh_r)[NW][SG], T (&carry)[SG]) {
+  T ia = a, ir[SG];
 #pragma unroll
-  for (int s = 0; s < kSG; ++s) ir[s] = r[s];
-  warp_scan<T, kForward>(ia, ir, lane);
-  // exclusive: neighbour's inclusive result
-  const int src = kForward ? lane - 1 : lane + 1;
+  for (int s = 0; s < SG; ++s) ir[s] = r[s];
+  warp_scan<T, SG, kForward>(ia, ir, lane);
+  // exclusive: the neighbour's inclusive result
   const bool edge_lane = kForward ? (lane == 0) : (lane == 31);
   T ea = kForward ? __shfl_up_sync(kFull, ia, 1) : __shfl_down_sync(kFull, ia, 1);
-  T er[kSG];
+  T er[SG];
 #pragma unroll
-  for (int s = 0; s < kSG; ++s)
+  for (int s = 0; s < SG; ++s)
     er[s] = kForward ? __shfl_up_sync(kFull, ir[s], 1) : __shfl_down_sync(kFull, ir[s], 1);
-  (void)src;
   if (edge_lane) {
     ea = (T)1;
 #pragma unroll
-    for (int s = 0; s < kSG; ++s) er[s] = (T)0;
+    for (int s = 0; s < SG; ++s) er[s] = (T)0;
   }
-  T win[kSG];
+  T win[SG];
 #pragma unroll
-  for (int s = 0; s < kSG; ++s) win[s] = (T)0;
+  for (int s = 0; s < SG; ++s) win[s] = (T)0;
   if (NW > 1) {
     const int tot_lane = kForward ? 31 : 0;
     const int dir = kForward ? 0 : 1;
     if (lane == tot_lane) {
       sh_a[dir][wi] = ia;
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) sh_r[dir][wi][s] = ir[s];
+      for (int s = 0; s < SG; ++s) sh_r[dir][wi][s] = ir[s];
     }
     __syncthreads();
     if (kForward) {
       for (int j = 0; j < wi; ++j) {
 #pragma unroll
-        for (int s = 0; s < kSG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
+        for (int s = 0; s < SG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
       }
     } else {
       for (int j = NW - 1; j > wi; --j) {
 #pragma unroll
-        for (int s = 0; s < kSG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
+        for (int s = 0; s < SG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
       }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int s = 0; s < kSG; ++s) carry[s] = fma(ea, win[s], er[s]);
+  for (int s = 0; s < SG; ++s) carry[s] = fma(ea, win[s], er[s]);
 }
 
-// Dynamic shared memory per CTA: the FP64 node sums [warp][B*kSG][32], and for
-// kRbSmem the unit's noise [warp][B][32][kSG].
-template <typename T, int B, int NW, int UPC, bool kRbSmem>
+// Dynamic shared memory per CTA: the FP64 node sums [warp][B*SG][32], and for
+// kRbSmem the unit's noise [warp][B][32][SG].
+template <typename T, int B, int NW, int UPC, bool kRbSmem, int SG>
 constexpr size_t seg_smem_bytes() {
-  return (size_t)UPC * NW * B * kSG * 32 * (sizeof(double) + (kRbSmem ? sizeof(T) : 0));
+  return (size_t)UPC * NW * B * SG * 32 * (sizeof(double) + (kRbSmem ? sizeof(T) : 0));
 }
 
-template <typename T, typename OutT, int B, int NW, int UPC, bool kRbSmem>
+template <typename T, int B, int NW, int UPC, bool kRbSmem, int SG>
 __global__ void __launch_bounds__(32 * NW * UPC)
     recover_seg_kernel(DevGraph g, int32_t L, int64_t S, const int32_t* __restrict__ edges,
                        int32_t n_edges, const T* __restrict__ b,
                        const SweepParams<T>* __restrict__ prm, const T* __restrict__ xw,
-                       OutT* __restrict__ out, int group) {
+                       void* __restrict__ out, int out_f64, int group) {
   __shared__ T sh_a[2][NW];
-  __shared__ T sh_r[2][NW][kSG];
+  __shared__ T sh_r[2][NW][SG];
   extern __shared__ __align__(16) unsigned char dyn[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ul = warp / NW, wi = warp % NW;
-  double(*acc)[32] = reinterpret_cast<double(*)[32]>(dyn) + (size_t)warp * B * kSG;
-  T* rbs = reinterpret_cast<T*>(dyn + (size_t)UPC * NW * B * kSG * 32 * sizeof(double)) +
-           (size_t)warp * B * 32 * kSG;
-  const int64_t nsg = (S + kSG - 1) / kSG;
+  double(*acc)[32] = reinterpret_cast<double(*)[32]>(dyn) + (size_t)warp * B * SG;
+  T* rbs = reinterpret_cast<T*>(dyn + (size_t)UPC * NW * B * SG * 32 * sizeof(double)) +
+           (size_t)warp * B * 32 * SG;
+  const int64_t nsg = (S + SG - 1) / SG;
   const int64_t n_units = (int64_t)n_edges * nsg;
   // all warps of a CTA take the same number of trips (NW > 1 uses __syncthreads)
   const int64_t trips = (n_units + (int64_t)gridDim.x * UPC - 1) / ((int64_t)gridDim.x * UPC);
@@ -147,37 +148,37 @@ __global__ void __launch_bounds__(32 * NW * UPC)
     const int64_t unit = (trip * gridDim.x + blockIdx.x) * UPC + ul;
     const bool live = unit < n_units;
     const int32_t e = live ? edges[unit / nsg] : 0;
-    const int64_t s0 = live ? (unit % nsg) * kSG : 0;
+    const int64_t s0 = live ? (unit % nsg) * SG : 0;
     const int32_t m = live ? g.nel[e] - 1 : 0;
     const int64_t off = live ? g.ioff[e] : 0;
     const int32_t va = live ? g.eu[e] : 0, vb = live ? g.ev[e] : 0;
     const int K0 = (wi * 32 + lane) * B + 1;  // 1-based first node of this lane
-    T rb[kRbSmem ? 1 : B][kSG];
+    T rb[kRbSmem ? 1 : B][SG];
 #pragma unroll
     for (int k = 0; k < B; ++k) {
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) {
+      for (int s = 0; s < SG; ++s) {
         const bool ok = (K0 + k <= m) && (s0 + s < S);
         const T v = ok ? b[(g.nv + off + K0 + k - 1) * S + s0 + s] : (T)0;
         if (kRbSmem)
-          rbs[(k * 32 + lane) * kSG + s] = v;
+          rbs[(k * 32 + lane) * SG + s] = v;
         else
           rb[kRbSmem ? 0 : k][s] = v;
-        acc[k * kSG + s][lane] = 0.0;
+        acc[k * SG + s][lane] = 0.0;
       }
     }
-    T accf[B][kSG];
+    T accf[B][SG];
 #pragma unroll
     for (int k = 0; k < B; ++k)
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) accf[k][s] = (T)0;
+      for (int s = 0; s < SG; ++s) accf[k][s] = (T)0;
 
     for (int32_t l = 0; l < L; ++l) {
       const SweepParams<T> pr = prm[(int64_t)l * g.ne + e];
       const T dl = pr.delta, sc = pr.sc, shv = pr.sh, th = pr.theta;
-      T xa[kSG], xb[kSG];
+      T xa[SG], xb[SG];
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) {
+      for (int s = 0; s < SG; ++s) {
         const bool ok = live && (s0 + s < S);
         const int64_t base = ((int64_t)l * S + (ok ? s0 + s : 0)) * g.nv;
         xa[s] = ok ? xw[base + va] : (T)0;
@@ -202,13 +203,13 @@ __global__ void __launch_bounds__(32 * NW * UPC)
       }
       if (K0 > m) rp_prev = (T)0;
       // right-hand side and forward elimination from a zero carry
-      T y[B][kSG];
+      T y[B][SG];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
         const int K = K0 + k;
 #pragma unroll
-        for (int s = 0; s < kSG; ++s) {
-          const T bv = kRbSmem ? rbs[(k * 32 + lane) * kSG + s] : rb[kRbSmem ? 0 : k][s];
+        for (int s = 0; s < SG; ++s) {
+          const T bv = kRbSmem ? rbs[(k * 32 + lane) * SG + s] : rb[kRbSmem ? 0 : k][s];
           T r = bv * sc;
           if (K == 1) r += xa[s];
           if (K == m) r += xb[s];
@@ -218,22 +219,22 @@ __global__ void __launch_bounds__(32 * NW * UPC)
       T af = rp_prev;
 #pragma unroll
       for (int k = 0; k < B - 1; ++k) af *= rp[k];
-      T yin[kSG];
-      lane_carry<T, true, NW>(af, y[B - 1], lane, wi, sh_a, sh_r, yin);
+      T yin[SG];
+      lane_carry<T, SG, true, NW>(af, y[B - 1], lane, wi, sh_a, sh_r, yin);
       {
         T c = rp_prev;
 #pragma unroll
         for (int k = 0; k < B; ++k) {
           if (k > 0) c *= rp[k - 1];
 #pragma unroll
-          for (int s = 0; s < kSG; ++s) y[k][s] = fma(c, yin[s], y[k][s]);
+          for (int s = 0; s < SG; ++s) y[k][s] = fma(c, yin[s], y[k][s]);
         }
       }
       // back substitution from a zero carry: x_K = y_K / p_K + x_{K+1} / p_K
 #pragma unroll
       for (int k = B - 1; k >= 0; --k) {
 #pragma unroll
-        for (int s = 0; s < kSG; ++s) {
+        for (int s = 0; s < SG; ++s) {
           const T u = y[k][s] * rp[k];
           y[k][s] = (k == B - 1) ? u : fma(rp[k], y[k + 1][s], u);
         }
@@ -241,23 +242,23 @@ __global__ void __launch_bounds__(32 * NW * UPC)
       T ab = (T)1;
 #pragma unroll
       for (int k = 0; k < B; ++k) ab *= rp[k];
-      T xin[kSG];
-      lane_carry<T, false, NW>(ab, y[0], lane, wi, sh_a, sh_r, xin);
+      T xin[SG];
+      lane_carry<T, SG, false, NW>(ab, y[0], lane, wi, sh_a, sh_r, xin);
       {
         T c = (T)1;
 #pragma unroll
         for (int k = B - 1; k >= 0; --k) {
           c *= rp[k];
 #pragma unroll
-          for (int s = 0; s < kSG; ++s) accf[k][s] += fma(c, xin[s], y[k][s]);
+          for (int s = 0; s < SG; ++s) accf[k][s] += fma(c, xin[s], y[k][s]);
         }
       }
       if ((l + 1) % group == 0 || l + 1 == L) {
 #pragma unroll
         for (int k = 0; k < B; ++k)
 #pragma unroll
-          for (int s = 0; s < kSG; ++s) {
-            acc[k * kSG + s][lane] += (double)accf[k][s];
+          for (int s = 0; s < SG; ++s) {
+            acc[k * SG + s][lane] += (double)accf[k][s];
             accf[k][s] = (T)0;
           }
       }
@@ -266,9 +267,15 @@ __global__ void __launch_bounds__(32 * NW * UPC)
     for (int k = 0; k < B; ++k) {
       const int K = K0 + k;
 #pragma unroll
-      for (int s = 0; s < kSG; ++s) {
-        if (live && K <= m && s0 + s < S)
-          out[(s0 + s) * g.n + g.nv + off + K - 1] = (OutT)acc[k * kSG + s][lane];
+      for (int s = 0; s < SG; ++s) {
+        if (live && K <= m && s0 + s < S) {
+          const int64_t o = (s0 + s) * g.n + g.nv + off + K - 1;
+          const double val = acc[k * SG + s][lane];
+          if (out_f64)
+            static_cast<double*>(out)[o] = val;
+          else
+            static_cast<float*>(out)[o] = (float)val;
+        }
       }
     }
   }
@@ -280,20 +287,44 @@ int grid_for(int64_t units, int upc) {
   return blocks < 1 ? 1 : (int)blocks;
 }
 
-template <typename T, typename OutT, int B, int NW>
+template <typename T, int B, int NW, int SG>
 void launch_bin(const DevGraph& g, int32_t L, int64_t S, const int32_t* edges, int32_t n,
-                const T* b, const SweepParams<T>* prm, const T* xw, OutT* out, int group,
-                cudaStream_t st) {
+                const T* b, const SweepParams<T>* prm, const T* xw, void* out, int out_f64,
+                int group, cudaStream_t st) {
   if (n <= 0) return;
   constexpr int UPC = NW == 1 ? 4 : 1;
   constexpr bool kRbSmem = NW > 4;
-  constexpr size_t smem = seg_smem_bytes<T, B, NW, UPC, kRbSmem>();
-  auto kern = recover_seg_kernel<T, OutT, B, NW, UPC, kRbSmem>;
-  if (smem > 48 * 1024)  // the attribute is per device, so set it at every launch
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int64_t units = (int64_t)n * ((S + kSG - 1) / kSG);
+  constexpr size_t smem = seg_smem_bytes<T, B, NW, UPC, kRbSmem, SG>();
+  auto kern = recover_seg_kernel<T, B, NW, UPC, kRbSmem, SG>;
+  // dynamic + static shared memory may pass the 48 KB default; the attribute is
+  // per device, so it is set at every launch
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t units = (int64_t)n * ((S + SG - 1) / SG);
   kern<<<grid_for(units, UPC), 32 * NW * UPC, smem, st>>>(g, L, S, edges, n, b, prm, xw, out,
-                                                        group);
+                                                        out_f64, group);
+}
+
+template <typename T, int SG>
+int launch_all_bins(const DevGraph& g, int32_t L, int64_t S, const T* b,
+                    const SweepParams<T>* prm, const T* xw, void* out, int out_f64,
+                    const int32_t* bin_edges, const int32_t* bin_count, cudaStream_t st) {
+  // partial sums over 32 consecutive nodes before each FP64 addition
+  const int group = sizeof(T) == 4 ? 32 : (1 << 30);
+  const int32_t* e = bin_edges;
+  int n = 0;
+#define GRF_BIN(i, B_, NW_)                                                                \
+  launch_bin<T, B_, NW_, SG>(g, L, S, e, bin_count[i], b, prm, xw, out, out_f64, group, st); \
+  n += bin_count[i] > 0;                                                                   \
+  e += bin_count[i];
+  if constexpr (sizeof(T) == 4) {
+    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 8, 1)
+    GRF_BIN(4, 8, 2) GRF_BIN(5, 8, 4) GRF_BIN(6, 8, 8) GRF_BIN(7, 8, 16)
+  } else {
+    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 4, 2)
+    GRF_BIN(4, 4, 4) GRF_BIN(5, 4, 8) GRF_BIN(6, 4, 16)
+  }
+#undef GRF_BIN
+  return n;
 }
 
 }  // namespace
@@ -316,30 +347,24 @@ int recover_bins(bool fp64, int32_t* B_out, int32_t* NW_out) {
 template <typename T, typename OutT>
 int launch_recover_bins(const DevGraph& g, int32_t L, int64_t S, const T* b,
                         const SweepParams<T>* prm, const T* xw, OutT* out,
-                        const int32_t* bin_edges, const int32_t* bin_count, cudaStream_t st) {
-  // FP32 partial sums over 16 consecutive nodes before each FP64 addition
-  const int group = sizeof(T) == 4 ? 16 : (1 << 30);
-  const int32_t* e = bin_edges;
-  int n = 0;
-#define GRF_BIN(i, B_, NW_)                                                               \
-  launch_bin<T, OutT, B_, NW_>(g, L, S, e, bin_count[i], b, prm, xw, out, group, st); \
-  n += bin_count[i] > 0;                                                              \
-  e += bin_count[i];
+                        const int32_t* bin_edges, const int32_t* bin_count, int sg,
+                        cudaStream_t st) {
+  const int f64 = sizeof(OutT) == 8;
   if constexpr (sizeof(T) == 4) {
-    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 8, 1)
-    GRF_BIN(4, 8, 2) GRF_BIN(5, 8, 4) GRF_BIN(6, 8, 8) GRF_BIN(7, 8, 16)
+    if (sg == 1)
+      return launch_all_bins<T, 1>(g, L, S, b, prm, xw, out, f64, bin_edges, bin_count, st);
+    if (sg == 2)
+      return launch_all_bins<T, 2>(g, L, S, b, prm, xw, out, f64, bin_edges, bin_count, st);
+    return launch_all_bins<T, 4>(g, L, S, b, prm, xw, out, f64, bin_edges, bin_count, st);
   } else {
-    GRF_BIN(0, 1, 1) GRF_BIN(1, 2, 1) GRF_BIN(2, 4, 1) GRF_BIN(3, 4, 2)
-    GRF_BIN(4, 4, 4) GRF_BIN(5, 4, 8) GRF_BIN(6, 4, 16)
+    return launch_all_bins<T, 2>(g, L, S, b, prm, xw, out, f64, bin_edges, bin_count, st);
   }
-#undef GRF_BIN
-  return n;
 }
 
 #define GRF_INST(T, O)                                                                         \
   template int launch_recover_bins<T, O>(const DevGraph&, int32_t, int64_t, const T*,          \
                                          const SweepParams<T>*, const T*, O*, const int32_t*, \
-                                         const int32_t*, cudaStream_t);
+                                         const int32_t*, int, cudaStream_t);
 GRF_INST(float, float)
 GRF_INST(float, double)
 GRF_INST(double, double)

@@ -238,11 +238,12 @@ template <typename T, typename OutT>
 int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
                    const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins, double* acc,
-                   T* yscr, T* rpscr, cudaStream_t st) {
+                   T* yscr, T* rpscr, int sg, cudaStream_t st) {
   vertex_accum_kernel<T, OutT><<<grid_for(S * g.nv, 256), 256, 0, st>>>(g, nd, S, xv, out, xw);
   int launches = 1;
   if (g.ni == 0) return launches;
-  launches += launch_recover_bins<T, OutT>(g, nd.L, S, b, prm, xw, out, bin_edges, bin_count, st);
+  launches +=
+      launch_recover_bins<T, OutT>(g, nd.L, S, b, prm, xw, out, bin_edges, bin_count, sg, st);
   int64_t skip = 0;
   for (int i = 0; i < n_bins; ++i) skip += bin_count[i];
   const int32_t n_long = bin_count[n_bins];  // edges longer than the largest bin
@@ -270,7 +271,7 @@ template void launch_condense<double>(const DevGraph&, const DevNodes&, double, 
   template int launch_recover<T, O>(const DevGraph&, const DevNodes&, double, int64_t, const T*, \
                                     const double*, O*, const SweepParams<T>*, T*,                \
                                     const int32_t*, const int32_t*, int32_t, double*, T*, T*,    \
-                                    cudaStream_t);
+                                    int, cudaStream_t);
 GRF_INST_RECOVER(float, float)
 GRF_INST_RECOVER(float, double)
 GRF_INST_RECOVER(double, double)

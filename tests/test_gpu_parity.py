@@ -186,11 +186,12 @@ def test_sample_pcg_layouts(layout, name):
     assert st["n_unconverged"] == 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_sample_every_recovery_bin(precision):
+@pytest.mark.parametrize("precision,sg", [("fp64", 0), ("mixed", 1), ("mixed", 2), ("mixed", 4)])
+def test_sample_every_recovery_bin(precision, sg):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
-    recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps) and the
-    sequential kernel for edges longer than the largest bin."""
+    recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps), each
+    samples-per-lane variant, and the sequential kernel for edges longer than
+    the largest bin."""
     ne = [2, 33, 65, 129, 257, 513, 1025, 2049, 4097, 5000, 3, 31]
     E = len(ne)
     eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 3])
@@ -199,7 +200,8 @@ def test_sample_every_recovery_bin(precision):
     g = gi.Graph(10, eu, ev, lengths)
     G, m = make(g, n_elems=ne)
     kappa, beta, k, seed, S = 6.0, 0.6, 0.5, 21, 6
-    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     recover_sg=sg)
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, n_elems=ne)
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
 
