@@ -171,6 +171,8 @@ int ensure_device(grf_graph* g) {
   CUDA_TRY(cudaMemcpy(mlv, g->ml_vertex.data(), V * 8, cudaMemcpyHostToDevice));
   DevGraph& d = g->d;
   d.nv = g->nv; d.ne = g->ne; d.ni = g->ni; d.n = g->n;
+  d.max_m = 0;
+  for (int32_t e = 0; e < g->ne; ++e) d.max_m = std::max(d.max_m, g->nel[e] - 1);
   d.eu = eu; d.ev = ev; d.nel = nel; d.he = he; d.ioff = ioff;
   d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.sqrt_ml = sml;
   int64_t blocks = (g->n + 255) / 256;

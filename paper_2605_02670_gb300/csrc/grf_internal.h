@@ -12,6 +12,7 @@ struct DevGraph {
   int32_t ne;        // edges
   int64_t ni;        // interior nodes
   int64_t n;         // DOFs = nv + ni
+  int32_t max_m;     // largest interior node count of an edge
   const int32_t* eu;     // [ne] endpoint at x = 0
   const int32_t* ev;     // [ne] endpoint at x = l_e
   const int32_t* nel;    // [ne] elements n_e (>= 1)

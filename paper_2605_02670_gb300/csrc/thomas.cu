@@ -42,54 +42,81 @@ __global__ void gvec_init_kernel(DevGraph g, int32_t L, int64_t S, const T* __re
   }
 }
 
-// thread -> (e, l, sample group); lanes of one warp share e, so their b loads
-// coincide across l.
+// One CTA per (edge, group of kSG samples): the edge's noise rows are staged in
+// shared memory once ([m][kSG]) and every thread runs the two end eliminations
+// of one quadrature node from there (all threads read the same row at the same
+// step: broadcast). The pivot recurrence of a node is shared by its kSG samples.
+// The two end eliminations of one node over rows src[i * stride .. + kSG).
+// Only the first kv (<= kSG) samples of a row are read.
 template <typename T>
-__global__ void condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
-                                const T* __restrict__ b, double* __restrict__ gvec) {
-  const int64_t nsg = (S + kSG - 1) / kSG;
-  const int64_t total = (int64_t)g.ne * nd.L * nsg;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sg = t % nsg;
-    const int64_t r = t / nsg;
-    const int32_t l = (int32_t)(r % nd.L);
-    const int32_t e = (int32_t)(r / nd.L);
-    const int32_t m = g.nel[e] - 1;
-    if (m <= 0) continue;
-    const double h = g.he[e];
-    const T delta = (T)((nd.alpha[l] / nd.gamma[l] + kappa2) * h * h);
-    const T* bI = b + (g.nv + g.ioff[e]) * S;
-    const int64_t s0 = sg * kSG;
-    T yf[kSG], yr[kSG];
+__device__ __forceinline__ void end_sweeps(const T* src, int64_t stride, int32_t m, T delta,
+                                           int kv, T (&yf)[kSG], T (&yr)[kSG], T& rp_out) {
+#pragma unroll
+  for (int k = 0; k < kSG; ++k) {
+    yf[k] = k < kv ? src[k] : (T)0;
+    yr[k] = k < kv ? src[(int64_t)(m - 1) * stride + k] : (T)0;
+  }
+  T q = (T)1 + delta;
+  T rp = (T)1 / ((T)1 + q);
+  for (int32_t i = 1; i < m; ++i) {
+    const T* rowf = src + (int64_t)i * stride;
+    const T* rowr = src + (int64_t)(m - 1 - i) * stride;
 #pragma unroll
     for (int k = 0; k < kSG; ++k) {
-      const bool ok = s0 + k < S;
-      yf[k] = ok ? bI[s0 + k] : (T)0;
-      yr[k] = ok ? bI[(int64_t)(m - 1) * S + s0 + k] : (T)0;
+      if (k < kv) {
+        yf[k] = rowf[k] + rp * yf[k];
+        yr[k] = rowr[k] + rp * yr[k];
+      }
     }
-    T q = (T)1 + delta;
-    T rp = (T)1 / ((T)1 + q);
-    for (int32_t i = 1; i < m; ++i) {
-      const T* rowf = bI + (int64_t)i * S + s0;
-      const T* rowr = bI + (int64_t)(m - 1 - i) * S + s0;
+    q = delta + q * rp;
+    rp = (T)1 / ((T)1 + q);
+  }
+  rp_out = rp;
+}
+
+// Edges with more than stage_max interior nodes read their rows from global
+// memory instead of shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, double kappa2,
+                                                      int64_t S, const T* __restrict__ b,
+                                                      double* __restrict__ gvec,
+                                                      int32_t stage_max) {
+  extern __shared__ __align__(16) unsigned char cond_sm[];
+  T* sb = reinterpret_cast<T*>(cond_sm);
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  const int64_t units = (int64_t)g.ne * nsg;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int32_t e = (int32_t)(u / nsg);
+    const int64_t s0 = (u % nsg) * kSG;
+    const int32_t m = g.nel[e] - 1;
+    if (m <= 0) continue;  // uniform across the CTA
+    const bool staged = m <= stage_max;
+    const int kv = (int)(S - s0 < kSG ? S - s0 : kSG);
+    const T* bI = b + (g.nv + g.ioff[e]) * S;
+    if (staged) {
+      __syncthreads();  // the previous unit is done with sb
+      for (int32_t i = threadIdx.x; i < m * kSG; i += blockDim.x) {
+        const int32_t row = i / kSG, k = i - row * kSG;
+        sb[i] = s0 + k < S ? bI[(int64_t)row * S + s0 + k] : (T)0;
+      }
+      __syncthreads();
+    }
+    const double h = g.he[e];
+    const int32_t a = g.eu[e], bv = g.ev[e];
+    for (int32_t l = threadIdx.x; l < nd.L; l += blockDim.x) {
+      const T delta = (T)((nd.alpha[l] / nd.gamma[l] + kappa2) * h * h);
+      T yf[kSG], yr[kSG], rp;
+      if (staged)
+        end_sweeps<T>(sb, kSG, m, delta, kSG, yf, yr, rp);
+      else
+        end_sweeps<T>(bI + s0, S, m, delta, kv, yf, yr, rp);
+      double* gl = gvec + (int64_t)l * S * g.nv;
 #pragma unroll
       for (int k = 0; k < kSG; ++k) {
         if (s0 + k < S) {
-          yf[k] = rowf[k] + rp * yf[k];
-          yr[k] = rowr[k] + rp * yr[k];
+          atomicAdd(gl + (s0 + k) * g.nv + bv, (double)(yf[k] * rp));
+          atomicAdd(gl + (s0 + k) * g.nv + a, (double)(yr[k] * rp));
         }
-      }
-      q = delta + q * rp;
-      rp = (T)1 / ((T)1 + q);
-    }
-    double* gl = gvec + (int64_t)l * S * g.nv;
-    const int32_t a = g.eu[e], bv = g.ev[e];
-#pragma unroll
-    for (int k = 0; k < kSG; ++k) {
-      if (s0 + k < S) {
-        atomicAdd(gl + (s0 + k) * g.nv + bv, (double)(yf[k] * rp));
-        atomicAdd(gl + (s0 + k) * g.nv + a, (double)(yr[k] * rp));
       }
     }
   }
@@ -229,9 +256,20 @@ template <typename T>
 void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
                      double* gvec, cudaStream_t st) {
   gvec_init_kernel<T><<<grid_for((int64_t)nd.L * S * g.nv, 256), 256, 0, st>>>(g, nd.L, S, b, gvec);
+  if (g.ni == 0) return;
   const int64_t nsg = (S + kSG - 1) / kSG;
-  condense_kernel<T><<<grid_for((int64_t)g.ne * nd.L * nsg, 128), 128, 0, st>>>(g, nd, kappa2, S, b,
-                                                                               gvec);
+  // one thread per node (rounded up to whole warps, at most 256 per pass)
+  int threads = ((nd.L + 31) / 32) * 32;
+  if (threads > 256) threads = 256;
+  // stage edges up to 64 KB of rows (4096 FP32 rows of 4 samples); longer ones
+  // stream from global memory
+  const int32_t cap = (int32_t)((64 * 1024) / (kSG * sizeof(T)));
+  const int32_t stage_max = g.max_m < cap ? g.max_m : cap;
+  const size_t smem = (size_t)(stage_max > 0 ? stage_max : 1) * kSG * sizeof(T);
+  cudaFuncSetAttribute(condense_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int64_t blocks = (int64_t)g.ne * nsg;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  condense_kernel<T><<<(int)blocks, threads, smem, st>>>(g, nd, kappa2, S, b, gvec, stage_max);
 }
 
 template <typename T, typename OutT>
