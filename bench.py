@@ -231,10 +231,17 @@ def run_grf(args, w, graph):
     stream = torch.cuda.current_stream()
     seed0 = w.seed + 1000003 * rank
 
+    knobs = {"pcg_layout": args.pcg_layout, "recover_sg": args.recover_sg}
+    tune_ms = None
+    if args.autotune and args.pcg_layout == "auto" and args.recover_sg == 0:
+        # launch-schedule autotuner (setup, outside the timed region)
+        knobs, tune_ms = G.autotune(w.kappa, w.beta, w.k_step, S, precision=prec,
+                                    out_dtype=out_dtype, reps=2)
+
     def step(i, timing=True):
         return G.sample(w.kappa, w.beta, w.k_step, seed0 + i, S, precision=prec,
-                        out_dtype=out_dtype, out=out, timing=timing, pcg_layout=args.pcg_layout,
-                        recover_sg=args.recover_sg)
+                        out_dtype=out_dtype, out=out, timing=timing and not args.use_graph,
+                        use_graph=args.use_graph, **knobs)
 
     for i in range(args.warmup):
         step(i)
@@ -286,6 +293,17 @@ def run_grf(args, w, graph):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    phase_source = "timed steps"
+    if args.use_graph:
+        # graph replays carry no per-phase events: time the same kernels in
+        # direct calls (after the timed region) for the per-kernel roofline
+        phases = []
+        for i in range(3):
+            flush.zero_()
+            phases.append(G.sample(w.kappa, w.beta, w.k_step, seed0 + 20_000 + i, S,
+                                   precision=prec, out_dtype=out_dtype, out=out, timing=True,
+                                   **knobs)[1]["phase_ms"])
+        phase_source = "direct calls after the timed graph replays"
     if rank != 0:
         dist.destroy_process_group()
         return
@@ -319,10 +337,11 @@ def run_grf(args, w, graph):
         "config": {"workload": w.name, "n_dofs": G.n_dofs, "n_vertices": G.n_kept,
                    "n_edges": G.n_edges, "quadrature_nodes": L, "samples_per_gpu": S,
                    "precision": prec, "l2": "flushed between timed steps",
+                   "knobs": knobs, "autotune_ms": tune_ms, "cuda_graph": args.use_graph,
                    "parallelism": f"replicas x{world}"},
         "dof_solves_per_s": dof_solves,
         "pcg_iters_total": st["pcg_iters_total"], "pcg_iters_max": st["pcg_iters_max"],
-        "phase_ms": mean_ph,
+        "phase_ms": mean_ph, "phase_ms_source": phase_source,
         "roofline": roof,
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
@@ -348,6 +367,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--use-graph", action="store_true",
+                    help="replay the call as a captured CUDA graph (no per-phase timing)")
     args = ap.parse_args()
     w = gi.WORKLOADS[args.workload]
     graph = w.graph()

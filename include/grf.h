@@ -73,7 +73,10 @@ typedef struct grf_options {
   int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
   int32_t recover_sg;  /* samples per lane in the interior recovery: 0 = auto, or 1, 2, 4
                           (FP32 sweeps; FP64 sweeps always use 2) */
-  int32_t reserved;
+  int32_t use_graph;   /* grf_sample only: nonzero captures the call's launch sequence into a
+                          CUDA graph cached on the handle (re-captured when the parameters,
+                          options, sample count or output pointer change) and replays it;
+                          phase timing is then not reported */
 } grf_options;
 
 /* Vertex PCG launch layouts (same results up to rounding):
@@ -206,6 +209,20 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
 int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double gamma,
                              int64_t n_rhs, const double* rhs, double* g_out, double* u_out,
                              const grf_options* opts, void* stream, grf_stats* stats);
+
+/* Launch-schedule autotuner (the paper has no counterpart; it picks GPU launch
+ * knobs only and does not change the computed field beyond rounding): times
+ * grf_sample with CUDA events on `stream` for every candidate
+ * (pcg_layout in {PER_SYSTEM, STAGED where it applies} x recover_sg in {1, 2, 4}
+ * for FP32 sweeps) after one warm-up call each, `reps` timed calls each.
+ *   out: device buffer [n_samples][n_dofs] of base->out_dtype for the trials;
+ *   base: options whose precision, out_dtype, rtol and max_iter are kept (NULL:
+ *     defaults); best: receives base with the fastest knobs; best_ms: its mean
+ *     milliseconds per call (may be NULL).
+ * Synchronises `stream`. */
+int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t n_samples,
+                 void* out, const grf_options* base, void* stream, int32_t reps,
+                 grf_options* best, double* best_ms);
 
 /* Bytes of device workspace grf_sample would cache for this graph and size. */
 int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t n_samples,

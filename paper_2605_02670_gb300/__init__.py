@@ -27,7 +27,8 @@ PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged":
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
-             "grf_vertex_solve_noalloc", "grf_workspace_bytes", "grf_last_error")
+             "grf_vertex_solve_noalloc", "grf_autotune", "grf_workspace_bytes",
+             "grf_last_error")
 
 
 class GrfError(RuntimeError):
@@ -41,7 +42,11 @@ class grf_options(ctypes.Structure):
                 ("out_dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
                 ("pcg_layout", ctypes.c_int32), ("recover_sg", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32)]
+
+    def knobs(self) -> dict:
+        inv = {v: k for k, v in PCG_LAYOUTS.items()}
+        return {"pcg_layout": inv[self.pcg_layout], "recover_sg": self.recover_sg}
 
 
 class grf_stats(ctypes.Structure):
@@ -77,6 +82,7 @@ def _load() -> ctypes.CDLL:
         "grf_vertex_solve": [P, D, D, D, I64, P, P, P, P, P, P],
         "grf_vertex_solve_noalloc": [P, D, D, D, I64, P, P, P, P, P, P],
         "grf_workspace_bytes": [P, D, D, I64, P, P],
+        "grf_autotune": [P, D, D, D, I64, P, P, P, I32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -114,13 +120,14 @@ def _stream(stream):
 
 
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
-                 timing=False, pcg_layout="auto", recover_sg=0) -> grf_options:
+                 timing=False, pcg_layout="auto", recover_sg=0, use_graph=False) -> grf_options:
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, GRF_PRECOND_JACOBI, od, int(max_iter), float(rtol),
-                       1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg), 0)
+                       1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg),
+                       1 if use_graph else 0)
 
 
 # ------------------------------------------------------------ C-named functions
@@ -220,6 +227,17 @@ def grf_vertex_solve_noalloc(handle, kappa, alpha, gamma, n_rhs, rhs_ptr: int, g
     return st.as_dict()
 
 
+def grf_autotune(handle, kappa, beta, k_step, n_samples, out_ptr: int, base: grf_options,
+                 stream=None, reps=2):
+    """Fastest launch knobs for this configuration; returns (options, ms)."""
+    best = grf_options()
+    ms = ctypes.c_double()
+    _check(_lib.grf_autotune(handle, float(kappa), float(beta), float(k_step), int(n_samples),
+                             ctypes.c_void_p(out_ptr), ctypes.byref(base), _stream(stream),
+                             int(reps), ctypes.byref(best), ctypes.byref(ms)))
+    return best, ms.value
+
+
 def grf_workspace_bytes(handle, beta, k_step, n_samples, opts: grf_options) -> int:
     b = ctypes.c_size_t()
     _check(_lib.grf_workspace_bytes(handle, float(beta), float(k_step), int(n_samples),
@@ -258,9 +276,10 @@ class Graph:
 
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
                rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
-               pcg_layout="auto", recover_sg=0):
+               pcg_layout="auto", recover_sg=0, use_graph=False):
         import torch
-        opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg)
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
+                            use_graph)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
@@ -279,6 +298,17 @@ class Graph:
         stats = grf_sample_host(self.handle, kappa, beta, k_step, seed, n_samples, out, opts,
                                 stream)
         return out, stats
+
+    def autotune(self, kappa, beta, k_step, n_samples, precision="fp64", out_dtype=None,
+                 rtol=0.0, max_iter=0, reps=2, stream=None):
+        """Times the launch knobs and returns ({pcg_layout, recover_sg}, ms per call)."""
+        import torch
+        base = make_options(precision, out_dtype, rtol, max_iter)
+        dt = torch.float64 if base.out_dtype == GRF_OUT_F64 else torch.float32
+        out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
+        best, ms = grf_autotune(self.handle, kappa, beta, k_step, n_samples, out.data_ptr(), base,
+                                stream, reps)
+        return best.knobs(), ms
 
     def noise(self, seed, n_samples, raw=False, stream=None):
         import torch

@@ -93,11 +93,45 @@ struct grf_graph {
   void* ws = nullptr;
   size_t ws_bytes = 0;
 
+  // Captured launch sequence of one grf_sample configuration (options.use_graph).
+  // Device pointers (workspace, output, node arrays) are baked into the graph,
+  // so any change of them or of the configuration re-captures.
+  struct GraphCache {
+    bool valid = false;
+    int precision = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
+    double rtol = 0, kappa = 0, beta = 0, k = 0;
+    int64_t S = 0;
+    void* out = nullptr;
+    void* ws = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    double* nodes_dev = nullptr;   // per stage alpha|gamma|weight, then the seed word
+    uint64_t* d_seed = nullptr;
+    uint64_t* h_seed = nullptr;    // pinned
+    PcgStatus* h_status = nullptr; // pinned, one per stage
+    int h_status_cap = 0;
+    std::vector<int32_t> stage_L;
+    int launches = 0;
+  } gc;
+  cudaStream_t cap_stream = nullptr;
+
+  void drop_graph() {
+    if (gc.exec) cudaGraphExecDestroy(gc.exec);
+    if (gc.nodes_dev) cudaFree(gc.nodes_dev);
+    gc.exec = nullptr;
+    gc.nodes_dev = nullptr;
+    gc.d_seed = nullptr;
+    gc.valid = false;
+  }
+
   ~grf_graph() {
     if (device >= 0) {
       int cur = 0;
       cudaGetDevice(&cur);
       cudaSetDevice(device);
+      drop_graph();
+      if (gc.h_seed) cudaFreeHost(gc.h_seed);
+      if (gc.h_status) cudaFreeHost(gc.h_status);
+      if (cap_stream) cudaStreamDestroy(cap_stream);
       if (dev_block) cudaFree(dev_block);
       if (ws) cudaFree(ws);
       cudaSetDevice(cur);
@@ -187,6 +221,7 @@ int ensure_ws(grf_graph* g, size_t bytes) {
   if (g->ws && g->ws_bytes >= bytes) return GRF_OK;
   if (g->ws) {
     CUDA_TRY(cudaDeviceSynchronize());
+    g->drop_graph();  // the captured graph refers to the old workspace
     CUDA_TRY(cudaFree(g->ws));
     g->ws = nullptr;
     g->ws_bytes = 0;
@@ -233,10 +268,12 @@ struct Opts {
   bool timing;
   int pcg_layout;  // 1 per system, 2 staged
   int recover_sg;  // 1, 2 or 4
+  bool use_graph;
 };
 
 int read_opts(const grf_options* o, Opts* r) {
-  r->timing = o && o->timing != 0;
+  r->use_graph = o && o->use_graph != 0;
+  r->timing = o && o->timing != 0 && !r->use_graph;
   const int sg = o ? o->recover_sg : 0;
   if (sg != 0 && sg != 1 && sg != 2 && sg != 4)
     return fail(GRF_EINVAL, "recover_sg must be 0, 1, 2 or 4 (got %d)", sg);
@@ -306,6 +343,10 @@ struct RunStats {
   int64_t nodes = 0, systems = 0, iters_total = 0;
   int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0;
   bool timing = false;
+  // graph capture: status words are copied to pinned host slots, no syncs
+  bool capturing = false;
+  PcgStatus* h_status = nullptr;
+  int stage_idx = 0;
   struct Span {
     int phase;
     cudaEvent_t a, b;
@@ -357,7 +398,22 @@ int upload_nodes(const HostNodes& h, const ApplyWs& w, cudaStream_t st) {
   return GRF_OK;
 }
 
+void add_status(const PcgStatus& h, RunStats* rs) {
+  rs->iters_total += (int64_t)h.iters_total;
+  if (h.iters_max > rs->iters_max) rs->iters_max = h.iters_max;
+  rs->unconverged += h.n_unconverged;
+  rs->numeric += h.numeric_flag;
+}
+
 int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* rs) {
+  if (rs->capturing) {
+    CUDA_TRY(cudaMemcpyAsync(rs->h_status + rs->stage_idx, w.status, sizeof(PcgStatus),
+                             cudaMemcpyDeviceToHost, st));
+    rs->stage_idx++;
+    rs->nodes += L;
+    rs->systems += (int64_t)L * S;
+    return GRF_OK;
+  }
   PcgStatus h{};
   CUDA_TRY(cudaMemcpyAsync(&h, w.status, sizeof h, cudaMemcpyDeviceToHost, st));
   CUDA_TRY(cudaStreamSynchronize(st));
@@ -398,14 +454,22 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
 }
 
 // out = sum_l w_l A_l^{-1} b with b sample-minor [n][S] in precision T.
+// nodes_dev (optional): alpha | gamma | weight already on the device.
 template <typename T, typename OutT>
 int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T* b, OutT* out,
-             const Opts& o, cudaStream_t st, void* ws_tail, RunStats* rs) {
+             const Opts& o, cudaStream_t st, void* ws_tail, RunStats* rs,
+             const double* nodes_dev = nullptr) {
   Carve c(ws_tail);
   ApplyWs w;
   carve_apply(c, g, hn.L(), S, sizeof(T), &w);
   const double k2 = kappa * kappa;
-  GRF_TRY(upload_nodes(hn, w, st));
+  if (nodes_dev) {
+    w.alpha = const_cast<double*>(nodes_dev);
+    w.gamma = const_cast<double*>(nodes_dev) + hn.L();
+    w.weight = const_cast<double*>(nodes_dev) + 2 * hn.L();
+  } else {
+    GRF_TRY(upload_nodes(hn, w, st));
+  }
   GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
   const int p = sizeof(T) == 8 ? 1 : 0;
   rs->begin(st);
@@ -462,28 +526,36 @@ void plan(double beta, double k_step, std::vector<HostNodes>* stages) {
   }
 }
 
-template <typename T, typename OutT>
-int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed, int64_t S,
-                OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
-  std::vector<HostNodes> stages;
-  plan(beta, k_step, &stages);
-  size_t need = align_up((size_t)g->n * S * sizeof(T));
+size_t sample_ws_bytes(const grf_graph* g, const std::vector<HostNodes>& stages, int64_t S,
+                       size_t tsize) {
+  size_t need = align_up((size_t)g->n * S * tsize);
   size_t tail = 0;
-  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, sizeof(T)));
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize));
+  if (stages.size() > 1) need += align_up((size_t)g->n * S * sizeof(double));
+  return need + tail;
+}
+
+// Enqueues one whole sample call on st (workspace already sized). With
+// seed_dev / nodes_dev the seed and the node arrays come from device memory
+// (graph capture); otherwise they are passed and uploaded here.
+template <typename T, typename OutT>
+int enqueue_sample(grf_graph* g, const std::vector<HostNodes>& stages, double kappa,
+                   uint64_t seed, int64_t S, OutT* out, const Opts& o, cudaStream_t st,
+                   RunStats* rs, const uint64_t* seed_dev = nullptr,
+                   const std::vector<const double*>* nodes_dev = nullptr) {
   const bool multi = stages.size() > 1;
-  if (multi) need += align_up((size_t)g->n * S * sizeof(double));
-  GRF_TRY(ensure_ws(g, need + tail));
   Carve c(g->ws);
   T* b = c.take<T>((size_t)g->n * S);
   double* tmp = multi ? c.take<double>((size_t)g->n * S) : nullptr;
   void* ws_tail = g->ws ? (char*)g->ws + c.off : nullptr;
   rs->begin(st);
-  launch_noise_minor<T>(g->d, seed, S, b, st);
+  launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev);
   rs->end(0, st);
   rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
   for (size_t i = 0; i < stages.size(); ++i) {
     const bool last = i + 1 == stages.size();
+    const double* nd = nodes_dev ? (*nodes_dev)[i] : nullptr;
     if (i > 0) {
       rs->begin(st);
       launch_to_minor<T>(g->d, S, tmp, b, true, st);
@@ -491,11 +563,107 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
       rs->launches += 1;
     }
     if (last) {
-      GRF_TRY((dd_apply<T, OutT>(g, stages[i], kappa, S, b, out, o, st, ws_tail, rs)));
+      GRF_TRY((dd_apply<T, OutT>(g, stages[i], kappa, S, b, out, o, st, ws_tail, rs, nd)));
     } else {
-      GRF_TRY((dd_apply<T, double>(g, stages[i], kappa, S, b, tmp, o, st, ws_tail, rs)));
+      GRF_TRY((dd_apply<T, double>(g, stages[i], kappa, S, b, tmp, o, st, ws_tail, rs, nd)));
     }
   }
+  return GRF_OK;
+}
+
+template <typename T, typename OutT>
+int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed, int64_t S,
+                OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
+  std::vector<HostNodes> stages;
+  plan(beta, k_step, &stages);
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T))));
+  return enqueue_sample<T, OutT>(g, stages, kappa, seed, S, out, o, st, rs);
+}
+
+// The same call through a captured CUDA graph: captured once per configuration
+// (on an internal stream), then replayed on the caller's stream with the seed
+// copied in from pinned memory. Iteration statistics come back through pinned
+// status slots; per-phase timing is not available on this path.
+template <typename T, typename OutT>
+int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
+                      int64_t S, OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
+  std::vector<HostNodes> stages;
+  plan(beta, k_step, &stages);
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T))));
+  auto& gc = g->gc;
+  const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
+                   gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
+                   gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
+                   gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
+                   gc.ws == g->ws;
+  if (!hit) {
+    g->drop_graph();
+    size_t nd_count = 1;
+    for (auto& s : stages) nd_count += 3 * (size_t)s.L();
+    CUDA_TRY(cudaMalloc(&gc.nodes_dev, nd_count * sizeof(double)));
+    std::vector<const double*> ptrs;
+    size_t off = 0;
+    for (auto& s : stages) {
+      const size_t L = s.L();
+      CUDA_TRY(cudaMemcpy(gc.nodes_dev + off, s.alpha.data(), L * 8, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy(gc.nodes_dev + off + L, s.gamma.data(), L * 8, cudaMemcpyHostToDevice));
+      CUDA_TRY(
+          cudaMemcpy(gc.nodes_dev + off + 2 * L, s.weight.data(), L * 8, cudaMemcpyHostToDevice));
+      ptrs.push_back(gc.nodes_dev + off);
+      off += 3 * L;
+    }
+    gc.d_seed = reinterpret_cast<uint64_t*>(gc.nodes_dev + off);
+    if (!gc.h_seed) CUDA_TRY(cudaMallocHost(&gc.h_seed, sizeof(uint64_t)));
+    if (gc.h_status_cap < (int)stages.size()) {
+      if (gc.h_status) CUDA_TRY(cudaFreeHost(gc.h_status));
+      gc.h_status = nullptr;
+      CUDA_TRY(cudaMallocHost(&gc.h_status, sizeof(PcgStatus) * stages.size()));
+      gc.h_status_cap = (int)stages.size();
+    }
+    if (!g->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    RunStats cap;
+    cap.capturing = true;
+    cap.h_status = gc.h_status;
+    CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
+    const int r = enqueue_sample<T, OutT>(g, stages, kappa, 0, S, out, o, g->cap_stream, &cap,
+                                          gc.d_seed, &ptrs);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (r != GRF_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r;
+    }
+    if (ec != cudaSuccess) return fail(GRF_ECUDA, "graph capture: %s", cudaGetErrorString(ec));
+    const cudaError_t ei = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return fail(GRF_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    gc.stage_L.clear();
+    for (auto& s : stages) gc.stage_L.push_back(s.L());
+    gc.launches = cap.launches;
+    gc.precision = o.precision;
+    gc.out_dtype = o.out_dtype;
+    gc.pcg_layout = o.pcg_layout;
+    gc.recover_sg = o.recover_sg;
+    gc.max_iter = o.max_iter;
+    gc.rtol = o.rtol;
+    gc.kappa = kappa;
+    gc.beta = beta;
+    gc.k = k_step;
+    gc.S = S;
+    gc.out = (void*)out;
+    gc.ws = g->ws;
+    gc.valid = true;
+  }
+  *gc.h_seed = seed;
+  CUDA_TRY(cudaMemcpyAsync(gc.d_seed, gc.h_seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaGraphLaunch(gc.exec, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (size_t i = 0; i < gc.stage_L.size(); ++i) {
+    add_status(gc.h_status[i], rs);
+    rs->nodes += gc.stage_L[i];
+    rs->systems += (int64_t)gc.stage_L[i] * S;
+  }
+  rs->launches += gc.launches;
   return GRF_OK;
 }
 
@@ -729,17 +897,78 @@ int grf_sample(grf_graph* g, double kappa, double beta, double k_step, uint64_t 
   RunStats rs;
   rs.timing = o.timing;
   int r;
+#define GRF_RUN(T, O)                                                                      \
+  (o.use_graph ? sample_graph_impl<T, O>(g, kappa, beta, k_step, seed, n_samples, (O*)out, o, \
+                                         st, &rs)                                          \
+               : sample_impl<T, O>(g, kappa, beta, k_step, seed, n_samples, (O*)out, o, st, &rs))
   if (o.precision == GRF_FP64) {
-    r = o.out_dtype == GRF_OUT_F64
-            ? sample_impl<double, double>(g, kappa, beta, k_step, seed, n_samples, (double*)out, o, st, &rs)
-            : sample_impl<double, float>(g, kappa, beta, k_step, seed, n_samples, (float*)out, o, st, &rs);
+    r = o.out_dtype == GRF_OUT_F64 ? GRF_RUN(double, double) : GRF_RUN(double, float);
   } else {
-    r = o.out_dtype == GRF_OUT_F64
-            ? sample_impl<float, double>(g, kappa, beta, k_step, seed, n_samples, (double*)out, o, st, &rs)
-            : sample_impl<float, float>(g, kappa, beta, k_step, seed, n_samples, (float*)out, o, st, &rs);
+    r = o.out_dtype == GRF_OUT_F64 ? GRF_RUN(float, double) : GRF_RUN(float, float);
   }
+#undef GRF_RUN
   if (r != GRF_OK) return r;
   return finish(rs, g, stats);
+}
+
+int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t n_samples,
+                 void* out, const grf_options* base, void* stream, int32_t reps,
+                 grf_options* best, double* best_ms) {
+  GRF_TRY(check_graph(g));
+  GRF_TRY(check_params(kappa, beta, k_step));
+  if (!best) return fail(GRF_EINVAL, "best is null");
+  if (n_samples < 1 || !out) return fail(GRF_EINVAL, "need n_samples >= 1 and an out buffer");
+  if (reps < 1) reps = 1;
+  grf_options b0{};
+  if (base) b0 = *base;
+  b0.timing = 0;
+  b0.use_graph = 0;
+  Opts o;
+  GRF_TRY(read_opts(&b0, &o));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fp32 = o.precision == GRF_MIXED;
+  std::vector<int> layouts = {GRF_PCG_PER_SYSTEM};
+  if (fp32) layouts.push_back(GRF_PCG_STAGED);
+  std::vector<int> sgs = fp32 ? std::vector<int>{1, 2, 4} : std::vector<int>{2};
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  double best_t = 1e300;
+  grf_options best_o = b0;
+  int rc = GRF_OK;
+  for (int lay : layouts) {
+    for (int sg : sgs) {
+      grf_options c = b0;
+      c.pcg_layout = lay;
+      c.recover_sg = fp32 ? sg : 0;
+      rc = grf_sample(g, kappa, beta, k_step, 1, n_samples, out, &c, stream, nullptr);
+      if (rc != GRF_OK && rc != GRF_ENOCONV) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { rc = fail(GRF_ECUDA, "event record"); break; }
+      for (int r = 0; r < reps && (rc == GRF_OK || rc == GRF_ENOCONV); ++r)
+        rc = grf_sample(g, kappa, beta, k_step, 2 + r, n_samples, out, &c, stream, nullptr);
+      if (rc != GRF_OK && rc != GRF_ENOCONV) break;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double t = ms / reps;
+      if (t < best_t) {
+        best_t = t;
+        best_o = c;
+      }
+    }
+    if (rc != GRF_OK && rc != GRF_ENOCONV) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GRF_OK && rc != GRF_ENOCONV) return rc;
+  if (base) {
+    best_o.timing = base->timing;
+    best_o.use_graph = base->use_graph;
+  }
+  *best = best_o;
+  if (best_ms) *best_ms = best_t;
+  return GRF_OK;
 }
 
 int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,

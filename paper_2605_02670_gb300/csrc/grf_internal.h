@@ -41,9 +41,11 @@ struct PcgStatus {
 };
 
 // ---- noise.cu
-// b[j][s] (sample-minor, T = float or double) = sqrt(M_L,j) xi_{s,j}
+// b[j][s] (sample-minor, T = float or double) = sqrt(M_L,j) xi_{s,j};
+// the seed is read from seed_dev when it is not null (graph replays).
 template <typename T>
-void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st);
+void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st,
+                        const uint64_t* seed_dev = nullptr);
 // sample-major output: raw words (uint32) or b in double
 void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
                         cudaStream_t st);

@@ -55,7 +55,9 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& n0, 
 
 // thread -> (q, s) with s fastest: a warp writes whole rows b[j][s0..s0+31]
 template <typename T>
-__global__ void noise_minor_kernel(DevGraph g, uint64_t seed, int64_t S, T* __restrict__ b) {
+__global__ void noise_minor_kernel(DevGraph g, uint64_t seed, const uint64_t* seed_dev, int64_t S,
+                                   T* __restrict__ b) {
+  if (seed_dev) seed = *seed_dev;
   const int64_t nq = (g.n + 3) / 4;
   const int64_t total = nq * S;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -109,13 +111,15 @@ int grid_for(int64_t total, int threads) {
 }  // namespace
 
 template <typename T>
-void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st) {
+void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st,
+                        const uint64_t* seed_dev) {
   const int64_t total = ((g.n + 3) / 4) * S;
-  noise_minor_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(g, seed, S, b);
+  noise_minor_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(g, seed, seed_dev, S, b);
 }
-template void launch_noise_minor<float>(const DevGraph&, uint64_t, int64_t, float*, cudaStream_t);
+template void launch_noise_minor<float>(const DevGraph&, uint64_t, int64_t, float*, cudaStream_t,
+                                        const uint64_t*);
 template void launch_noise_minor<double>(const DevGraph&, uint64_t, int64_t, double*,
-                                         cudaStream_t);
+                                         cudaStream_t, const uint64_t*);
 
 void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
                         cudaStream_t st) {

@@ -243,6 +243,36 @@ def test_sample_is_deterministic_in_seed_and_sample_index():
     assert not np.allclose(c.cpu().numpy(), b.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cuda_graph_replay_matches_direct_calls(precision):
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    ml = fem.lumped_mass(m)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    out = torch.empty((5, G.n_dofs), dtype=torch.float64, device="cuda")
+    for beta, seed in [(0.6, 3), (0.6, 4), (1.3, 4), (0.6, 3)]:
+        direct, st_d = G.sample(2.5, beta, 0.45, seed, 5, precision=precision, out_dtype="f64")
+        graphed, st_g = G.sample(2.5, beta, 0.45, seed, 5, precision=precision, out_dtype="f64",
+                                 out=out, use_graph=True)
+        assert rel_l2(graphed.cpu().numpy(), direct.cpu().numpy(), ml) < tol
+        assert st_g["n_nodes"] == st_d["n_nodes"] and st_g["n_systems"] == st_d["n_systems"]
+        assert st_g["pcg_iters_total"] > 0
+        # and the replay really used this seed: matches the oracle
+        _, ref, _ = sampler.sample(g, 2.5, beta, 0.45, seed, 5, h=h)
+        assert rel_l2(graphed.cpu().numpy(), ref, ml) < TOL[precision]
+
+
+def test_autotune_returns_working_knobs():
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    knobs, ms = G.autotune(3.0, 0.7, 0.5, 8, precision="mixed")
+    assert knobs["pcg_layout"] in ("per_system", "staged") and knobs["recover_sg"] in (1, 2, 4)
+    assert ms > 0
+    u, _ = G.sample(3.0, 0.7, 0.5, 9, 8, precision="mixed", out_dtype="f64", **knobs)
+    _, ref, _ = sampler.sample(g, 3.0, 0.7, 0.5, 9, 8, h=h)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+
+
 def test_zero_samples_and_max_iter_flag():
     g, h = GRAPHS["random12"]()
     G, _ = make(g, h)
