@@ -89,6 +89,30 @@ def vertex_condensation(mesh: fem.Mesh, ml, kmat, t: float, b: np.ndarray,
     return g.T, u[:nv].T
 
 
+def edge_schur_blocks(mesh: fem.Mesh, kappa: float, t: float, alpha: float = 1.0):
+    """Per-edge 2x2 Schur blocks (Eq. local_reduced_schur) of A = alpha M_L + t K
+    by dense elimination of each edge's own element-assembled matrix: returns
+    (s_uu [E], s_uv [E]); the blocks are symmetric with s_vv = s_uu on a uniform
+    edge mesh. Small meshes only."""
+    E = mesh.edge_u.shape[0]
+    suu = np.zeros(E)
+    suv = np.zeros(E)
+    for e in range(E):
+        n, h = int(mesh.n_elems[e]), float(mesh.h_e[e])
+        a = np.zeros((n + 1, n + 1))
+        for k in range(n):
+            idx = [k, k + 1]
+            a[np.ix_(idx, idx)] += (alpha + t * kappa ** 2) * h / 2 * np.eye(2) + \
+                t / h * np.array([[1.0, -1.0], [-1.0, 1.0]])
+        bnd = [0, n]
+        inn = list(range(1, n))
+        s = a[np.ix_(bnd, bnd)]
+        if inn:
+            s = s - a[np.ix_(bnd, inn)] @ np.linalg.solve(a[np.ix_(inn, inn)], a[np.ix_(inn, bnd)])
+        suu[e], suv[e] = s[0, 0], s[0, 1]
+    return suu, suv
+
+
 def vertex_schur_dense(mesh: fem.Mesh, ml, kmat, t: float, alpha: float = 1.0):
     """S = A_GG - A_GI A_II^{-1} A_IG as a dense |V| x |V| matrix (small graphs)."""
     nv = mesh.n_vertices
