@@ -56,7 +56,9 @@ extern "C" {
 #define GRF_FP64 0        /* every step in FP64 */
 #define GRF_MIXED 1       /* FP32 edge sweeps; FP64 Schur blocks, PCG, quadrature sum */
 
-#define GRF_PRECOND_JACOBI 0
+#define GRF_PRECOND_JACOBI 0   /* z = D^-1 r */
+#define GRF_PRECOND_LEARNED 1  /* z = B B^T r on the Jacobi-scaled system, B from the network
+                                  of grf_precond_* (GRF_MIXED only; see below) */
 
 #define GRF_OUT_F64 0
 #define GRF_OUT_F32 1
@@ -65,7 +67,7 @@ typedef struct grf_graph grf_graph;
 
 typedef struct grf_options {
   int32_t precision;   /* GRF_FP64 or GRF_MIXED */
-  int32_t precond;     /* GRF_PRECOND_JACOBI */
+  int32_t precond;     /* GRF_PRECOND_JACOBI or GRF_PRECOND_LEARNED */
   int32_t out_dtype;   /* GRF_OUT_F64 or GRF_OUT_F32 */
   int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
   double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */
@@ -99,11 +101,15 @@ typedef struct grf_stats {
   int32_t n_unconverged;   /* systems that hit max_iter */
   int32_t numeric_flag;    /* nonzero: NaN/Inf or p.Sp <= 0 met */
   int32_t kernel_launches; /* kernels this call launched */
+  int32_t n_precond_fallback; /* systems whose learned preconditioner broke down
+                                 (r.z <= 0 or p.Sp <= 0) and that finished with Jacobi */
+  int32_t reserved;
   /* with grf_options.timing: device milliseconds per phase, measured with CUDA
    * events on the call's stream: [0] noise, [1] Schur blocks, [2] condensed
    * right-hand side, [3] vertex PCG, [4] recovery + quadrature sum,
-   * [5] layout/mass scaling between stages; zero otherwise */
-  double phase_ms[6];
+   * [5] layout/mass scaling between stages, [6] learned-preconditioner network,
+   * [7] unused; zero otherwise */
+  double phase_ms[8];
 } grf_stats;
 
 /* Build a metric graph and its uniform mesh (Sec. 2.1 graph; Sec. 3, Phase 1
@@ -223,6 +229,85 @@ int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double ga
 int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t n_samples,
                  void* out, const grf_options* base, void* stream, int32_t reps,
                  grf_options* best, double* best_ms);
+
+/* ---- Learned B B^T preconditioner of the vertex Schur systems (Phase 4).
+ * An extension: the paper's own vertex PCG uses a Neumann-Neumann
+ * preconditioner (Sec. 3, Phase 4, Neumann step). This one acts on the
+ * Jacobi-scaled system S_hat = D^-1/2 S D^-1/2 (unit diagonal, off-diagonal
+ * o_k = S^(e)_vw / sqrt(D_v D_w) for incidence k: vertex v, edge e, other end w;
+ * a_k = -o_k >= 0):
+ *   P = B B^T,  B = diag(exp(s)) + N,  N_{v w} = n_k on the incidence pattern,
+ * so P is symmetric positive semi-definite and linear in the residual and
+ * plain PCG stays valid. s and n come from a message-passing network whose
+ * weights are shared by all nodes and graphs:
+ *   x_v = [1, log(1+deg v)/3, sig_v, amax_v, sig_v^2, tanh(log(gamma/alpha)/20),
+ *          sig_v/deg_v, 0],  sig_v = sum_k a_k,  amax_v = max_k a_k;
+ *   h0 = relu(x W0 + b0);  h_i = relu([h_{i-1}, m_i] W_i + b_i),
+ *   m_i(v) = sum_k a_k h_{i-1}(w_k),  i = 1..3 (width 64);
+ *   s_v = h3_v . ws + cs;  n_k = a_k (h3_v . u + h3_w . up + cn).
+ * Flat FP32 parameter vector (GRF_LP_PARAMS floats): W0 [8][64], b0 [64], then
+ * W_i [128][64], b_i [64] for i = 1..3, then ws [64], cs, u [64], up [64], cn.
+ * Matrices are row-major with the input index first. The dense layers run on
+ * the tensor cores with BF16 operands and FP32 accumulation.
+ * With the four heads (ws, cs, u/up, cn) at zero, B = I: exactly Jacobi.
+ * Training loss over pairs (r, e) with S_hat e = r:
+ *   mean over pairs of (P r - e)^T S_hat (P r - e) / (r^T e).
+ * The weights live on the graph handle (device memory of its device). */
+#define GRF_LP_PARAMS 25538
+
+/* He-scaled random layers (normal, std sqrt(2 / fan_in), from `seed`) and zero
+ * heads; resets the optimiser state. */
+int grf_precond_init(grf_graph* g, uint64_t seed);
+
+/* Copy the FP32 parameters in (host [n], n == GRF_LP_PARAMS) / out. set resets
+ * the optimiser state. get fails if no weights have been set. */
+int grf_precond_set(grf_graph* g, const float* params, int64_t n);
+int grf_precond_get(const grf_graph* g, float* params, int64_t n);
+
+/* Weights file: 48-byte little-endian header ("GRFLPBB1", version 1,
+ * GRF_LP_PARAMS, 8 features, width 64, 3 layers, feature set 1, zeros) then
+ * the FP32 parameter vector. load checks every header field. */
+int grf_precond_save(const grf_graph* g, const char* path);
+int grf_precond_load(grf_graph* g, const char* path);
+
+/* Network output for one shifted system A = alpha M_L + gamma K (alpha > 0):
+ *   s_out: host float [n_kept] (s_v), n_out: host float [2 n_edges] (n_k, in
+ *   vertex-incidence order: vertices in kept order, each vertex's edges in
+ *   increasing edge id). Either may be NULL. Synchronises `stream`. */
+int grf_precond_forward(grf_graph* g, double kappa, double alpha, double gamma, float* s_out,
+                        float* n_out, void* stream);
+
+/* Training loss and its gradient for one shifted system and n_pairs given pairs:
+ *   R, E: host float [n_pairs][n_kept] (r and e with S_hat e = r, e in the
+ *   scaled unknowns); loss: host double; grad: host float [GRF_LP_PARAMS]
+ *   (either may be NULL). Does not touch the optimiser state. Synchronises. */
+int grf_precond_loss_grad(grf_graph* g, double kappa, double alpha, double gamma,
+                          int64_t n_pairs, const float* R, const float* E, double* loss,
+                          float* grad, void* stream);
+
+typedef struct grf_train_options {
+  int32_t epochs;           /* passes over the training nodes; <= 0: 40 */
+  int32_t nodes_per_batch;  /* quadrature nodes per optimiser step; <= 0: 8 */
+  int32_t n_samples;        /* white-noise right-hand sides per node; <= 0: 8 */
+  int32_t pairs_per_system; /* (r, e) records per system; <= 0: 16 */
+  int32_t record_stride;    /* CG iterations between records; <= 0: 2 */
+  int32_t max_iter;         /* CG cap of the pair generation; <= 0: 4000 */
+  double rtol;              /* CG stop of the pair generation; <= 0: 1e-10 */
+  double lr;                /* Adam step; <= 0: 1e-3 */
+  uint64_t seed;            /* noise seed and batch order */
+} grf_train_options;
+
+/* Train the network on this graph (weights must exist: init/set/load first).
+ * Pairs: for every node of the sample call (kappa, beta, k_step) -- the
+ * quadrature nodes, plus the stiffness node when beta >= 1 -- and n_samples
+ * condensed white-noise right-hand sides, plain FP64 CG on S_hat records
+ * r_i / ||r_i|| and e_i = (x* - x_i) / ||r_i|| every record_stride iterations
+ * (x* = the converged iterate). Then Adam over random batches of nodes.
+ *   loss_history: host float [epochs], mean batch loss per epoch (may be NULL);
+ *   n_pairs: host, pairs recorded (may be NULL). Synchronises `stream`. */
+int grf_precond_train(grf_graph* g, double kappa, double beta, double k_step,
+                      const grf_train_options* opts, float* loss_history, int64_t* n_pairs,
+                      void* stream);
 
 /* Bytes of device workspace grf_sample would cache for this graph and size. */
 int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t n_samples,

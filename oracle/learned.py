@@ -147,8 +147,9 @@ def s_hat_apply(inc: Incidence, a: np.ndarray, v: np.ndarray) -> np.ndarray:
 
 
 def loss_and_grad(p: dict, inc: Incidence, a: np.ndarray, x: np.ndarray, R: np.ndarray,
-                  E: np.ndarray):
-    """R, E: [P, V] pairs with S_hat e = r. Returns (loss, grads dict)."""
+                  E: np.ndarray, details: bool = False):
+    """R, E: [P, V] pairs with S_hat e = r. Returns (loss, grads dict), and with
+    details=True also the head gradients {"ds": dL/ds, "dn": dL/dn}."""
     s, n, (x, hs, ms, alpha, beta) = forward(p, inc, a, x)
     P = R.shape[0]
     ds = np.zeros_like(s)
@@ -188,6 +189,8 @@ def loss_and_grad(p: dict, inc: Incidence, a: np.ndarray, x: np.ndarray, R: np.n
     da0 = dh * (hs[0] > 0)
     g["W0"] = x.T @ da0
     g["b0"] = da0.sum(axis=0)
+    if details:
+        return loss, g, {"ds": ds, "dn": dn}
     return loss, g
 
 

@@ -20,7 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libgrf.so")
 
 GRF_OK, GRF_EINVAL, GRF_ENOMEM, GRF_ENOCONV, GRF_ECUDA, GRF_ENOTSUP, GRF_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 GRF_FP64, GRF_MIXED = 0, 1
-GRF_PRECOND_JACOBI = 0
+GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED = 0, 1
+PRECONDS = {"jacobi": GRF_PRECOND_JACOBI, "learned": GRF_PRECOND_LEARNED}
+GRF_LP_PARAMS = 25538
 GRF_OUT_F64, GRF_OUT_F32 = 0, 1
 GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED = 0, 1, 2
 PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged": GRF_PCG_STAGED}
@@ -28,7 +30,9 @@ PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged":
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
              "grf_vertex_solve_noalloc", "grf_autotune", "grf_workspace_bytes",
-             "grf_last_error")
+             "grf_precond_init", "grf_precond_set", "grf_precond_get", "grf_precond_save",
+             "grf_precond_load", "grf_precond_forward", "grf_precond_loss_grad",
+             "grf_precond_train", "grf_last_error")
 
 
 class GrfError(RuntimeError):
@@ -49,17 +53,25 @@ class grf_options(ctypes.Structure):
         return {"pcg_layout": inv[self.pcg_layout], "recover_sg": self.recover_sg}
 
 
+class grf_train_options(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("nodes_per_batch", ctypes.c_int32),
+                ("n_samples", ctypes.c_int32), ("pairs_per_system", ctypes.c_int32),
+                ("record_stride", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("rtol", ctypes.c_double), ("lr", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class grf_stats(ctypes.Structure):
     _fields_ = [("n_dofs", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
                 ("n_systems", ctypes.c_int64), ("pcg_iters_total", ctypes.c_int64),
                 ("pcg_iters_max", ctypes.c_int32), ("n_unconverged", ctypes.c_int32),
                 ("numeric_flag", ctypes.c_int32), ("kernel_launches", ctypes.c_int32),
-                ("phase_ms", ctypes.c_double * 6)]
+                ("n_precond_fallback", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("phase_ms", ctypes.c_double * 8)]
 
-    PHASES = ("noise", "schur", "condense", "pcg", "recover", "layout")
+    PHASES = ("noise", "schur", "condense", "pcg", "recover", "layout", "precond_net", "unused")
 
     def as_dict(self) -> dict:
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("phase_ms", "reserved")}
         d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
         return d
 
@@ -83,6 +95,14 @@ def _load() -> ctypes.CDLL:
         "grf_vertex_solve_noalloc": [P, D, D, D, I64, P, P, P, P, P, P],
         "grf_workspace_bytes": [P, D, D, I64, P, P],
         "grf_autotune": [P, D, D, D, I64, P, P, P, I32, P, P],
+        "grf_precond_init": [P, U64],
+        "grf_precond_set": [P, P, I64],
+        "grf_precond_get": [P, P, I64],
+        "grf_precond_save": [P, ctypes.c_char_p],
+        "grf_precond_load": [P, ctypes.c_char_p],
+        "grf_precond_forward": [P, D, D, D, P, P, P],
+        "grf_precond_loss_grad": [P, D, D, D, I64, P, P, P, P, P],
+        "grf_precond_train": [P, D, D, D, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -120,12 +140,13 @@ def _stream(stream):
 
 
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
-                 timing=False, pcg_layout="auto", recover_sg=0, use_graph=False) -> grf_options:
+                 timing=False, pcg_layout="auto", recover_sg=0, use_graph=False,
+                 precond="jacobi") -> grf_options:
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
-    return grf_options(prec, GRF_PRECOND_JACOBI, od, int(max_iter), float(rtol),
+    return grf_options(prec, PRECONDS[precond], od, int(max_iter), float(rtol),
                        1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg),
                        1 if use_graph else 0)
 
@@ -245,6 +266,61 @@ def grf_workspace_bytes(handle, beta, k_step, n_samples, opts: grf_options) -> i
     return b.value
 
 
+def grf_precond_init(handle, seed: int) -> None:
+    _check(_lib.grf_precond_init(handle, int(seed)))
+
+
+def grf_precond_set(handle, params) -> None:
+    p = np.ascontiguousarray(params, np.float32)
+    _check(_lib.grf_precond_set(handle, _ptr(p), int(p.size)))
+
+
+def grf_precond_get(handle) -> np.ndarray:
+    p = np.empty(GRF_LP_PARAMS, np.float32)
+    _check(_lib.grf_precond_get(handle, _ptr(p), int(p.size)))
+    return p
+
+
+def grf_precond_save(handle, path: str) -> None:
+    _check(_lib.grf_precond_save(handle, os.fsencode(path)))
+
+
+def grf_precond_load(handle, path: str) -> None:
+    _check(_lib.grf_precond_load(handle, os.fsencode(path)))
+
+
+def grf_precond_forward(handle, kappa, alpha, gamma, n_kept: int, n_edges: int, stream=None):
+    """Network output (s [n_kept], n [2 n_edges]) for A = alpha M_L + gamma K."""
+    s = np.empty(n_kept, np.float32)
+    n = np.empty(2 * n_edges, np.float32)
+    _check(_lib.grf_precond_forward(handle, float(kappa), float(alpha), float(gamma), _ptr(s),
+                                    _ptr(n), _stream(stream)))
+    return s, n
+
+
+def grf_precond_loss_grad(handle, kappa, alpha, gamma, R, E, stream=None):
+    """Loss and FP32 gradient over host pairs R, E [n_pairs][n_kept]."""
+    R = np.ascontiguousarray(R, np.float32)
+    E = np.ascontiguousarray(E, np.float32)
+    assert R.shape == E.shape and R.ndim == 2
+    loss = ctypes.c_double()
+    grad = np.empty(GRF_LP_PARAMS, np.float32)
+    _check(_lib.grf_precond_loss_grad(handle, float(kappa), float(alpha), float(gamma),
+                                      int(R.shape[0]), _ptr(R), _ptr(E), ctypes.byref(loss),
+                                      _ptr(grad), _stream(stream)))
+    return loss.value, grad
+
+
+def grf_precond_train(handle, kappa, beta, k_step, opts: grf_train_options, stream=None):
+    """Trains the handle's network; returns (per-epoch mean loss, pairs recorded)."""
+    hist = np.zeros(max(int(opts.epochs), 1) if opts.epochs > 0 else 40, np.float32)
+    npairs = ctypes.c_int64()
+    _check(_lib.grf_precond_train(handle, float(kappa), float(beta), float(k_step),
+                                  ctypes.byref(opts), _ptr(hist), ctypes.byref(npairs),
+                                  _stream(stream)))
+    return hist, npairs.value
+
+
 # ------------------------------------------------------------ convenience wrapper
 
 
@@ -276,10 +352,10 @@ class Graph:
 
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
                rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
-               pcg_layout="auto", recover_sg=0, use_graph=False):
+               pcg_layout="auto", recover_sg=0, use_graph=False, precond="jacobi"):
         import torch
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            use_graph)
+                            use_graph, precond)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
@@ -290,8 +366,9 @@ class Graph:
         return out, stats
 
     def sample_host(self, kappa, beta, k_step, seed, n_samples, precision="fp64",
-                    out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False):
-        opts = make_options(precision, out_dtype, rtol, max_iter, timing)
+                    out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False,
+                    precond="jacobi"):
+        opts = make_options(precision, out_dtype, rtol, max_iter, timing, precond=precond)
         dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
         if out is None:
             out = np.empty((n_samples, self.n_dofs), dtype=dt)
@@ -300,10 +377,10 @@ class Graph:
         return out, stats
 
     def autotune(self, kappa, beta, k_step, n_samples, precision="fp64", out_dtype=None,
-                 rtol=0.0, max_iter=0, reps=2, stream=None):
+                 rtol=0.0, max_iter=0, reps=2, stream=None, precond="jacobi"):
         """Times the launch knobs and returns ({pcg_layout, recover_sg}, ms per call)."""
         import torch
-        base = make_options(precision, out_dtype, rtol, max_iter)
+        base = make_options(precision, out_dtype, rtol, max_iter, precond=precond)
         dt = torch.float64 if base.out_dtype == GRF_OUT_F64 else torch.float32
         out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
         best, ms = grf_autotune(self.handle, kappa, beta, k_step, n_samples, out.data_ptr(), base,
@@ -336,9 +413,9 @@ class Graph:
         return diag, off
 
     def vertex_solve(self, kappa, alpha, gamma, rhs, precision="fp64", rtol=0.0, max_iter=0,
-                     stream=None):
+                     stream=None, precond="jacobi"):
         import torch
-        opts = make_options(precision, None, rtol, max_iter)
+        opts = make_options(precision, None, rtol, max_iter, precond=precond)
         rhs = rhs.to(dtype=torch.float64).contiguous()
         g = torch.empty((rhs.shape[0], self.n_kept), dtype=torch.float64, device="cuda")
         u = torch.empty_like(g)
@@ -346,8 +423,40 @@ class Graph:
                                  g.data_ptr(), u.data_ptr(), opts, stream)
         return g, u, stats
 
-    def workspace_bytes(self, beta, k_step, n_samples, precision="fp64") -> int:
-        return grf_workspace_bytes(self.handle, beta, k_step, n_samples, make_options(precision))
+    def workspace_bytes(self, beta, k_step, n_samples, precision="fp64", precond="jacobi") -> int:
+        return grf_workspace_bytes(self.handle, beta, k_step, n_samples,
+                                   make_options(precision, precond=precond))
+
+    # learned B B^T preconditioner of the vertex systems
+    def precond_init(self, seed=0):
+        grf_precond_init(self.handle, seed)
+
+    def precond_set(self, params):
+        grf_precond_set(self.handle, params)
+
+    def precond_get(self) -> np.ndarray:
+        return grf_precond_get(self.handle)
+
+    def precond_save(self, path):
+        grf_precond_save(self.handle, path)
+
+    def precond_load(self, path):
+        grf_precond_load(self.handle, path)
+
+    def precond_forward(self, kappa, alpha, gamma, stream=None):
+        return grf_precond_forward(self.handle, kappa, alpha, gamma, self.n_kept, self.n_edges,
+                                   stream)
+
+    def precond_loss_grad(self, kappa, alpha, gamma, R, E, stream=None):
+        return grf_precond_loss_grad(self.handle, kappa, alpha, gamma, R, E, stream)
+
+    def precond_train(self, kappa, beta, k_step, epochs=40, nodes_per_batch=8, n_samples=8,
+                      pairs_per_system=16, record_stride=2, max_iter=0, rtol=0.0, lr=1e-3,
+                      seed=0, stream=None):
+        o = grf_train_options(int(epochs), int(nodes_per_batch), int(n_samples),
+                              int(pairs_per_system), int(record_stride), int(max_iter),
+                              float(rtol), float(lr), int(seed))
+        return grf_precond_train(self.handle, kappa, beta, k_step, o, stream)
 
 
 def mesh_elements(lengths, h: float, clip=None) -> np.ndarray:

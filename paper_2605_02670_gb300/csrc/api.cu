@@ -65,6 +65,19 @@ struct Carve {
   }
 };
 
+// Learned B B^T preconditioner state kept on a graph handle: FP32 master
+// weights, their BF16 copies (layers and transposed layers), Adam moments, a
+// gradient accumulator, a node-index ramp and per-step loss slots.
+constexpr int kRamp = 1 << 16;
+struct LearnedModel {
+  void* blk = nullptr;
+  float *P = nullptr, *G = nullptr, *m = nullptr, *v = nullptr;
+  __nv_bfloat16 *wb = nullptr, *wt = nullptr;
+  int32_t* ramp = nullptr;  // 0, 1, ..., kRamp - 1
+  int step = 0;             // Adam steps taken since the weights were set
+  bool ready = false;
+};
+
 }  // namespace
 
 struct grf_graph {
@@ -74,7 +87,7 @@ struct grf_graph {
   int64_t ni = 0;
   int64_t n = 0;
   std::vector<int64_t> vertex_map;
-  std::vector<int32_t> eu, ev, nel, vptr, adj_edge, adj_nbr;
+  std::vector<int32_t> eu, ev, nel, vptr, adj_edge, adj_nbr, adj_rev;
   std::vector<double> he;
   std::vector<int64_t> ioff;
   std::vector<double> ml_vertex;  // lumped mass at kept vertices
@@ -98,7 +111,7 @@ struct grf_graph {
   // so any change of them or of the configuration re-captures.
   struct GraphCache {
     bool valid = false;
-    int precision = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
+    int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
     int64_t S = 0;
     void* out = nullptr;
@@ -113,6 +126,7 @@ struct grf_graph {
     int launches = 0;
   } gc;
   cudaStream_t cap_stream = nullptr;
+  LearnedModel lm;
 
   void drop_graph() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -134,6 +148,7 @@ struct grf_graph {
       if (cap_stream) cudaStreamDestroy(cap_stream);
       if (dev_block) cudaFree(dev_block);
       if (ws) cudaFree(ws);
+      if (lm.blk) cudaFree(lm.blk);
       cudaSetDevice(cur);
     }
   }
@@ -171,7 +186,7 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(E); c.take<int32_t>(E); c.take<int32_t>(E); c.take<double>(E);
   c.take<int64_t>(E + 1); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   c.take<double>((size_t)g->n); c.take<double>(V);
-  c.take<int32_t>(E + 1); c.take<int32_t>(E + 1);
+  c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(2 * E);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -202,13 +217,15 @@ int ensure_device(grf_graph* g) {
   CUDA_TRY(cudaMemcpy(vptr, g->vptr.data(), (V + 1) * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(ae, g->adj_edge.data(), 2 * E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(an, g->adj_nbr.data(), 2 * E * 4, cudaMemcpyHostToDevice));
+  int32_t* arev = k.take<int32_t>(2 * E);
+  CUDA_TRY(cudaMemcpy(arev, g->adj_rev.data(), 2 * E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(mlv, g->ml_vertex.data(), V * 8, cudaMemcpyHostToDevice));
   DevGraph& d = g->d;
   d.nv = g->nv; d.ne = g->ne; d.ni = g->ni; d.n = g->n;
   d.max_m = 0;
   for (int32_t e = 0; e < g->ne; ++e) d.max_m = std::max(d.max_m, g->nel[e] - 1);
   d.eu = eu; d.ev = ev; d.nel = nel; d.he = he; d.ioff = ioff;
-  d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.sqrt_ml = sml;
+  d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.adj_rev = arev; d.sqrt_ml = sml;
   int64_t blocks = (g->n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml);
@@ -289,8 +306,10 @@ int read_opts(const grf_options* o, Opts* r) {
   r->rtol = (o && o->rtol > 0) ? o->rtol : (r->precision == GRF_FP64 ? 1e-12 : 1e-9);
   if (r->precision != GRF_FP64 && r->precision != GRF_MIXED)
     return fail(GRF_EINVAL, "unknown precision %d", r->precision);
-  if (r->precond != GRF_PRECOND_JACOBI)
+  if (r->precond != GRF_PRECOND_JACOBI && r->precond != GRF_PRECOND_LEARNED)
     return fail(GRF_ENOTSUP, "preconditioner %d not available", r->precond);
+  if (r->precond == GRF_PRECOND_LEARNED && r->precision != GRF_MIXED)
+    return fail(GRF_ENOTSUP, "the learned preconditioner needs precision GRF_MIXED");
   if (r->out_dtype != GRF_OUT_F64 && r->out_dtype != GRF_OUT_F32)
     return fail(GRF_EINVAL, "unknown out_dtype %d", r->out_dtype);
   return GRF_OK;
@@ -299,7 +318,10 @@ int read_opts(const grf_options* o, Opts* r) {
 // Device workspace of one domain-decomposed apply with L nodes and S right-hand sides.
 struct ApplyWs {
   double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv, *gvec, *x, *acc;
-  void *r, *p, *q, *d;  // PCG vectors in the sweep precision T [L][S][V]
+  void *r, *p, *q, *d, *y;  // PCG vectors in the sweep precision T [L][S][V]
+  float *lp_es, *lp_n;      // learned preconditioner per node: [L][V], [L][2E]
+  LpActs lpa;               // network activations of lp_chunk nodes (es, n set per chunk)
+  int32_t lp_chunk;
   void* dscale;         // T [L][V]
   void* offv_t;         // float [L][2E] (mixed precision only)
   void *yscr, *rpscr;
@@ -309,7 +331,34 @@ struct ApplyWs {
   PcgStatus* status;
 };
 
-void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w) {
+// Nodes per network pass when the learned preconditioner runs inside a sample
+// call: about 2^20 activation rows per pass.
+int32_t lp_chunk_nodes(const grf_graph* g, int32_t L) {
+  int64_t c = ((int64_t)1 << 20) / std::max<int32_t>(g->nv, 1);
+  if (c < 1) c = 1;
+  return (int32_t)std::min<int64_t>(c, L);
+}
+
+// Inference activations of `nodes` nodes: two alternating hidden and two
+// alternating concatenated-input buffers suffice for a forward pass.
+void carve_lp_infer(Carve& c, const grf_graph* g, int32_t nodes, LpActs* a) {
+  const size_t M = (size_t)nodes * g->nv;
+  a->X0 = c.take<__nv_bfloat16>(M * 16);
+  float* h0 = c.take<float>(M * 64);
+  float* h1 = c.take<float>(M * 64);
+  __nv_bfloat16* x0 = c.take<__nv_bfloat16>(M * 128);
+  __nv_bfloat16* x1 = c.take<__nv_bfloat16>(M * 128);
+  a->H[0] = h0; a->H[1] = h1; a->H[2] = h0; a->H[3] = h1;
+  a->Xc[0] = x0; a->Xc[1] = x1; a->Xc[2] = x0;
+  a->s = c.take<float>(M);
+  a->al = c.take<float>(M);
+  a->be = c.take<float>(M);
+  a->es = nullptr;
+  a->n = nullptr;
+}
+
+void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w,
+                 bool learned = false) {
   const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
   const size_t nsg = (Ss + recover_sample_group() - 1) / recover_sample_group();
   w->alpha = c.take<double>(Ls);
@@ -325,6 +374,18 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->p = c.take<char>(Ls * Ss * V * tsize);
   w->q = c.take<char>(Ls * Ss * V * tsize);
   w->d = c.take<char>(Ls * Ss * V * tsize);
+  w->lpa = LpActs{};
+  w->lp_chunk = 0;
+  if (learned) {
+    w->y = c.take<char>(Ls * Ss * V * tsize);
+    w->lp_es = c.take<float>(Ls * V);
+    w->lp_n = c.take<float>(Ls * 2 * E);
+    w->lp_chunk = lp_chunk_nodes(g, L);
+    carve_lp_infer(c, g, w->lp_chunk, &w->lpa);
+  } else {
+    w->y = nullptr;
+    w->lp_es = w->lp_n = nullptr;
+  }
   w->dscale = c.take<char>(Ls * V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(Ls * 2 * E * 4) : nullptr;
   // scratch of the sequential recovery, only for edges longer than every bin
@@ -341,7 +402,7 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
 // Per-call statistics, kernel-launch count and (optional) CUDA-event phase timing.
 struct RunStats {
   int64_t nodes = 0, systems = 0, iters_total = 0;
-  int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0;
+  int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0, fallback = 0;
   bool timing = false;
   // graph capture: status words are copied to pinned host slots, no syncs
   bool capturing = false;
@@ -353,7 +414,7 @@ struct RunStats {
   };
   std::vector<Span> spans;
   cudaEvent_t open = nullptr;
-  double phase_ms[6] = {0, 0, 0, 0, 0, 0};
+  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
   void begin(cudaStream_t st) {
     if (!timing) return;
@@ -403,6 +464,7 @@ void add_status(const PcgStatus& h, RunStats* rs) {
   if (h.iters_max > rs->iters_max) rs->iters_max = h.iters_max;
   rs->unconverged += h.n_unconverged;
   rs->numeric += h.numeric_flag;
+  rs->fallback += h.n_fallback;
 }
 
 int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* rs) {
@@ -420,10 +482,7 @@ int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* r
   rs->settle();
   rs->nodes += L;
   rs->systems += (int64_t)L * S;
-  rs->iters_total += (int64_t)h.iters_total;
-  if (h.iters_max > rs->iters_max) rs->iters_max = h.iters_max;
-  rs->unconverged += h.n_unconverged;
-  rs->numeric += h.numeric_flag;
+  add_status(h, rs);
   return GRF_OK;
 }
 
@@ -443,9 +502,26 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
   // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
   const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
+  const bool learned = sizeof(T) == 4 && o.precond == GRF_PRECOND_LEARNED;
+  if (learned) {
+    if (!g->lm.ready || !w.lp_es || w.lp_chunk < 1 || L > kRamp)
+      return fail(GRF_EINVAL, "learned preconditioner not set up for this call");
+    rs->begin(st);
+    const int64_t ne2 = 2 * (int64_t)g->ne;
+    for (int32_t l0 = 0; l0 < L; l0 += w.lp_chunk) {
+      LpActs a = w.lpa;
+      a.es = w.lp_es + (int64_t)l0 * g->nv;
+      a.n = w.lp_n + (int64_t)l0 * ne2;
+      const int32_t nb = std::min(w.lp_chunk, L - l0);
+      rs->launches += lp_forward(g->d, nb, g->lm.ramp + l0, (const float*)w.offv_t, w.alpha,
+                                 w.gamma, g->lm.P, g->lm.wb, a, st);
+    }
+    rs->end(6, st);
+  }
   rs->begin(st);
-  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, gvec, xv, (T*)w.d,
-                (T*)w.r, (T*)w.p, (T*)w.q, o.rtol, o.max_iter, w.iters, w.status,
+  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t,
+                learned ? w.lp_es : nullptr, learned ? w.lp_n : nullptr, gvec, xv, (T*)w.d,
+                (T*)w.r, (T*)w.p, (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status,
                 o.pcg_layout, st);
   rs->end(3, st);
   rs->launches += 3;
@@ -461,7 +537,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
              const double* nodes_dev = nullptr) {
   Carve c(ws_tail);
   ApplyWs w;
-  carve_apply(c, g, hn.L(), S, sizeof(T), &w);
+  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond == GRF_PRECOND_LEARNED);
   const double k2 = kappa * kappa;
   if (nodes_dev) {
     w.alpha = const_cast<double*>(nodes_dev);
@@ -482,10 +558,10 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   return collect(w, st, hn.L(), S, rs);
 }
 
-size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize) {
+size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize, bool learned = false) {
   Carve c(nullptr);
   ApplyWs w;
-  carve_apply(c, g, L, S, tsize, &w);
+  carve_apply(c, g, L, S, tsize, &w, learned);
   return c.off;
 }
 
@@ -499,7 +575,9 @@ int finish(const RunStats& rs, grf_graph* g, grf_stats* stats) {
     stats->n_unconverged = rs.unconverged;
     stats->numeric_flag = rs.numeric;
     stats->kernel_launches = rs.launches;
-    for (int i = 0; i < 6; ++i) stats->phase_ms[i] = rs.phase_ms[i];
+    stats->n_precond_fallback = rs.fallback;
+    stats->reserved = 0;
+    for (int i = 0; i < 8; ++i) stats->phase_ms[i] = rs.phase_ms[i];
   }
   if (rs.numeric) return fail(GRF_ENUMERIC, "NaN/Inf or non-positive p.Sp in %d PCG systems", rs.numeric);
   if (rs.unconverged)
@@ -527,10 +605,10 @@ void plan(double beta, double k_step, std::vector<HostNodes>* stages) {
 }
 
 size_t sample_ws_bytes(const grf_graph* g, const std::vector<HostNodes>& stages, int64_t S,
-                       size_t tsize) {
+                       size_t tsize, bool learned) {
   size_t need = align_up((size_t)g->n * S * tsize);
   size_t tail = 0;
-  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize));
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize, learned));
   if (stages.size() > 1) need += align_up((size_t)g->n * S * sizeof(double));
   return need + tail;
 }
@@ -576,7 +654,8 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
                 OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
-  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T))));
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T),
+                                       o.precond == GRF_PRECOND_LEARNED)));
   return enqueue_sample<T, OutT>(g, stages, kappa, seed, S, out, o, st, rs);
 }
 
@@ -589,9 +668,11 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
                       int64_t S, OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
-  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T))));
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T),
+                                       o.precond == GRF_PRECOND_LEARNED)));
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
+                   gc.precond == o.precond &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
                    gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
@@ -641,6 +722,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     for (auto& s : stages) gc.stage_L.push_back(s.L());
     gc.launches = cap.launches;
     gc.precision = o.precision;
+    gc.precond = o.precond;
     gc.out_dtype = o.out_dtype;
     gc.pcg_layout = o.pcg_layout;
     gc.recover_sg = o.recover_sg;
@@ -719,6 +801,8 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->p = c.take<char>(Ss * V * tsize);
   w->q = c.take<char>(Ss * V * tsize);
   w->d = c.take<char>(Ss * V * tsize);
+  w->y = nullptr;
+  w->lp_es = w->lp_n = nullptr;
   w->dscale = c.take<char>(V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(2 * E * 4) : nullptr;
   w->iters = c.take<int32_t>(Ss);
@@ -728,11 +812,458 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->prm = w->xw = nullptr;
 }
 
+// ---- learned preconditioner: model storage, initialisation and helpers
+
+int ensure_model(grf_graph* g) {
+  GRF_TRY(ensure_device(g));
+  LearnedModel& lm = g->lm;
+  if (lm.blk) return GRF_OK;
+  Carve dry(nullptr);
+  for (int i = 0; i < 4; ++i) dry.take<float>(kParams);
+  dry.take<__nv_bfloat16>(kWbf16);
+  dry.take<__nv_bfloat16>(kWtbf16);
+  dry.take<int32_t>(kRamp);
+  void* blk = nullptr;
+  CUDA_TRY(cudaMalloc(&blk, dry.off));
+  lm.blk = blk;
+  Carve c(blk);
+  lm.P = c.take<float>(kParams);
+  lm.G = c.take<float>(kParams);
+  lm.m = c.take<float>(kParams);
+  lm.v = c.take<float>(kParams);
+  lm.wb = c.take<__nv_bfloat16>(kWbf16);
+  lm.wt = c.take<__nv_bfloat16>(kWtbf16);
+  lm.ramp = c.take<int32_t>(kRamp);
+  CUDA_TRY(cudaMemset(blk, 0, dry.off));
+  std::vector<int32_t> ramp(kRamp);
+  for (int i = 0; i < kRamp; ++i) ramp[i] = i;
+  CUDA_TRY(cudaMemcpy(lm.ramp, ramp.data(), sizeof(int32_t) * kRamp, cudaMemcpyHostToDevice));
+  return GRF_OK;
+}
+
+// New FP32 weights: BF16 copies refreshed, optimiser state cleared.
+int model_set(grf_graph* g, const float* host) {
+  GRF_TRY(ensure_model(g));
+  LearnedModel& lm = g->lm;
+  CUDA_TRY(cudaMemcpy(lm.P, host, sizeof(float) * kParams, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemset(lm.G, 0, sizeof(float) * kParams));
+  CUDA_TRY(cudaMemset(lm.m, 0, sizeof(float) * kParams));
+  CUDA_TRY(cudaMemset(lm.v, 0, sizeof(float) * kParams));
+  lp_weights_bf16(lm.P, lm.wb, lm.wt, nullptr);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  lm.step = 0;
+  lm.ready = true;
+  return GRF_OK;
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) and Box-Muller normals for the host-side
+// weight initialisation.
+uint64_t splitmix64(uint64_t* s) {
+  uint64_t z = (*s += 0x9e3779b97f4a7c15ULL);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+double host_normal(uint64_t* s) {
+  const double u1 = ((double)(splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((double)(splitmix64(s) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+bool params_finite(const float* p) {
+  for (int i = 0; i < kParams; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// Full activations and gradients of a training pass over `nodes` nodes.
+void carve_lp_train(Carve& c, const grf_graph* g, int32_t nodes, int pair_ctas, LpActs* a,
+                    LpGrads* b) {
+  const size_t M = (size_t)nodes * g->nv, ne2 = 2 * (size_t)g->ne;
+  a->X0 = c.take<__nv_bfloat16>(M * 16);
+  for (int i = 0; i <= kLayers; ++i) a->H[i] = c.take<float>(M * 64);
+  for (int i = 0; i < kLayers; ++i) a->Xc[i] = c.take<__nv_bfloat16>(M * 128);
+  a->s = c.take<float>(M);
+  a->es = c.take<float>(M);
+  a->al = c.take<float>(M);
+  a->be = c.take<float>(M);
+  a->n = c.take<float>((size_t)nodes * ne2);
+  b->ds = c.take<float>(M);
+  b->dn = c.take<float>((size_t)nodes * ne2);
+  b->dH = c.take<float>(M * 64);
+  b->dX = c.take<float>(M * 128);
+  b->dA = c.take<__nv_bfloat16>(M * 64);
+  b->max_pair_ctas = pair_ctas;
+  b->scratch = c.take<float>((size_t)pair_ctas * 4 * g->nv);
+}
+
+// Per-node Schur data of a training or test pass (mixed-precision form).
+struct LpNodes {
+  double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv;
+  float *dscale, *offv_t;
+};
+void carve_lp_nodes(Carve& c, const grf_graph* g, int32_t L, LpNodes* n) {
+  const size_t Ls = L, E = g->ne, V = g->nv;
+  n->alpha = c.take<double>(Ls);
+  n->gamma = c.take<double>(Ls);
+  n->weight = c.take<double>(Ls);
+  n->saa = c.take<double>(Ls * E);
+  n->sab = c.take<double>(Ls * E);
+  n->diag = c.take<double>(Ls * V);
+  n->offv = c.take<double>(Ls * 2 * E);
+  n->dscale = c.take<float>(Ls * V);
+  n->offv_t = c.take<float>(Ls * 2 * E);
+}
+int lp_node_setup(grf_graph* g, const HostNodes& hn, double kappa, const LpNodes& n,
+                  cudaStream_t st) {
+  const size_t b = sizeof(double) * hn.alpha.size();
+  CUDA_TRY(cudaMemcpyAsync(n.alpha, hn.alpha.data(), b, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(n.gamma, hn.gamma.data(), b, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(n.weight, hn.weight.data(), b, cudaMemcpyHostToDevice, st));
+  DevNodes nd{hn.L(), n.alpha, n.gamma, n.weight};
+  launch_schur<float>(g->d, nd, kappa * kappa, n.saa, n.sab, n.diag, n.offv, nullptr, n.dscale,
+                      n.offv_t, st);
+  CUDA_TRY(cudaGetLastError());
+  return GRF_OK;
+}
+
+struct DeviceBlock {
+  void* p = nullptr;
+  ~DeviceBlock() {
+    if (p) cudaFree(p);
+  }
+};
+
+// Forward (and, with pairs, loss and gradient) of the network for one node.
+int lp_single(grf_graph* g, double kappa, double alpha, double gamma, int64_t n_pairs,
+              const float* R, const float* E, float* s_out, float* n_out, double* loss,
+              float* grad, cudaStream_t st) {
+  GRF_TRY(check_graph(g));
+  if (!(kappa > 0) || !(alpha > 0) || !(gamma > 0) || !std::isfinite(alpha) ||
+      !std::isfinite(gamma))
+    return fail(GRF_EINVAL, "need kappa > 0, alpha > 0, gamma > 0");
+  if (n_pairs < 0 || (n_pairs > 0 && (!R || !E))) return fail(GRF_EINVAL, "bad pairs");
+  if (!g->lm.ready) return fail(GRF_EINVAL, "no preconditioner weights on this graph");
+  GRF_TRY(ensure_device(g));
+  const int pair_ctas = (int)std::max<int64_t>(1, std::min<int64_t>(n_pairs, 1024));
+  const size_t V = g->nv, ne2 = 2 * (size_t)g->ne;
+  HostNodes hn;
+  hn.alpha = {alpha};
+  hn.gamma = {gamma};
+  hn.weight = {1.0};
+  LpNodes nn;
+  LpActs a;
+  LpGrads b;
+  float *dR = nullptr, *dE = nullptr, *G = nullptr, *dloss = nullptr;
+  int32_t* pj = nullptr;
+  DeviceBlock blk;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carve c(pass ? blk.p : nullptr);
+    carve_lp_nodes(c, g, 1, &nn);
+    carve_lp_train(c, g, 1, pair_ctas, &a, &b);
+    dR = c.take<float>((size_t)n_pairs * V);
+    dE = c.take<float>((size_t)n_pairs * V);
+    pj = c.take<int32_t>((size_t)n_pairs);
+    G = c.take<float>(kParams);
+    dloss = c.take<float>(1);
+    if (!pass) CUDA_TRY(cudaMalloc(&blk.p, c.off));
+  }
+  GRF_TRY(lp_node_setup(g, hn, kappa, nn, st));
+  lp_forward(g->d, 1, g->lm.ramp, nn.offv_t, nn.alpha, nn.gamma, g->lm.P, g->lm.wb, a, st);
+  CUDA_TRY(cudaGetLastError());
+  if (n_pairs > 0) {
+    CUDA_TRY(cudaMemcpyAsync(dR, R, sizeof(float) * n_pairs * V, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(dE, E, sizeof(float) * n_pairs * V, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(pj, 0, sizeof(int32_t) * n_pairs, st));
+    CUDA_TRY(cudaMemsetAsync(G, 0, sizeof(float) * kParams, st));
+    CUDA_TRY(cudaMemsetAsync(dloss, 0, sizeof(float), st));
+    lp_backward(g->d, 1, g->lm.ramp, nn.offv_t, g->lm.P, g->lm.wt, a, n_pairs, pj, nullptr, dR,
+                dE, (float)(1.0 / (double)n_pairs), b, G, dloss, st);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (s_out) CUDA_TRY(cudaMemcpyAsync(s_out, a.s, sizeof(float) * V, cudaMemcpyDeviceToHost, st));
+  if (n_out)
+    CUDA_TRY(cudaMemcpyAsync(n_out, a.n, sizeof(float) * ne2, cudaMemcpyDeviceToHost, st));
+  float hl = 0.f;
+  if (n_pairs > 0) {
+    if (grad) CUDA_TRY(cudaMemcpyAsync(grad, G, sizeof(float) * kParams, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&hl, dloss, sizeof(float), cudaMemcpyDeviceToHost, st));
+  } else if (grad) {
+    std::memset(grad, 0, sizeof(float) * kParams);
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (loss) *loss = hl;
+  return GRF_OK;
+}
+
+struct LpFileHeader {
+  char magic[8];
+  int32_t version, n_params, n_features, width, layers, feature_set;
+  int32_t reserved[4];
+};
+static_assert(sizeof(LpFileHeader) == 48, "weights file header is 48 bytes");
+
 }  // namespace
 
 extern "C" {
 
 const char* grf_last_error(void) { return g_last_error.c_str(); }
+
+int grf_precond_init(grf_graph* g, uint64_t seed) {
+  GRF_TRY(check_graph(g));
+  std::vector<float> p(kParams, 0.f);
+  uint64_t st = seed ^ 0x6c8e9cf570932bd5ULL;
+  for (int i = 0; i < kFeat * 64; ++i)
+    p[kOffW0 + i] = (float)(host_normal(&st) * std::sqrt(2.0 / kFeat));
+  for (int l = 1; l <= kLayers; ++l)
+    for (int i = 0; i < 128 * 64; ++i)
+      p[layer_w_off(l) + i] = (float)(host_normal(&st) * std::sqrt(2.0 / 128));
+  return model_set(g, p.data());
+}
+
+int grf_precond_set(grf_graph* g, const float* params, int64_t n) {
+  GRF_TRY(check_graph(g));
+  if (!params || n != kParams)
+    return fail(GRF_EINVAL, "need %d parameters (got %lld)", kParams, (long long)n);
+  if (!params_finite(params)) return fail(GRF_EINVAL, "non-finite parameter");
+  return model_set(g, params);
+}
+
+int grf_precond_get(const grf_graph* g, float* params, int64_t n) {
+  GRF_TRY(check_graph(g));
+  if (!params || n != kParams)
+    return fail(GRF_EINVAL, "need room for %d parameters (got %lld)", kParams, (long long)n);
+  if (!g->lm.ready) return fail(GRF_EINVAL, "no preconditioner weights on this graph");
+  int cur = 0;
+  CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != g->device) return fail(GRF_EINVAL, "graph lives on device %d", g->device);
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(params, g->lm.P, sizeof(float) * kParams, cudaMemcpyDeviceToHost));
+  return GRF_OK;
+}
+
+int grf_precond_save(const grf_graph* g, const char* path) {
+  if (!path) return fail(GRF_EINVAL, "null path");
+  std::vector<float> p(kParams);
+  GRF_TRY(grf_precond_get(g, p.data(), kParams));
+  LpFileHeader h{};
+  std::memcpy(h.magic, "GRFLPBB1", 8);
+  h.version = 1;
+  h.n_params = kParams;
+  h.n_features = kFeat;
+  h.width = 64;
+  h.layers = kLayers;
+  h.feature_set = 1;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(GRF_EINVAL, "cannot open %s for writing", path);
+  const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+                  std::fwrite(p.data(), sizeof(float), kParams, f) == (size_t)kParams;
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed) return fail(GRF_EINVAL, "write to %s failed", path);
+  return GRF_OK;
+}
+
+int grf_precond_load(grf_graph* g, const char* path) {
+  GRF_TRY(check_graph(g));
+  if (!path) return fail(GRF_EINVAL, "null path");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(GRF_EINVAL, "cannot open %s", path);
+  LpFileHeader h{};
+  std::vector<float> p(kParams);
+  const bool ok = std::fread(&h, sizeof h, 1, f) == 1 &&
+                  std::fread(p.data(), sizeof(float), kParams, f) == (size_t)kParams;
+  char extra;
+  const bool at_end = std::fread(&extra, 1, 1, f) == 0;
+  std::fclose(f);
+  if (!ok) return fail(GRF_EINVAL, "%s is too short for a weights file", path);
+  if (std::memcmp(h.magic, "GRFLPBB1", 8) != 0 || h.version != 1 || h.n_params != kParams ||
+      h.n_features != kFeat || h.width != 64 || h.layers != kLayers || h.feature_set != 1 ||
+      h.reserved[0] || h.reserved[1] || h.reserved[2] || h.reserved[3] || !at_end)
+    return fail(GRF_EINVAL, "%s is not a version-1 weights file of this network", path);
+  if (!params_finite(p.data())) return fail(GRF_EINVAL, "%s holds non-finite weights", path);
+  return model_set(g, p.data());
+}
+
+int grf_precond_forward(grf_graph* g, double kappa, double alpha, double gamma, float* s_out,
+                        float* n_out, void* stream) {
+  return lp_single(g, kappa, alpha, gamma, 0, nullptr, nullptr, s_out, n_out, nullptr, nullptr,
+                   (cudaStream_t)stream);
+}
+
+int grf_precond_loss_grad(grf_graph* g, double kappa, double alpha, double gamma,
+                          int64_t n_pairs, const float* R, const float* E, double* loss,
+                          float* grad, void* stream) {
+  if (n_pairs < 1) return fail(GRF_EINVAL, "need n_pairs >= 1");
+  return lp_single(g, kappa, alpha, gamma, n_pairs, R, E, nullptr, nullptr, loss, grad,
+                   (cudaStream_t)stream);
+}
+
+int grf_precond_train(grf_graph* g, double kappa, double beta, double k_step,
+                      const grf_train_options* opts, float* loss_history, int64_t* n_pairs,
+                      void* stream) {
+  GRF_TRY(check_graph(g));
+  GRF_TRY(check_params(kappa, beta, k_step));
+  if (!g->lm.ready) return fail(GRF_EINVAL, "initialise or load the weights before training");
+  grf_train_options o{};
+  if (opts) o = *opts;
+  const int epochs = o.epochs > 0 ? o.epochs : 40;
+  const int nb = o.nodes_per_batch > 0 ? o.nodes_per_batch : 8;
+  const int St = o.n_samples > 0 ? o.n_samples : 8;
+  const int per = o.pairs_per_system > 0 ? o.pairs_per_system : 16;
+  const int stride = o.record_stride > 0 ? o.record_stride : 2;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : 4000;
+  const double rtol = o.rtol > 0 ? o.rtol : 1e-10;
+  const float lr = (float)(o.lr > 0 ? o.lr : 1e-3);
+  if (epochs > 100000 || St > 4096 || per > 4096 || nb > 4096)
+    return fail(GRF_EINVAL, "training options out of range");
+  GRF_TRY(ensure_device(g));
+  cudaStream_t st = (cudaStream_t)stream;
+  // training nodes: those of the sample call, each (alpha, gamma) once
+  std::vector<HostNodes> stages;
+  plan(beta, k_step, &stages);
+  HostNodes hn;
+  for (auto& sg : stages)
+    for (int32_t i = 0; i < sg.L(); ++i) {
+      bool seen = false;
+      for (int32_t j = 0; j < hn.L(); ++j)
+        seen = seen || (hn.alpha[j] == sg.alpha[i] && hn.gamma[j] == sg.gamma[i]);
+      if (!seen) {
+        hn.alpha.push_back(sg.alpha[i]);
+        hn.gamma.push_back(sg.gamma[i]);
+        hn.weight.push_back(1.0);
+      }
+    }
+  const int32_t L = hn.L();
+  if (L > kRamp) return fail(GRF_ENOTSUP, "too many quadrature nodes (%d)", L);
+  const int32_t Lb = std::min<int32_t>(nb, L);
+  const size_t V = g->nv, nsys = (size_t)L * St, nrec = nsys * per;
+  const int rec_ctas = (int)std::min<size_t>(nsys, 304);
+  // batches: every epoch a random order of the nodes, cut into groups of Lb
+  std::vector<int32_t> order(L);
+  uint64_t rs = o.seed ^ 0x243f6a8885a308d3ULL;
+  struct Step {
+    int64_t lnode_off, pair_off, npairs;
+    int32_t nodes, epoch;
+  };
+  std::vector<Step> steps;
+  std::vector<int32_t> lnode_all;
+  const int pair_ctas = 1024;
+  // phase 1: pairs
+  LpNodes nn;
+  float *b = nullptr, *R = nullptr, *E = nullptr;
+  double *gvec = nullptr, *work = nullptr, *xrec = nullptr, *rinv = nullptr;
+  int32_t* count = nullptr;
+  DeviceBlock data;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carve c(pass ? data.p : nullptr);
+    carve_lp_nodes(c, g, L, &nn);
+    b = c.take<float>((size_t)g->n * St);
+    gvec = c.take<double>(nsys * V);
+    work = c.take<double>((size_t)rec_ctas * 4 * V);
+    xrec = c.take<double>((size_t)rec_ctas * per * V);
+    R = c.take<float>(nrec * V);
+    E = c.take<float>(nrec * V);
+    rinv = c.take<double>(nrec);
+    count = c.take<int32_t>(nsys);
+    if (!pass) CUDA_TRY(cudaMalloc(&data.p, c.off));
+  }
+  GRF_TRY(lp_node_setup(g, hn, kappa, nn, st));
+  DevNodes nd{L, nn.alpha, nn.gamma, nn.weight};
+  launch_noise_minor<float>(g->d, o.seed, St, b, st);
+  launch_condense<float>(g->d, nd, kappa * kappa, St, b, gvec, st);
+  lp_record_pairs(g->d, (int64_t)nsys, St, nn.diag, nn.offv, gvec, work, xrec, R, E, rinv, count,
+                  per, stride, rtol, max_iter, rec_ctas, st);
+  CUDA_TRY(cudaGetLastError());
+  std::vector<int32_t> cnt(nsys);
+  CUDA_TRY(cudaMemcpyAsync(cnt.data(), count, sizeof(int32_t) * nsys, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  // pair lists per node: slot = (l * St + s) * per + i
+  std::vector<std::vector<int64_t>> node_slots(L);
+  int64_t total_pairs = 0;
+  for (int32_t l = 0; l < L; ++l)
+    for (int s = 0; s < St; ++s) {
+      const size_t sys = (size_t)l * St + s;
+      for (int i = 0; i < cnt[sys] && i < per; ++i) node_slots[l].push_back((int64_t)sys * per + i);
+      total_pairs += std::min(cnt[sys], per);
+    }
+  if (n_pairs) *n_pairs = total_pairs;
+  std::vector<int32_t> pj_all;
+  std::vector<int64_t> slot_all;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int32_t i = 0; i < L; ++i) order[i] = i;
+    for (int32_t i = L - 1; i > 0; --i) {
+      const int32_t j = (int32_t)(splitmix64(&rs) % (uint64_t)(i + 1));
+      std::swap(order[i], order[j]);
+    }
+    for (int32_t i0 = 0; i0 < L; i0 += Lb) {
+      Step s{(int64_t)lnode_all.size(), (int64_t)pj_all.size(), 0,
+             std::min<int32_t>(Lb, L - i0), ep};
+      for (int32_t j = 0; j < s.nodes; ++j) {
+        const int32_t l = order[i0 + j];
+        lnode_all.push_back(l);
+        for (int64_t sl : node_slots[l]) {
+          pj_all.push_back(j);
+          slot_all.push_back(sl);
+        }
+      }
+      s.npairs = (int64_t)pj_all.size() - s.pair_off;
+      if (s.npairs > 0) steps.push_back(s);
+    }
+  }
+  // phase 2: Adam steps
+  LpActs a;
+  LpGrads gr;
+  int32_t *d_lnode = nullptr, *d_pj = nullptr;
+  int64_t* d_slot = nullptr;
+  float* d_loss = nullptr;
+  DeviceBlock tb;
+  for (int pass = 0; pass < 2; ++pass) {
+    Carve c(pass ? tb.p : nullptr);
+    carve_lp_train(c, g, Lb, pair_ctas, &a, &gr);
+    d_lnode = c.take<int32_t>(std::max<size_t>(1, lnode_all.size()));
+    d_pj = c.take<int32_t>(std::max<size_t>(1, pj_all.size()));
+    d_slot = c.take<int64_t>(std::max<size_t>(1, slot_all.size()));
+    d_loss = c.take<float>(std::max<size_t>(1, steps.size()));
+    if (!pass) CUDA_TRY(cudaMalloc(&tb.p, c.off));
+  }
+  CUDA_TRY(cudaMemcpyAsync(d_lnode, lnode_all.data(), 4 * lnode_all.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(d_pj, pj_all.data(), 4 * pj_all.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemcpyAsync(d_slot, slot_all.data(), 8 * slot_all.size(), cudaMemcpyHostToDevice, st));
+  CUDA_TRY(cudaMemsetAsync(d_loss, 0, sizeof(float) * std::max<size_t>(1, steps.size()), st));
+  LearnedModel& lm = g->lm;
+  CUDA_TRY(cudaMemsetAsync(lm.G, 0, sizeof(float) * kParams, st));
+  for (size_t i = 0; i < steps.size(); ++i) {
+    const Step& s = steps[i];
+    lp_forward(g->d, s.nodes, d_lnode + s.lnode_off, nn.offv_t, nn.alpha, nn.gamma, lm.P, lm.wb,
+               a, st);
+    lp_backward(g->d, s.nodes, d_lnode + s.lnode_off, nn.offv_t, lm.P, lm.wt, a, s.npairs,
+                d_pj + s.pair_off, d_slot + s.pair_off, R, E, (float)(1.0 / (double)s.npairs),
+                gr, lm.G, d_loss + i, st);
+    lp_adam(lm.P, lm.G, lm.m, lm.v, lr, ++lm.step, st);
+    lp_weights_bf16(lm.P, lm.wb, lm.wt, st);
+  }
+  CUDA_TRY(cudaGetLastError());
+  std::vector<float> hl(std::max<size_t>(1, steps.size()));
+  CUDA_TRY(cudaMemcpyAsync(hl.data(), d_loss, sizeof(float) * hl.size(), cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(cudaStreamSynchronize(st));
+  if (loss_history) {
+    std::vector<double> sum(epochs, 0.0);
+    std::vector<int> n(epochs, 0);
+    for (size_t i = 0; i < steps.size(); ++i) {
+      sum[steps[i].epoch] += hl[i];
+      n[steps[i].epoch]++;
+    }
+    for (int e = 0; e < epochs; ++e) loss_history[e] = n[e] ? (float)(sum[e] / n[e]) : 0.f;
+  }
+  std::vector<float> p(kParams);
+  CUDA_TRY(cudaMemcpy(p.data(), lm.P, sizeof(float) * kParams, cudaMemcpyDeviceToHost));
+  if (!params_finite(p.data())) {
+    lm.ready = false;
+    return fail(GRF_ENUMERIC, "training diverged (non-finite weights); weights disabled");
+  }
+  return GRF_OK;
+}
 
 int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
                      const int64_t* edge_v, const double* lengths, const int32_t* n_elems,
@@ -843,6 +1374,20 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
     g->adj_edge[fill[b]] = (int32_t)e;
     g->adj_nbr[fill[b]++] = a;
   }
+  // reverse incidence: the same edge seen from its other end
+  g->adj_rev.assign(2 * E, -1);
+  {
+    std::vector<int32_t> first(E, -1);
+    for (int32_t k = 0; k < 2 * (int32_t)E; ++k) {
+      const int32_t e = g->adj_edge[k];
+      if (first[e] < 0) {
+        first[e] = k;
+      } else {
+        g->adj_rev[k] = first[e];
+        g->adj_rev[first[e]] = k;
+      }
+    }
+  }
   *out = g;
   return GRF_OK;
 }
@@ -877,7 +1422,8 @@ int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t 
   size_t need = align_up((size_t)g->n * n_samples * ts);
   if (stages.size() > 1) need += align_up((size_t)g->n * n_samples * 8);
   size_t tail = 0;
-  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), n_samples, ts));
+  for (auto& s : stages)
+    tail = std::max(tail, apply_bytes(g, s.L(), n_samples, ts, o.precond == GRF_PRECOND_LEARNED));
   *bytes = need + tail;
   return GRF_OK;
 }
@@ -1027,7 +1573,8 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   hn.weight.assign(weight, weight + n_nodes);
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
-  GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts)));
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts,
+                                          o.precond == GRF_PRECOND_LEARNED)));
   cudaStream_t st = (cudaStream_t)stream;
   RunStats rs;
   rs.timing = o.timing;
@@ -1087,10 +1634,11 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
   hn.weight = {1.0};
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
-  GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts)));
+  const bool learned = o.precond == GRF_PRECOND_LEARNED;
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts, learned)));
   Carve c((char*)g->ws + head);
   ApplyWs w;
-  carve_apply(c, g, 1, n_rhs, ts, &w);
+  carve_apply(c, g, 1, n_rhs, ts, &w, learned);
   cudaStream_t st = (cudaStream_t)stream;
   GRF_TRY(upload_nodes(hn, w, st));
   const double k2 = kappa * kappa;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the sampler's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -21,6 +22,7 @@ struct DevGraph {
   const int32_t* vptr;   // [nv + 1] vertex -> incidence list
   const int32_t* adj_edge;  // [2 ne] incident edge
   const int32_t* adj_nbr;   // [2 ne] vertex at the other end
+  const int32_t* adj_rev;   // [2 ne] index of the same edge in the other end's list
   const double* sqrt_ml;    // [n] sqrt of the lumped mass per DOF
 };
 
@@ -36,7 +38,7 @@ struct PcgStatus {
   int32_t n_unconverged;
   int32_t numeric_flag;
   int32_t iters_max;
-  int32_t pad;
+  int32_t n_fallback;  // systems whose learned preconditioner fell back to Jacobi
   unsigned long long iters_total;
 };
 
@@ -102,13 +104,65 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 // offv_t = scaled blocks). d, r, p, q: [L][S][nv] scratch used when a system's
 // vectors do not fit in shared memory. layout: 1 one CTA per system, 2 staged
 // matrix per (node, sample group) when it fits (mixed only), else layout 1.
+// lp_es / lp_n (mixed only, may be null): learned preconditioner B = diag(es) + N
+// per node ([L][V], [L][2E]); y: one more [L][S][nv] scratch for it.
 template <typename VT>
 void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, const double* gvec, double* x, VT* d,
-                VT* r, VT* p, VT* q, double rtol, int32_t max_iter, int32_t* iters,
-                PcgStatus* status, int layout, cudaStream_t st);
+                const VT* dscale_t, const VT* offv_t, const float* lp_es, const float* lp_n,
+                const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
+                int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
+                cudaStream_t st);
 
 int recover_sample_group();
+
+// ---- learned.cu: learned BB^T preconditioner of the scaled Schur systems.
+// FP32 parameter vector layout (fixed flat order):
+// W0 [8 x 64], b0, then W_i [128 x 64], b_i for i = 1..3, then ws [64], cs, u [64],
+// up [64], cn.
+constexpr int kFeat = 8;
+constexpr int kLayers = 3;
+constexpr int kOffW0 = 0;
+constexpr int kOffB0 = kFeat * 64;
+__host__ __device__ constexpr int layer_w_off(int i) { return kOffB0 + 64 + (i - 1) * (8192 + 64); }
+constexpr int kOffWs = layer_w_off(kLayers + 1);
+constexpr int kOffCs = kOffWs + 64;
+constexpr int kOffU = kOffCs + 1;
+constexpr int kOffUp = kOffU + 64;
+constexpr int kOffCn = kOffUp + 64;
+constexpr int kParams = kOffCn + 1;
+constexpr int kWbf16 = 16 * 64 + 3 * 8192;  // BF16 copies: W0 padded to 16 rows, W1..W3
+constexpr int kWtbf16 = 3 * 8192;           // W1..W3 transposed
+
+// Activations of a forward pass over Lb nodes (M = Lb * V rows).
+struct LpActs {
+  __nv_bfloat16* X0;     // [M x 16]
+  float* H[kLayers + 1]; // [M x 64]
+  __nv_bfloat16* Xc[kLayers];  // [M x 128] = [h_{i-1} | m_i]
+  float *s, *es, *al, *be;     // [M]
+  float* n;                    // [Lb x 2E]
+};
+struct LpGrads {
+  float *ds, *dn;        // [M], [Lb x 2E]
+  float *dH, *dX;        // [M x 64], [M x 128]
+  __nv_bfloat16* dA;     // [M x 64]
+  float* scratch;        // [max_pair_ctas x 4 V]
+  int max_pair_ctas;
+};
+
+void lp_weights_bf16(const float* P, __nv_bfloat16* wb, __nv_bfloat16* wt, cudaStream_t st);
+// Returns the number of kernels launched.
+int lp_forward(const DevGraph& g, int32_t Lb, const int32_t* lnode, const float* offv_t,
+               const double* alpha, const double* gamma, const float* P,
+               const __nv_bfloat16* wb, const LpActs& a, cudaStream_t st);
+void lp_backward(const DevGraph& g, int32_t Lb, const int32_t* lnode, const float* offv_t,
+                 const float* P, const __nv_bfloat16* wt, const LpActs& a, int64_t npairs,
+                 const int32_t* pj, const int64_t* slot, const float* R, const float* E,
+                 float inv_p, const LpGrads& b, float* G, float* loss, cudaStream_t st);
+void lp_adam(float* P, float* G, float* m, float* v, float lr, int step, cudaStream_t st);
+void lp_record_pairs(const DevGraph& g, int64_t nsys, int64_t S, const double* diag,
+                     const double* offv, const double* gvec, double* work, double* xrec,
+                     float* R, float* E, double* rinv, int32_t* count, int per_sys, int stride,
+                     double rtol, int max_iter, int ctas, cudaStream_t st);
 
 // ---- recover.cu
 // Edge bins of the register-resident recovery: bin i takes edges with

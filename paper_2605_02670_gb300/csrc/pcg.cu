@@ -89,11 +89,13 @@ __device__ __forceinline__ VT sum_partials(const VT* shw, int k, int N) {
   return a;
 }
 
-// Per-system vectors: VT d (update), r, p, q; FP64 x (the iterate) when refining.
+// Per-system vectors: VT d (update), r, p, q; FP64 x (the iterate) when
+// refining; y (learned preconditioner only) holds B^T r.
 template <typename VT>
 struct SysVecs {
   VT *d, *r, *p, *q;
   double* x;
+  VT* y;
 };
 
 // One node's matrix as seen by the solver. vptr/nbr/Ot/Ds may point to shared
@@ -106,7 +108,35 @@ struct SysMatrix {
   const VT* Ds;      // FP64 mode: 1 / D; mixed: 1 / sqrt(D)
   const double* D;   // FP64 diagonal
   const double* O;   // FP64 blocks
+  // learned preconditioner of the scaled system (mixed mode), else null:
+  // B = diag(es) + N, N_{v, nbr k} = nb[k]; rev = reverse incidence
+  const float* es;
+  const float* nb;
+  const int32_t* rev;
 };
+
+// z = B (B^T r) for the learned preconditioner: y_w = es_w r_w +
+// sum_k' nb_{rev k'} r_{nbr k'}; z_v = es_v y_v + sum_k nb_k y_{nbr k}. Writes z
+// and returns this thread's share of r.z; ends with all threads past a barrier.
+template <int kThreads, typename VT>
+__device__ __forceinline__ VT learned_apply(int32_t nv, const SysMatrix<VT>& M, const VT* r,
+                                            VT* y, VT* z) {
+  for (int32_t w = threadIdx.x; w < nv; w += kThreads) {
+    VT acc = (VT)M.es[w] * r[w];
+    for (int32_t k = M.vptr[w]; k < M.vptr[w + 1]; ++k)
+      acc += (VT)M.nb[M.rev[k]] * r[M.nbr[k]];
+    y[w] = acc;
+  }
+  __syncthreads();
+  VT rz = (VT)0;
+  for (int32_t v = threadIdx.x; v < nv; v += kThreads) {
+    VT acc = (VT)M.es[v] * y[v];
+    for (int32_t k = M.vptr[v]; k < M.vptr[v + 1]; ++k) acc += (VT)M.nb[k] * y[M.nbr[k]];
+    z[v] = acc;
+    rz += r[v] * acc;
+  }
+  return rz;
+}
 
 template <int kThreads, typename VT>
 struct Shared {
@@ -117,7 +147,7 @@ struct Shared {
 
 struct SysResult {
   int32_t it;
-  bool done, bad;
+  bool done, bad, fallback;
 };
 
 // FP64 residual r_i = g_i - (S x)_i
@@ -154,6 +184,12 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
   bool bad = !isfinite(gg[0]) || !isfinite(gg[1]);
   bool done = bad || !(gg[0] > 0.0);
   double sig2 = gg[1];  // ||D^-1/2 r||^2 of the current refinement step
+  // z = B B^T r (learned), else z = r on the scaled system (Jacobi). A learned
+  // preconditioner that breaks down (r.z <= 0, p.Sp <= 0 or a non-finite
+  // scalar) is dropped for the rest of this system's solve, which continues
+  // with Jacobi from the last refined iterate.
+  bool learned = kRefine && M.es != nullptr;
+  bool fallback = false;
   while (!done && it < max_iter) {
     double sigma = 1.0;
     if (kRefine) {
@@ -194,11 +230,15 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
     }
     // (P)CG on the inner system from d = 0
     VT rz0 = (VT)0;
-    for (int32_t i = threadIdx.x; i < nv; i += kThreads) {
-      const VT ri = v.r[i];
-      const VT z = kRefine ? ri : ri * M.Ds[i];
-      v.p[i] = z;
-      rz0 += ri * z;
+    if (learned) {
+      rz0 = learned_apply<kThreads, VT>(nv, M, v.r, v.y, v.p);
+    } else {
+      for (int32_t i = threadIdx.x; i < nv; i += kThreads) {
+        const VT ri = v.r[i];
+        const VT z = kRefine ? ri : ri * M.Ds[i];
+        v.p[i] = z;
+        rz0 += ri * z;
+      }
     }
     double a0[1] = {(double)rz0};
     block_sum<kThreads, 1>(a0, S.sh);
@@ -213,8 +253,8 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
     const VT inner2 = kRefine ? (VT)(kInnerRtol * kInnerRtol) : (VT)tol2;
     VT best = kRefine ? (VT)1 : (VT)gg[0];
     int since_best = 0;
-    int verdict = 0;
-    while (it < max_iter) {
+    int verdict = learned && !(rz > (VT)0 && isfinite((double)rz)) ? kBad : 0;
+    while (verdict == 0 && it < max_iter) {
       ++it;
       __syncthreads();  // p from the previous update is visible
       VT pqf = (VT)0;
@@ -233,7 +273,7 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
         break;
       }
       if (!(pq > (VT)0)) {  // p vanished (mixed: at the FP32 floor)
-        verdict = kRefine ? kStop : kBad;
+        verdict = kRefine && !learned ? kStop : kBad;
         break;
       }
       const VT af = rz / pq;
@@ -244,6 +284,10 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
         v.r[i] = ri;
         rzf += kRefine ? ri * ri : ri * ri * M.Ds[i];
         rrf += ri * ri;
+      }
+      if (learned) {  // z = B B^T r into q (q is consumed above)
+        __syncthreads();
+        rzf = learned_apply<kThreads, VT>(nv, M, v.r, v.y, v.q);
       }
       VT part2[2] = {rzf, rrf};
       warp_partials<VT, 2>(part2, S.shw2);
@@ -270,9 +314,14 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
       const VT bf = rzn / rz;
       rz = rzn;
       for (int32_t i = threadIdx.x; i < nv; i += kThreads)
-        v.p[i] = (kRefine ? v.r[i] : v.r[i] * M.Ds[i]) + bf * v.p[i];
+        v.p[i] = (learned ? v.q[i] : (kRefine ? v.r[i] : v.r[i] * M.Ds[i])) + bf * v.p[i];
     }
     const bool inner_done = verdict == kDone;
+    if (verdict == kBad && learned) {  // drop the correction, go on with Jacobi
+      learned = false;
+      fallback = true;
+      continue;
+    }
     if (verdict == kBad) bad = true;
     if (bad) break;
     if (!kRefine) {
@@ -301,7 +350,7 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
   } else {
     for (int32_t i = threadIdx.x; i < nv; i += kThreads) xo[i] = (double)v.d[i];
   }
-  return SysResult{it, done, bad};
+  return SysResult{it, done, bad, fallback};
 }
 
 template <int kThreads>
@@ -311,6 +360,7 @@ __device__ __forceinline__ void report(int64_t sys, const SysResult& r, int32_t*
     iters[sys] = r.it;
     atomicAdd(&status->iters_total, (unsigned long long)r.it);
     atomicMax(&status->iters_max, r.it);
+    if (r.fallback) atomicAdd(&status->n_fallback, 1);
     if (r.bad) atomicAdd(&status->numeric_flag, 1);
     else if (!r.done) atomicAdd(&status->n_unconverged, 1);
   }
@@ -320,13 +370,17 @@ constexpr int kThreadsA = 256;
 
 // dscale: FP64 mode 1 / D; mixed mode 1 / sqrt(D).
 // offv_t: FP64 mode the blocks; mixed mode the Jacobi-scaled blocks.
+// lp_es / lp_n (mixed mode, may be null): learned preconditioner per node,
+// diag(es) [L][V] and the incidence entries [L][2E].
 template <typename VT, bool kSmem>
 __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
     DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const VT* __restrict__ dscale_t,
-    const VT* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
+    const VT* __restrict__ offv_t, const float* __restrict__ lp_es,
+    const float* __restrict__ lp_n, const double* __restrict__ gvec, double* __restrict__ xout,
     VT* __restrict__ gd, VT* __restrict__ gr, VT* __restrict__ gp, VT* __restrict__ gq,
-    double rtol, int32_t max_iter, int32_t* __restrict__ iters, PcgStatus* status) {
+    VT* __restrict__ gy, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
+    PcgStatus* status) {
   constexpr bool kRefine = sizeof(VT) == 4;
   __shared__ Shared<kThreadsA, VT> shs;
   extern __shared__ __align__(16) unsigned char vec_sm[];
@@ -335,8 +389,15 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
   const int64_t ne2 = 2 * (int64_t)g.ne;
   for (int64_t sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
     const int64_t l = sys / S;
-    SysMatrix<VT> M{g.vptr, g.adj_nbr, offv_t + l * ne2, dscale_t + l * nv, diag + l * nv,
-                    offv + l * ne2};
+    SysMatrix<VT> M{g.vptr,
+                    g.adj_nbr,
+                    offv_t + l * ne2,
+                    dscale_t + l * nv,
+                    diag + l * nv,
+                    offv + l * ne2,
+                    lp_es ? lp_es + l * nv : nullptr,
+                    lp_n ? lp_n + l * ne2 : nullptr,
+                    g.adj_rev};
     double* xo = xout + sys * nv;
     SysVecs<VT> v;
     if (kSmem) {
@@ -346,12 +407,14 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
       v.r = base + nv;
       v.p = base + 2 * (int64_t)nv;
       v.q = base + 3 * (int64_t)nv;
+      v.y = base + 4 * (int64_t)nv;  // allocated only with the learned preconditioner
     } else {
       v.x = xo;
       v.d = gd + sys * nv;
       v.r = gr + sys * nv;
       v.p = gp + sys * nv;
       v.q = gq + sys * nv;
+      v.y = gy + sys * nv;
     }
     const SysResult res = solve_system<kThreadsA, VT>(nv, M, gvec + sys * nv, xo, v, !kSmem,
                                                       rtol, max_iter, shs);
@@ -391,6 +454,7 @@ __global__ void __launch_bounds__(kThreadsB) pcg_staged_kernel(
   v.r = v.d + nv;
   v.p = v.r + nv;
   v.q = v.p + nv;
+  v.y = nullptr;
   const int64_t nchunk = (S + chunk - 1) / chunk;
   const int64_t units = (int64_t)L * nchunk;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
@@ -405,7 +469,8 @@ __global__ void __launch_bounds__(kThreadsB) pcg_staged_kernel(
     }
     for (int32_t i = threadIdx.x; i < nv; i += kThreadsB) Ds[i] = dscale_t[l * nv + i];
     __syncthreads();
-    SysMatrix<float> M{vptr, nbr, Ot, Ds, diag + l * nv, offv + l * ne2};
+    SysMatrix<float> M{vptr, nbr, Ot, Ds, diag + l * nv, offv + l * ne2, nullptr, nullptr,
+                       nullptr};
     for (int64_t s = s_begin; s < s_end; ++s) {
       const int64_t sys = l * S + s;
       const SysResult res = solve_system<kThreadsB, float>(nv, M, gvec + sys * nv,
@@ -421,13 +486,14 @@ __global__ void __launch_bounds__(kThreadsB) pcg_staged_kernel(
 
 template <typename VT>
 void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, const double* gvec, double* x, VT* d,
-                VT* r, VT* p, VT* q, double rtol, int32_t max_iter, int32_t* iters,
-                PcgStatus* status, int layout, cudaStream_t st) {
+                const VT* dscale_t, const VT* offv_t, const float* lp_es, const float* lp_n,
+                const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
+                int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
+                cudaStream_t st) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
     const size_t sb = staged_bytes(g.nv, g.ne) + sizeof(Shared<kThreadsB, float>);
-    if (sb <= kSmemMax && layout == 2) {
+    if (sb <= kSmemMax && layout == 2 && !lp_es) {
       // enough (node, sample-group) units to fill the GPU, one CTA per SM
       int64_t groups = (2 * 152 + L - 1) / L;
       if (groups > S) groups = S;
@@ -447,24 +513,25 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
   int blocks = (int)(nsys < 152 * 16 ? nsys : 152 * 16);
   if (blocks < 1) blocks = 1;
   const size_t smem = (sizeof(VT) == 4 ? sizeof(double) : 0) * (size_t)g.nv +
-                      4 * sizeof(VT) * (size_t)g.nv;
+                      (lp_es ? 5 : 4) * sizeof(VT) * (size_t)g.nv;
   if (smem <= kSmemMax - 16 * 1024) {
     // dynamic + static may pass the 48 KB default; per device: set at every launch
     cudaFuncSetAttribute(pcg_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     pcg_kernel<VT, true><<<blocks, kThreadsA, smem, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                          gvec, x, d, r, p, q, rtol, max_iter,
-                                                          iters, status);
+                                                          lp_es, lp_n, gvec, x, d, r, p, q, y,
+                                                          rtol, max_iter, iters, status);
   } else {
     pcg_kernel<VT, false><<<blocks, kThreadsA, 0, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                        gvec, x, d, r, p, q, rtol, max_iter,
-                                                        iters, status);
+                                                        lp_es, lp_n, gvec, x, d, r, p, q, y,
+                                                        rtol, max_iter, iters, status);
   }
 }
 #define GRF_INST(VT)                                                                          \
   template void launch_pcg<VT>(const DevGraph&, int32_t, int64_t, const double*, const double*, \
-                               const VT*, const VT*, const double*, double*, VT*, VT*, VT*, VT*, \
-                               double, int32_t, int32_t*, PcgStatus*, int, cudaStream_t);
+                               const VT*, const VT*, const float*, const float*, const double*,  \
+                               double*, VT*, VT*, VT*, VT*, VT*, double, int32_t, int32_t*,      \
+                               PcgStatus*, int, cudaStream_t);
 GRF_INST(float)
 GRF_INST(double)
 #undef GRF_INST

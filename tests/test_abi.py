@@ -90,3 +90,44 @@ def test_workspace_query_is_host_only():
     b2 = G.workspace_bytes(0.75, 0.5, 8)
     b3 = G.workspace_bytes(1.75, 0.5, 8)
     assert 0 < b1 < b2 < b3
+
+
+def test_weights_file_header_is_checked_before_device_work(tmp_path):
+    """grf_precond_load rejects anything but a version-1 weights file of this
+    network without touching the device."""
+    g = gi.square_diagonal(0)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.1)
+    header = bytearray(48)
+    header[:8] = b"GRFLPBB1"
+    vals = np.array([1, grf.GRF_LP_PARAMS, 8, 64, 3, 1], np.int32).tobytes()
+    header[8:8 + len(vals)] = vals
+    body = np.zeros(grf.GRF_LP_PARAMS, np.float32).tobytes()
+    cases = {
+        "short": bytes(header) + body[:100],
+        "magic": b"XXXXXXXX" + bytes(header[8:]) + body,
+        "version": bytes(header[:8]) + np.int32(2).tobytes() + bytes(header[12:]) + body,
+        "width": bytes(header[:20]) + np.int32(32).tobytes() + bytes(header[24:]) + body,
+        "trailing": bytes(header) + body + b"\0",
+    }
+    for name, blob in cases.items():
+        p = os.path.join(tmp_path, name + ".bin")
+        with open(p, "wb") as f:
+            f.write(blob)
+        with pytest.raises(grf.GrfError) as ei:
+            G.precond_load(p)
+        assert ei.value.code == grf.GRF_EINVAL, name
+    with pytest.raises(grf.GrfError):
+        G.precond_load(os.path.join(tmp_path, "missing.bin"))
+
+
+def test_learned_options_rejected_without_weights_or_in_fp64():
+    g = gi.square_diagonal(0)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.1)
+    with pytest.raises(grf.GrfError) as ei:
+        G.workspace_bytes(0.7, 0.5, 4, precision="fp64", precond="learned")
+    assert ei.value.code == grf.GRF_ENOTSUP
+    assert G.workspace_bytes(0.7, 0.5, 4, precision="mixed", precond="learned") > \
+        G.workspace_bytes(0.7, 0.5, 4, precision="mixed")
+    with pytest.raises(grf.GrfError) as ei:
+        G.precond_get()
+    assert ei.value.code == grf.GRF_EINVAL
