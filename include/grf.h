@@ -79,7 +79,22 @@ typedef struct grf_options {
                           CUDA graph cached on the handle (re-captured when the parameters,
                           options, sample count or output pointer change) and replays it;
                           phase timing is then not reported */
+  int32_t interior;    /* edge-interior solver of the condensation and recovery steps:
+                          GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS or GRF_INTERIOR_SPECTRAL */
 } grf_options;
+
+/* Edge-interior solvers (same results up to rounding):
+ *   THOMAS: per node l a tridiagonal elimination along the edge (Sec. 3, Phases
+ *     3 and 5 as printed);
+ *   SPECTRAL (GRF_MIXED only): the interior blocks of all nodes share the
+ *     discrete sine transform's eigenvectors on a uniform edge mesh, so the
+ *     sum over nodes is applied as one sine-transform pair per edge and sample
+ *     plus a dense (interior nodes x nodes) by (nodes x samples) contraction;
+ *     edges with more than 1024 interior nodes still use THOMAS;
+ *   AUTO: SPECTRAL in GRF_MIXED, THOMAS in GRF_FP64. */
+#define GRF_INTERIOR_AUTO 0
+#define GRF_INTERIOR_THOMAS 1
+#define GRF_INTERIOR_SPECTRAL 2
 
 /* Vertex PCG launch layouts (same results up to rounding):
  *   PER_SYSTEM: one CTA per (node, sample) system, Schur matrix read through

@@ -91,14 +91,25 @@ struct grf_graph {
   std::vector<double> he;
   std::vector<int64_t> ioff;
   std::vector<double> ml_vertex;  // lumped mass at kept vertices
-  // recovery edge bins per precision ([0] FP32 sweeps, [1] FP64): edge ids
-  // grouped by bin, the count per bin, and last the edges beyond every bin
-  std::vector<int32_t> bin_edges[2];
-  int32_t bin_count[2][kMaxBins + 1] = {};
-  int32_t n_bins[2] = {0, 0};
-  const int32_t* d_bin_edges[2] = {nullptr, nullptr};
+  // Thomas recovery edge bins ([0] FP32 sweeps, [1] FP64, [2] FP32 sweeps of the
+  // edges the spectral path leaves to Thomas): edge ids grouped by bin, the
+  // count per bin, and last the edges beyond every bin
+  std::vector<int32_t> bin_edges[3];
+  int32_t bin_count[3][kMaxBins + 1] = {};
+  int32_t n_bins[3] = {0, 0, 0};
+  const int32_t* d_bin_edges[3] = {nullptr, nullptr, nullptr};
+  // spectral bins (edges with 1 <= m <= the largest spectral bin)
+  std::vector<int32_t> spec_edges;
+  int32_t spec_count[kMaxBins] = {};
+  int32_t n_spec_bins = 0;
+  const int32_t* d_spec_edges = nullptr;
 
   int64_t long_edges(bool fp64) const { return bin_count[fp64 ? 1 : 0][n_bins[fp64 ? 1 : 0]]; }
+  int64_t thomas_rest() const {  // edges of bins [2]
+    int64_t n = 0;
+    for (int i = 0; i <= n_bins[2]; ++i) n += bin_count[2][i];
+    return n;
+  }
 
   int device = -1;
   void* dev_block = nullptr;
@@ -112,6 +123,7 @@ struct grf_graph {
   struct GraphCache {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
+    bool spectral = false;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
     int64_t S = 0;
     void* out = nullptr;
@@ -186,7 +198,8 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(E); c.take<int32_t>(E); c.take<int32_t>(E); c.take<double>(E);
   c.take<int64_t>(E + 1); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   c.take<double>((size_t)g->n); c.take<double>(V);
-  c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(2 * E);
+  c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1);
+  c.take<int32_t>(2 * E);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -202,12 +215,19 @@ int ensure_device(grf_graph* g) {
   int32_t* an = k.take<int32_t>(2 * E);
   double* sml = k.take<double>((size_t)g->n);
   double* mlv = k.take<double>(V);
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     int32_t* be = k.take<int32_t>(E + 1);
     if (!g->bin_edges[p].empty())
       CUDA_TRY(cudaMemcpy(be, g->bin_edges[p].data(), g->bin_edges[p].size() * 4,
                           cudaMemcpyHostToDevice));
     g->d_bin_edges[p] = be;
+  }
+  {
+    int32_t* se = k.take<int32_t>(E + 1);
+    if (!g->spec_edges.empty())
+      CUDA_TRY(cudaMemcpy(se, g->spec_edges.data(), g->spec_edges.size() * 4,
+                          cudaMemcpyHostToDevice));
+    g->d_spec_edges = se;
   }
   CUDA_TRY(cudaMemcpy(eu, g->eu.data(), E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(ev, g->ev.data(), E * 4, cudaMemcpyHostToDevice));
@@ -286,6 +306,7 @@ struct Opts {
   int pcg_layout;  // 1 per system, 2 staged
   int recover_sg;  // 1, 2 or 4
   bool use_graph;
+  bool spectral;   // edge interiors in the sine basis (mixed precision)
 };
 
 int read_opts(const grf_options* o, Opts* r) {
@@ -312,6 +333,12 @@ int read_opts(const grf_options* o, Opts* r) {
     return fail(GRF_ENOTSUP, "the learned preconditioner needs precision GRF_MIXED");
   if (r->out_dtype != GRF_OUT_F64 && r->out_dtype != GRF_OUT_F32)
     return fail(GRF_EINVAL, "unknown out_dtype %d", r->out_dtype);
+  const int in = o ? o->interior : GRF_INTERIOR_AUTO;
+  if (in < GRF_INTERIOR_AUTO || in > GRF_INTERIOR_SPECTRAL)
+    return fail(GRF_EINVAL, "unknown interior solver %d", in);
+  if (in == GRF_INTERIOR_SPECTRAL && r->precision != GRF_MIXED)
+    return fail(GRF_ENOTSUP, "the spectral interior solver needs precision GRF_MIXED");
+  r->spectral = r->precision == GRF_MIXED && in != GRF_INTERIOR_THOMAS;
   return GRF_OK;
 }
 
@@ -327,6 +354,7 @@ struct ApplyWs {
   void *yscr, *rpscr;
   void* prm;  // SweepParams<T> [L][E]
   void* xw;   // T [L][S][V]
+  float* bhat;  // sine transform of the interior noise [n_interior][S] (spectral path)
   int32_t* iters;
   PcgStatus* status;
 };
@@ -358,7 +386,7 @@ void carve_lp_infer(Carve& c, const grf_graph* g, int32_t nodes, LpActs* a) {
 }
 
 void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w,
-                 bool learned = false) {
+                 bool learned = false, bool spectral = false) {
   const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
   const size_t nsg = (Ss + recover_sample_group() - 1) / recover_sample_group();
   w->alpha = c.take<double>(Ls);
@@ -395,6 +423,7 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->rpscr = c.take<char>(ni_long * nsg * tsize);
   w->prm = c.take<char>(Ls * E * 4 * tsize);
   w->xw = c.take<char>(Ls * Ss * V * tsize);
+  w->bhat = spectral && tsize == 4 ? c.take<float>((size_t)g->ni * Ss) : nullptr;
   w->iters = c.take<int32_t>(Ls * Ss);
   w->status = c.take<PcgStatus>(1);
 }
@@ -497,7 +526,15 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                                   (SweepParams<T>*)w.prm, (T*)w.dscale, (T*)w.offv_t, st);
   rs->end(1, st);
   rs->begin(st);
-  launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
+  if (sizeof(T) == 4 && o.spectral && w.bhat) {
+    // edges beyond the spectral bins by Thomas, then the spectral bins
+    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[2],
+                                       (int32_t)g->thomas_rest());
+    rs->launches += launch_spec_condense(g->d, nd, kappa2, S, (const float*)b, g->d_spec_edges,
+                                         g->spec_count, w.bhat, gvec, st);
+  } else {
+    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
+  }
   rs->end(2, st);
   CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
   // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
@@ -524,7 +561,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                 (T*)w.r, (T*)w.p, (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status,
                 o.pcg_layout, st);
   rs->end(3, st);
-  rs->launches += 3;
+  rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
   return GRF_OK;
 }
@@ -537,7 +574,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
              const double* nodes_dev = nullptr) {
   Carve c(ws_tail);
   ApplyWs w;
-  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond == GRF_PRECOND_LEARNED);
+  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
   const double k2 = kappa * kappa;
   if (nodes_dev) {
     w.alpha = const_cast<double*>(nodes_dev);
@@ -547,21 +584,25 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
     GRF_TRY(upload_nodes(hn, w, st));
   }
   GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
-  const int p = sizeof(T) == 8 ? 1 : 0;
+  const bool spec = sizeof(T) == 4 && o.spectral;
+  const int p = sizeof(T) == 8 ? 1 : (spec ? 2 : 0);
   rs->begin(st);
   rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
                                           (const SweepParams<T>*)w.prm, (T*)w.xw,
                                           g->d_bin_edges[p], g->bin_count[p], g->n_bins[p], w.acc,
                                           (T*)w.yscr, (T*)w.rpscr, o.recover_sg, st);
+  if (spec)
+    rs->launches += launch_spec_recover<OutT>(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
+                                              g->spec_count, w.bhat, (const float*)w.xw, out, st);
   rs->end(4, st);
   CUDA_TRY(cudaGetLastError());
   return collect(w, st, hn.L(), S, rs);
 }
 
-size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize, bool learned = false) {
+size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize, const Opts& o) {
   Carve c(nullptr);
   ApplyWs w;
-  carve_apply(c, g, L, S, tsize, &w, learned);
+  carve_apply(c, g, L, S, tsize, &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
   return c.off;
 }
 
@@ -605,10 +646,10 @@ void plan(double beta, double k_step, std::vector<HostNodes>* stages) {
 }
 
 size_t sample_ws_bytes(const grf_graph* g, const std::vector<HostNodes>& stages, int64_t S,
-                       size_t tsize, bool learned) {
+                       size_t tsize, const Opts& o) {
   size_t need = align_up((size_t)g->n * S * tsize);
   size_t tail = 0;
-  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize, learned));
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize, o));
   if (stages.size() > 1) need += align_up((size_t)g->n * S * sizeof(double));
   return need + tail;
 }
@@ -654,8 +695,7 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
                 OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
-  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T),
-                                       o.precond == GRF_PRECOND_LEARNED)));
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   return enqueue_sample<T, OutT>(g, stages, kappa, seed, S, out, o, st, rs);
 }
 
@@ -668,11 +708,10 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
                       int64_t S, OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
-  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T),
-                                       o.precond == GRF_PRECOND_LEARNED)));
+  GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
-                   gc.precond == o.precond &&
+                   gc.precond == o.precond && gc.spectral == o.spectral &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
                    gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
@@ -723,6 +762,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.launches = cap.launches;
     gc.precision = o.precision;
     gc.precond = o.precond;
+    gc.spectral = o.spectral;
     gc.out_dtype = o.out_dtype;
     gc.pcg_layout = o.pcg_layout;
     gc.recover_sg = o.recover_sg;
@@ -810,6 +850,7 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->gvec = w->x = w->acc = nullptr;
   w->yscr = w->rpscr = nullptr;
   w->prm = w->xw = nullptr;
+  w->bhat = nullptr;
 }
 
 // ---- learned preconditioner: model storage, initialisation and helpers
@@ -1334,8 +1375,27 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
     g->ml_vertex[g->ev[e]] += 0.5 * g->he[e];
   }
   g->ni = g->ioff[E];
+  // spectral bins: smallest bin whose limit holds the interior
+  int32_t spec_mmax[kMaxBins];
+  g->n_spec_bins = spec_bins(spec_mmax);
+  {
+    std::vector<std::vector<int32_t>> lists(g->n_spec_bins);
+    for (int64_t e = 0; e < E; ++e) {
+      const int64_t m = g->nel[e] - 1;
+      for (int i = 0; i < g->n_spec_bins && m >= 1; ++i)
+        if (m <= spec_mmax[i]) {
+          lists[i].push_back((int32_t)e);
+          break;
+        }
+    }
+    for (int i = 0; i < g->n_spec_bins; ++i) {
+      g->spec_count[i] = (int32_t)lists[i].size();
+      g->spec_edges.insert(g->spec_edges.end(), lists[i].begin(), lists[i].end());
+    }
+  }
+  const int64_t spec_limit = spec_mmax[g->n_spec_bins - 1];
   // recovery bins: smallest bin whose 32 * NW * B lanes x nodes hold the interior
-  for (int p = 0; p < 2; ++p) {
+  for (int p = 0; p < 3; ++p) {
     int32_t Bs[kMaxBins], NWs[kMaxBins];
     const int nb = recover_bins(p == 1, Bs, NWs);
     g->n_bins[p] = nb;
@@ -1343,6 +1403,7 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
     for (int64_t e = 0; e < E; ++e) {
       const int64_t m = g->nel[e] - 1;
       if (m <= 0) continue;
+      if (p == 2 && m <= spec_limit) continue;  // left to the spectral path
       int bin = nb;
       for (int i = 0; i < nb; ++i)
         if (m <= (int64_t)32 * NWs[i] * Bs[i]) {
@@ -1422,8 +1483,7 @@ int grf_workspace_bytes(const grf_graph* g, double beta, double k_step, int64_t 
   size_t need = align_up((size_t)g->n * n_samples * ts);
   if (stages.size() > 1) need += align_up((size_t)g->n * n_samples * 8);
   size_t tail = 0;
-  for (auto& s : stages)
-    tail = std::max(tail, apply_bytes(g, s.L(), n_samples, ts, o.precond == GRF_PRECOND_LEARNED));
+  for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), n_samples, ts, o));
   *bytes = need + tail;
   return GRF_OK;
 }
@@ -1475,7 +1535,18 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   const bool fp32 = o.precision == GRF_MIXED;
   std::vector<int> layouts = {GRF_PCG_PER_SYSTEM};
   if (fp32) layouts.push_back(GRF_PCG_STAGED);
-  std::vector<int> sgs = fp32 ? std::vector<int>{1, 2, 4} : std::vector<int>{2};
+  // candidates (interior solver, recover_sg); recover_sg only matters for the
+  // edges a solver leaves to the Thomas bins
+  std::vector<std::pair<int, int>> cands;
+  if (fp32) {
+    for (int sg : {1, 2, 4}) cands.push_back({GRF_INTERIOR_THOMAS, sg});
+    if (g->thomas_rest() > 0)
+      for (int sg : {1, 2, 4}) cands.push_back({GRF_INTERIOR_SPECTRAL, sg});
+    else
+      cands.push_back({GRF_INTERIOR_SPECTRAL, 4});
+  } else {
+    cands.push_back({GRF_INTERIOR_THOMAS, 0});
+  }
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
@@ -1483,10 +1554,11 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   grf_options best_o = b0;
   int rc = GRF_OK;
   for (int lay : layouts) {
-    for (int sg : sgs) {
+    for (auto cand : cands) {
       grf_options c = b0;
       c.pcg_layout = lay;
-      c.recover_sg = fp32 ? sg : 0;
+      c.interior = cand.first;
+      c.recover_sg = cand.second;
       rc = grf_sample(g, kappa, beta, k_step, 1, n_samples, out, &c, stream, nullptr);
       if (rc != GRF_OK && rc != GRF_ENOCONV) break;
       float ms = 0.f;
@@ -1573,8 +1645,7 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   hn.weight.assign(weight, weight + n_nodes);
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
-  GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts,
-                                          o.precond == GRF_PRECOND_LEARNED)));
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts, o)));
   cudaStream_t st = (cudaStream_t)stream;
   RunStats rs;
   rs.timing = o.timing;
@@ -1605,7 +1676,9 @@ int grf_schur(grf_graph* g, double kappa, double alpha, double gamma, double* di
   hn.alpha = {alpha};
   hn.gamma = {gamma};
   hn.weight = {1.0};
-  GRF_TRY(ensure_ws(g, apply_bytes(g, 1, 1, 8)));
+  Opts o64{};
+  o64.precision = GRF_FP64;
+  GRF_TRY(ensure_ws(g, apply_bytes(g, 1, 1, 8, o64)));
   Carve c(g->ws);
   ApplyWs w;
   carve_apply(c, g, 1, 1, 8, &w);
@@ -1634,11 +1707,10 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
   hn.weight = {1.0};
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
-  const bool learned = o.precond == GRF_PRECOND_LEARNED;
-  GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts, learned)));
+  GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts, o)));
   Carve c((char*)g->ws + head);
   ApplyWs w;
-  carve_apply(c, g, 1, n_rhs, ts, &w, learned);
+  carve_apply(c, g, 1, n_rhs, ts, &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
   cudaStream_t st = (cudaStream_t)stream;
   GRF_TRY(upload_nodes(hn, w, st));
   const double k2 = kappa * kappa;

@@ -74,10 +74,13 @@ int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* s
                  T* offv_t, cudaStream_t st);
 
 // ---- thomas.cu
-// rhs (sample-minor [n][S], T) -> condensed right-hand side gvec[l][s][v] (double)
+// rhs (sample-minor [n][S], T) -> condensed right-hand side gvec[l][s][v] (double):
+// gvec = b at the vertices plus the end values of the listed edges (edges null:
+// every edge). Returns the number of kernels launched.
 template <typename T>
-void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const T* b, double* gvec, cudaStream_t st);
+int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                    const T* b, double* gvec, cudaStream_t st, const int32_t* edges = nullptr,
+                    int32_t n_edges = 0);
 // Vertex accumulation out[s][v] = sum_l w_l x[l][s][v], and fused interior
 // recovery + quadrature sum for the interior DOFs: binned register-resident
 // kernels (recover.cu) for edges up to the largest bin, the sequential kernel
@@ -163,6 +166,22 @@ void lp_record_pairs(const DevGraph& g, int64_t nsys, int64_t S, const double* d
                      const double* offv, const double* gvec, double* work, double* xrec,
                      float* R, float* E, double* rinv, int32_t* count, int per_sys, int stride,
                      double rtol, int max_iter, int ctas, cudaStream_t st);
+
+// ---- spectral.cu: edge interiors in the sine basis (FP32 sweeps only).
+// Spectral bins: bin i holds edges with 1 <= m <= mmax[i] interior nodes (and
+// above the previous bin's limit). Returns the number of bins.
+constexpr int kSpecSG = 16;  // samples per CTA
+int spec_bins(int32_t* mmax);
+// bhat [n_interior][S] receives the sine transform of the interior noise rows;
+// gvec [L][S][nv] gets the two end values of T_l^-1 b_I added per edge.
+int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                         const float* b, const int32_t* bin_edges, const int32_t* bin_count,
+                         float* bhat, double* gvec, cudaStream_t st);
+// Interior field of the binned edges from bhat and xw = w_l u_v^(l).
+template <typename OutT>
+int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                        const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
+                        const float* xw, OutT* out, cudaStream_t st);
 
 // ---- recover.cu
 // Edge bins of the register-resident recovery: bin i takes edges with

@@ -76,17 +76,20 @@ __device__ __forceinline__ void end_sweeps(const T* src, int64_t stride, int32_t
 
 // Edges with more than stage_max interior nodes read their rows from global
 // memory instead of shared memory.
+// edges (may be null: every edge) lists the n_edges edges to process.
 template <typename T>
 __global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, double kappa2,
                                                       int64_t S, const T* __restrict__ b,
                                                       double* __restrict__ gvec,
-                                                      int32_t stage_max) {
+                                                      int32_t stage_max,
+                                                      const int32_t* __restrict__ edges,
+                                                      int32_t n_edges) {
   extern __shared__ __align__(16) unsigned char cond_sm[];
   T* sb = reinterpret_cast<T*>(cond_sm);
   const int64_t nsg = (S + kSG - 1) / kSG;
-  const int64_t units = (int64_t)g.ne * nsg;
+  const int64_t units = (int64_t)n_edges * nsg;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int32_t e = (int32_t)(u / nsg);
+    const int32_t e = edges ? edges[u / nsg] : (int32_t)(u / nsg);
     const int64_t s0 = (u % nsg) * kSG;
     const int32_t m = g.nel[e] - 1;
     if (m <= 0) continue;  // uniform across the CTA
@@ -253,10 +256,11 @@ __global__ void to_minor_kernel(DevGraph g, int64_t S, const double* __restrict_
 int recover_sample_group() { return kSG; }
 
 template <typename T>
-void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
-                     double* gvec, cudaStream_t st) {
+int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
+                    double* gvec, cudaStream_t st, const int32_t* edges, int32_t n_edges) {
   gvec_init_kernel<T><<<grid_for((int64_t)nd.L * S * g.nv, 256), 256, 0, st>>>(g, nd.L, S, b, gvec);
-  if (g.ni == 0) return;
+  if (!edges) n_edges = g.ne;
+  if (g.ni == 0 || n_edges == 0) return 1;
   const int64_t nsg = (S + kSG - 1) / kSG;
   // one thread per node (rounded up to whole warps, at most 256 per pass)
   int threads = ((nd.L + 31) / 32) * 32;
@@ -267,9 +271,11 @@ void launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64
   const int32_t stage_max = g.max_m < cap ? g.max_m : cap;
   const size_t smem = (size_t)(stage_max > 0 ? stage_max : 1) * kSG * sizeof(T);
   cudaFuncSetAttribute(condense_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int64_t blocks = (int64_t)g.ne * nsg;
+  int64_t blocks = (int64_t)n_edges * nsg;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  condense_kernel<T><<<(int)blocks, threads, smem, st>>>(g, nd, kappa2, S, b, gvec, stage_max);
+  condense_kernel<T><<<(int)blocks, threads, smem, st>>>(g, nd, kappa2, S, b, gvec, stage_max,
+                                                         edges, n_edges);
+  return 2;
 }
 
 template <typename T, typename OutT>
@@ -301,10 +307,12 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
   to_minor_kernel<T><<<grid_for(S * g.n, 256), 256, 0, st>>>(g, S, src, dst, mass_scale ? 1 : 0);
 }
 
-template void launch_condense<float>(const DevGraph&, const DevNodes&, double, int64_t,
-                                     const float*, double*, cudaStream_t);
-template void launch_condense<double>(const DevGraph&, const DevNodes&, double, int64_t,
-                                      const double*, double*, cudaStream_t);
+template int launch_condense<float>(const DevGraph&, const DevNodes&, double, int64_t,
+                                    const float*, double*, cudaStream_t, const int32_t*,
+                                    int32_t);
+template int launch_condense<double>(const DevGraph&, const DevNodes&, double, int64_t,
+                                     const double*, double*, cudaStream_t, const int32_t*,
+                                     int32_t);
 #define GRF_INST_RECOVER(T, O)                                                                 \
   template int launch_recover<T, O>(const DevGraph&, const DevNodes&, double, int64_t, const T*, \
                                     const double*, O*, const SweepParams<T>*, T*,                \

@@ -109,16 +109,17 @@ def test_schur_blocks(name, alpha, gamma):
 # ---------------------------------------------------------------- condensation + PCG
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision,interior", [("fp64", "auto"), ("mixed", "thomas"),
+                                                ("mixed", "spectral")])
 @pytest.mark.parametrize("gamma", [1e-12, 0.05, 3.0, 1e7])
-def test_vertex_condensation_and_pcg(precision, gamma):
+def test_vertex_condensation_and_pcg(precision, interior, gamma):
     g, h = GRAPHS["random12"]()
     G, m = make(g, h)
     kappa = 1.7
     ml, _, kmat = sampler.assemble(m, kappa)
     rhs = noise.white_noise(ml, 4, 5)
     gv, uv, st = G.vertex_solve(kappa, 1.0, gamma, torch.tensor(rhs, device="cuda"),
-                                precision=precision)
+                                precision=precision, interior=interior)
     g_ref, u_ref = sampler.vertex_condensation(m, ml, kmat, gamma, rhs)
     tol = 1e-10 if precision == "fp64" else 1e-5
     for got, ref in ((gv, g_ref), (uv, u_ref)):
@@ -157,14 +158,16 @@ def test_apply_matches_oracle(precision, name):
 # ---------------------------------------------------------------- whole sampler
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision,interior", [("fp64", "auto"), ("mixed", "thomas"),
+                                                ("mixed", "spectral")])
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("beta", [0.3, 0.75])
-def test_sample_matches_oracle(precision, name, beta):
+def test_sample_matches_oracle(precision, interior, name, beta):
     g, h = GRAPHS[name]()
     G, m = make(g, h)
     kappa, k, seed, S = 4.0, 0.45, 11, 5
-    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     interior=interior)
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
     ml = fem.lumped_mass(m)
     assert rel_l2(u.cpu().numpy(), ref, ml) < TOL[precision]
@@ -186,12 +189,15 @@ def test_sample_pcg_layouts(layout, name):
     assert st["n_unconverged"] == 0
 
 
-@pytest.mark.parametrize("precision,sg", [("fp64", 0), ("mixed", 1), ("mixed", 2), ("mixed", 4)])
-def test_sample_every_recovery_bin(precision, sg):
+@pytest.mark.parametrize("precision,sg,interior", [
+    ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
+    ("mixed", 1, "spectral"), ("mixed", 4, "spectral")])
+def test_sample_every_recovery_bin(precision, sg, interior):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
-    recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps), each
-    samples-per-lane variant, and the sequential kernel for edges longer than
-    the largest bin."""
+    Thomas recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps),
+    each samples-per-lane variant, the sequential kernel for edges longer than
+    the largest bin, and every bin of the spectral path (m <= 32 .. 1024) with
+    the longer edges left to Thomas."""
     ne = [2, 33, 65, 129, 257, 513, 1025, 2049, 4097, 5000, 3, 31]
     E = len(ne)
     eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 3])
@@ -201,7 +207,7 @@ def test_sample_every_recovery_bin(precision, sg):
     G, m = make(g, n_elems=ne)
     kappa, beta, k, seed, S = 6.0, 0.6, 0.5, 21, 6
     u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
-                     recover_sg=sg)
+                     recover_sg=sg, interior=interior)
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, n_elems=ne)
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
 
