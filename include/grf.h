@@ -99,9 +99,10 @@ typedef struct grf_options {
 /* Vertex PCG launch layouts (same results up to rounding):
  *   PER_SYSTEM: one CTA per (node, sample) system, Schur matrix read through
  *     the caches, vectors in shared memory when they fit;
- *   STAGED (mixed precision, graphs whose Schur matrix fits in shared memory):
- *     one CTA per (node, sample group) stages the node's matrix in shared
- *     memory and solves its samples one after another;
+ *   STAGED (mixed precision, Jacobi, graphs up to 4096 kept vertices whose
+ *     Schur matrix fits in shared memory): one CTA per (node, group of 2-4
+ *     samples) stages the node's matrix in shared memory and iterates the
+ *     group's samples together (per-sample scalars, stopping tests and counts);
  *   AUTO: the library's choice. */
 #define GRF_PCG_AUTO 0
 #define GRF_PCG_PER_SYSTEM 1

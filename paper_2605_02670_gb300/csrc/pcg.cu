@@ -29,9 +29,11 @@
 // loop is bounded by max_iter. Two layouts:
 //   pcg_kernel: one system after another per CTA, matrix read through L1/L2,
 //     vectors in shared memory when they fit (else global scratch);
-//   pcg_staged_kernel (mixed mode, small graphs): one CTA per (node, group of
-//     samples) stages that node's FP32 matrix and the incidence lists in
-//     shared memory once and solves its samples from shared memory only.
+//   pcg_group_kernel (mixed mode, graphs up to 4096 vertices): one CTA per
+//     (node, group of 2 or 4 samples) stages that node's FP32 matrix in shared
+//     memory and runs the group's samples together, so every matrix load
+//     serves the whole group; per-vertex vectors live in registers of the
+//     owning thread, only the search directions are shared.
 #include "grf_internal.h"
 
 namespace grf {
@@ -43,6 +45,10 @@ constexpr double kInnerRtol = 1e-4;
 // Verdicts of the inner loop.
 constexpr int kDone = 1, kStop = 2, kBad = 3;
 
+// Block sums of N doubles (sh: ((kThreads / 32) + 1) * N doubles). Thread k < N
+// adds the per-warp partials of value k (FP64 runs at a small fraction of the
+// FP32 rate on GB300, so every thread summing every partial would cost far
+// more than the extra barrier).
 template <int kThreads, int N>
 __device__ __forceinline__ void block_sum(double (&v)[N], double* sh) {
 #pragma unroll
@@ -50,6 +56,7 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* sh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
+  constexpr int W = kThreads / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();  // previous readers of sh are done
   if (lane == 0) {
@@ -57,12 +64,14 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* sh) {
     for (int k = 0; k < N; ++k) sh[warp * N + k] = v[k];
   }
   __syncthreads();
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
+  if (threadIdx.x < N) {
     double a = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) a += sh[w * N + k];
-    v[k] = a;
+    for (int w = 0; w < W; ++w) a += sh[w * N + threadIdx.x];
+    sh[W * N + threadIdx.x] = a;
   }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = sh[W * N + k];
 }
 
 // Shuffle-reduce N per-thread partials within each warp; lane 0 stores the
@@ -140,7 +149,7 @@ __device__ __forceinline__ VT learned_apply(int32_t nv, const SysMatrix<VT>& M, 
 
 template <int kThreads, typename VT>
 struct Shared {
-  double sh[(kThreads / 32) * 2];
+  double sh[(kThreads / 32 + 1) * 2];
   VT shw[(kThreads / 32)];
   VT shw2[(kThreads / 32) * 2];
 };
@@ -184,6 +193,7 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
   bool bad = !isfinite(gg[0]) || !isfinite(gg[1]);
   bool done = bad || !(gg[0] > 0.0);
   double sig2 = gg[1];  // ||D^-1/2 r||^2 of the current refinement step
+  double inner_e = kInnerRtol;  // relative stop of the current inner solve
   // z = B B^T r (learned), else z = r on the scaled system (Jacobi). A learned
   // preconditioner that breaks down (r.z <= 0, p.Sp <= 0 or a non-finite
   // scalar) is dropped for the rest of this system's solve, which continues
@@ -212,6 +222,9 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
           break;
         }
         sig2 = acc[1];
+        // solve the correction only as far as this step needs (a tenth of the
+        // remaining ratio), never tighter than the FP32 floor
+        inner_e = fmax(kInnerRtol, 0.1 * sqrt(tol2 / acc[0]));
       }
       if (!(sig2 > 0.0)) {
         done = true;
@@ -250,7 +263,7 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
     // iteration suffice.
     VT rz = (VT)a0[0];
     // inner stop: mixed relative to the unit start, FP64 on the true residual
-    const VT inner2 = kRefine ? (VT)(kInnerRtol * kInnerRtol) : (VT)tol2;
+    const VT inner2 = kRefine ? (VT)(inner_e * inner_e) : (VT)tol2;
     VT best = kRefine ? (VT)1 : (VT)gg[0];
     int since_best = 0;
     int verdict = learned && !(rz > (VT)0 && isfinite((double)rz)) ? kBad : 0;
@@ -423,63 +436,418 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
   }
 }
 
-constexpr int kThreadsB = 512;
+constexpr int kThreadsG = 512;
 
-// Shared memory of the staged kernel: matrix (vptr, nbr, scaled FP32 blocks,
-// 1 / sqrt(D)) then the vectors (FP64 x; FP32 d, r, p, q).
-__host__ __device__ inline size_t staged_bytes(int32_t nv, int32_t ne) {
-  const size_t a = 4 * ((size_t)nv + 1) + 4 * 2 * (size_t)ne + 4 * 2 * (size_t)ne + 4 * (size_t)nv;
-  const size_t a16 = (a + 15) & ~(size_t)15;
-  return a16 + 8 * (size_t)nv + 4 * 4 * (size_t)nv;
+// Shared memory of the group kernel: P [nv][SGP] (search directions of the
+// group's samples, interleaved), the node's scaled FP32 off-diagonals [2E] and
+// 1 / sqrt(D) [nv].
+template <int SGP>
+__host__ __device__ inline size_t group_bytes(int32_t nv, int32_t ne) {
+  return 4 * ((size_t)nv * SGP + 2 * (size_t)ne + (size_t)nv) + 16;
 }
 
-__global__ void __launch_bounds__(kThreadsB) pcg_staged_kernel(
-    DevGraph g, int32_t L, int64_t S, int32_t chunk, const double* __restrict__ diag,
+// One vertex's row of the interleaved search directions (SGP floats, 8- or
+// 16-byte aligned): a single vector access per vertex, no bank conflicts
+// from strided scalar accesses.
+template <int SGP>
+__device__ __forceinline__ void load_row(const float* p, float (&v)[SGP]) {
+  if constexpr (SGP == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int SGP>
+__device__ __forceinline__ void store_row(float* p, const float (&v)[SGP]) {
+  if constexpr (SGP == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+// Block sums of N floats; every thread sums the per-warp partials in the same
+// order, so all threads hold identical values without a broadcast.
+template <int N>
+__device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
+  warp_partials<float, N>(v, shw);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = sum_partials<kThreadsG, float>(shw, k, N);
+}
+
+// Mixed-precision PCG for one node and a group of SGP samples at a time: the
+// same FP32 Jacobi-scaled inner CG inside FP64 refinement as solve_system,
+// run for the group's samples together so that every load of the node's
+// matrix serves SGP samples. Thread t owns vertices t + k * kThreadsG
+// (k < VPT): their r, q and d stay in registers; only the search directions,
+// which neighbours read, are shared. Each sample keeps its own scalars,
+// stopping tests and iteration count; the CTA iterates while any sample of the
+// group is still working (every loop bounded by max_iter).
+template <int VPT, int SGP>
+__global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
+    DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const float* __restrict__ dscale_t,
     const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
     double rtol, int32_t max_iter, int32_t* __restrict__ iters, PcgStatus* status) {
-  __shared__ Shared<kThreadsB, float> shs;
-  extern __shared__ __align__(16) unsigned char sm[];
+  static_assert(SGP == 2 || SGP == 4, "sample groups of 2 or 4");
+  __shared__ float shw[2][(kThreadsG / 32) * SGP];
+  __shared__ double shd[(kThreadsG / 32 + 1) * 2 * SGP];
+  // per-sample scalars of the current refinement step, written by thread 0:
+  // stop threshold, sigma^2 = ||D^-1/2 r||^2, sigma, 1 / sigma, inner stop
+  __shared__ double tol2[SGP], sig2[SGP], sgm[SGP];
+  __shared__ float isg[SGP], in2[SGP];
+  extern __shared__ __align__(16) unsigned char grp_sm[];
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
-  int32_t* vptr = reinterpret_cast<int32_t*>(sm);
-  int32_t* nbr = vptr + nv + 1;
-  float* Ot = reinterpret_cast<float*>(nbr + ne2);
-  float* Ds = Ot + ne2;
-  const size_t a = 4 * ((size_t)nv + 1) + 8 * (size_t)ne2 + 4 * (size_t)nv;
-  unsigned char* vb = sm + ((a + 15) & ~(size_t)15);
-  SysVecs<float> v;
-  v.x = reinterpret_cast<double*>(vb);
-  v.d = reinterpret_cast<float*>(v.x + nv);
-  v.r = v.d + nv;
-  v.p = v.r + nv;
-  v.q = v.p + nv;
-  v.y = nullptr;
-  const int64_t nchunk = (S + chunk - 1) / chunk;
-  const int64_t units = (int64_t)L * nchunk;
+  float* P = reinterpret_cast<float*>(grp_sm);  // [nv][SGP]
+  float* Ot = P + (size_t)nv * SGP;             // [2E]
+  float* Ds = Ot + ne2;                         // [nv]
+  const int64_t ngrp = (S + SGP - 1) / SGP;
+  const int64_t units = (int64_t)L * ngrp;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t l = u / nchunk;
-    const int64_t s_begin = (u % nchunk) * chunk;
-    const int64_t s_end = s_begin + chunk < S ? s_begin + chunk : S;
-    __syncthreads();  // the previous unit is done with the staged matrix
-    for (int32_t i = threadIdx.x; i <= nv; i += kThreadsB) vptr[i] = g.vptr[i];
-    for (int64_t k = threadIdx.x; k < ne2; k += kThreadsB) {
-      nbr[k] = g.adj_nbr[k];
-      Ot[k] = offv_t[l * ne2 + k];
-    }
-    for (int32_t i = threadIdx.x; i < nv; i += kThreadsB) Ds[i] = dscale_t[l * nv + i];
+    const int64_t l = u / ngrp;
+    const int64_t s0 = (u % ngrp) * SGP;
+    const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
+    __syncthreads();  // the previous unit is done with the shared arrays
+    for (int64_t k = threadIdx.x; k < ne2; k += kThreadsG) Ot[k] = offv_t[l * ne2 + k];
+    for (int32_t v = threadIdx.x; v < nv; v += kThreadsG) Ds[v] = dscale_t[l * nv + v];
     __syncthreads();
-    SysMatrix<float> M{vptr, nbr, Ot, Ds, diag + l * nv, offv + l * ne2, nullptr, nullptr,
-                       nullptr};
-    for (int64_t s = s_begin; s < s_end; ++s) {
-      const int64_t sys = l * S + s;
-      const SysResult res = solve_system<kThreadsB, float>(nv, M, gvec + sys * nv,
-                                                           xout + sys * nv, v, false, rtol,
-                                                           max_iter, shs);
-      report<kThreadsB>(sys, res, iters, status);
+    const double* D = diag + l * nv;
+    const double* O = offv + l * ne2;
+    const double* gl = gvec + (l * S + s0) * nv;  // sample s at gl + s * nv
+    double* xl = xout + (l * S + s0) * nv;
+    double nrm[2 * SGP];
+#pragma unroll
+    for (int s = 0; s < 2 * SGP; ++s) nrm[s] = 0.0;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const int32_t v = threadIdx.x + k * kThreadsG;
+      if (v < nv) {
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          if (s < kv) {
+            const double gv = gl[(int64_t)s * nv + v];
+            const double sv = gv * (double)Ds[v];
+            nrm[s] += gv * gv;
+            nrm[SGP + s] += sv * sv;
+            xl[(int64_t)s * nv + v] = 0.0;
+          }
+        }
+      }
+    }
+    block_sum<kThreadsG, 2 * SGP>(nrm, shd);
+    bool act[SGP], done[SGP], bad[SGP];
+    int32_t its[SGP];
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) {
+        tol2[s] = rtol * rtol * nrm[s];
+        sig2[s] = nrm[SGP + s];
+        sgm[s] = sqrt(sig2[s]);
+        isg[s] = sgm[s] > 0.0 ? (float)(1.0 / sgm[s]) : 0.f;
+        in2[s] = (float)(kInnerRtol * kInnerRtol);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < SGP; ++s) {
+      bad[s] = s < kv && !(isfinite(nrm[s]) && isfinite(nrm[SGP + s]));
+      done[s] = s >= kv || (!bad[s] && !(nrm[s] > 0.0));
+      act[s] = !done[s] && !bad[s];
+      its[s] = 0;
+    }
+    float r[VPT][SGP], q[VPT][SGP], d[VPT][SGP];
+    int32_t it = 0;
+    bool first = true;
+    while (it < max_iter) {
+      if (!first) {  // FP64 residual of the current iterates
+        __syncthreads();
+        double acc[2 * SGP];
+#pragma unroll
+        for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.0;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * kThreadsG;
+          if (v < nv) {
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              float rs = 0.f;
+              if (act[s]) {
+                const double* xs = xl + (int64_t)s * nv;
+                double y = D[v] * xs[v];
+                for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
+                  y += O[kk] * xs[g.adj_nbr[kk]];
+                const double ri = gl[(int64_t)s * nv + v] - y;
+                const double si = ri * (double)Ds[v];
+                acc[s] += ri * ri;
+                acc[SGP + s] += si * si;
+                rs = (float)si;
+              }
+              r[k][s] = rs;
+            }
+          }
+        }
+        block_sum<kThreadsG, 2 * SGP>(acc, shd);
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          if (!act[s]) continue;
+          if (!isfinite(acc[s]) || !isfinite(acc[SGP + s])) {
+            bad[s] = true;
+            act[s] = false;
+          } else if (acc[s] <= tol2[s]) {
+            done[s] = true;
+            act[s] = false;
+          }
+        }
+        __syncthreads();  // every thread has read tol2
+        if (threadIdx.x == 0) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s) {
+            if (act[s]) {
+              sig2[s] = acc[SGP + s];
+              sgm[s] = sqrt(sig2[s]);
+              isg[s] = (float)(1.0 / sgm[s]);
+              // solve the correction only as far as this step needs (a tenth
+              // of the remaining ratio), never tighter than the FP32 floor
+              const double need = 0.1 * sqrt(tol2[s] / acc[s]);
+              const double e = need > kInnerRtol ? need : kInnerRtol;
+              in2[s] = (float)(e * e);
+            }
+          }
+        }
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * kThreadsG;
+#pragma unroll
+          for (int s = 0; s < SGP; ++s)
+            r[k][s] = (act[s] && v < nv) ? (float)(gl[(int64_t)s * nv + v] * (double)Ds[v]) : 0.f;
+        }
+      }
+      first = false;
+      bool any = false;
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) any = any || act[s];
+      if (!any) break;
+      // inner CG on the scaled system from d = 0, right-hand side of unit norm
+      float rz[SGP];
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) rz[s] = 0.f;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * kThreadsG;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          const float rk = act[s] ? r[k][s] * isg[s] : 0.f;
+          r[k][s] = rk;
+          d[k][s] = 0.f;
+          rz[s] += rk * rk;
+        }
+        if (v < nv) store_row<SGP>(P + (size_t)v * SGP, r[k]);
+      }
+      group_sum<SGP>(rz, shw[0]);
+      bool in[SGP];
+      float best[SGP];
+      int since[SGP];
+      bool anyin = false;
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) {
+        in[s] = act[s] && rz[s] > 0.f && isfinite(rz[s]);
+        best[s] = 1.f;
+        since[s] = 0;
+        anyin = anyin || in[s];
+      }
+      if (!anyin) break;  // nothing left to reduce in FP32: final test below
+      while (it < max_iter) {
+        ++it;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) its[s] += in[s] ? 1 : 0;
+        __syncthreads();  // P from the previous update is visible
+        float pq[SGP];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) pq[s] = 0.f;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * kThreadsG;
+          if (v < nv) {
+            float acc[SGP], pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) acc[s] = pv[s];
+            const int32_t kend = g.vptr[v + 1];
+            for (int32_t kk = g.vptr[v]; kk < kend; ++kk) {
+              const int32_t w = g.adj_nbr[kk];
+              const float o = Ot[kk];
+              if constexpr (SGP == 4) {
+                const float4 t = *reinterpret_cast<const float4*>(P + (size_t)w * 4);
+                acc[0] = fmaf(o, t.x, acc[0]);
+                acc[1] = fmaf(o, t.y, acc[1]);
+                acc[2] = fmaf(o, t.z, acc[2]);
+                acc[3] = fmaf(o, t.w, acc[3]);
+              } else {
+                const float2 t = *reinterpret_cast<const float2*>(P + (size_t)w * 2);
+                acc[0] = fmaf(o, t.x, acc[0]);
+                acc[1] = fmaf(o, t.y, acc[1]);
+              }
+            }
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              q[k][s] = acc[s];
+              pq[s] = fmaf(pv[s], acc[s], pq[s]);
+            }
+          }
+        }
+        group_sum<SGP>(pq, shw[0]);
+        float al[SGP];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          al[s] = 0.f;
+          if (!in[s]) continue;
+          if (!isfinite(pq[s])) {
+            bad[s] = true;
+            act[s] = false;
+            in[s] = false;
+          } else if (!(pq[s] > 0.f)) {
+            in[s] = false;  // p vanished at the FP32 floor: refine
+          } else {
+            al[s] = rz[s] / pq[s];
+          }
+        }
+        float rr[SGP];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) rr[s] = 0.f;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * kThreadsG;
+          if (v < nv) {
+            float pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              d[k][s] = fmaf(al[s], pv[s], d[k][s]);
+              r[k][s] = fmaf(-al[s], q[k][s], r[k][s]);
+              rr[s] = fmaf(r[k][s], r[k][s], rr[s]);
+            }
+          }
+        }
+        group_sum<SGP>(rr, shw[1]);
+        float be[SGP];
+        bool still = false;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          be[s] = 0.f;
+          if (!in[s]) continue;
+          if (!isfinite(rr[s])) {
+            bad[s] = true;
+            act[s] = false;
+            in[s] = false;
+          } else if (rr[s] <= in2[s]) {
+            in[s] = false;
+          } else {
+            if (rr[s] < 0.98f * best[s]) {
+              best[s] = rr[s];
+              since[s] = 0;
+            } else if (++since[s] >= 32) {
+              in[s] = false;  // the FP32 recurrence reached its rounding floor
+            }
+            be[s] = rr[s] / rz[s];
+            rz[s] = rr[s];
+          }
+          still = still || in[s];
+        }
+        if (!still) break;
+        // P = r + beta P for the samples still iterating (own rows only)
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * kThreadsG;
+          if (v < nv) {
+            float pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s)
+              if (in[s]) pv[s] = fmaf(be[s], pv[s], r[k][s]);
+            store_row<SGP>(P + (size_t)v * SGP, pv);
+          }
+        }
+      }
+      // x += sigma D^-1/2 d for the samples of this refinement step
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * kThreadsG;
+        if (v < nv) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s)
+            if (act[s]) xl[(int64_t)s * nv + v] += sgm[s] * (double)Ds[v] * (double)d[k][s];
+        }
+      }
+    }
+    // iteration budget spent or nothing left to reduce: FP64 test of the final iterates
+    bool pending = false;
+#pragma unroll
+    for (int s = 0; s < SGP; ++s) pending = pending || act[s];
+    if (pending) {
       __syncthreads();
+      double acc[SGP];
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) acc[s] = 0.0;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * kThreadsG;
+        if (v < nv) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s) {
+            if (act[s]) {
+              const double* xs = xl + (int64_t)s * nv;
+              double y = D[v] * xs[v];
+              for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
+                y += O[kk] * xs[g.adj_nbr[kk]];
+              const double ri = gl[(int64_t)s * nv + v] - y;
+              acc[s] += ri * ri;
+            }
+          }
+        }
+      }
+      block_sum<kThreadsG, SGP>(acc, shd);
+#pragma unroll
+      for (int s = 0; s < SGP; ++s)
+        if (act[s]) done[s] = acc[s] <= tol2[s];
+    }
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kv; ++s) {
+        iters[l * S + s0 + s] = its[s];
+        atomicAdd(&status->iters_total, (unsigned long long)its[s]);
+        atomicMax(&status->iters_max, its[s]);
+        if (bad[s]) atomicAdd(&status->numeric_flag, 1);
+        else if (!done[s]) atomicAdd(&status->n_unconverged, 1);
+      }
     }
   }
+}
+
+template <int VPT, int SGP>
+void launch_group(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
+                  const float* dscale_t, const float* offv_t, const double* gvec, double* x,
+                  double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
+                  cudaStream_t st) {
+  const size_t dyn = group_bytes<SGP>(g.nv, g.ne);
+  cudaFuncSetAttribute(pcg_group_kernel<VPT, SGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)dyn);
+  const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
+  const int blocks = (int)(units < 152 * 4 ? units : 152 * 4);
+  pcg_group_kernel<VPT, SGP><<<blocks, kThreadsG, dyn, st>>>(g, L, S, diag, offv, dscale_t,
+                                                             offv_t, gvec, x, rtol, max_iter,
+                                                             iters, status);
+}
+
+// The group layout applies when every vertex fits the per-thread register
+// arrays and the node's data fits shared memory.
+bool group_fits(const DevGraph& g) {
+  const int sgp = g.nv <= 4 * kThreadsG ? 4 : 2;
+  const size_t dyn = sgp == 4 ? group_bytes<4>(g.nv, g.ne) : group_bytes<2>(g.nv, g.ne);
+  return g.nv <= 8 * kThreadsG && dyn + 8 * 1024 <= kSmemMax;
 }
 
 }  // namespace
@@ -492,21 +860,15 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
                 cudaStream_t st) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
-    const size_t sb = staged_bytes(g.nv, g.ne) + sizeof(Shared<kThreadsB, float>);
-    if (sb <= kSmemMax && layout == 2 && !lp_es) {
-      // enough (node, sample-group) units to fill the GPU, one CTA per SM
-      int64_t groups = (2 * 152 + L - 1) / L;
-      if (groups > S) groups = S;
-      if (groups < 1) groups = 1;
-      const int32_t chunk = (int32_t)((S + groups - 1) / groups);
-      const int64_t units = (int64_t)L * ((S + chunk - 1) / chunk);
-      const size_t dyn = staged_bytes(g.nv, g.ne);
-      cudaFuncSetAttribute(pcg_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)dyn);
-      const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
-      pcg_staged_kernel<<<blocks, kThreadsB, dyn, st>>>(g, L, S, chunk, diag, offv, dscale_t,
-                                                        offv_t, gvec, x, rtol, max_iter, iters,
-                                                        status);
+    if (layout == 2 && !lp_es && group_fits(g)) {
+#define GRF_GROUP(VPT, SGP)                                                                   \
+  launch_group<VPT, SGP>(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter, iters, \
+                         status, st)
+      if (g.nv <= kThreadsG) GRF_GROUP(1, 4);
+      else if (g.nv <= 2 * kThreadsG) GRF_GROUP(2, 4);
+      else if (g.nv <= 4 * kThreadsG) GRF_GROUP(4, 4);
+      else GRF_GROUP(8, 2);
+#undef GRF_GROUP
       return;
     }
   }

@@ -189,6 +189,24 @@ def test_sample_pcg_layouts(layout, name):
     assert st["n_unconverged"] == 0
 
 
+@pytest.mark.parametrize("nx", [20, 30, 40, 50])
+def test_sample_group_pcg_every_vertex_split(nx):
+    """The sample-group PCG layout on grids of about 400, 870, 1550 and 2400
+    kept vertices: 1, 2, 4 and 8 vertices per thread (groups of 4, 4, 4 and 2
+    samples), with a ragged last sample group (S = 5)."""
+    g = gi.grid_deleted(nx, nx, 0.15, 2)
+    G, m = make(g, 0.5)
+    kappa, beta, k, seed, S = 1.5, 0.7, 0.5, 17, 5
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     pcg_layout="staged")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.5)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    u1, s1 = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                      pcg_layout="per_system")
+    assert rel_l2(u.cpu().numpy(), u1.cpu().numpy(), fem.lumped_mass(m)) < TOL["mixed"] / 10
+
+
 @pytest.mark.parametrize("precision,sg,interior", [
     ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
     ("mixed", 1, "spectral"), ("mixed", 4, "spectral")])
