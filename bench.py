@@ -365,7 +365,7 @@ def main():
     ap.add_argument("--workload", default="rgg2000", choices=sorted(gi.WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged"])
+    ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--use-graph", action="store_true",

@@ -107,6 +107,8 @@ typedef struct grf_options {
 #define GRF_PCG_AUTO 0
 #define GRF_PCG_PER_SYSTEM 1
 #define GRF_PCG_STAGED 2
+#define GRF_PCG_STAGED_PAIRS 3  /* as STAGED with 256-thread CTAs and groups of 2 samples:
+                                   more resident CTAs per SM, half the matrix reuse */
 
 typedef struct grf_stats {
   int64_t n_dofs;          /* N = |V_kept| + sum_e (n_e - 1) */

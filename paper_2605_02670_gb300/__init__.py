@@ -24,8 +24,9 @@ GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED = 0, 1
 PRECONDS = {"jacobi": GRF_PRECOND_JACOBI, "learned": GRF_PRECOND_LEARNED}
 GRF_LP_PARAMS = 25538
 GRF_OUT_F64, GRF_OUT_F32 = 0, 1
-GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED = 0, 1, 2
-PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged": GRF_PCG_STAGED}
+GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED, GRF_PCG_STAGED_PAIRS = 0, 1, 2, 3
+PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged": GRF_PCG_STAGED,
+               "staged_pairs": GRF_PCG_STAGED_PAIRS}
 GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL = 0, 1, 2
 INTERIORS = {"auto": GRF_INTERIOR_AUTO, "thomas": GRF_INTERIOR_THOMAS,
              "spectral": GRF_INTERIOR_SPECTRAL}

@@ -317,7 +317,7 @@ int read_opts(const grf_options* o, Opts* r) {
     return fail(GRF_EINVAL, "recover_sg must be 0, 1, 2 or 4 (got %d)", sg);
   r->recover_sg = sg == 0 ? 4 : sg;
   const int lay = o ? o->pcg_layout : GRF_PCG_AUTO;
-  if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED)
+  if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED_PAIRS)
     return fail(GRF_EINVAL, "unknown pcg_layout %d", lay);
   r->pcg_layout = lay == GRF_PCG_AUTO ? GRF_PCG_PER_SYSTEM : lay;
   r->precision = o ? o->precision : GRF_FP64;
@@ -1534,7 +1534,10 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   cudaStream_t st = (cudaStream_t)stream;
   const bool fp32 = o.precision == GRF_MIXED;
   std::vector<int> layouts = {GRF_PCG_PER_SYSTEM};
-  if (fp32) layouts.push_back(GRF_PCG_STAGED);
+  if (fp32) {
+    layouts.push_back(GRF_PCG_STAGED);
+    layouts.push_back(GRF_PCG_STAGED_PAIRS);
+  }
   // candidates (interior solver, recover_sg); recover_sg only matters for the
   // edges a solver leaves to the Thomas bins
   std::vector<std::pair<int, int>> cands;

@@ -443,7 +443,7 @@ constexpr int kThreadsG = 512;
 // 1 / sqrt(D) [nv].
 template <int SGP>
 __host__ __device__ inline size_t group_bytes(int32_t nv, int32_t ne) {
-  return 4 * ((size_t)nv * SGP + 2 * (size_t)ne + (size_t)nv) + 16;
+  return 4 * ((size_t)nv * SGP + 2 * (size_t)ne + (size_t)nv + (size_t)nv + 1) + 16;
 }
 
 // One vertex's row of the interleaved search directions (SGP floats, 8- or
@@ -467,14 +467,34 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[SGP]) {
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
 }
 
-// Block sums of N floats; every thread sums the per-warp partials in the same
-// order, so all threads hold identical values without a broadcast.
-template <int N>
+// Block sums of N floats (N = 2, 4 or 8): a warp butterfly, one row of N
+// partials per warp in shared memory (16-byte aligned rows), then every thread
+// adds the rows with vector loads in the same order, so all threads hold
+// identical values without a broadcast step.
+template <int NT, int N>
 __device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
-  warp_partials<float, N>(v, shw);
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2)
+      *reinterpret_cast<float2*>(shw + (threadIdx.x >> 5) * N + k) = make_float2(v[k], v[k + 1]);
+  }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = sum_partials<kThreadsG, float>(shw, k, N);
+  for (int k = 0; k < N; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(shw + w * N + k);
+      v[k] += t.x;
+      v[k + 1] += t.y;
+    }
+  }
 }
 
 // Mixed-precision PCG for one node and a group of SGP samples at a time: the
@@ -485,25 +505,30 @@ __device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
 // which neighbours read, are shared. Each sample keeps its own scalars,
 // stopping tests and iteration count; the CTA iterates while any sample of the
 // group is still working (every loop bounded by max_iter).
-template <int VPT, int SGP>
-__global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
+template <int NT, int VPT, int SGP>
+__global__ void __launch_bounds__(NT) pcg_group_kernel(
     DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const float* __restrict__ dscale_t,
     const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
     double rtol, int32_t max_iter, int32_t* __restrict__ iters, PcgStatus* status) {
   static_assert(SGP == 2 || SGP == 4, "sample groups of 2 or 4");
-  __shared__ float shw[2][(kThreadsG / 32) * SGP];
-  __shared__ double shd[(kThreadsG / 32 + 1) * 2 * SGP];
-  // per-sample scalars of the current refinement step, written by thread 0:
-  // stop threshold, sigma^2 = ||D^-1/2 r||^2, sigma, 1 / sigma, inner stop
-  __shared__ double tol2[SGP], sig2[SGP], sgm[SGP];
-  __shared__ float isg[SGP], in2[SGP];
+  __shared__ __align__(16) float shw[2][(NT / 32) * 2 * SGP];
+  __shared__ double shd[(NT / 32 + 1) * 2 * SGP];
+  // Per-sample scalars, written by thread 0. The refinement residual r is
+  // carried in FP32 in two normalised forms: r / ||g|| (stop test against
+  // rtol) and D^-1/2 r / sigma0 (sigma0 = ||D^-1/2 g||), so only S x and g - S x
+  // need FP64. igd = 1 / ||g||, cgs = ||g|| / sigma0, sgm = sigma of the
+  // current step, isg = sigma0 / sigma, in2 = inner stop.
+  __shared__ double igd[SGP], sgm0[SGP], isg0[SGP], sgm[SGP];
+  __shared__ float cgs[SGP], isg[SGP], in2[SGP];
   extern __shared__ __align__(16) unsigned char grp_sm[];
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
   float* P = reinterpret_cast<float*>(grp_sm);  // [nv][SGP]
   float* Ot = P + (size_t)nv * SGP;             // [2E]
   float* Ds = Ot + ne2;                         // [nv]
+  int32_t* vp = reinterpret_cast<int32_t*>(Ds + nv);  // [nv + 1] incidence offsets
+  for (int32_t v = threadIdx.x; v <= nv; v += NT) vp[v] = g.vptr[v];
   const int64_t ngrp = (S + SGP - 1) / SGP;
   const int64_t units = (int64_t)L * ngrp;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
@@ -511,8 +536,8 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
     const int64_t s0 = (u % ngrp) * SGP;
     const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
     __syncthreads();  // the previous unit is done with the shared arrays
-    for (int64_t k = threadIdx.x; k < ne2; k += kThreadsG) Ot[k] = offv_t[l * ne2 + k];
-    for (int32_t v = threadIdx.x; v < nv; v += kThreadsG) Ds[v] = dscale_t[l * nv + v];
+    for (int64_t k = threadIdx.x; k < ne2; k += NT) Ot[k] = offv_t[l * ne2 + k];
+    for (int32_t v = threadIdx.x; v < nv; v += NT) Ds[v] = dscale_t[l * nv + v];
     __syncthreads();
     const double* D = diag + l * nv;
     const double* O = offv + l * ne2;
@@ -523,7 +548,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
     for (int s = 0; s < 2 * SGP; ++s) nrm[s] = 0.0;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      const int32_t v = threadIdx.x + k * kThreadsG;
+      const int32_t v = threadIdx.x + k * NT;
       if (v < nv) {
 #pragma unroll
         for (int s = 0; s < SGP; ++s) {
@@ -537,20 +562,24 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
         }
       }
     }
-    block_sum<kThreadsG, 2 * SGP>(nrm, shd);
+    block_sum<NT, 2 * SGP>(nrm, shd);
     bool act[SGP], done[SGP], bad[SGP];
     int32_t its[SGP];
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int s = 0; s < SGP; ++s) {
-        tol2[s] = rtol * rtol * nrm[s];
-        sig2[s] = nrm[SGP + s];
-        sgm[s] = sqrt(sig2[s]);
-        isg[s] = sgm[s] > 0.0 ? (float)(1.0 / sgm[s]) : 0.f;
+        const double gn = sqrt(nrm[s]);
+        sgm0[s] = sqrt(nrm[SGP + s]);
+        isg0[s] = sgm0[s] > 0.0 ? 1.0 / sgm0[s] : 0.0;
+        sgm[s] = sgm0[s];
+        igd[s] = gn > 0.0 ? 1.0 / gn : 0.0;
+        cgs[s] = sgm0[s] > 0.0 ? (float)(gn / sgm0[s]) : 0.f;
+        isg[s] = 1.f;
         in2[s] = (float)(kInnerRtol * kInnerRtol);
       }
     }
     __syncthreads();
+    const float rtol2f = (float)(rtol * rtol);
 #pragma unroll
     for (int s = 0; s < SGP; ++s) {
       bad[s] = s < kv && !(isfinite(nrm[s]) && isfinite(nrm[SGP + s]));
@@ -562,14 +591,14 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
     int32_t it = 0;
     bool first = true;
     while (it < max_iter) {
-      if (!first) {  // FP64 residual of the current iterates
+      if (!first) {  // FP64 residual of the current iterates, normalised into FP32
         __syncthreads();
-        double acc[2 * SGP];
+        float acc[2 * SGP];
 #pragma unroll
-        for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.0;
+        for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.f;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-          const int32_t v = threadIdx.x + k * kThreadsG;
+          const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
 #pragma unroll
             for (int s = 0; s < SGP; ++s) {
@@ -579,39 +608,38 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
                 double y = D[v] * xs[v];
                 for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
                   y += O[kk] * xs[g.adj_nbr[kk]];
-                const double ri = gl[(int64_t)s * nv + v] - y;
-                const double si = ri * (double)Ds[v];
-                acc[s] += ri * ri;
-                acc[SGP + s] += si * si;
-                rs = (float)si;
+                const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+                rs = ri * Ds[v] * cgs[s];
+                acc[s] = fmaf(ri, ri, acc[s]);
+                acc[SGP + s] = fmaf(rs, rs, acc[SGP + s]);
               }
               r[k][s] = rs;
             }
           }
         }
-        block_sum<kThreadsG, 2 * SGP>(acc, shd);
+        group_sum<NT, 2 * SGP>(acc, shw[0]);
 #pragma unroll
         for (int s = 0; s < SGP; ++s) {
           if (!act[s]) continue;
           if (!isfinite(acc[s]) || !isfinite(acc[SGP + s])) {
             bad[s] = true;
             act[s] = false;
-          } else if (acc[s] <= tol2[s]) {
+          } else if (acc[s] <= rtol2f) {
             done[s] = true;
             act[s] = false;
           }
         }
-        __syncthreads();  // every thread has read tol2
+        __syncthreads();  // every thread is done with isg / sgm of the last step
         if (threadIdx.x == 0) {
 #pragma unroll
           for (int s = 0; s < SGP; ++s) {
             if (act[s]) {
-              sig2[s] = acc[SGP + s];
-              sgm[s] = sqrt(sig2[s]);
-              isg[s] = (float)(1.0 / sgm[s]);
+              const double ratio = sqrt((double)acc[SGP + s]);  // sigma / sigma0
+              sgm[s] = sgm0[s] * ratio;
+              isg[s] = (float)(1.0 / ratio);
               // solve the correction only as far as this step needs (a tenth
               // of the remaining ratio), never tighter than the FP32 floor
-              const double need = 0.1 * sqrt(tol2[s] / acc[s]);
+              const double need = 0.1 * rtol / sqrt((double)acc[s]);
               const double e = need > kInnerRtol ? need : kInnerRtol;
               in2[s] = (float)(e * e);
             }
@@ -621,10 +649,12 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
       } else {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-          const int32_t v = threadIdx.x + k * kThreadsG;
+          const int32_t v = threadIdx.x + k * NT;
 #pragma unroll
           for (int s = 0; s < SGP; ++s)
-            r[k][s] = (act[s] && v < nv) ? (float)(gl[(int64_t)s * nv + v] * (double)Ds[v]) : 0.f;
+            r[k][s] = (act[s] && v < nv)
+                          ? (float)(gl[(int64_t)s * nv + v] * (double)Ds[v] * isg0[s])
+                          : 0.f;
         }
       }
       first = false;
@@ -638,7 +668,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
       for (int s = 0; s < SGP; ++s) rz[s] = 0.f;
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
-        const int32_t v = threadIdx.x + k * kThreadsG;
+        const int32_t v = threadIdx.x + k * NT;
 #pragma unroll
         for (int s = 0; s < SGP; ++s) {
           const float rk = act[s] ? r[k][s] * isg[s] : 0.f;
@@ -648,7 +678,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
         }
         if (v < nv) store_row<SGP>(P + (size_t)v * SGP, r[k]);
       }
-      group_sum<SGP>(rz, shw[0]);
+      group_sum<NT, SGP>(rz, shw[0]);
       bool in[SGP];
       float best[SGP];
       int since[SGP];
@@ -671,27 +701,20 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
         for (int s = 0; s < SGP; ++s) pq[s] = 0.f;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-          const int32_t v = threadIdx.x + k * kThreadsG;
+          const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
             float acc[SGP], pv[SGP];
             load_row<SGP>(P + (size_t)v * SGP, pv);
 #pragma unroll
             for (int s = 0; s < SGP; ++s) acc[s] = pv[s];
-            const int32_t kend = g.vptr[v + 1];
-            for (int32_t kk = g.vptr[v]; kk < kend; ++kk) {
+            const int32_t kend = vp[v + 1];
+            for (int32_t kk = vp[v]; kk < kend; ++kk) {
               const int32_t w = g.adj_nbr[kk];
               const float o = Ot[kk];
-              if constexpr (SGP == 4) {
-                const float4 t = *reinterpret_cast<const float4*>(P + (size_t)w * 4);
-                acc[0] = fmaf(o, t.x, acc[0]);
-                acc[1] = fmaf(o, t.y, acc[1]);
-                acc[2] = fmaf(o, t.z, acc[2]);
-                acc[3] = fmaf(o, t.w, acc[3]);
-              } else {
-                const float2 t = *reinterpret_cast<const float2*>(P + (size_t)w * 2);
-                acc[0] = fmaf(o, t.x, acc[0]);
-                acc[1] = fmaf(o, t.y, acc[1]);
-              }
+              float pw[SGP];
+              load_row<SGP>(P + (size_t)w * SGP, pw);
+#pragma unroll
+              for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, pw[s], acc[s]);
             }
 #pragma unroll
             for (int s = 0; s < SGP; ++s) {
@@ -700,7 +723,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
             }
           }
         }
-        group_sum<SGP>(pq, shw[0]);
+        group_sum<NT, SGP>(pq, shw[0]);
         float al[SGP];
 #pragma unroll
         for (int s = 0; s < SGP; ++s) {
@@ -721,7 +744,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
         for (int s = 0; s < SGP; ++s) rr[s] = 0.f;
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-          const int32_t v = threadIdx.x + k * kThreadsG;
+          const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
             float pv[SGP];
             load_row<SGP>(P + (size_t)v * SGP, pv);
@@ -733,7 +756,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
             }
           }
         }
-        group_sum<SGP>(rr, shw[1]);
+        group_sum<NT, SGP>(rr, shw[1]);
         float be[SGP];
         bool still = false;
 #pragma unroll
@@ -762,7 +785,7 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
         // P = r + beta P for the samples still iterating (own rows only)
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-          const int32_t v = threadIdx.x + k * kThreadsG;
+          const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
             float pv[SGP];
             load_row<SGP>(P + (size_t)v * SGP, pv);
@@ -776,11 +799,11 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
       // x += sigma D^-1/2 d for the samples of this refinement step
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
-        const int32_t v = threadIdx.x + k * kThreadsG;
+        const int32_t v = threadIdx.x + k * NT;
         if (v < nv) {
 #pragma unroll
           for (int s = 0; s < SGP; ++s)
-            if (act[s]) xl[(int64_t)s * nv + v] += sgm[s] * (double)Ds[v] * (double)d[k][s];
+            if (act[s]) xl[(int64_t)s * nv + v] = fma(sgm[s], (double)(Ds[v] * d[k][s]), xl[(int64_t)s * nv + v]);
         }
       }
     }
@@ -790,12 +813,12 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
     for (int s = 0; s < SGP; ++s) pending = pending || act[s];
     if (pending) {
       __syncthreads();
-      double acc[SGP];
+      float acc[2 * SGP];
 #pragma unroll
-      for (int s = 0; s < SGP; ++s) acc[s] = 0.0;
+      for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.f;
 #pragma unroll
       for (int k = 0; k < VPT; ++k) {
-        const int32_t v = threadIdx.x + k * kThreadsG;
+        const int32_t v = threadIdx.x + k * NT;
         if (v < nv) {
 #pragma unroll
           for (int s = 0; s < SGP; ++s) {
@@ -804,16 +827,16 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
               double y = D[v] * xs[v];
               for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
                 y += O[kk] * xs[g.adj_nbr[kk]];
-              const double ri = gl[(int64_t)s * nv + v] - y;
-              acc[s] += ri * ri;
+              const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+              acc[s] = fmaf(ri, ri, acc[s]);
             }
           }
         }
       }
-      block_sum<kThreadsG, SGP>(acc, shd);
+      group_sum<NT, 2 * SGP>(acc, shw[0]);
 #pragma unroll
       for (int s = 0; s < SGP; ++s)
-        if (act[s]) done[s] = acc[s] <= tol2[s];
+        if (act[s]) done[s] = acc[s] <= rtol2f;
     }
     if (threadIdx.x == 0) {
       for (int s = 0; s < kv; ++s) {
@@ -827,19 +850,18 @@ __global__ void __launch_bounds__(kThreadsG) pcg_group_kernel(
   }
 }
 
-template <int VPT, int SGP>
+template <int NT, int VPT, int SGP>
 void launch_group(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
                   const float* dscale_t, const float* offv_t, const double* gvec, double* x,
                   double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
                   cudaStream_t st) {
   const size_t dyn = group_bytes<SGP>(g.nv, g.ne);
-  cudaFuncSetAttribute(pcg_group_kernel<VPT, SGP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)dyn);
+  cudaFuncSetAttribute(pcg_group_kernel<NT, VPT, SGP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
-  const int blocks = (int)(units < 152 * 4 ? units : 152 * 4);
-  pcg_group_kernel<VPT, SGP><<<blocks, kThreadsG, dyn, st>>>(g, L, S, diag, offv, dscale_t,
-                                                             offv_t, gvec, x, rtol, max_iter,
-                                                             iters, status);
+  const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
+  pcg_group_kernel<NT, VPT, SGP><<<blocks, NT, dyn, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
+                                                          gvec, x, rtol, max_iter, iters, status);
 }
 
 // The group layout applies when every vertex fits the per-thread register
@@ -860,14 +882,22 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
                 cudaStream_t st) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
-    if (layout == 2 && !lp_es && group_fits(g)) {
-#define GRF_GROUP(VPT, SGP)                                                                   \
-  launch_group<VPT, SGP>(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter, iters, \
-                         status, st)
-      if (g.nv <= kThreadsG) GRF_GROUP(1, 4);
-      else if (g.nv <= 2 * kThreadsG) GRF_GROUP(2, 4);
-      else if (g.nv <= 4 * kThreadsG) GRF_GROUP(4, 4);
-      else GRF_GROUP(8, 2);
+    if ((layout == 2 || layout == 3) && !lp_es && group_fits(g)) {
+#define GRF_GROUP(NT, VPT, SGP)                                                               \
+  launch_group<NT, VPT, SGP>(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter,  \
+                             iters, status, st)
+      if (layout == 2) {  // 512 threads, groups of 4 samples
+        if (g.nv <= kThreadsG) GRF_GROUP(512, 1, 4);
+        else if (g.nv <= 2 * kThreadsG) GRF_GROUP(512, 2, 4);
+        else if (g.nv <= 4 * kThreadsG) GRF_GROUP(512, 4, 4);
+        else GRF_GROUP(512, 8, 2);
+      } else {  // 256 threads, groups of 2 samples: more resident CTAs per SM
+        if (g.nv <= 256) GRF_GROUP(256, 1, 2);
+        else if (g.nv <= 512) GRF_GROUP(256, 2, 2);
+        else if (g.nv <= 1024) GRF_GROUP(256, 4, 2);
+        else if (g.nv <= 2048) GRF_GROUP(256, 8, 2);
+        else GRF_GROUP(512, 8, 2);
+      }
 #undef GRF_GROUP
       return;
     }

@@ -29,18 +29,17 @@
 namespace grf {
 namespace {
 
-constexpr int kSpecThreads = 128;
 constexpr int kSpecLChunk = 128;  // nodes staged per pass in the recovery
 
-// sin(pi k / (m+1)) for k < 2(m+1) (argument reduced to [0, 1/2] before
-// rounding), the mode shifts sig_j = 4 sin^2(pi j / (2(m+1))), j = 1..m.
-__device__ __forceinline__ void spec_tables(int32_t m, float* tab, float* sig) {
+// sin(pi k / (m+1)) and cos(pi k / (m+1)) for k < 2(m+1), the mode shifts
+// sig_j = 4 sin^2(pi j / (2(m+1))), j = 1..m.
+__device__ __forceinline__ void spec_tables(int32_t m, float* tab, float* ctab, float* sig) {
   const int32_t P = 2 * (m + 1);
   for (int32_t k = threadIdx.x; k < P; k += blockDim.x) {
-    int32_t kk = k < m + 1 ? k : k - (m + 1);  // sin(pi (k - (m+1)) / (m+1)) = -sin(...)
-    const float sgn = k < m + 1 ? 1.f : -1.f;
-    kk = kk <= (m + 1) / 2 ? kk : (m + 1) - kk;  // sin(pi x) = sin(pi (1 - x))
-    tab[k] = sgn * sinpif((float)kk / (float)(m + 1));
+    float sn, cs;
+    sincospif((float)k / (float)(m + 1), &sn, &cs);
+    tab[k] = sn;
+    ctab[k] = cs;
   }
   for (int32_t j = threadIdx.x; j < m; j += blockDim.x) {
     const float sh = 2.f * sinpif((float)(j + 1) / (float)(2 * (m + 1)));
@@ -48,26 +47,53 @@ __device__ __forceinline__ void spec_tables(int32_t m, float* tab, float* sig) {
   }
 }
 
-// acc[s] = sum_{i=1..m} sin(pi i j / (m+1)) src[i-1][s]   (table index i j mod P)
-template <int SG>
-__device__ __forceinline__ void dst_row(int32_t m, int32_t j, const float* tab,
-                                        const float* src, float (&acc)[SG]) {
+// acc[q][s] = sum_{i=1..m} sin(pi i j_q / (m+1)) src[i-1][s] for the thread's QJ
+// indices j_q (1-based; j_q = 0 gives zeros). The pair (cos, sin)(pi i j_q / (m+1))
+// advances by a rotation through pi j_q / (m+1) and is re-read from the tables
+// every 32 steps, so the rounding drift stays within a few dozen ulp; the rows
+// of src are loaded once for the QJ indices.
+template <int SG, int QJ>
+__device__ __forceinline__ void dst_rows(int32_t m, const int32_t (&j)[QJ], const float* tab,
+                                         const float* ctab, const float* src,
+                                         float (&acc)[QJ][SG]) {
   const int32_t P = 2 * (m + 1);
+  float c1[QJ], s1[QJ], cs[QJ], sn[QJ];
+  int32_t idx[QJ];
 #pragma unroll
-  for (int s = 0; s < SG; ++s) acc[s] = 0.f;
-  int32_t idx = 0;
+  for (int q = 0; q < QJ; ++q) {
+    c1[q] = ctab[j[q]];
+    s1[q] = tab[j[q]];
+    cs[q] = 1.f;
+    sn[q] = 0.f;
+    idx[q] = 0;
+#pragma unroll
+    for (int s = 0; s < SG; ++s) acc[q][s] = 0.f;
+  }
   for (int32_t i = 0; i < m; ++i) {
-    idx += j;
-    if (idx >= P) idx -= P;
-    const float f = tab[idx];
+#pragma unroll
+    for (int q = 0; q < QJ; ++q) {
+      idx[q] += j[q];
+      if (idx[q] >= P) idx[q] -= P;
+      if ((i & 31) == 0) {
+        cs[q] = ctab[idx[q]];
+        sn[q] = tab[idx[q]];
+      } else {
+        const float c = cs[q] * c1[q] - sn[q] * s1[q];
+        sn[q] = fmaf(sn[q], c1[q], cs[q] * s1[q]);
+        cs[q] = c;
+      }
+    }
     const float4* row = reinterpret_cast<const float4*>(src + (size_t)i * SG);
 #pragma unroll
-    for (int q = 0; q < SG / 4; ++q) {
-      const float4 v = row[q];
-      acc[4 * q + 0] = fmaf(f, v.x, acc[4 * q + 0]);
-      acc[4 * q + 1] = fmaf(f, v.y, acc[4 * q + 1]);
-      acc[4 * q + 2] = fmaf(f, v.z, acc[4 * q + 2]);
-      acc[4 * q + 3] = fmaf(f, v.w, acc[4 * q + 3]);
+    for (int p = 0; p < SG / 4; ++p) {
+      const float4 v = row[p];
+#pragma unroll
+      for (int q = 0; q < QJ; ++q) {
+        acc[q][4 * p + 0] = fmaf(sn[q], v.x, acc[q][4 * p + 0]);
+        acc[q][4 * p + 1] = fmaf(sn[q], v.y, acc[q][4 * p + 1]);
+        acc[q][4 * p + 2] = fmaf(sn[q], v.z, acc[q][4 * p + 2]);
+        acc[q][4 * p + 3] = fmaf(sn[q], v.w, acc[q][4 * p + 3]);
+      }
     }
   }
 }
@@ -86,15 +112,34 @@ __device__ __forceinline__ void spec_acc(float r, const float* rowp, float (&a)[
   }
 }
 
+// a[s] += r * row[s], b[s] += t * row[s]
+template <int SG>
+__device__ __forceinline__ void spec_acc2(float r, float t, const float* rowp, float (&a)[SG],
+                                          float (&b)[SG]) {
+  const float4* row = reinterpret_cast<const float4*>(rowp);
+#pragma unroll
+  for (int q = 0; q < SG / 4; ++q) {
+    const float4 v = row[q];
+    a[4 * q + 0] = fmaf(r, v.x, a[4 * q + 0]);
+    a[4 * q + 1] = fmaf(r, v.y, a[4 * q + 1]);
+    a[4 * q + 2] = fmaf(r, v.z, a[4 * q + 2]);
+    a[4 * q + 3] = fmaf(r, v.w, a[4 * q + 3]);
+    b[4 * q + 0] = fmaf(t, v.x, b[4 * q + 0]);
+    b[4 * q + 1] = fmaf(t, v.y, b[4 * q + 1]);
+    b[4 * q + 2] = fmaf(t, v.z, b[4 * q + 2]);
+    b[4 * q + 3] = fmaf(t, v.w, b[4 * q + 3]);
+  }
+}
+
 template <int SG>
 __host__ __device__ constexpr size_t spec_condense_floats(int32_t mmax) {
-  return 2 * ((size_t)mmax + 1) + (size_t)mmax + 2 * (size_t)mmax * SG + 4;
+  return 4 * ((size_t)mmax + 1) + (size_t)mmax + 2 * (size_t)mmax * SG + 4;
 }
 
 // Forward transform of the edge's noise (written to bhat, rows like b) and
 // the two end values of T_l^-1 b_I for every node, added into gvec.
-template <int SG>
-__global__ void __launch_bounds__(kSpecThreads)
+template <int SG, int QJ>
+__global__ void __launch_bounds__(256)
     spec_condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                          const float* __restrict__ b, const int32_t* __restrict__ edges,
                          int32_t n_edges, int32_t mmax, float* __restrict__ bhat,
@@ -102,8 +147,9 @@ __global__ void __launch_bounds__(kSpecThreads)
   extern __shared__ __align__(16) float spec_sm[];
   float* bs = spec_sm;                          // [mmax][SG] noise rows
   float* bt = bs + (size_t)mmax * SG;           // [mmax][SG] phi_j bh_j
-  float* tab = bt + (size_t)mmax * SG;          // [2 (mmax + 1)]
-  float* sig = tab + 2 * ((size_t)mmax + 1);    // [mmax]
+  float* tab = bt + (size_t)mmax * SG;          // [2 (mmax + 1)] sin
+  float* ctab = tab + 2 * ((size_t)mmax + 1);   // [2 (mmax + 1)] cos
+  float* sig = ctab + 2 * ((size_t)mmax + 1);   // [mmax]
   const int64_t nsg = (S + SG - 1) / SG;
   const int64_t units = (int64_t)n_edges * nsg;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
@@ -113,7 +159,7 @@ __global__ void __launch_bounds__(kSpecThreads)
     const int64_t off = g.ioff[e];
     const int kv = (int)(S - s0 < SG ? S - s0 : SG);
     __syncthreads();  // the previous unit is done with the shared arrays
-    spec_tables(m, tab, sig);
+    spec_tables(m, tab, ctab, sig);
     const float* bI = b + (g.nv + off) * S + s0;
     for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
       const int32_t i = t / SG, s = t - i * SG;
@@ -121,37 +167,61 @@ __global__ void __launch_bounds__(kSpecThreads)
     }
     __syncthreads();
     const float scale = sqrtf(2.f / (float)(m + 1));
-    for (int32_t j = threadIdx.x; j < m; j += blockDim.x) {
-      float acc[SG];
-      dst_row<SG>(m, j + 1, tab, bs, acc);
-      const float phi = scale * tab[j + 1];
-      float* bo = bhat + (off + j) * S + s0;
+    // forward transform: modes t + q blockDim (q < QJ) per thread share every
+    // row load; the bin's QJ blockDim >= m, so one pass covers the edge
+    for (int32_t jb = 0; jb < m; jb += QJ * blockDim.x) {
+      int32_t jj[QJ];
 #pragma unroll
-      for (int s = 0; s < SG; ++s) {
-        const float bh = scale * acc[s];
-        if (s < kv) bo[s] = bh;
-        bt[(size_t)j * SG + s] = phi * bh;
+      for (int q = 0; q < QJ; ++q) {
+        const int32_t j = jb + q * blockDim.x + threadIdx.x;
+        jj[q] = j < m ? j + 1 : 0;
+      }
+      if (jj[0] == 0) continue;
+      float acc[QJ][SG];
+      dst_rows<SG, QJ>(m, jj, tab, ctab, bs, acc);
+#pragma unroll
+      for (int q = 0; q < QJ; ++q) {
+        if (jj[q] == 0) continue;
+        const int32_t j = jj[q] - 1;
+        const float phi = scale * tab[j + 1];
+        float* bo = bhat + (off + j) * S + s0;
+#pragma unroll
+        for (int s = 0; s < SG; ++s) {
+          const float bh = scale * acc[q][s];
+          if (s < kv) bo[s] = bh;
+          bt[(size_t)j * SG + s] = phi * bh;
+        }
       }
     }
     __syncthreads();
     const double h = g.he[e];
     const int32_t va = g.eu[e], vb = g.ev[e];
-    for (int32_t l = threadIdx.x; l < nd.L; l += blockDim.x) {
-      const float dl = (float)((nd.alpha[l] / nd.gamma[l] + kappa2) * h * h);
-      float od[SG], ev[SG];
+    // end values: two nodes per thread share every row load
+    for (int32_t l0 = 2 * threadIdx.x; l0 < nd.L; l0 += 2 * blockDim.x) {
+      const bool two = l0 + 1 < nd.L;
+      const float dl0 = (float)((nd.alpha[l0] / nd.gamma[l0] + kappa2) * h * h);
+      const float dl1 = two ? (float)((nd.alpha[l0 + 1] / nd.gamma[l0 + 1] + kappa2) * h * h) : 1.f;
+      float od[2][SG], ev[2][SG];
 #pragma unroll
-      for (int s = 0; s < SG; ++s) od[s] = ev[s] = 0.f;
+      for (int s = 0; s < SG; ++s) od[0][s] = ev[0][s] = od[1][s] = ev[1][s] = 0.f;
       // modes j + 1 in pairs: odd mode (j even) into od, even mode into ev
       for (int32_t j = 0; j < m; j += 2) {
-        spec_acc<SG>(__fdividef(1.f, dl + sig[j]), bt + (size_t)j * SG, od);
-        if (j + 1 < m) spec_acc<SG>(__fdividef(1.f, dl + sig[j + 1]), bt + (size_t)(j + 1) * SG, ev);
+        spec_acc2<SG>(__fdividef(1.f, dl0 + sig[j]), __fdividef(1.f, dl1 + sig[j]),
+                      bt + (size_t)j * SG, od[0], od[1]);
+        if (j + 1 < m)
+          spec_acc2<SG>(__fdividef(1.f, dl0 + sig[j + 1]), __fdividef(1.f, dl1 + sig[j + 1]),
+                        bt + (size_t)(j + 1) * SG, ev[0], ev[1]);
       }
-      double* gl = gvec + ((int64_t)l * S + s0) * g.nv;
 #pragma unroll
-      for (int s = 0; s < SG; ++s) {
-        if (s < kv) {
-          atomicAdd(gl + (int64_t)s * g.nv + va, (double)(od[s] + ev[s]));
-          atomicAdd(gl + (int64_t)s * g.nv + vb, (double)(od[s] - ev[s]));
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
+        double* gl = gvec + ((int64_t)(l0 + q) * S + s0) * g.nv;
+#pragma unroll
+        for (int s = 0; s < SG; ++s) {
+          if (s < kv) {
+            atomicAdd(gl + (int64_t)s * g.nv + va, (double)(od[q][s] + ev[q][s]));
+            atomicAdd(gl + (int64_t)s * g.nv + vb, (double)(od[q][s] - ev[q][s]));
+          }
         }
       }
     }
@@ -160,13 +230,13 @@ __global__ void __launch_bounds__(kSpecThreads)
 
 template <int SG>
 __host__ __device__ constexpr size_t spec_recover_floats(int32_t mmax) {
-  return (size_t)mmax * SG + 2 * ((size_t)mmax + 1) + (size_t)mmax +
+  return (size_t)mmax * SG + 4 * ((size_t)mmax + 1) + (size_t)mmax +
          (size_t)kSpecLChunk * (2 + 2 * SG) + 4;
 }
 
 // U_I = Phi c with c from bhat and the weighted vertex values xw = w_l u_v^(l).
-template <int SG, typename OutT>
-__global__ void __launch_bounds__(kSpecThreads)
+template <int SG, int QJ, typename OutT>
+__global__ void __launch_bounds__(256)
     spec_recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                         const int32_t* __restrict__ edges, int32_t n_edges, int32_t mmax,
                         const float* __restrict__ bhat, const float* __restrict__ xw,
@@ -177,11 +247,12 @@ __global__ void __launch_bounds__(kSpecThreads)
   float* xm = xp + (size_t)kSpecLChunk * SG;      // [chunk][SG] xa - xb
   float* dls = xm + (size_t)kSpecLChunk * SG;     // [chunk] delta_l
   float* scs = dls + kSpecLChunk;                 // [chunk] sc_l
-  float* tab = scs + kSpecLChunk;                 // [2 (mmax + 1)]
-  float* sig = tab + 2 * ((size_t)mmax + 1);      // [mmax]
+  float* tab = scs + kSpecLChunk;                 // [2 (mmax + 1)] sin
+  float* ctab = tab + 2 * ((size_t)mmax + 1);     // [2 (mmax + 1)] cos
+  float* sig = ctab + 2 * ((size_t)mmax + 1);     // [mmax]
   const int64_t nsg = (S + SG - 1) / SG;
   const int64_t units = (int64_t)n_edges * nsg;
-  constexpr int kJ = 2;  // modes per thread held in registers (pass over l shared)
+  constexpr int kJ = QJ;  // modes per thread held in registers (pass over l shared)
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int32_t e = edges[u / nsg];
     const int64_t s0 = (u % nsg) * SG;
@@ -191,7 +262,7 @@ __global__ void __launch_bounds__(kSpecThreads)
     const double h = g.he[e];
     const int32_t va = g.eu[e], vb = g.ev[e];
     __syncthreads();
-    spec_tables(m, tab, sig);
+    spec_tables(m, tab, ctab, sig);
     const float* bh = bhat + off * S + s0;
     for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
       const int32_t i = t / SG, s = t - i * SG;
@@ -255,13 +326,25 @@ __global__ void __launch_bounds__(kSpecThreads)
       }
     }
     __syncthreads();
-    for (int32_t i = threadIdx.x; i < m; i += blockDim.x) {
-      float acc[SG];
-      dst_row<SG>(m, i + 1, tab, cs, acc);
-      OutT* o = out + (int64_t)s0 * g.n + g.nv + off + i;
+    // inverse transform: output nodes t + q blockDim (q < QJ) per thread
+    for (int32_t ib = 0; ib < m; ib += QJ * blockDim.x) {
+      int32_t ii[QJ];
 #pragma unroll
-      for (int s = 0; s < SG; ++s)
-        if (s < kv) o[(int64_t)s * g.n] = (OutT)(scale * acc[s]);
+      for (int q = 0; q < QJ; ++q) {
+        const int32_t i = ib + q * blockDim.x + threadIdx.x;
+        ii[q] = i < m ? i + 1 : 0;
+      }
+      if (ii[0] == 0) continue;
+      float acc[QJ][SG];
+      dst_rows<SG, QJ>(m, ii, tab, ctab, cs, acc);
+#pragma unroll
+      for (int q = 0; q < QJ; ++q) {
+        if (ii[q] == 0) continue;
+        OutT* o = out + (int64_t)s0 * g.n + g.nv + off + ii[q] - 1;
+#pragma unroll
+        for (int s = 0; s < SG; ++s)
+          if (s < kv) o[(int64_t)s * g.n] = (OutT)(scale * acc[q][s]);
+      }
     }
   }
 }
@@ -273,28 +356,47 @@ int grid_units(int64_t units) {
 
 }  // namespace
 
+// Spectral bins: interior-node limit, threads per CTA and modes per thread
+// (threads x modes >= limit: one pass over the edge per transform).
+struct SpecBin {
+  int32_t mmax, threads, qj;
+};
+constexpr SpecBin kSpecBins[] = {{64, 128, 1},  {128, 128, 1}, {256, 128, 2}, {384, 128, 3},
+                                 {512, 128, 4}, {768, 256, 3}, {1024, 256, 4}};
+constexpr int kNumSpecBins = sizeof(kSpecBins) / sizeof(kSpecBins[0]);
+
 int spec_bins(int32_t* mmax) {
-  static const int32_t mm[] = {32, 64, 128, 256, 512, 1024};
-  for (int i = 0; i < 6; ++i) mmax[i] = mm[i];
-  return 6;
+  for (int i = 0; i < kNumSpecBins; ++i) mmax[i] = kSpecBins[i].mmax;
+  return kNumSpecBins;
+}
+
+template <int QJ>
+void spec_condense_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                       const float* b, const int32_t* e, int32_t n, const SpecBin& bin,
+                       float* bhat, double* gvec, cudaStream_t st) {
+  const size_t smem = spec_condense_floats<kSpecSG>(bin.mmax) * sizeof(float);
+  cudaFuncSetAttribute(spec_condense_kernel<kSpecSG, QJ>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
+  spec_condense_kernel<kSpecSG, QJ><<<grid_units(units), bin.threads, smem, st>>>(
+      g, nd, kappa2, S, b, e, n, bin.mmax, bhat, gvec);
 }
 
 int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                          const float* b, const int32_t* bin_edges, const int32_t* bin_count,
                          float* bhat, double* gvec, cudaStream_t st) {
-  int32_t mm[kMaxBins];
-  const int nb = spec_bins(mm);
   const int32_t* e = bin_edges;
   int launches = 0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = 0; i < kNumSpecBins; ++i) {
     const int32_t n = bin_count[i];
     if (n > 0) {
-      const size_t smem = spec_condense_floats<kSpecSG>(mm[i]) * sizeof(float);
-      cudaFuncSetAttribute(spec_condense_kernel<kSpecSG>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-      spec_condense_kernel<kSpecSG><<<grid_units(units), kSpecThreads, smem, st>>>(
-          g, nd, kappa2, S, b, e, n, mm[i], bhat, gvec);
+      const SpecBin& bn = kSpecBins[i];
+      switch (bn.qj) {
+        case 1: spec_condense_bin<1>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 2: spec_condense_bin<2>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 3: spec_condense_bin<3>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        default: spec_condense_bin<4>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+      }
       ++launches;
     }
     e += n;
@@ -302,23 +404,34 @@ int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, i
   return launches;
 }
 
+template <int QJ, typename OutT>
+void spec_recover_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                      const int32_t* e, int32_t n, const SpecBin& bin, const float* bhat,
+                      const float* xw, OutT* out, cudaStream_t st) {
+  const size_t smem = spec_recover_floats<kSpecSG>(bin.mmax) * sizeof(float);
+  cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, QJ, OutT>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
+  spec_recover_kernel<kSpecSG, QJ, OutT><<<grid_units(units), bin.threads, smem, st>>>(
+      g, nd, kappa2, S, e, n, bin.mmax, bhat, xw, out);
+}
+
 template <typename OutT>
 int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                         const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
                         const float* xw, OutT* out, cudaStream_t st) {
-  int32_t mm[kMaxBins];
-  const int nb = spec_bins(mm);
   const int32_t* e = bin_edges;
   int launches = 0;
-  for (int i = 0; i < nb; ++i) {
+  for (int i = 0; i < kNumSpecBins; ++i) {
     const int32_t n = bin_count[i];
     if (n > 0) {
-      const size_t smem = spec_recover_floats<kSpecSG>(mm[i]) * sizeof(float);
-      cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, OutT>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-      spec_recover_kernel<kSpecSG, OutT><<<grid_units(units), kSpecThreads, smem, st>>>(
-          g, nd, kappa2, S, e, n, mm[i], bhat, xw, out);
+      const SpecBin& bn = kSpecBins[i];
+      switch (bn.qj) {
+        case 1: spec_recover_bin<1, OutT>(g, nd, kappa2, S, e, n, bn, bhat, xw, out, st); break;
+        case 2: spec_recover_bin<2, OutT>(g, nd, kappa2, S, e, n, bn, bhat, xw, out, st); break;
+        case 3: spec_recover_bin<3, OutT>(g, nd, kappa2, S, e, n, bn, bhat, xw, out, st); break;
+        default: spec_recover_bin<4, OutT>(g, nd, kappa2, S, e, n, bn, bhat, xw, out, st); break;
+      }
       ++launches;
     }
     e += n;

@@ -176,7 +176,7 @@ def test_sample_matches_oracle(precision, interior, name, beta):
     assert st["n_unconverged"] == 0
 
 
-@pytest.mark.parametrize("layout", ["per_system", "staged"])
+@pytest.mark.parametrize("layout", ["per_system", "staged", "staged_pairs"])
 @pytest.mark.parametrize("name", ["square5", "random12", "isolated"])
 def test_sample_pcg_layouts(layout, name):
     g, h = GRAPHS[name]()
@@ -189,16 +189,18 @@ def test_sample_pcg_layouts(layout, name):
     assert st["n_unconverged"] == 0
 
 
-@pytest.mark.parametrize("nx", [20, 30, 40, 50])
-def test_sample_group_pcg_every_vertex_split(nx):
-    """The sample-group PCG layout on grids of about 400, 870, 1550 and 2400
-    kept vertices: 1, 2, 4 and 8 vertices per thread (groups of 4, 4, 4 and 2
-    samples), with a ragged last sample group (S = 5)."""
+@pytest.mark.parametrize("layout", ["staged", "staged_pairs"])
+@pytest.mark.parametrize("nx", [12, 20, 30, 40, 50])
+def test_sample_group_pcg_every_vertex_split(nx, layout):
+    """The sample-group PCG layouts on grids of about 144, 400, 870, 1550 and
+    2400 kept vertices: every vertices-per-thread split of the 512-thread
+    groups of 4 samples and of the 256-thread pairs, with a ragged last sample
+    group (S = 5)."""
     g = gi.grid_deleted(nx, nx, 0.15, 2)
     G, m = make(g, 0.5)
     kappa, beta, k, seed, S = 1.5, 0.7, 0.5, 17, 5
     u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
-                     pcg_layout="staged")
+                     pcg_layout=layout)
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.5)
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
@@ -290,7 +292,8 @@ def test_autotune_returns_working_knobs():
     g, h = GRAPHS["random12"]()
     G, m = make(g, h)
     knobs, ms = G.autotune(3.0, 0.7, 0.5, 8, precision="mixed")
-    assert knobs["pcg_layout"] in ("per_system", "staged") and knobs["recover_sg"] in (1, 2, 4)
+    assert knobs["pcg_layout"] in ("per_system", "staged", "staged_pairs")
+    assert knobs["recover_sg"] in (1, 2, 4) and knobs["interior"] in ("thomas", "spectral")
     assert ms > 0
     u, _ = G.sample(3.0, 0.7, 0.5, 9, 8, precision="mixed", out_dtype="f64", **knobs)
     _, ref, _ = sampler.sample(g, 3.0, 0.7, 0.5, 9, 8, h=h)
