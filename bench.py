@@ -190,6 +190,11 @@ def algorithmic(w, G, stats, phase, S, tsize, out_size):
         return N * S * tsize + N * 8, "hbm"
     if phase == "pcg":
         it = stats["pcg_iters_total"]
+        if L * S * V * 8 <= L2_BYTES:
+            # the vertex vectors of every system stay on chip (shared memory and
+            # registers of the sample-group layout): bounded by the FP32 work,
+            # SpMV 2 (|V| + 2|E|) + dots and updates ~10 |V| flops per iteration
+            return it * (2 * (V + 2 * E) + 10 * V), "alu"
         return it * 10 * V * 8 + (it / S) * ((V + 2 * E) * 8 + 2 * E * 4), "hbm"
     if phase == "recover":
         # FP32 FMA work: ~6 flops per (interior node, quadrature node, sample)
@@ -285,7 +290,7 @@ def run_grf(args, w, graph):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         grf.grf_sample_host(G.handle, w.kappa, w.beta, w.k_step, seed0 + 10_000 + i, S,
-                            host.numpy(), grf.make_options(prec, out_dtype), stream)
+                            host.numpy(), grf.make_options(prec, out_dtype, **knobs), stream)
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t)
     if dist:
@@ -314,8 +319,11 @@ def run_grf(args, w, graph):
     roof = {}
     work, bound = algorithmic(w, G, st, dom, S, tsize, osz)
     dur_s = mean_ph[dom] / 1000.0
-    kernel_file = {"noise": "noise.cu", "schur": "schur.cu", "condense": "thomas.cu",
-                   "pcg": "pcg.cu", "recover": "thomas.cu"}.get(dom, "api.cu")
+    spectral = knobs.get("interior", "spectral" if prec == "mixed" else "thomas") == "spectral"
+    kernel_file = {"noise": "noise.cu", "schur": "schur.cu",
+                   "condense": "spectral.cu" if spectral else "thomas.cu",
+                   "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else "recover.cu",
+                   "precond_net": "learned.cu"}.get(dom, "api.cu")
     if bound == "hbm":
         ach = work / dur_s / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",

@@ -59,6 +59,10 @@ extern "C" {
 #define GRF_PRECOND_JACOBI 0   /* z = D^-1 r */
 #define GRF_PRECOND_LEARNED 1  /* z = B B^T r on the Jacobi-scaled system, B from the network
                                   of grf_precond_* (GRF_MIXED only; see below) */
+#define GRF_PRECOND_NEUMANN 2  /* the paper's Neumann-Neumann preconditioner (Sec. 3, Phase 4,
+                                  Neumann step): z = D_G^-1 (sum_e (S^(e))^-1) D_G^-1 r with
+                                  D_G = diag(vertex degree) and the exact 2x2 edge blocks
+                                  S^(e); on the Jacobi-scaled system in GRF_MIXED */
 
 #define GRF_OUT_F64 0
 #define GRF_OUT_F32 1
@@ -67,7 +71,7 @@ typedef struct grf_graph grf_graph;
 
 typedef struct grf_options {
   int32_t precision;   /* GRF_FP64 or GRF_MIXED */
-  int32_t precond;     /* GRF_PRECOND_JACOBI or GRF_PRECOND_LEARNED */
+  int32_t precond;     /* GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED or GRF_PRECOND_NEUMANN */
   int32_t out_dtype;   /* GRF_OUT_F64 or GRF_OUT_F32 */
   int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
   double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libgrf.so")
 
 GRF_OK, GRF_EINVAL, GRF_ENOMEM, GRF_ENOCONV, GRF_ECUDA, GRF_ENOTSUP, GRF_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
 GRF_FP64, GRF_MIXED = 0, 1
-GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED = 0, 1
-PRECONDS = {"jacobi": GRF_PRECOND_JACOBI, "learned": GRF_PRECOND_LEARNED}
+GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED, GRF_PRECOND_NEUMANN = 0, 1, 2
+PRECONDS = {"jacobi": GRF_PRECOND_JACOBI, "learned": GRF_PRECOND_LEARNED,
+            "neumann": GRF_PRECOND_NEUMANN}
 GRF_LP_PARAMS = 25538
 GRF_OUT_F64, GRF_OUT_F32 = 0, 1
 GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED, GRF_PCG_STAGED_PAIRS = 0, 1, 2, 3

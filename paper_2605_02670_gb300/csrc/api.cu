@@ -319,7 +319,9 @@ int read_opts(const grf_options* o, Opts* r) {
   const int lay = o ? o->pcg_layout : GRF_PCG_AUTO;
   if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED_PAIRS)
     return fail(GRF_EINVAL, "unknown pcg_layout %d", lay);
-  r->pcg_layout = lay == GRF_PCG_AUTO ? GRF_PCG_PER_SYSTEM : lay;
+  // AUTO: the sample-group layout where it applies (launch_pcg falls back to
+  // one CTA per system otherwise)
+  r->pcg_layout = lay == GRF_PCG_AUTO ? GRF_PCG_STAGED : lay;
   r->precision = o ? o->precision : GRF_FP64;
   r->precond = o ? o->precond : GRF_PRECOND_JACOBI;
   r->out_dtype = o ? o->out_dtype : GRF_OUT_F64;
@@ -327,7 +329,8 @@ int read_opts(const grf_options* o, Opts* r) {
   r->rtol = (o && o->rtol > 0) ? o->rtol : (r->precision == GRF_FP64 ? 1e-12 : 1e-9);
   if (r->precision != GRF_FP64 && r->precision != GRF_MIXED)
     return fail(GRF_EINVAL, "unknown precision %d", r->precision);
-  if (r->precond != GRF_PRECOND_JACOBI && r->precond != GRF_PRECOND_LEARNED)
+  if (r->precond != GRF_PRECOND_JACOBI && r->precond != GRF_PRECOND_LEARNED &&
+      r->precond != GRF_PRECOND_NEUMANN)
     return fail(GRF_ENOTSUP, "preconditioner %d not available", r->precond);
   if (r->precond == GRF_PRECOND_LEARNED && r->precision != GRF_MIXED)
     return fail(GRF_ENOTSUP, "the learned preconditioner needs precision GRF_MIXED");
@@ -346,7 +349,8 @@ int read_opts(const grf_options* o, Opts* r) {
 struct ApplyWs {
   double *alpha, *gamma, *weight, *saa, *sab, *diag, *offv, *gvec, *x, *acc;
   void *r, *p, *q, *d, *y;  // PCG vectors in the sweep precision T [L][S][V]
-  float *lp_es, *lp_n;      // learned preconditioner per node: [L][V], [L][2E]
+  void *pre_c, *pre_n;      // preconditioner coefficients per node: [L][V], [L][2E]
+                            // (learned: float es, N; Neumann-Neumann: T)
   LpActs lpa;               // network activations of lp_chunk nodes (es, n set per chunk)
   int32_t lp_chunk;
   void* dscale;         // T [L][V]
@@ -386,7 +390,7 @@ void carve_lp_infer(Carve& c, const grf_graph* g, int32_t nodes, LpActs* a) {
 }
 
 void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w,
-                 bool learned = false, bool spectral = false) {
+                 int precond = GRF_PRECOND_JACOBI, bool spectral = false) {
   const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
   const size_t nsg = (Ss + recover_sample_group() - 1) / recover_sample_group();
   w->alpha = c.take<double>(Ls);
@@ -404,15 +408,16 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->d = c.take<char>(Ls * Ss * V * tsize);
   w->lpa = LpActs{};
   w->lp_chunk = 0;
-  if (learned) {
+  w->y = nullptr;
+  w->pre_c = w->pre_n = nullptr;
+  if (precond != GRF_PRECOND_JACOBI) {
+    w->pre_c = c.take<char>(Ls * V * tsize);
+    w->pre_n = c.take<char>(Ls * 2 * E * tsize);
+  }
+  if (precond == GRF_PRECOND_LEARNED) {
     w->y = c.take<char>(Ls * Ss * V * tsize);
-    w->lp_es = c.take<float>(Ls * V);
-    w->lp_n = c.take<float>(Ls * 2 * E);
     w->lp_chunk = lp_chunk_nodes(g, L);
     carve_lp_infer(c, g, w->lp_chunk, &w->lpa);
-  } else {
-    w->y = nullptr;
-    w->lp_es = w->lp_n = nullptr;
   }
   w->dscale = c.take<char>(Ls * V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(Ls * 2 * E * 4) : nullptr;
@@ -540,15 +545,24 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
   const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
   const bool learned = sizeof(T) == 4 && o.precond == GRF_PRECOND_LEARNED;
+  const bool neumann = o.precond == GRF_PRECOND_NEUMANN;
+  if ((learned || neumann) && !w.pre_c)
+    return fail(GRF_ENOTSUP, "this entry point has no workspace for preconditioner %d",
+                o.precond);
+  if (neumann) {
+    launch_nn_coeffs<T>(g->d, L, w.saa, w.sab, w.diag, sizeof(T) == 4, (T*)w.pre_c,
+                        (T*)w.pre_n, st);
+    rs->launches += 1;
+  }
   if (learned) {
-    if (!g->lm.ready || !w.lp_es || w.lp_chunk < 1 || L > kRamp)
+    if (!g->lm.ready || w.lp_chunk < 1 || L > kRamp)
       return fail(GRF_EINVAL, "learned preconditioner not set up for this call");
     rs->begin(st);
     const int64_t ne2 = 2 * (int64_t)g->ne;
     for (int32_t l0 = 0; l0 < L; l0 += w.lp_chunk) {
       LpActs a = w.lpa;
-      a.es = w.lp_es + (int64_t)l0 * g->nv;
-      a.n = w.lp_n + (int64_t)l0 * ne2;
+      a.es = (float*)w.pre_c + (int64_t)l0 * g->nv;
+      a.n = (float*)w.pre_n + (int64_t)l0 * ne2;
       const int32_t nb = std::min(w.lp_chunk, L - l0);
       rs->launches += lp_forward(g->d, nb, g->lm.ramp + l0, (const float*)w.offv_t, w.alpha,
                                  w.gamma, g->lm.P, g->lm.wb, a, st);
@@ -556,10 +570,10 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     rs->end(6, st);
   }
   rs->begin(st);
-  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t,
-                learned ? w.lp_es : nullptr, learned ? w.lp_n : nullptr, gvec, xv, (T*)w.d,
-                (T*)w.r, (T*)w.p, (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status,
-                o.pcg_layout, st);
+  const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
+  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
+                (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
+                (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st);
   rs->end(3, st);
   rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
@@ -574,7 +588,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
              const double* nodes_dev = nullptr) {
   Carve c(ws_tail);
   ApplyWs w;
-  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
+  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond, o.spectral);
   const double k2 = kappa * kappa;
   if (nodes_dev) {
     w.alpha = const_cast<double*>(nodes_dev);
@@ -602,7 +616,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
 size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize, const Opts& o) {
   Carve c(nullptr);
   ApplyWs w;
-  carve_apply(c, g, L, S, tsize, &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
+  carve_apply(c, g, L, S, tsize, &w, o.precond, o.spectral);
   return c.off;
 }
 
@@ -842,7 +856,7 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->q = c.take<char>(Ss * V * tsize);
   w->d = c.take<char>(Ss * V * tsize);
   w->y = nullptr;
-  w->lp_es = w->lp_n = nullptr;
+  w->pre_c = w->pre_n = nullptr;
   w->dscale = c.take<char>(V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(2 * E * 4) : nullptr;
   w->iters = c.take<int32_t>(Ss);
@@ -1713,7 +1727,7 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
   GRF_TRY(ensure_ws(g, head + apply_bytes(g, 1, n_rhs, ts, o)));
   Carve c((char*)g->ws + head);
   ApplyWs w;
-  carve_apply(c, g, 1, n_rhs, ts, &w, o.precond == GRF_PRECOND_LEARNED, o.spectral);
+  carve_apply(c, g, 1, n_rhs, ts, &w, o.precond, o.spectral);
   cudaStream_t st = (cudaStream_t)stream;
   GRF_TRY(upload_nodes(hn, w, st));
   const double k2 = kappa * kappa;
@@ -1750,6 +1764,8 @@ int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double ga
   if (n_rhs < 0) return fail(GRF_EINVAL, "bad n_rhs");
   if (n_rhs == 0) return finish(RunStats{}, g, stats);
   if (!rhs || !g_out || !u_out) return fail(GRF_EINVAL, "null buffer");
+  if (o.precond != GRF_PRECOND_JACOBI)
+    return fail(GRF_ENOTSUP, "grf_vertex_solve_noalloc supports GRF_PRECOND_JACOBI only");
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   Carve dry(nullptr);
   ApplyWs w;

@@ -73,6 +73,12 @@ int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* s
                  double* sab, double* diag, double* offv, SweepParams<T>* prm, T* dscale,
                  T* offv_t, cudaStream_t st);
 
+// Neumann-Neumann preconditioner coefficients per node: pc[l][v] (diagonal) and
+// pn[l][k] (incidence k), for the Jacobi-scaled system (scaled) or S itself.
+template <typename T>
+void launch_nn_coeffs(const DevGraph& g, int32_t L, const double* saa, const double* sab,
+                      const double* diag, bool scaled, T* pc, T* pn, cudaStream_t st);
+
 // ---- thomas.cu
 // rhs (sample-minor [n][S], T) -> condensed right-hand side gvec[l][s][v] (double):
 // gvec = b at the vertices plus the end values of the listed edges (edges null:
@@ -107,11 +113,14 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 // offv_t = scaled blocks). d, r, p, q: [L][S][nv] scratch used when a system's
 // vectors do not fit in shared memory. layout: 1 one CTA per system, 2 staged
 // matrix per (node, sample group) when it fits (mixed only), else layout 1.
-// lp_es / lp_n (mixed only, may be null): learned preconditioner B = diag(es) + N
-// per node ([L][V], [L][2E]); y: one more [L][S][nv] scratch for it.
+// Preconditioner: pre = kPreJacobi (pc, pn unused), kPreNeumann (pc [L][V] and
+// pn [L][2E] in VT: z_v = pc_v r_v + sum_k pn_k r_nbr(k)) or kPreLearned (mixed
+// only, float es = pc and N = pn per node: z = B B^T r, B = diag(es) + N);
+// y: one more [L][S][nv] scratch for the learned form.
+constexpr int kPreJacobi = 0, kPreNeumann = 1, kPreLearned = 2;
 template <typename VT>
 void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, const float* lp_es, const float* lp_n,
+                const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
                 cudaStream_t st);

@@ -117,30 +117,36 @@ struct SysMatrix {
   const VT* Ds;      // FP64 mode: 1 / D; mixed: 1 / sqrt(D)
   const double* D;   // FP64 diagonal
   const double* O;   // FP64 blocks
-  // learned preconditioner of the scaled system (mixed mode), else null:
-  // B = diag(es) + N, N_{v, nbr k} = nb[k]; rev = reverse incidence
-  const float* es;
-  const float* nb;
+  // preconditioner: kPreJacobi, kPreNeumann (z_v = pc_v r_v + sum_k pn_k r_nbr(k))
+  // or kPreLearned (z = B B^T r, B = diag(pc) + N, N_{v, nbr k} = pn[k]);
+  // rev = reverse incidence
+  int pre;
+  const VT* pc;
+  const VT* pn;
   const int32_t* rev;
 };
 
-// z = B (B^T r) for the learned preconditioner: y_w = es_w r_w +
-// sum_k' nb_{rev k'} r_{nbr k'}; z_v = es_v y_v + sum_k nb_k y_{nbr k}. Writes z
-// and returns this thread's share of r.z; ends with all threads past a barrier.
+// z = P r for the sparse preconditioners (r must be complete: call after a
+// barrier). Neumann-Neumann: one sweep. Learned: y_w = pc_w r_w +
+// sum_k' pn_{rev k'} r_{nbr k'}, barrier, z_v = pc_v y_v + sum_k pn_k y_{nbr k}.
+// Writes z and returns this thread's share of r.z.
 template <int kThreads, typename VT>
-__device__ __forceinline__ VT learned_apply(int32_t nv, const SysMatrix<VT>& M, const VT* r,
-                                            VT* y, VT* z) {
-  for (int32_t w = threadIdx.x; w < nv; w += kThreads) {
-    VT acc = (VT)M.es[w] * r[w];
-    for (int32_t k = M.vptr[w]; k < M.vptr[w + 1]; ++k)
-      acc += (VT)M.nb[M.rev[k]] * r[M.nbr[k]];
-    y[w] = acc;
+__device__ __forceinline__ VT prec_apply(int32_t nv, const SysMatrix<VT>& M, const VT* r, VT* y,
+                                         VT* z) {
+  const VT* src = r;
+  if (M.pre == kPreLearned) {
+    for (int32_t w = threadIdx.x; w < nv; w += kThreads) {
+      VT acc = M.pc[w] * r[w];
+      for (int32_t k = M.vptr[w]; k < M.vptr[w + 1]; ++k) acc += M.pn[M.rev[k]] * r[M.nbr[k]];
+      y[w] = acc;
+    }
+    __syncthreads();
+    src = y;
   }
-  __syncthreads();
   VT rz = (VT)0;
   for (int32_t v = threadIdx.x; v < nv; v += kThreads) {
-    VT acc = (VT)M.es[v] * y[v];
-    for (int32_t k = M.vptr[v]; k < M.vptr[v + 1]; ++k) acc += (VT)M.nb[k] * y[M.nbr[k]];
+    VT acc = M.pc[v] * src[v];
+    for (int32_t k = M.vptr[v]; k < M.vptr[v + 1]; ++k) acc += M.pn[k] * src[M.nbr[k]];
     z[v] = acc;
     rz += r[v] * acc;
   }
@@ -194,11 +200,11 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
   bool done = bad || !(gg[0] > 0.0);
   double sig2 = gg[1];  // ||D^-1/2 r||^2 of the current refinement step
   double inner_e = kInnerRtol;  // relative stop of the current inner solve
-  // z = B B^T r (learned), else z = r on the scaled system (Jacobi). A learned
-  // preconditioner that breaks down (r.z <= 0, p.Sp <= 0 or a non-finite
-  // scalar) is dropped for the rest of this system's solve, which continues
-  // with Jacobi from the last refined iterate.
-  bool learned = kRefine && M.es != nullptr;
+  // z = P r (Neumann-Neumann or learned), else Jacobi (z = r on the scaled
+  // system, r / D in FP64). A preconditioner that breaks down (r.z <= 0,
+  // p.Sp <= 0 or a non-finite scalar) is dropped for the rest of this
+  // system's solve, which continues with Jacobi from the last refined iterate.
+  bool learned = M.pre != kPreJacobi;
   bool fallback = false;
   while (!done && it < max_iter) {
     double sigma = 1.0;
@@ -238,13 +244,17 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
         v.d[i] = (VT)0;
       }
       __syncthreads();
-    } else {
-      for (int32_t i = threadIdx.x; i < nv; i += kThreads) v.r[i] = (VT)gs[i];
+    } else {  // FP64: one PCG run from d = 0 (again from 0 after a fallback)
+      for (int32_t i = threadIdx.x; i < nv; i += kThreads) {
+        v.r[i] = (VT)gs[i];
+        v.d[i] = (VT)0;
+      }
     }
     // (P)CG on the inner system from d = 0
     VT rz0 = (VT)0;
     if (learned) {
-      rz0 = learned_apply<kThreads, VT>(nv, M, v.r, v.y, v.p);
+      __syncthreads();
+      rz0 = prec_apply<kThreads, VT>(nv, M, v.r, v.y, v.p);
     } else {
       for (int32_t i = threadIdx.x; i < nv; i += kThreads) {
         const VT ri = v.r[i];
@@ -300,7 +310,7 @@ __device__ SysResult solve_system(int32_t nv, const SysMatrix<VT>& M, const doub
       }
       if (learned) {  // z = B B^T r into q (q is consumed above)
         __syncthreads();
-        rzf = learned_apply<kThreads, VT>(nv, M, v.r, v.y, v.q);
+        rzf = prec_apply<kThreads, VT>(nv, M, v.r, v.y, v.q);
       }
       VT part2[2] = {rzf, rrf};
       warp_partials<VT, 2>(part2, S.shw2);
@@ -383,14 +393,14 @@ constexpr int kThreadsA = 256;
 
 // dscale: FP64 mode 1 / D; mixed mode 1 / sqrt(D).
 // offv_t: FP64 mode the blocks; mixed mode the Jacobi-scaled blocks.
-// lp_es / lp_n (mixed mode, may be null): learned preconditioner per node,
-// diag(es) [L][V] and the incidence entries [L][2E].
+// pre / pc / pn: preconditioner kind and its per-node coefficients
+// ([L][V] and [L][2E]; see launch_pcg).
 template <typename VT, bool kSmem>
 __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
     DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const VT* __restrict__ dscale_t,
-    const VT* __restrict__ offv_t, const float* __restrict__ lp_es,
-    const float* __restrict__ lp_n, const double* __restrict__ gvec, double* __restrict__ xout,
+    const VT* __restrict__ offv_t, int pre, const VT* __restrict__ pc,
+    const VT* __restrict__ pn, const double* __restrict__ gvec, double* __restrict__ xout,
     VT* __restrict__ gd, VT* __restrict__ gr, VT* __restrict__ gp, VT* __restrict__ gq,
     VT* __restrict__ gy, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
     PcgStatus* status) {
@@ -408,8 +418,9 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
                     dscale_t + l * nv,
                     diag + l * nv,
                     offv + l * ne2,
-                    lp_es ? lp_es + l * nv : nullptr,
-                    lp_n ? lp_n + l * ne2 : nullptr,
+                    pre,
+                    pre != kPreJacobi ? pc + l * nv : nullptr,
+                    pre != kPreJacobi ? pn + l * ne2 : nullptr,
                     g.adj_rev};
     double* xo = xout + sys * nv;
     SysVecs<VT> v;
@@ -465,6 +476,75 @@ __device__ __forceinline__ void store_row(float* p, const float (&v)[SGP]) {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
   else
     *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+
+// z = P r for the owned vertices of the group kernels (R holds every
+// vertex's r, complete behind a barrier that this function starts with).
+// Neumann-Neumann: z_v = pc_v r_v + sum_k pn_k r_nbr(k). Learned: Y = B^T r
+// (barrier), z = B Y. Samples whose preconditioner is off get z = r. Returns
+// rz[s] = r.z and rz[SGP + s] = r.r (thread partials).
+template <int NT, int VPT, int SGP, bool kLearned>
+__device__ __forceinline__ void prec_group_apply(const DevGraph& g, int32_t nv,
+                                                 const int32_t* vp, const float* Pc,
+                                                 const float* Pn, const float* R, float* Y,
+                                                 const float (&r)[VPT][SGP],
+                                                 const bool (&on)[SGP], float (&z)[VPT][SGP],
+                                                 float (&rz)[2 * SGP]) {
+  __syncthreads();  // R complete
+  const float* src = R;
+  if constexpr (kLearned) {
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const int32_t w = threadIdx.x + k * NT;
+      if (w < nv) {
+        float acc[SGP], rw[SGP];
+        load_row<SGP>(R + (size_t)w * SGP, rw);
+        const float c = Pc[w];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) acc[s] = c * rw[s];
+        for (int32_t kk = vp[w]; kk < vp[w + 1]; ++kk) {
+          const float o = Pn[g.adj_rev[kk]];
+          float rv[SGP];
+          load_row<SGP>(R + (size_t)g.adj_nbr[kk] * SGP, rv);
+#pragma unroll
+          for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, rv[s], acc[s]);
+        }
+        store_row<SGP>(Y + (size_t)w * SGP, acc);
+      }
+    }
+    __syncthreads();  // Y complete
+    src = Y;
+  }
+#pragma unroll
+  for (int s = 0; s < 2 * SGP; ++s) rz[s] = 0.f;
+#pragma unroll
+  for (int k = 0; k < VPT; ++k) {
+    const int32_t v = threadIdx.x + k * NT;
+    if (v < nv) {
+      float acc[SGP], sv[SGP];
+      load_row<SGP>(src + (size_t)v * SGP, sv);
+      const float c = Pc[v];
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) acc[s] = c * sv[s];
+      for (int32_t kk = vp[v]; kk < vp[v + 1]; ++kk) {
+        const float o = Pn[kk];
+        float sw[SGP];
+        load_row<SGP>(src + (size_t)g.adj_nbr[kk] * SGP, sw);
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, sw[s], acc[s]);
+      }
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) {
+        const float zs = on[s] ? acc[s] : r[k][s];
+        z[k][s] = zs;
+        rz[s] = fmaf(r[k][s], zs, rz[s]);
+        rz[SGP + s] = fmaf(r[k][s], r[k][s], rz[SGP + s]);
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) z[k][s] = 0.f;
+    }
+  }
 }
 
 // Block sums of N floats (N = 2, 4 or 8): a warp butterfly, one row of N
@@ -850,6 +930,422 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
   }
 }
 
+// Shared memory of the preconditioned group kernel: P, R (and Y for the
+// learned form) [nv][SGP], Ot and pn [2E], Ds and pc [nv], incidence offsets.
+template <int SGP, int PRE>
+__host__ __device__ inline size_t group_pre_bytes(int32_t nv, int32_t ne) {
+  const size_t vecs = PRE == kPreLearned ? 3 : 2;
+  return 4 * ((size_t)nv * SGP * vecs + 4 * (size_t)ne + 3 * (size_t)nv + 1) + 16;
+}
+
+// The sample-group PCG with a sparse preconditioner on the Jacobi-scaled
+// system: PRE = kPreNeumann (z = pc r + N r, one sweep over the incidences) or
+// kPreLearned (z = B B^T r, two sweeps). The residuals of the group are shared
+// (R) because the preconditioner reads the neighbours' values. A sample whose
+// preconditioner breaks down (r.z <= 0, p.Sp <= 0, non-finite) drops that
+// step's correction and continues with Jacobi (z = r) from its last refined
+// iterate. Otherwise as pcg_group_kernel.
+template <int NT, int VPT, int SGP, int PRE>
+__global__ void __launch_bounds__(NT) pcg_group_pre_kernel(
+    DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
+    const double* __restrict__ offv, const float* __restrict__ dscale_t,
+    const float* __restrict__ offv_t, const float* __restrict__ pcoef,
+    const float* __restrict__ ncoef, const double* __restrict__ gvec,
+    double* __restrict__ xout, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
+    PcgStatus* status) {
+  static_assert(SGP == 2 || SGP == 4, "sample groups of 2 or 4");
+  constexpr bool kLearned = PRE == kPreLearned;
+  __shared__ __align__(16) float shw[2][(NT / 32) * 2 * SGP];
+  __shared__ double shd[(NT / 32 + 1) * 2 * SGP];
+  __shared__ double igd[SGP], sgm0[SGP], isg0[SGP], sgm[SGP];
+  __shared__ float cgs[SGP], isg[SGP], in2[SGP];
+  extern __shared__ __align__(16) unsigned char grp_sm[];
+  const int32_t nv = g.nv;
+  const int64_t ne2 = 2 * (int64_t)g.ne;
+  float* P = reinterpret_cast<float*>(grp_sm);    // [nv][SGP]
+  float* R = P + (size_t)nv * SGP;                // [nv][SGP]
+  float* Y = R + (size_t)nv * SGP;                // [nv][SGP] (learned only)
+  float* Ot = kLearned ? Y + (size_t)nv * SGP : Y;  // [2E]
+  float* Pn = Ot + ne2;                           // [2E]
+  float* Ds = Pn + ne2;                           // [nv]
+  float* Pc = Ds + nv;                            // [nv]
+  int32_t* vp = reinterpret_cast<int32_t*>(Pc + nv);  // [nv + 1]
+  for (int32_t v = threadIdx.x; v <= nv; v += NT) vp[v] = g.vptr[v];
+  const int64_t ngrp = (S + SGP - 1) / SGP;
+  const int64_t units = (int64_t)L * ngrp;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int64_t l = u / ngrp;
+    const int64_t s0 = (u % ngrp) * SGP;
+    const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
+    __syncthreads();  // the previous unit is done with the shared arrays
+    for (int64_t k = threadIdx.x; k < ne2; k += NT) {
+      Ot[k] = offv_t[l * ne2 + k];
+      Pn[k] = ncoef[l * ne2 + k];
+    }
+    for (int32_t v = threadIdx.x; v < nv; v += NT) {
+      Ds[v] = dscale_t[l * nv + v];
+      Pc[v] = pcoef[l * nv + v];
+    }
+    __syncthreads();
+    const double* D = diag + l * nv;
+    const double* O = offv + l * ne2;
+    const double* gl = gvec + (l * S + s0) * nv;
+    double* xl = xout + (l * S + s0) * nv;
+    double nrm[2 * SGP];
+#pragma unroll
+    for (int s = 0; s < 2 * SGP; ++s) nrm[s] = 0.0;
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const int32_t v = threadIdx.x + k * NT;
+      if (v < nv) {
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          if (s < kv) {
+            const double gv = gl[(int64_t)s * nv + v];
+            const double sv = gv * (double)Ds[v];
+            nrm[s] += gv * gv;
+            nrm[SGP + s] += sv * sv;
+            xl[(int64_t)s * nv + v] = 0.0;
+          }
+        }
+      }
+    }
+    block_sum<NT, 2 * SGP>(nrm, shd);
+    bool act[SGP], done[SGP], bad[SGP], pre_on[SGP];
+    int32_t its[SGP], nfb = 0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) {
+        const double gn = sqrt(nrm[s]);
+        sgm0[s] = sqrt(nrm[SGP + s]);
+        isg0[s] = sgm0[s] > 0.0 ? 1.0 / sgm0[s] : 0.0;
+        sgm[s] = sgm0[s];
+        igd[s] = gn > 0.0 ? 1.0 / gn : 0.0;
+        cgs[s] = sgm0[s] > 0.0 ? (float)(gn / sgm0[s]) : 0.f;
+        isg[s] = 1.f;
+        in2[s] = (float)(kInnerRtol * kInnerRtol);
+      }
+    }
+    __syncthreads();
+    const float rtol2f = (float)(rtol * rtol);
+#pragma unroll
+    for (int s = 0; s < SGP; ++s) {
+      bad[s] = s < kv && !(isfinite(nrm[s]) && isfinite(nrm[SGP + s]));
+      done[s] = s >= kv || (!bad[s] && !(nrm[s] > 0.0));
+      act[s] = !done[s] && !bad[s];
+      pre_on[s] = true;
+      its[s] = 0;
+    }
+    float r[VPT][SGP], q[VPT][SGP], d[VPT][SGP];
+    int32_t it = 0;
+    bool first = true;
+    while (it < max_iter) {
+      if (!first) {
+        __syncthreads();
+        float acc[2 * SGP];
+#pragma unroll
+        for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.f;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * NT;
+          if (v < nv) {
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              float rs = 0.f;
+              if (act[s]) {
+                const double* xs = xl + (int64_t)s * nv;
+                double y = D[v] * xs[v];
+                for (int32_t kk = vp[v]; kk < vp[v + 1]; ++kk) y += O[kk] * xs[g.adj_nbr[kk]];
+                const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+                rs = ri * Ds[v] * cgs[s];
+                acc[s] = fmaf(ri, ri, acc[s]);
+                acc[SGP + s] = fmaf(rs, rs, acc[SGP + s]);
+              }
+              r[k][s] = rs;
+            }
+          }
+        }
+        group_sum<NT, 2 * SGP>(acc, shw[0]);
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          if (!act[s]) continue;
+          if (!isfinite(acc[s]) || !isfinite(acc[SGP + s])) {
+            bad[s] = true;
+            act[s] = false;
+          } else if (acc[s] <= rtol2f) {
+            done[s] = true;
+            act[s] = false;
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s) {
+            if (act[s]) {
+              const double ratio = sqrt((double)acc[SGP + s]);
+              sgm[s] = sgm0[s] * ratio;
+              isg[s] = (float)(1.0 / ratio);
+              const double need = 0.1 * rtol / sqrt((double)acc[s]);
+              const double e = need > kInnerRtol ? need : kInnerRtol;
+              in2[s] = (float)(e * e);
+            }
+          }
+        }
+        __syncthreads();
+      } else {
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * NT;
+#pragma unroll
+          for (int s = 0; s < SGP; ++s)
+            r[k][s] = (act[s] && v < nv)
+                          ? (float)(gl[(int64_t)s * nv + v] * (double)Ds[v] * isg0[s])
+                          : 0.f;
+        }
+      }
+      first = false;
+      bool any = false;
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) any = any || act[s];
+      if (!any) break;
+      // inner start: r (unit scaled residual) shared, z = P r, p = z
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * NT;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          r[k][s] = act[s] ? r[k][s] * isg[s] : 0.f;
+          d[k][s] = 0.f;
+        }
+        if (v < nv) store_row<SGP>(R + (size_t)v * SGP, r[k]);
+      }
+      float rz[2 * SGP];  // r.z, then r.r
+      prec_group_apply<NT, VPT, SGP, kLearned>(g, nv, vp, Pc, Pn, R, Y, r, pre_on, q, rz);
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * NT;
+        if (v < nv) store_row<SGP>(P + (size_t)v * SGP, q[k]);
+      }
+      group_sum<NT, 2 * SGP>(rz, shw[1]);
+      bool in[SGP], drop[SGP];
+      float best[SGP], rrv[SGP];
+      int since[SGP];
+      bool anyin = false;
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) {
+        drop[s] = false;
+        rrv[s] = rz[SGP + s];
+        in[s] = act[s] && rz[SGP + s] > 0.f && isfinite(rz[SGP + s]);
+        if (in[s] && pre_on[s] && !(rz[s] > 0.f && isfinite(rz[s]))) {
+          pre_on[s] = false;  // breakdown at the start: Jacobi from here on
+          ++nfb;
+          in[s] = false;
+          drop[s] = true;
+        }
+        best[s] = 1.f;
+        since[s] = 0;
+        anyin = anyin || in[s];
+      }
+      bool restart = false;
+#pragma unroll
+      for (int s = 0; s < SGP; ++s) restart = restart || (drop[s] && act[s]);
+      if (!anyin && !restart) break;
+      while (anyin && it < max_iter) {
+        ++it;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) its[s] += in[s] ? 1 : 0;
+        __syncthreads();  // P visible
+        float pq[SGP];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) pq[s] = 0.f;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * NT;
+          if (v < nv) {
+            float acc[SGP], pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) acc[s] = pv[s];
+            const int32_t kend = vp[v + 1];
+            for (int32_t kk = vp[v]; kk < kend; ++kk) {
+              const float o = Ot[kk];
+              float pw[SGP];
+              load_row<SGP>(P + (size_t)g.adj_nbr[kk] * SGP, pw);
+#pragma unroll
+              for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, pw[s], acc[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              q[k][s] = acc[s];
+              pq[s] = fmaf(pv[s], acc[s], pq[s]);
+            }
+          }
+        }
+        group_sum<NT, SGP>(pq, shw[0]);
+        float al[SGP];
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          al[s] = 0.f;
+          if (!in[s]) continue;
+          if (!isfinite(pq[s]) || !(pq[s] > 0.f)) {
+            in[s] = false;
+            // p vanishing next to an FP32-small residual is the rounding floor;
+            // otherwise the preconditioner broke down
+            if (pre_on[s] && (!isfinite(pq[s]) || rrv[s] > 1e-10f)) {
+              pre_on[s] = false;
+              ++nfb;
+              drop[s] = true;
+            } else if (!isfinite(pq[s])) {
+              bad[s] = true;
+              act[s] = false;
+            }
+          } else {
+            al[s] = rz[s] / pq[s];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * NT;
+          if (v < nv) {
+            float pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s) {
+              d[k][s] = fmaf(al[s], pv[s], d[k][s]);
+              r[k][s] = fmaf(-al[s], q[k][s], r[k][s]);
+            }
+            store_row<SGP>(R + (size_t)v * SGP, r[k]);
+          }
+        }
+        float rzn[2 * SGP];
+        prec_group_apply<NT, VPT, SGP, kLearned>(g, nv, vp, Pc, Pn, R, Y, r, pre_on, q, rzn);
+        group_sum<NT, 2 * SGP>(rzn, shw[1]);
+        float be[SGP];
+        bool still = false;
+#pragma unroll
+        for (int s = 0; s < SGP; ++s) {
+          be[s] = 0.f;
+          if (!in[s]) continue;
+          const float rr = rzn[SGP + s];
+          if (!isfinite(rr)) {
+            bad[s] = true;
+            act[s] = false;
+            in[s] = false;
+          } else if (rr <= in2[s]) {
+            in[s] = false;  // converged (r.z may have lost its sign at this size)
+          } else if (pre_on[s] && !(rzn[s] > 0.f && isfinite(rzn[s]))) {
+            in[s] = false;  // breakdown: drop this step's correction
+            pre_on[s] = false;
+            ++nfb;
+            drop[s] = true;
+          } else {
+            if (rr < 0.98f * best[s]) {
+              best[s] = rr;
+              since[s] = 0;
+            } else if (++since[s] >= 32) {
+              in[s] = false;
+            }
+            be[s] = rzn[s] / rz[s];
+            rz[s] = rzn[s];
+          }
+          rrv[s] = rr;
+          still = still || in[s];
+        }
+        if (!still) break;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const int32_t v = threadIdx.x + k * NT;
+          if (v < nv) {
+            float pv[SGP];
+            load_row<SGP>(P + (size_t)v * SGP, pv);
+#pragma unroll
+            for (int s = 0; s < SGP; ++s)
+              if (in[s]) pv[s] = fmaf(be[s], pv[s], q[k][s]);
+            store_row<SGP>(P + (size_t)v * SGP, pv);
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * NT;
+        if (v < nv) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s)
+            if (act[s] && !drop[s])
+              xl[(int64_t)s * nv + v] = fma(sgm[s], (double)(Ds[v] * d[k][s]), xl[(int64_t)s * nv + v]);
+        }
+      }
+    }
+    bool pending = false;
+#pragma unroll
+    for (int s = 0; s < SGP; ++s) pending = pending || act[s];
+    if (pending) {
+      __syncthreads();
+      float acc[2 * SGP];
+#pragma unroll
+      for (int s = 0; s < 2 * SGP; ++s) acc[s] = 0.f;
+#pragma unroll
+      for (int k = 0; k < VPT; ++k) {
+        const int32_t v = threadIdx.x + k * NT;
+        if (v < nv) {
+#pragma unroll
+          for (int s = 0; s < SGP; ++s) {
+            if (act[s]) {
+              const double* xs = xl + (int64_t)s * nv;
+              double y = D[v] * xs[v];
+              for (int32_t kk = vp[v]; kk < vp[v + 1]; ++kk) y += O[kk] * xs[g.adj_nbr[kk]];
+              const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+              acc[s] = fmaf(ri, ri, acc[s]);
+            }
+          }
+        }
+      }
+      group_sum<NT, 2 * SGP>(acc, shw[0]);
+#pragma unroll
+      for (int s = 0; s < SGP; ++s)
+        if (act[s]) done[s] = acc[s] <= rtol2f;
+    }
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < kv; ++s) {
+        iters[l * S + s0 + s] = its[s];
+        atomicAdd(&status->iters_total, (unsigned long long)its[s]);
+        atomicMax(&status->iters_max, its[s]);
+        if (!pre_on[s]) atomicAdd(&status->n_fallback, 1);
+        if (bad[s]) atomicAdd(&status->numeric_flag, 1);
+        else if (!done[s]) atomicAdd(&status->n_unconverged, 1);
+      }
+    }
+    (void)nfb;
+  }
+}
+
+template <int NT, int VPT, int SGP, int PRE>
+void launch_group_pre(const DevGraph& g, int32_t L, int64_t S, const double* diag,
+                      const double* offv, const float* dscale_t, const float* offv_t,
+                      const float* pc, const float* pn, const double* gvec, double* x,
+                      double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
+                      cudaStream_t st) {
+  const size_t dyn = group_pre_bytes<SGP, PRE>(g.nv, g.ne);
+  cudaFuncSetAttribute(pcg_group_pre_kernel<NT, VPT, SGP, PRE>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
+  const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
+  pcg_group_pre_kernel<NT, VPT, SGP, PRE><<<blocks, NT, dyn, st>>>(
+      g, L, S, diag, offv, dscale_t, offv_t, pc, pn, gvec, x, rtol, max_iter, iters, status);
+}
+
+bool group_pre_fits(const DevGraph& g, int pre) {
+  const int sgp = g.nv <= 4 * kThreadsG ? 4 : 2;
+  size_t dyn;
+  if (pre == kPreLearned)
+    dyn = sgp == 4 ? group_pre_bytes<4, kPreLearned>(g.nv, g.ne)
+                   : group_pre_bytes<2, kPreLearned>(g.nv, g.ne);
+  else
+    dyn = sgp == 4 ? group_pre_bytes<4, kPreNeumann>(g.nv, g.ne)
+                   : group_pre_bytes<2, kPreNeumann>(g.nv, g.ne);
+  return g.nv <= 8 * kThreadsG && dyn + 8 * 1024 <= kSmemMax;
+}
+
 template <int NT, int VPT, int SGP>
 void launch_group(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
                   const float* dscale_t, const float* offv_t, const double* gvec, double* x,
@@ -876,13 +1372,13 @@ bool group_fits(const DevGraph& g) {
 
 template <typename VT>
 void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, const float* lp_es, const float* lp_n,
+                const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
                 cudaStream_t st) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
-    if ((layout == 2 || layout == 3) && !lp_es && group_fits(g)) {
+    if ((layout == 2 || layout == 3) && pre == kPreJacobi && group_fits(g)) {
 #define GRF_GROUP(NT, VPT, SGP)                                                               \
   launch_group<NT, VPT, SGP>(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter,  \
                              iters, status, st)
@@ -901,27 +1397,45 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
 #undef GRF_GROUP
       return;
     }
+    if ((layout == 2 || layout == 3) && pre != kPreJacobi && group_pre_fits(g, pre)) {
+#define GRF_GROUP_PRE(VPT, SGP, PRE)                                                          \
+  launch_group_pre<512, VPT, SGP, PRE>(g, L, S, diag, offv, dscale_t, offv_t, pc, pn, gvec, x, \
+                                       rtol, max_iter, iters, status, st)
+#define GRF_GROUP_PRE_ALL(PRE)                                                 \
+  if (g.nv <= kThreadsG) GRF_GROUP_PRE(1, 4, PRE);                             \
+  else if (g.nv <= 2 * kThreadsG) GRF_GROUP_PRE(2, 4, PRE);                    \
+  else if (g.nv <= 4 * kThreadsG) GRF_GROUP_PRE(4, 4, PRE);                    \
+  else GRF_GROUP_PRE(8, 2, PRE);
+      if (pre == kPreLearned) {
+        GRF_GROUP_PRE_ALL(kPreLearned)
+      } else {
+        GRF_GROUP_PRE_ALL(kPreNeumann)
+      }
+#undef GRF_GROUP_PRE_ALL
+#undef GRF_GROUP_PRE
+      return;
+    }
   }
   int blocks = (int)(nsys < 152 * 16 ? nsys : 152 * 16);
   if (blocks < 1) blocks = 1;
   const size_t smem = (sizeof(VT) == 4 ? sizeof(double) : 0) * (size_t)g.nv +
-                      (lp_es ? 5 : 4) * sizeof(VT) * (size_t)g.nv;
+                      (pre == kPreLearned ? 5 : 4) * sizeof(VT) * (size_t)g.nv;
   if (smem <= kSmemMax - 16 * 1024) {
     // dynamic + static may pass the 48 KB default; per device: set at every launch
     cudaFuncSetAttribute(pcg_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     pcg_kernel<VT, true><<<blocks, kThreadsA, smem, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                          lp_es, lp_n, gvec, x, d, r, p, q, y,
+                                                          pre, pc, pn, gvec, x, d, r, p, q, y,
                                                           rtol, max_iter, iters, status);
   } else {
     pcg_kernel<VT, false><<<blocks, kThreadsA, 0, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                        lp_es, lp_n, gvec, x, d, r, p, q, y,
+                                                        pre, pc, pn, gvec, x, d, r, p, q, y,
                                                         rtol, max_iter, iters, status);
   }
 }
 #define GRF_INST(VT)                                                                          \
   template void launch_pcg<VT>(const DevGraph&, int32_t, int64_t, const double*, const double*, \
-                               const VT*, const VT*, const float*, const float*, const double*,  \
+                               const VT*, const VT*, int, const VT*, const VT*, const double*,    \
                                double*, VT*, VT*, VT*, VT*, VT*, double, int32_t, int32_t*,      \
                                PcgStatus*, int, cudaStream_t);
 GRF_INST(float)

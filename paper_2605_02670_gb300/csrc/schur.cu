@@ -91,6 +91,43 @@ __global__ void scaled_offdiag_kernel(DevGraph g, int32_t L, const double* __res
   }
 }
 
+// Neumann-Neumann preconditioner of the vertex system (Sec. 3, Phase 4, the
+// Neumann step): P = D_G^-1 (sum_e (S^(e))^-1) D_G^-1, D_G = diag(vertex
+// degree), with the 2x2 block inverses (S^(e))^-1 = [[a, -b], [-b, a]] / det,
+// a = saa_e, b = sab_e, det = (a - b)(a + b) = c^2 sinh^2(theta) > 0. For
+// incidence k (v -> w over edge e):
+//   unscaled:  pc_v = sum_e a / det / d_v^2,   pn_k = -b / det / (d_v d_w);
+//   scaled (the same operator on D^-1/2 S D^-1/2): D^1/2 P D^1/2, i.e.
+//              pc_v = D_v sum_e a / det / d_v^2,
+//              pn_k = -sqrt(D_v D_w) b / det / (d_v d_w).
+template <typename T>
+__global__ void nn_coeff_kernel(DevGraph g, int32_t L, const double* __restrict__ saa,
+                                const double* __restrict__ sab, const double* __restrict__ diag,
+                                int scaled, T* __restrict__ pc, T* __restrict__ pn) {
+  const int64_t total = (int64_t)L * g.nv;
+  const int64_t nadj = 2 * (int64_t)g.ne;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / g.nv;
+    const int32_t v = (int32_t)(t - l * g.nv);
+    const double dv = (double)(g.vptr[v + 1] - g.vptr[v]);
+    const double Dv = diag[t];
+    double acc = 0.0;
+    for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
+      const int64_t i = l * g.ne + g.adj_edge[k];
+      const double a = saa[i], b = sab[i];
+      const double det = (a - b) * (a + b);
+      acc += a / det;
+      const int32_t w = g.adj_nbr[k];
+      const double dw = (double)(g.vptr[w + 1] - g.vptr[w]);
+      double c = -b / det / (dv * dw);
+      if (scaled) c *= sqrt(Dv * diag[l * g.nv + w]);
+      pn[l * nadj + k] = (T)c;
+    }
+    pc[t] = (T)(acc / (dv * dv) * (scaled ? Dv : 1.0));
+  }
+}
+
 int grid_for(int64_t total, int threads) {
   int64_t blocks = (total + threads - 1) / threads;
   if (blocks > 152 * 32) blocks = 152 * 32;
@@ -116,6 +153,17 @@ int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* s
   }
   return 2;
 }
+template <typename T>
+void launch_nn_coeffs(const DevGraph& g, int32_t L, const double* saa, const double* sab,
+                      const double* diag, bool scaled, T* pc, T* pn, cudaStream_t st) {
+  nn_coeff_kernel<T><<<grid_for((int64_t)L * g.nv, 256), 256, 0, st>>>(g, L, saa, sab, diag,
+                                                                      scaled ? 1 : 0, pc, pn);
+}
+template void launch_nn_coeffs<float>(const DevGraph&, int32_t, const double*, const double*,
+                                      const double*, bool, float*, float*, cudaStream_t);
+template void launch_nn_coeffs<double>(const DevGraph&, int32_t, const double*, const double*,
+                                       const double*, bool, double*, double*, cudaStream_t);
+
 template int launch_schur<float>(const DevGraph&, const DevNodes&, double, double*, double*,
                                  double*, double*, SweepParams<float>*, float*, float*,
                                  cudaStream_t);

@@ -188,11 +188,12 @@ def trained():
     return g, h, G, m
 
 
-def test_learned_sample_matches_oracle(trained):
+@pytest.mark.parametrize("layout", ["per_system", "staged"])
+def test_learned_sample_matches_oracle(trained, layout):
     g, h, G, m = trained
-    kappa, beta, k, seed, S = 2.0, 0.75, 0.5, 21, 4
+    kappa, beta, k, seed, S = 2.0, 0.75, 0.5, 21, 5
     u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
-                     precond="learned")
+                     precond="learned", pcg_layout=layout)
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < 1e-4
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
@@ -221,7 +222,8 @@ def test_learned_path_in_graph_capture_and_integer_beta(trained):
         assert rel_l2(c.cpu().numpy(), ref, ml) < 1e-4
 
 
-def test_breakdown_falls_back_to_jacobi():
+@pytest.mark.parametrize("layout", ["per_system", "staged"])
+def test_breakdown_falls_back_to_jacobi(layout):
     """exp(cs) underflows to 0 and N = 0: B = 0, r.z = 0 at the first step of
     every system, which must then finish with Jacobi and still match."""
     g, h = GRAPH()
@@ -231,7 +233,7 @@ def test_breakdown_falls_back_to_jacobi():
     G.precond_set(learned.flatten(p).astype(np.float32))
     kappa, beta, k, seed, S = 3.0, 0.6, 0.5, 8, 3
     u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
-                     precond="learned")
+                     precond="learned", pcg_layout=layout)
     assert st["n_precond_fallback"] == st["n_systems"]
     _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < 1e-4

@@ -351,3 +351,49 @@ def test_rgg2000_full_size_sample_properties():
     a = u32.cpu().numpy()
     assert np.isfinite(a).all() and st["n_unconverged"] == 0
     assert rel_l2(a[:2], u64.cpu().numpy(), ml) < TOL["mixed"]
+
+
+# ---------------------------------------------------------------- preconditioners
+
+
+@pytest.mark.parametrize("precision,layout", [("fp64", "per_system"), ("mixed", "per_system"),
+                                              ("mixed", "staged")])
+@pytest.mark.parametrize("name", ["random12", "square5", "isolated"])
+def test_neumann_neumann_preconditioner_matches_oracle(precision, layout, name):
+    """The paper's Neumann-Neumann preconditioner changes how PCG converges,
+    not what it converges to: same field tolerance as Jacobi."""
+    g, h = GRAPHS[name]()
+    G, m = make(g, h)
+    kappa, beta, k, seed, S = 3.0, 0.7, 0.45, 19, 6
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     pcg_layout=layout, precond="neumann")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=h)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    assert st["n_precond_fallback"] == 0
+
+
+@pytest.mark.parametrize("layout", ["per_system", "staged"])
+def test_neumann_neumann_on_larger_grid(layout):
+    g = gi.grid_deleted(40, 40, 0.15, 2)
+    G, m = make(g, 0.5)
+    kappa, beta, k, seed, S = 1.5, 0.7, 0.5, 23, 5
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     pcg_layout=layout, precond="neumann")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.5)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
+def test_neumann_neumann_vertex_solve():
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    kappa = 1.7
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = noise.white_noise(ml, 4, 5)
+    for precision, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        gv, uv, st = G.vertex_solve(kappa, 1.0, 0.05, torch.tensor(rhs, device="cuda"),
+                                    precision=precision, precond="neumann")
+        _, u_ref = sampler.vertex_condensation(m, ml, kmat, 0.05, rhs)
+        err = np.linalg.norm(uv.cpu().numpy() - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
+        assert err.max() < tol, (precision, err)
