@@ -40,7 +40,7 @@ namespace grf {
 namespace {
 
 constexpr size_t kSmemMax = 220 * 1024;
-constexpr double kInnerRtol = 1e-4;
+constexpr double kInnerRtol = 1e-5;
 
 // Verdicts of the inner loop.
 constexpr int kDone = 1, kStop = 2, kBad = 3;
@@ -450,11 +450,11 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
 constexpr int kThreadsG = 512;
 
 // Shared memory of the group kernel: P [nv][SGP] (search directions of the
-// group's samples, interleaved), the node's scaled FP32 off-diagonals [2E] and
-// 1 / sqrt(D) [nv].
+// group's samples, interleaved), the node's incidences as (neighbour, scaled
+// FP32 off-diagonal) pairs [2E], 1 / sqrt(D) [nv] and the incidence offsets.
 template <int SGP>
 __host__ __device__ inline size_t group_bytes(int32_t nv, int32_t ne) {
-  return 4 * ((size_t)nv * SGP + 2 * (size_t)ne + (size_t)nv + (size_t)nv + 1) + 16;
+  return 4 * ((size_t)nv * SGP + 4 * (size_t)ne + (size_t)nv + (size_t)nv + 1) + 16;
 }
 
 // One vertex's row of the interleaved search directions (SGP floats, 8- or
@@ -547,12 +547,14 @@ __device__ __forceinline__ void prec_group_apply(const DevGraph& g, int32_t nv,
   }
 }
 
-// Block sums of N floats (N = 2, 4 or 8): a warp butterfly, one row of N
-// partials per warp in shared memory (16-byte aligned rows), then every thread
-// adds the rows with vector loads in the same order, so all threads hold
-// identical values without a broadcast step.
+// Block sums of N floats (N = 2, 4 or 8) for NT <= 1024 threads: a warp
+// butterfly, one row of N partials per warp in shared memory (16-byte aligned
+// rows), then every warp reads the rows back with lane i taking row i mod W
+// and finishes with a butterfly over W lanes (W = NT / 32). All warps run the
+// same operations on the same data, so every thread ends with identical sums.
 template <int NT, int N>
 __device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
+  constexpr int W = NT / 32;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
 #pragma unroll
@@ -564,16 +566,17 @@ __device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
       *reinterpret_cast<float2*>(shw + (threadIdx.x >> 5) * N + k) = make_float2(v[k], v[k + 1]);
   }
   __syncthreads();
+  const int row = (threadIdx.x & 31) % W;
 #pragma unroll
-  for (int k = 0; k < N; ++k) v[k] = 0.f;
+  for (int k = 0; k < N; k += 2) {
+    const float2 t = *reinterpret_cast<const float2*>(shw + row * N + k);
+    v[k] = t.x;
+    v[k + 1] = t.y;
+  }
 #pragma unroll
-  for (int w = 0; w < NT / 32; ++w) {
+  for (int k = 0; k < N; ++k) {
 #pragma unroll
-    for (int k = 0; k < N; k += 2) {
-      const float2 t = *reinterpret_cast<const float2*>(shw + w * N + k);
-      v[k] += t.x;
-      v[k + 1] += t.y;
-    }
+    for (int o = W / 2; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   }
 }
 
@@ -605,8 +608,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
   float* P = reinterpret_cast<float*>(grp_sm);  // [nv][SGP]
-  float* Ot = P + (size_t)nv * SGP;             // [2E]
-  float* Ds = Ot + ne2;                         // [nv]
+  int2* NO = reinterpret_cast<int2*>(P + (size_t)nv * SGP);  // [2E] (neighbour, bits of o)
+  float* Ds = reinterpret_cast<float*>(NO + ne2);  // [nv]
   int32_t* vp = reinterpret_cast<int32_t*>(Ds + nv);  // [nv + 1] incidence offsets
   for (int32_t v = threadIdx.x; v <= nv; v += NT) vp[v] = g.vptr[v];
   const int64_t ngrp = (S + SGP - 1) / SGP;
@@ -616,7 +619,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
     const int64_t s0 = (u % ngrp) * SGP;
     const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
     __syncthreads();  // the previous unit is done with the shared arrays
-    for (int64_t k = threadIdx.x; k < ne2; k += NT) Ot[k] = offv_t[l * ne2 + k];
+    for (int64_t k = threadIdx.x; k < ne2; k += NT)
+      NO[k] = make_int2(g.adj_nbr[k], __float_as_int(offv_t[l * ne2 + k]));
     for (int32_t v = threadIdx.x; v < nv; v += NT) Ds[v] = dscale_t[l * nv + v];
     __syncthreads();
     const double* D = diag + l * nv;
@@ -789,10 +793,10 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
             for (int s = 0; s < SGP; ++s) acc[s] = pv[s];
             const int32_t kend = vp[v + 1];
             for (int32_t kk = vp[v]; kk < kend; ++kk) {
-              const int32_t w = g.adj_nbr[kk];
-              const float o = Ot[kk];
+              const int2 no = NO[kk];
+              const float o = __int_as_float(no.y);
               float pw[SGP];
-              load_row<SGP>(P + (size_t)w * SGP, pw);
+              load_row<SGP>(P + (size_t)no.x * SGP, pw);
 #pragma unroll
               for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, pw[s], acc[s]);
             }
@@ -816,7 +820,7 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
           } else if (!(pq[s] > 0.f)) {
             in[s] = false;  // p vanished at the FP32 floor: refine
           } else {
-            al[s] = rz[s] / pq[s];
+            al[s] = __fdividef(rz[s], pq[s]);
           }
         }
         float rr[SGP];
@@ -856,7 +860,7 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
             } else if (++since[s] >= 32) {
               in[s] = false;  // the FP32 recurrence reached its rounding floor
             }
-            be[s] = rr[s] / rz[s];
+            be[s] = __fdividef(rr[s], rz[s]);
             rz[s] = rr[s];
           }
           still = still || in[s];
@@ -1200,7 +1204,7 @@ __global__ void __launch_bounds__(NT) pcg_group_pre_kernel(
               act[s] = false;
             }
           } else {
-            al[s] = rz[s] / pq[s];
+            al[s] = __fdividef(rz[s], pq[s]);
           }
         }
 #pragma unroll
@@ -1245,7 +1249,7 @@ __global__ void __launch_bounds__(NT) pcg_group_pre_kernel(
             } else if (++since[s] >= 32) {
               in[s] = false;
             }
-            be[s] = rzn[s] / rz[s];
+            be[s] = __fdividef(rzn[s], rz[s]);
             rz[s] = rzn[s];
           }
           rrv[s] = rr;
