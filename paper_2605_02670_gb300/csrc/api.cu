@@ -359,6 +359,7 @@ struct ApplyWs {
   void* prm;  // SweepParams<T> [L][E]
   void* xw;   // T [L][S][V]
   float* bhat;  // sine transform of the interior noise [n_interior][S] (spectral path)
+  float *nshift, *nwgam;  // FP32 node constants [L] (spectral path)
   int32_t* iters;
   PcgStatus* status;
 };
@@ -429,6 +430,8 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->prm = c.take<char>(Ls * E * 4 * tsize);
   w->xw = c.take<char>(Ls * Ss * V * tsize);
   w->bhat = spectral && tsize == 4 ? c.take<float>((size_t)g->ni * Ss) : nullptr;
+  w->nshift = c.take<float>(Ls);
+  w->nwgam = c.take<float>(Ls);
   w->iters = c.take<int32_t>(Ls * Ss);
   w->status = c.take<PcgStatus>(1);
 }
@@ -482,6 +485,8 @@ DevNodes dev_nodes(const ApplyWs& w, int32_t L) {
   d.alpha = w.alpha;
   d.gamma = w.gamma;
   d.weight = w.weight;
+  d.shift = w.nshift;
+  d.wgam = w.nwgam;
   return d;
 }
 
@@ -532,6 +537,8 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   rs->end(1, st);
   rs->begin(st);
   if (sizeof(T) == 4 && o.spectral && w.bhat) {
+    launch_node_consts(nd, kappa2, w.nshift, w.nwgam, st);
+    rs->launches += 1;
     // edges beyond the spectral bins by Thomas, then the spectral bins
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[2],
                                        (int32_t)g->thomas_rest());
@@ -865,6 +872,7 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->yscr = w->rpscr = nullptr;
   w->prm = w->xw = nullptr;
   w->bhat = nullptr;
+  w->nshift = w->nwgam = nullptr;
 }
 
 // ---- learned preconditioner: model storage, initialisation and helpers

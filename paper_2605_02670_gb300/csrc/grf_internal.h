@@ -32,6 +32,11 @@ struct DevNodes {
   const double* alpha;
   const double* gamma;
   const double* weight;
+  // FP32 per-node constants of the FP32 interior kernels (may be null):
+  // shift_l = alpha_l / gamma_l + kappa^2 (delta_l = shift_l h_e^2) and
+  // wgam_l = w_l / gamma_l (w_l / c_l = wgam_l h_e)
+  const float* shift = nullptr;
+  const float* wgam = nullptr;
 };
 
 struct PcgStatus {
@@ -177,6 +182,9 @@ void lp_record_pairs(const DevGraph& g, int64_t nsys, int64_t S, const double* d
                      double rtol, int max_iter, int ctas, cudaStream_t st);
 
 // ---- spectral.cu: edge interiors in the sine basis (FP32 sweeps only).
+// shift[l], wgam[l] of DevNodes from alpha, gamma, weight (one launch).
+void launch_node_consts(const DevNodes& nd, double kappa2, float* shift, float* wgam,
+                        cudaStream_t st);
 // Spectral bins: bin i holds edges with 1 <= m <= mmax[i] interior nodes (and
 // above the previous bin's limit). Returns the number of bins.
 constexpr int kSpecSG = 16;  // samples per CTA

@@ -195,12 +195,13 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     const double h = g.he[e];
+    const float h2f = (float)(h * h);
     const int32_t va = g.eu[e], vb = g.ev[e];
     // end values: two nodes per thread share every row load
     for (int32_t l0 = 2 * threadIdx.x; l0 < nd.L; l0 += 2 * blockDim.x) {
       const bool two = l0 + 1 < nd.L;
-      const float dl0 = (float)((nd.alpha[l0] / nd.gamma[l0] + kappa2) * h * h);
-      const float dl1 = two ? (float)((nd.alpha[l0 + 1] / nd.gamma[l0 + 1] + kappa2) * h * h) : 1.f;
+      const float dl0 = nd.shift[l0] * h2f;
+      const float dl1 = two ? nd.shift[l0 + 1] * h2f : 1.f;
       float od[2][SG], ev[2][SG];
 #pragma unroll
       for (int s = 0; s < SG; ++s) od[0][s] = ev[0][s] = od[1][s] = ev[1][s] = 0.f;
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(256)
     const int64_t off = g.ioff[e];
     const int kv = (int)(S - s0 < SG ? S - s0 : SG);
     const double h = g.he[e];
+    const float hf = (float)h, h2f = (float)(h * h);
     const int32_t va = g.eu[e], vb = g.ev[e];
     __syncthreads();
     spec_tables(m, tab, ctab, sig);
@@ -283,9 +285,8 @@ __global__ void __launch_bounds__(256)
         __syncthreads();  // tables and cs visible; previous chunk consumed
         for (int32_t t = threadIdx.x; t < lc; t += blockDim.x) {
           const int32_t l = l0 + t;
-          const double gam = nd.gamma[l];
-          dls[t] = (float)((nd.alpha[l] / gam + kappa2) * h * h);
-          scs[t] = (float)(nd.weight[l] * h / gam);
+          dls[t] = nd.shift[l] * h2f;
+          scs[t] = nd.wgam[l] * hf;
         }
         for (int32_t t = threadIdx.x; t < lc * SG; t += blockDim.x) {
           const int32_t lq = t / SG, s = t - lq * SG;
@@ -349,6 +350,15 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+__global__ void node_consts_kernel(DevNodes nd, double kappa2, float* __restrict__ shift,
+                                   float* __restrict__ wgam) {
+  for (int32_t l = blockIdx.x * blockDim.x + threadIdx.x; l < nd.L; l += gridDim.x * blockDim.x) {
+    const double gam = nd.gamma[l];
+    shift[l] = (float)(nd.alpha[l] / gam + kappa2);
+    wgam[l] = (float)(nd.weight[l] / gam);
+  }
+}
+
 int grid_units(int64_t units) {
   int64_t b = units < 152 * 16 ? units : 152 * 16;
   return b < 1 ? 1 : (int)b;
@@ -364,6 +374,13 @@ struct SpecBin {
 constexpr SpecBin kSpecBins[] = {{64, 128, 1},  {128, 128, 1}, {256, 128, 2}, {384, 128, 3},
                                  {512, 128, 4}, {768, 256, 3}, {1024, 256, 4}};
 constexpr int kNumSpecBins = sizeof(kSpecBins) / sizeof(kSpecBins[0]);
+
+void launch_node_consts(const DevNodes& nd, double kappa2, float* shift, float* wgam,
+                        cudaStream_t st) {
+  int blocks = (nd.L + 255) / 256;
+  if (blocks > 152) blocks = 152;
+  node_consts_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(nd, kappa2, shift, wgam);
+}
 
 int spec_bins(int32_t* mmax) {
   for (int i = 0; i < kNumSpecBins; ++i) mmax[i] = kSpecBins[i].mmax;
