@@ -454,8 +454,10 @@ constexpr int kThreadsG = 512;
 // FP32 off-diagonal) pairs [2E], 1 / sqrt(D) [nv] and the incidence offsets.
 template <int SGP>
 __host__ __device__ inline size_t group_bytes(int32_t nv, int32_t ne) {
-  return 4 * ((size_t)nv * SGP + 4 * (size_t)ne + (size_t)nv + (size_t)nv + 1) + 16;
+  return 8 * (size_t)nv * SGP +
+         4 * ((size_t)nv * SGP + 4 * (size_t)ne + (size_t)nv + (size_t)nv + 1) + 16;
 }
+
 
 // One vertex's row of the interleaved search directions (SGP floats, 8- or
 // 16-byte aligned): a single vector access per vertex, no bank conflicts
@@ -547,6 +549,56 @@ __device__ __forceinline__ void prec_group_apply(const DevGraph& g, int32_t nv,
   }
 }
 
+// A vertex's row of the shared FP64 iterates (SGP doubles, 16-byte aligned).
+template <int SGP>
+__device__ __forceinline__ void load_xrow(const double* p, double (&v)[SGP]) {
+#pragma unroll
+  for (int s = 0; s < SGP; s += 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p + s);
+    v[s] = t.x;
+    v[s + 1] = t.y;
+  }
+}
+
+// FP64 residual res[s] = g_s - (S x_s)_v of an owned vertex v for the group's
+// samples, from the shared FP64 iterates X [nv][SGP] and the node's FP64 blocks:
+// every incidence's coefficient and neighbour are loaded once for all samples,
+// two incidences per step so that their loads are in flight together.
+template <int SGP>
+__device__ __forceinline__ void group_residual(int32_t v, int32_t nv, const int32_t* vp,
+                                               const int2* NO, const double* D, const double* O,
+                                               const double* X, const double* gl,
+                                               const bool (&act)[SGP], double (&res)[SGP]) {
+  double y[SGP], xv[SGP];
+  load_xrow<SGP>(X + (size_t)v * SGP, xv);
+  const double dv = D[v];
+#pragma unroll
+  for (int s = 0; s < SGP; ++s) y[s] = dv * xv[s];
+  const int32_t kend = vp[v + 1];
+  int32_t kk = vp[v];
+  for (; kk + 1 < kend; kk += 2) {
+    const int32_t w0 = NO[kk].x, w1 = NO[kk + 1].x;
+    const double o0 = O[kk], o1 = O[kk + 1];
+    double x0[SGP], x1[SGP];
+    load_xrow<SGP>(X + (size_t)w0 * SGP, x0);
+    load_xrow<SGP>(X + (size_t)w1 * SGP, x1);
+#pragma unroll
+    for (int s = 0; s < SGP; ++s)
+      if (act[s]) y[s] = fma(o1, x1[s], fma(o0, x0[s], y[s]));
+  }
+  if (kk < kend) {
+    const int32_t w0 = NO[kk].x;
+    const double o0 = O[kk];
+    double x0[SGP];
+    load_xrow<SGP>(X + (size_t)w0 * SGP, x0);
+#pragma unroll
+    for (int s = 0; s < SGP; ++s)
+      if (act[s]) y[s] = fma(o0, x0[s], y[s]);
+  }
+#pragma unroll
+  for (int s = 0; s < SGP; ++s) res[s] = act[s] ? gl[(int64_t)s * nv + v] - y[s] : 0.0;
+}
+
 // Block sums of N floats (N = 2, 4 or 8) for NT <= 1024 threads: a warp
 // butterfly, one row of N partials per warp in shared memory (16-byte aligned
 // rows), then every warp reads the rows back with lane i taking row i mod W
@@ -607,7 +659,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
   extern __shared__ __align__(16) unsigned char grp_sm[];
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
-  float* P = reinterpret_cast<float*>(grp_sm);  // [nv][SGP]
+  double* X = reinterpret_cast<double*>(grp_sm);  // [nv][SGP] FP64 iterates
+  float* P = reinterpret_cast<float*>(X + (size_t)nv * SGP);  // [nv][SGP]
   int2* NO = reinterpret_cast<int2*>(P + (size_t)nv * SGP);  // [2E] (neighbour, bits of o)
   float* Ds = reinterpret_cast<float*>(NO + ne2);  // [nv]
   int32_t* vp = reinterpret_cast<int32_t*>(Ds + nv);  // [nv + 1] incidence offsets
@@ -641,8 +694,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
             const double sv = gv * (double)Ds[v];
             nrm[s] += gv * gv;
             nrm[SGP + s] += sv * sv;
-            xl[(int64_t)s * nv + v] = 0.0;
           }
+          X[(size_t)v * SGP + s] = 0.0;
         }
       }
     }
@@ -684,15 +737,13 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
         for (int k = 0; k < VPT; ++k) {
           const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
+            double res[SGP];
+            group_residual<SGP>(v, nv, vp, NO, D, O, X, gl, act, res);
 #pragma unroll
             for (int s = 0; s < SGP; ++s) {
               float rs = 0.f;
               if (act[s]) {
-                const double* xs = xl + (int64_t)s * nv;
-                double y = D[v] * xs[v];
-                for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
-                  y += O[kk] * xs[g.adj_nbr[kk]];
-                const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+                const float ri = (float)(res[s] * igd[s]);
                 rs = ri * Ds[v] * cgs[s];
                 acc[s] = fmaf(ri, ri, acc[s]);
                 acc[SGP + s] = fmaf(rs, rs, acc[SGP + s]);
@@ -792,13 +843,23 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
 #pragma unroll
             for (int s = 0; s < SGP; ++s) acc[s] = pv[s];
             const int32_t kend = vp[v + 1];
-            for (int32_t kk = vp[v]; kk < kend; ++kk) {
-              const int2 no = NO[kk];
-              const float o = __int_as_float(no.y);
-              float pw[SGP];
-              load_row<SGP>(P + (size_t)no.x * SGP, pw);
+            int32_t kk = vp[v];
+            for (; kk + 1 < kend; kk += 2) {  // two gathers in flight
+              const int2 n0 = NO[kk], n1 = NO[kk + 1];
+              float p0[SGP], p1[SGP];
+              load_row<SGP>(P + (size_t)n0.x * SGP, p0);
+              load_row<SGP>(P + (size_t)n1.x * SGP, p1);
+              const float o0 = __int_as_float(n0.y), o1 = __int_as_float(n1.y);
 #pragma unroll
-              for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o, pw[s], acc[s]);
+              for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o1, p1[s], fmaf(o0, p0[s], acc[s]));
+            }
+            if (kk < kend) {
+              const int2 n0 = NO[kk];
+              float p0[SGP];
+              load_row<SGP>(P + (size_t)n0.x * SGP, p0);
+              const float o0 = __int_as_float(n0.y);
+#pragma unroll
+              for (int s = 0; s < SGP; ++s) acc[s] = fmaf(o0, p0[s], acc[s]);
             }
 #pragma unroll
             for (int s = 0; s < SGP; ++s) {
@@ -887,7 +948,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
         if (v < nv) {
 #pragma unroll
           for (int s = 0; s < SGP; ++s)
-            if (act[s]) xl[(int64_t)s * nv + v] = fma(sgm[s], (double)(Ds[v] * d[k][s]), xl[(int64_t)s * nv + v]);
+            if (act[s])
+              X[(size_t)v * SGP + s] = fma(sgm[s], (double)(Ds[v] * d[k][s]), X[(size_t)v * SGP + s]);
         }
       }
     }
@@ -904,14 +966,12 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
       for (int k = 0; k < VPT; ++k) {
         const int32_t v = threadIdx.x + k * NT;
         if (v < nv) {
+          double res[SGP];
+          group_residual<SGP>(v, nv, vp, NO, D, O, X, gl, act, res);
 #pragma unroll
           for (int s = 0; s < SGP; ++s) {
             if (act[s]) {
-              const double* xs = xl + (int64_t)s * nv;
-              double y = D[v] * xs[v];
-              for (int32_t kk = g.vptr[v]; kk < g.vptr[v + 1]; ++kk)
-                y += O[kk] * xs[g.adj_nbr[kk]];
-              const float ri = (float)((gl[(int64_t)s * nv + v] - y) * igd[s]);
+              const float ri = (float)(res[s] * igd[s]);
               acc[s] = fmaf(ri, ri, acc[s]);
             }
           }
@@ -921,6 +981,16 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
 #pragma unroll
       for (int s = 0; s < SGP; ++s)
         if (act[s]) done[s] = acc[s] <= rtol2f;
+    }
+    // the group's solutions out of shared memory
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+      const int32_t v = threadIdx.x + k * NT;
+      if (v < nv) {
+#pragma unroll
+        for (int s = 0; s < SGP; ++s)
+          if (s < kv) xl[(int64_t)s * nv + v] = X[(size_t)v * SGP + s];
+      }
     }
     if (threadIdx.x == 0) {
       for (int s = 0; s < kv; ++s) {
