@@ -532,8 +532,11 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                  RunStats* rs) {
   const DevNodes nd = dev_nodes(w, L);
   rs->begin(st);
-  rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv,
-                                  (SweepParams<T>*)w.prm, (T*)w.dscale, (T*)w.offv_t, st);
+  // the Thomas sweep constants are needed only where an edge is left to Thomas
+  SweepParams<T>* prm = (SweepParams<T>*)w.prm;
+  if (sizeof(T) == 4 && o.spectral && w.bhat && g->thomas_rest() == 0) prm = nullptr;
+  rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, prm,
+                                  (T*)w.dscale, (T*)w.offv_t, st);
   rs->end(1, st);
   rs->begin(st);
   if (sizeof(T) == 4 && o.spectral && w.bhat) {

@@ -14,8 +14,8 @@
 // matrix-free through one Thomas solve per edge in every PCG iteration
 // (Eq. matrix_free_local); it has rank-2 coupling, so the block is exact and
 // costs O(1) per (node, edge) instead of O(n_e). sinh(theta) =
-// sqrt(delta (1 + delta / 4)) and theta = 2 asinh(sqrt(delta) / 2) avoid
-// cancellation for small delta; exp / expm1 keep large n theta finite.
+// sqrt(delta (1 + delta / 4)) and theta = log1p(delta / 2 + sinh(theta)) avoid
+// cancellation for small delta; expm1 keeps large n theta finite.
 #include "grf_internal.h"
 
 namespace grf {
@@ -33,11 +33,15 @@ __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, doubl
     const double gam = nd.gamma[l];
     const double c = gam / h;
     const double delta = (nd.alpha[l] / gam + kappa2) * h * h;
+    // sinh(theta) and theta = acosh(1 + delta/2) = log1p(delta/2 + sinh(theta));
+    // with u = expm1(-n theta): exp(-n theta) = 1 + u and
+    // 1 - exp(-2 n theta) = -u (2 + u), both free of cancellation
     const double sh = sqrt(delta * (1.0 + 0.25 * delta));
-    const double theta = 2.0 * asinh(0.5 * sqrt(delta));
+    const double theta = log1p(0.5 * delta + sh);
     const double nth = (double)g.nel[e] * theta;
-    const double e1 = exp(-nth);
-    const double e2 = -expm1(-2.0 * nth);  // 1 - exp(-2 n theta)
+    const double u = expm1(-nth);
+    const double e1 = 1.0 + u;
+    const double e2 = -u * (2.0 + u);  // 1 - exp(-2 n theta)
     saa[t] = c * sh * ((2.0 - e2) / e2);
     sab[t] = -c * sh * (2.0 * e1 / e2);
     if (prm) {
