@@ -17,10 +17,11 @@ namespace {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c.x;
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    // one 32x32 -> 64-bit product per multiplier gives both halves
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+    const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+    const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
     c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
@@ -43,27 +44,33 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& n0,
   n1 = r * sn;
 }
 
+// FP32 Box-Muller of the mixed-precision path: the hardware logarithm and
+// sine/cosine (absolute errors ~1e-6 on these arguments, far inside the FP32
+// sweeps' tolerance; the uint32 words stay bit-exact).
 __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& n0, float& n1) {
   const float ua = fmaf((float)xa, 0x1p-32f, 0x1p-33f);
   const float ub = fmaf((float)xb, 0x1p-32f, 0x1p-33f);
-  const float r = sqrtf(-2.0f * logf(ua));
+  const float r = sqrtf(-2.0f * __logf(ua));
   float sn, cs;
-  sincospif(2.0f * ub, &sn, &cs);
+  __sincosf(6.2831853071795865f * ub, &sn, &cs);
   n0 = r * cs;
   n1 = r * sn;
 }
 
-// thread -> (q, s) with s fastest: a warp writes whole rows b[j][s0..s0+31]
+// Each thread keeps one sample s and walks the Philox blocks q of its row
+// group: a CTA covers SB = min(S, 1024) samples (blockIdx.y picks the sample
+// chunk) and blockDim / SB rows, so a warp writes whole rows b[j][s0..s0+31]
+// and no thread divides per block.
 template <typename T>
 __global__ void noise_minor_kernel(DevGraph g, uint64_t seed, const uint64_t* seed_dev, int64_t S,
-                                   T* __restrict__ b) {
+                                   int32_t SB, T* __restrict__ b) {
   if (seed_dev) seed = *seed_dev;
   const int64_t nq = (g.n + 3) / 4;
-  const int64_t total = nq * S;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = t / S;
-    const int64_t s = t - q * S;
+  const int32_t rows = blockDim.x / SB;  // Philox blocks per CTA pass
+  const int32_t qi = threadIdx.x / SB;
+  const int64_t s = (int64_t)blockIdx.y * SB + threadIdx.x % SB;
+  if (qi >= rows || s >= S) return;
+  for (int64_t q = (int64_t)blockIdx.x * rows + qi; q < nq; q += (int64_t)gridDim.x * rows) {
     const uint4 w = noise_block(seed, (uint64_t)q, (uint32_t)s);
     T n[4];
     box_muller(w.x, w.y, n[0], n[1]);
@@ -113,8 +120,19 @@ int grid_for(int64_t total, int threads) {
 template <typename T>
 void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st,
                         const uint64_t* seed_dev) {
-  const int64_t total = ((g.n + 3) / 4) * S;
-  noise_minor_kernel<T><<<grid_for(total, 256), 256, 0, st>>>(g, seed, seed_dev, S, b);
+  // SB samples per CTA, blockDim a multiple of SB (at least 256 threads when S allows)
+  const int32_t SB = (int32_t)(S < 1024 ? S : 1024);
+  const int32_t rows = SB >= 256 ? 1 : (256 + SB - 1) / SB;
+  const int threads = rows * SB;
+  const int64_t nq = (g.n + 3) / 4;
+  int64_t bx = (nq + rows - 1) / rows;
+  const int64_t by = (S + SB - 1) / SB;
+  int64_t cap = 152 * 32 / by;
+  if (cap < 1) cap = 1;
+  if (bx > cap) bx = cap;
+  if (bx < 1) bx = 1;
+  noise_minor_kernel<T><<<dim3((unsigned)bx, (unsigned)by), threads, 0, st>>>(g, seed, seed_dev,
+                                                                             S, SB, b);
 }
 template void launch_noise_minor<float>(const DevGraph&, uint64_t, int64_t, float*, cudaStream_t,
                                         const uint64_t*);
