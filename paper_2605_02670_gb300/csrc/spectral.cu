@@ -98,6 +98,37 @@ __device__ __forceinline__ void dst_rows(int32_t m, const int32_t (&j)[QJ], cons
   }
 }
 
+// Rows [m][SG] of a sample-minor array (row stride S, first sample s0, kv valid
+// samples) into shared memory, zero-padded to SG: float4 loads with several in
+// flight per thread when the rows are 16-byte aligned and whole.
+template <int SG>
+__device__ __forceinline__ void stage_rows(const float* __restrict__ src, int64_t S, int kv,
+                                           int32_t m, float* dst) {
+  if (kv == SG && (S & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+    constexpr int Q = SG / 4;  // float4 per row
+    const int32_t total = m * Q;
+    int32_t t = threadIdx.x;
+    for (; t + 3 * (int32_t)blockDim.x < total; t += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t tt = t + u * blockDim.x;
+        v[u] = *reinterpret_cast<const float4*>(src + (int64_t)(tt / Q) * S + 4 * (tt % Q));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) reinterpret_cast<float4*>(dst)[t + u * blockDim.x] = v[u];
+    }
+    for (; t < total; t += blockDim.x)
+      reinterpret_cast<float4*>(dst)[t] =
+          *reinterpret_cast<const float4*>(src + (int64_t)(t / Q) * S + 4 * (t % Q));
+  } else {
+    for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
+      const int32_t i = t / SG, c = t - i * SG;
+      dst[t] = c < kv ? src[(int64_t)i * S + c] : 0.f;
+    }
+  }
+}
+
 // a[s] += r * row[s]
 template <int SG>
 __device__ __forceinline__ void spec_acc(float r, const float* rowp, float (&a)[SG]) {
@@ -160,11 +191,7 @@ __global__ void __launch_bounds__(256)
     const int kv = (int)(S - s0 < SG ? S - s0 : SG);
     __syncthreads();  // the previous unit is done with the shared arrays
     spec_tables(m, tab, ctab, sig);
-    const float* bI = b + (g.nv + off) * S + s0;
-    for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
-      const int32_t i = t / SG, s = t - i * SG;
-      bs[t] = s < kv ? bI[(int64_t)i * S + s] : 0.f;
-    }
+    stage_rows<SG>(b + (g.nv + off) * S + s0, S, kv, m, bs);
     __syncthreads();
     const float scale = sqrtf(2.f / (float)(m + 1));
     // forward transform: modes t + q blockDim (q < QJ) per thread share every
@@ -265,11 +292,7 @@ __global__ void __launch_bounds__(256)
     const int32_t va = g.eu[e], vb = g.ev[e];
     __syncthreads();
     spec_tables(m, tab, ctab, sig);
-    const float* bh = bhat + off * S + s0;
-    for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
-      const int32_t i = t / SG, s = t - i * SG;
-      cs[t] = s < kv ? bh[(int64_t)i * S + s] : 0.f;
-    }
+    stage_rows<SG>(bhat + off * S + s0, S, kv, m, cs);
     const float scale = sqrtf(2.f / (float)(m + 1));
     // modes j0 + kJ * blockDim * pass ...: each thread owns up to kJ modes per pass
     for (int32_t jb = 0; jb < m; jb += kJ * blockDim.x) {
