@@ -357,7 +357,7 @@ struct ApplyWs {
   void* offv_t;         // float [L][2E] (mixed precision only)
   void *yscr, *rpscr;
   void* prm;  // SweepParams<T> [L][E]
-  void* xw;   // T [L][S][V]
+  void* xw;   // T [L][V][S] (sample-minor)
   float* bhat;  // sine transform of the interior noise [n_interior][S] (spectral path)
   float *nshift, *nwgam;  // FP32 node constants [L] (spectral path)
   int32_t* iters;

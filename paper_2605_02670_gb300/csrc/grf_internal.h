@@ -98,8 +98,8 @@ int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_
 // for longer ones (bin_count[n_bins] of them, listed last in bin_edges; they
 // need acc/yscr/rpscr, sized [n_interior][S]). bin_count is a host array.
 // Returns the number of kernels launched.
-// prm: sweep constants from launch_schur; xw: [L][S][nv] scratch that receives
-// w_l u_v^(l) in precision T.
+// prm: sweep constants from launch_schur; xw: [L][nv][S] scratch that receives
+// w_l u_v^(l) in precision T (sample-minor).
 template <typename T, typename OutT>
 int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                    const T* b, const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
@@ -206,7 +206,7 @@ int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, in
 constexpr int kMaxBins = 8;
 int recover_bins(bool fp64, int32_t* B, int32_t* NW);
 // bin_edges: edge ids grouped by bin (bin_count[i] each, bins in order);
-// prm[l][e] sweep constants, xw[l][s][v] = w_l u_v^(l) in precision T.
+// prm[l][e] sweep constants, xw[l][v][s] = w_l u_v^(l) in precision T.
 // Returns the number of kernels launched.
 // sg: samples per lane (FP32 sweeps: 1, 2 or 4; FP64 sweeps use 2).
 template <typename T, typename OutT>

@@ -180,9 +180,9 @@ __global__ void __launch_bounds__(32 * NW * UPC)
 #pragma unroll
       for (int s = 0; s < SG; ++s) {
         const bool ok = live && (s0 + s < S);
-        const int64_t base = ((int64_t)l * S + (ok ? s0 + s : 0)) * g.nv;
-        xa[s] = ok ? xw[base + va] : (T)0;
-        xb[s] = ok ? xw[base + vb] : (T)0;
+        const int64_t sj = ok ? s0 + s : 0;
+        xa[s] = ok ? xw[((int64_t)l * g.nv + va) * S + sj] : (T)0;
+        xb[s] = ok ? xw[((int64_t)l * g.nv + vb) * S + sj] : (T)0;
       }
       // pivots of this lane's nodes (rp[k] = 1 / p_{K0+k}) and of the node before
       T q, rp_prev;

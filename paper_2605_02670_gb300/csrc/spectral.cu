@@ -262,7 +262,7 @@ __host__ __device__ constexpr size_t spec_recover_floats(int32_t mmax) {
          (size_t)kSpecLChunk * (2 + 2 * SG) + 4;
 }
 
-// U_I = Phi c with c from bhat and the weighted vertex values xw = w_l u_v^(l).
+// U_I = Phi c with c from bhat and the weighted vertex values xw[l][v][s] = w_l u_v^(l).
 template <int SG, int QJ, typename OutT>
 __global__ void __launch_bounds__(256)
     spec_recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
@@ -311,13 +311,14 @@ __global__ void __launch_bounds__(256)
           dls[t] = nd.shift[l] * h2f;
           scs[t] = nd.wgam[l] * hf;
         }
+        // the two ends' rows xw[l][v][s0 .. s0 + SG) (contiguous per node)
         for (int32_t t = threadIdx.x; t < lc * SG; t += blockDim.x) {
           const int32_t lq = t / SG, s = t - lq * SG;
           float a = 0.f, c = 0.f;
           if (s < kv) {
-            const int64_t base = ((int64_t)(l0 + lq) * S + s0 + s) * g.nv;
-            a = xw[base + va];
-            c = xw[base + vb];
+            const int64_t l = l0 + lq;
+            a = xw[(l * g.nv + va) * S + s0 + s];
+            c = xw[(l * g.nv + vb) * S + s0 + s];
           }
           xp[t] = a + c;
           xm[t] = a - c;

@@ -125,8 +125,9 @@ __global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, 
   }
 }
 
-// U_v = sum_l w_l u_v^(l) in FP64; also leaves xw = w_l u_v^(l) in the sweep
-// precision for the interior recovery.
+// U_v = sum_l w_l u_v^(l) in FP64; also leaves xw[l][v][s] = w_l u_v^(l) in the
+// sweep precision for the interior recovery (sample-minor: an edge end's
+// samples are one contiguous row).
 template <typename T, typename OutT>
 __global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
                                     OutT* __restrict__ out, T* __restrict__ xw) {
@@ -140,7 +141,7 @@ __global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const do
       const int64_t i = ((int64_t)l * S + s) * g.nv + v;
       const double wx = nd.weight[l] * xv[i];
       acc += wx;
-      xw[i] = (T)wx;
+      xw[((int64_t)l * g.nv + v) * S + s] = (T)wx;
     }
     out[s * g.n + v] = (OutT)acc;
   }
