@@ -74,7 +74,7 @@ typedef struct grf_options {
   int32_t precond;     /* GRF_PRECOND_JACOBI, GRF_PRECOND_LEARNED or GRF_PRECOND_NEUMANN */
   int32_t out_dtype;   /* GRF_OUT_F64 or GRF_OUT_F32 */
   int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
-  double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-9 (mixed) */
+  double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-8 (mixed) */
   int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms) */
   int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
   int32_t recover_sg;  /* samples per lane in the interior recovery: 0 = auto, or 1, 2, 4

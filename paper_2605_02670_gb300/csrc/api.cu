@@ -326,7 +326,7 @@ int read_opts(const grf_options* o, Opts* r) {
   r->precond = o ? o->precond : GRF_PRECOND_JACOBI;
   r->out_dtype = o ? o->out_dtype : GRF_OUT_F64;
   r->max_iter = (o && o->max_iter > 0) ? o->max_iter : 1000;
-  r->rtol = (o && o->rtol > 0) ? o->rtol : (r->precision == GRF_FP64 ? 1e-12 : 1e-9);
+  r->rtol = (o && o->rtol > 0) ? o->rtol : (r->precision == GRF_FP64 ? 1e-12 : 1e-8);
   if (r->precision != GRF_FP64 && r->precision != GRF_MIXED)
     return fail(GRF_EINVAL, "unknown precision %d", r->precision);
   if (r->precond != GRF_PRECOND_JACOBI && r->precond != GRF_PRECOND_LEARNED &&

@@ -216,12 +216,12 @@ def test_sample_every_recovery_bin(precision, sg, interior):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
     Thomas recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps),
     each samples-per-lane variant, the sequential kernel for edges longer than
-    the largest bin, and every bin of the spectral path (m <= 32 .. 1024) with
-    the longer edges left to Thomas."""
-    ne = [2, 33, 65, 129, 257, 513, 1025, 2049, 4097, 5000, 3, 31]
+    the largest bin, and every bin of the spectral path (m <= 64, 128, 256,
+    384, 512, 768, 1024) with the longer edges left to Thomas."""
+    ne = [2, 33, 65, 129, 257, 513, 1025, 2049, 4097, 5000, 3, 31, 301, 701]
     E = len(ne)
-    eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 3])
-    ev = np.array([1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 5, 8])
+    eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 3, 1, 2])
+    ev = np.array([1, 2, 3, 4, 5, 6, 7, 8, 9, 0, 5, 8, 6, 9])
     lengths = np.array(ne) * 1e-3 * np.linspace(0.8, 1.2, E)
     g = gi.Graph(10, eu, ev, lengths)
     G, m = make(g, n_elems=ne)
