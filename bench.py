@@ -236,12 +236,25 @@ def run_grf(args, w, graph):
     stream = torch.cuda.current_stream()
     seed0 = w.seed + 1000003 * rank
 
+    train = None
+    if args.precond == "learned":
+        # setup outside the timed region: train the network on this workload
+        G.precond_init(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist, npairs = G.precond_train(w.kappa, w.beta, w.k_step, epochs=args.train_epochs,
+                                       seed=w.seed)
+        torch.cuda.synchronize()
+        train = {"epochs": args.train_epochs, "pairs": npairs,
+                 "seconds": round(time.perf_counter() - t0, 3),
+                 "loss_first": float(hist[0]), "loss_last": float(hist[-1])}
     knobs = {"pcg_layout": args.pcg_layout, "recover_sg": args.recover_sg}
     tune_ms = None
     if args.autotune and args.pcg_layout == "auto" and args.recover_sg == 0:
         # launch-schedule autotuner (setup, outside the timed region)
         knobs, tune_ms = G.autotune(w.kappa, w.beta, w.k_step, S, precision=prec,
-                                    out_dtype=out_dtype, reps=2)
+                                    out_dtype=out_dtype, reps=2, precond=args.precond)
+    knobs["precond"] = args.precond
 
     def step(i, timing=True):
         return G.sample(w.kappa, w.beta, w.k_step, seed0 + i, S, precision=prec,
@@ -346,6 +359,7 @@ def run_grf(args, w, graph):
                    "n_edges": G.n_edges, "quadrature_nodes": L, "samples_per_gpu": S,
                    "precision": prec, "l2": "flushed between timed steps",
                    "knobs": knobs, "autotune_ms": tune_ms, "cuda_graph": args.use_graph,
+                   "training": train,
                    "parallelism": f"replicas x{world}"},
         "dof_solves_per_s": dof_solves,
         "pcg_iters_total": st["pcg_iters_total"], "pcg_iters_max": st["pcg_iters_max"],
@@ -378,6 +392,10 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--use-graph", action="store_true",
                     help="replay the call as a captured CUDA graph (no per-phase timing)")
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "neumann", "learned"],
+                    help="vertex PCG preconditioner (mixed precision for learned; the "
+                         "learned network is trained on the workload before timing)")
+    ap.add_argument("--train-epochs", type=int, default=40)
     args = ap.parse_args()
     w = gi.WORKLOADS[args.workload]
     graph = w.graph()
