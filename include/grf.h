@@ -170,7 +170,9 @@ int grf_sample(grf_graph* g, double kappa, double beta, double k_step, uint64_t 
                grf_stats* stats);
 
 /* The same through host memory: out_host is a host buffer of the layout above;
- * the call copies the field device -> host. For callers without device buffers. */
+ * the call copies the field device -> host. For callers without device buffers.
+ * The device-side output is a buffer cached on the handle (grown when needed),
+ * so grf_options.use_graph replays stay valid across calls. */
 int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
                     int64_t n_samples, void* out_host, const grf_options* opts,
                     void* stream, grf_stats* stats);

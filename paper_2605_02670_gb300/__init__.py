@@ -375,9 +375,10 @@ class Graph:
 
     def sample_host(self, kappa, beta, k_step, seed, n_samples, precision="fp64",
                     out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False,
-                    precond="jacobi", pcg_layout="auto", recover_sg=0, interior="auto"):
+                    precond="jacobi", pcg_layout="auto", recover_sg=0, interior="auto",
+                    use_graph=False):
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            precond=precond, interior=interior)
+                            use_graph, precond=precond, interior=interior)
         dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
         if out is None:
             out = np.empty((n_samples, self.n_dofs), dtype=dt)

@@ -139,6 +139,10 @@ struct grf_graph {
   } gc;
   cudaStream_t cap_stream = nullptr;
   LearnedModel lm;
+  // device output of grf_sample_host, kept between calls so that a captured
+  // CUDA graph (which bakes the output pointer in) stays valid
+  void* host_out = nullptr;
+  size_t host_out_bytes = 0;
 
   void drop_graph() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -161,6 +165,7 @@ struct grf_graph {
       if (dev_block) cudaFree(dev_block);
       if (ws) cudaFree(ws);
       if (lm.blk) cudaFree(lm.blk);
+      if (host_out) cudaFree(host_out);
       cudaSetDevice(cur);
     }
   }
@@ -1626,15 +1631,25 @@ int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint
   GRF_TRY(read_opts(opts, &o));
   GRF_TRY(ensure_device(g));
   const size_t bytes = (size_t)g->n * (size_t)n_samples * (o.out_dtype == GRF_OUT_F64 ? 8 : 4);
-  void* dout = nullptr;
-  CUDA_TRY(cudaMallocAsync(&dout, bytes ? bytes : 1, (cudaStream_t)stream));
-  int r = grf_sample(g, kappa, beta, k_step, seed, n_samples, dout, opts, stream, stats);
+  if (g->host_out_bytes < bytes) {  // grow the cached device output
+    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (g->host_out) {
+      CUDA_TRY(cudaDeviceSynchronize());
+      g->drop_graph();  // a captured graph may write to the old buffer
+      CUDA_TRY(cudaFree(g->host_out));
+      g->host_out = nullptr;
+      g->host_out_bytes = 0;
+    }
+    CUDA_TRY(cudaMalloc(&g->host_out, bytes ? bytes : 1));
+    g->host_out_bytes = bytes ? bytes : 1;
+  }
+  int r = grf_sample(g, kappa, beta, k_step, seed, n_samples, g->host_out, opts, stream, stats);
   if (r == GRF_OK || r == GRF_ENOCONV) {
-    cudaError_t e = cudaMemcpyAsync(out_host, dout, bytes, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    cudaError_t e = cudaMemcpyAsync(out_host, g->host_out, bytes, cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) r = fail(GRF_ECUDA, "copy to host: %s", cudaGetErrorString(e));
   }
-  cudaFreeAsync(dout, (cudaStream_t)stream);
   return r;
 }
 

@@ -288,6 +288,20 @@ def test_cuda_graph_replay_matches_direct_calls(precision):
         assert rel_l2(graphed.cpu().numpy(), ref, ml) < TOL[precision]
 
 
+def test_sample_host_graph_replay_across_calls():
+    """grf_sample_host keeps its device output on the handle, so a captured
+    graph is replayed (not re-captured) by later calls and still follows the
+    seed; a larger sample count regrows the buffer and re-captures."""
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    ml = fem.lumped_mass(m)
+    for seed, S in ((5, 3), (6, 3), (7, 5), (5, 3)):
+        d, _ = G.sample_host(2.0, 0.6, 0.5, seed, S, precision="mixed", out_dtype="f64")
+        r, st = G.sample_host(2.0, 0.6, 0.5, seed, S, precision="mixed", out_dtype="f64",
+                              use_graph=True)
+        assert rel_l2(r, d, ml) < 1e-6 and st["n_unconverged"] == 0
+
+
 def test_autotune_returns_working_knobs():
     g, h = GRAPHS["random12"]()
     G, m = make(g, h)
