@@ -410,7 +410,8 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
   const int64_t nsys = (int64_t)L * S;
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
-  for (int64_t sys = blockIdx.x; sys < nsys; sys += gridDim.x) {
+  for (int64_t sys_i = blockIdx.x; sys_i < nsys; sys_i += gridDim.x) {
+    const int64_t sys = nsys - 1 - sys_i;  // largest shifts first (longest solves)
     const int64_t l = sys / S;
     SysMatrix<VT> M{g.vptr,
                     g.adj_nbr,
@@ -668,7 +669,9 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
   const int64_t ngrp = (S + SGP - 1) / SGP;
   const int64_t units = (int64_t)L * ngrp;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t l = u / ngrp;
+    // nodes from the largest shift down: the nodes that need the most
+    // iterations start first, so the last wave is made of short solves
+    const int64_t l = L - 1 - u / ngrp;
     const int64_t s0 = (u % ngrp) * SGP;
     const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
     __syncthreads();  // the previous unit is done with the shared arrays
@@ -1048,7 +1051,9 @@ __global__ void __launch_bounds__(NT) pcg_group_pre_kernel(
   const int64_t ngrp = (S + SGP - 1) / SGP;
   const int64_t units = (int64_t)L * ngrp;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int64_t l = u / ngrp;
+    // nodes from the largest shift down: the nodes that need the most
+    // iterations start first, so the last wave is made of short solves
+    const int64_t l = L - 1 - u / ngrp;
     const int64_t s0 = (u % ngrp) * SGP;
     const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
     __syncthreads();  // the previous unit is done with the shared arrays
