@@ -85,6 +85,8 @@ typedef struct grf_options {
                           phase timing is then not reported */
   int32_t interior;    /* edge-interior solver of the condensation and recovery steps:
                           GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS or GRF_INTERIOR_SPECTRAL */
+  int32_t sweep;       /* how FP32 edges left to the tridiagonal solves are swept:
+                          GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS or GRF_SWEEP_NODES */
 } grf_options;
 
 /* Edge-interior solvers (same results up to rounding):
@@ -99,6 +101,21 @@ typedef struct grf_options {
 #define GRF_INTERIOR_AUTO 0
 #define GRF_INTERIOR_THOMAS 1
 #define GRF_INTERIOR_SPECTRAL 2
+
+/* Parallel layouts of the FP32 tridiagonal edge solves (same results up to
+ * rounding; FP64 sweeps always use SEGMENTS):
+ *   SEGMENTS: the lanes of up to 16 warps split one edge into segments, the
+ *     eliminations of one node at a time run as scans across the lanes, and
+ *     the sum over nodes stays in registers;
+ *   NODES: one warp per edge and group of 4 samples, each lane a set of nodes
+ *     (at most 256 nodes) swept along the whole edge; the recovery uses the
+ *     twisted factorisation x_K = (y_K + z_K - r_K) / gamma_K (one elimination
+ *     from each end, no back substitution) and sums over nodes across lanes;
+ *   AUTO: NODES for the condensation of edges with more than 64 interior nodes
+ *     and the recovery of edges with more than 1024, SEGMENTS otherwise. */
+#define GRF_SWEEP_AUTO 0
+#define GRF_SWEEP_SEGMENTS 1
+#define GRF_SWEEP_NODES 2
 
 /* Vertex PCG launch layouts (same results up to rounding):
  *   PER_SYSTEM: one CTA per (node, sample) system, Schur matrix read through

@@ -31,6 +31,8 @@ PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged":
 GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL = 0, 1, 2
 INTERIORS = {"auto": GRF_INTERIOR_AUTO, "thomas": GRF_INTERIOR_THOMAS,
              "spectral": GRF_INTERIOR_SPECTRAL}
+GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS, GRF_SWEEP_NODES = 0, 1, 2
+SWEEPS = {"auto": GRF_SWEEP_AUTO, "segments": GRF_SWEEP_SEGMENTS, "nodes": GRF_SWEEP_NODES}
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
@@ -51,13 +53,15 @@ class grf_options(ctypes.Structure):
                 ("out_dtype", ctypes.c_int32), ("max_iter", ctypes.c_int32),
                 ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
                 ("pcg_layout", ctypes.c_int32), ("recover_sg", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("interior", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("interior", ctypes.c_int32),
+                ("sweep", ctypes.c_int32)]
 
     def knobs(self) -> dict:
         inv = {v: k for k, v in PCG_LAYOUTS.items()}
         inv_i = {v: k for k, v in INTERIORS.items()}
+        inv_s = {v: k for k, v in SWEEPS.items()}
         return {"pcg_layout": inv[self.pcg_layout], "recover_sg": self.recover_sg,
-                "interior": inv_i[self.interior]}
+                "interior": inv_i[self.interior], "sweep": inv_s[self.sweep]}
 
 
 class grf_train_options(ctypes.Structure):
@@ -148,14 +152,14 @@ def _stream(stream):
 
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
                  timing=False, pcg_layout="auto", recover_sg=0, use_graph=False,
-                 precond="jacobi", interior="auto") -> grf_options:
+                 precond="jacobi", interior="auto", sweep="auto") -> grf_options:
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, PRECONDS[precond], od, int(max_iter), float(rtol),
                        1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg),
-                       1 if use_graph else 0, INTERIORS[interior])
+                       1 if use_graph else 0, INTERIORS[interior], SWEEPS[sweep])
 
 
 # ------------------------------------------------------------ C-named functions
@@ -360,10 +364,10 @@ class Graph:
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
                rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
                pcg_layout="auto", recover_sg=0, use_graph=False, precond="jacobi",
-               interior="auto"):
+               interior="auto", sweep="auto"):
         import torch
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            use_graph, precond, interior)
+                            use_graph, precond, interior, sweep)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
@@ -376,9 +380,9 @@ class Graph:
     def sample_host(self, kappa, beta, k_step, seed, n_samples, precision="fp64",
                     out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False,
                     precond="jacobi", pcg_layout="auto", recover_sg=0, interior="auto",
-                    use_graph=False):
+                    use_graph=False, sweep="auto"):
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            use_graph, precond=precond, interior=interior)
+                            use_graph, precond=precond, interior=interior, sweep=sweep)
         dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
         if out is None:
             out = np.empty((n_samples, self.n_dofs), dtype=dt)
@@ -405,9 +409,9 @@ class Graph:
         return out
 
     def apply(self, kappa, alpha, gamma, weight, rhs, precision="fp64", out_dtype=None,
-              rtol=0.0, max_iter=0, stream=None, interior="auto"):
+              rtol=0.0, max_iter=0, stream=None, interior="auto", sweep="auto"):
         import torch
-        opts = make_options(precision, out_dtype, rtol, max_iter, interior=interior)
+        opts = make_options(precision, out_dtype, rtol, max_iter, interior=interior, sweep=sweep)
         rhs = rhs.to(dtype=torch.float64).contiguous()
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         out = torch.empty(tuple(rhs.shape), dtype=dt, device="cuda")

@@ -124,6 +124,7 @@ struct grf_graph {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
     bool spectral = false;
+    int sweep = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
     int64_t S = 0;
     void* out = nullptr;
@@ -312,6 +313,7 @@ struct Opts {
   int recover_sg;  // 1, 2 or 4
   bool use_graph;
   bool spectral;   // edge interiors in the sine basis (mixed precision)
+  int sweep;       // GRF_SWEEP_* of the FP32 tridiagonal edges
 };
 
 int read_opts(const grf_options* o, Opts* r) {
@@ -347,8 +349,38 @@ int read_opts(const grf_options* o, Opts* r) {
   if (in == GRF_INTERIOR_SPECTRAL && r->precision != GRF_MIXED)
     return fail(GRF_ENOTSUP, "the spectral interior solver needs precision GRF_MIXED");
   r->spectral = r->precision == GRF_MIXED && in != GRF_INTERIOR_THOMAS;
+  r->sweep = o ? o->sweep : GRF_SWEEP_AUTO;
+  if (r->sweep < GRF_SWEEP_AUTO || r->sweep > GRF_SWEEP_NODES)
+    return fail(GRF_EINVAL, "unknown sweep layout %d", r->sweep);
   return GRF_OK;
 }
+
+// FP32 tridiagonal edges of path p (0: every edge, 2: the edges the spectral
+// path leaves over) are grouped by recovery bin in increasing length. The edges
+// from bin node_bin0 on (and those beyond every bin) are swept by the
+// node-parallel kernels. AUTO (measured on GB300 with 148 nodes): the node
+// kernels condense faster from about 100 interior nodes on, and recover faster
+// beyond 1024 (2.2x at 3072; segments are ahead between 256 and 1024).
+int node_bin0(const grf_graph* g, int p, const Opts& o, int32_t L, bool recover) {
+  const int nb = g->n_bins[p];
+  if (o.sweep == GRF_SWEEP_SEGMENTS || !node_sweep_fits(L)) return nb + 1;
+  if (o.sweep == GRF_SWEEP_NODES) return 0;
+  const int32_t above = recover ? 1024 : 64;
+  int32_t B[kMaxBins], NW[kMaxBins];
+  recover_bins(false, B, NW);
+  int32_t lo = 0;  // bin i holds lo < m <= 32 NW B
+  for (int i = 0; i < nb; ++i) {
+    if (lo >= above) return i;
+    lo = 32 * NW[i] * B[i];
+  }
+  return nb;
+}
+int32_t bins_before(const grf_graph* g, int p, int i0) {
+  int32_t n = 0;
+  for (int i = 0; i < i0 && i <= g->n_bins[p]; ++i) n += g->bin_count[p][i];
+  return n;
+}
+int32_t bins_total(const grf_graph* g, int p) { return bins_before(g, p, g->n_bins[p] + 1); }
 
 // Device workspace of one domain-decomposed apply with L nodes and S right-hand sides.
 struct ApplyWs {
@@ -544,14 +576,26 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                                   (T*)w.dscale, (T*)w.offv_t, st);
   rs->end(1, st);
   rs->begin(st);
-  if (sizeof(T) == 4 && o.spectral && w.bhat) {
-    launch_node_consts(nd, kappa2, w.nshift, w.nwgam, st);
-    rs->launches += 1;
-    // edges beyond the spectral bins by Thomas, then the spectral bins
-    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[2],
-                                       (int32_t)g->thomas_rest());
-    rs->launches += launch_spec_condense(g->d, nd, kappa2, S, (const float*)b, g->d_spec_edges,
-                                         g->spec_count, w.bhat, gvec, st);
+  if (sizeof(T) == 4) {
+    // FP32: the tridiagonal edges (all of them, or those the spectral path
+    // leaves over), short ones by segments and long ones by nodes; then the
+    // spectral bins
+    const bool spec = o.spectral && w.bhat;
+    const int p = spec ? 2 : 0;
+    if (spec) {
+      launch_node_consts(nd, kappa2, w.nshift, w.nwgam, st);
+      rs->launches += 1;
+    }
+    const int32_t head = bins_before(g, p, node_bin0(g, p, o, L, false));
+    const int32_t tail = bins_total(g, p) - head;
+    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head);
+    if (tail > 0)
+      rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
+                                            (const SweepParams<float>*)prm,
+                                            g->d_bin_edges[p] + head, tail, gvec, st);
+    if (spec)
+      rs->launches += launch_spec_condense(g->d, nd, kappa2, S, (const float*)b, g->d_spec_edges,
+                                           g->spec_count, w.bhat, gvec, st);
   } else {
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
   }
@@ -615,11 +659,20 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
   const bool spec = sizeof(T) == 4 && o.spectral;
   const int p = sizeof(T) == 8 ? 1 : (spec ? 2 : 0);
+  // FP32: bins from i0 on (and the edges beyond every bin) by the node sweeps
+  const int i0 = sizeof(T) == 4 ? node_bin0(g, p, o, hn.L(), true) : g->n_bins[p] + 1;
+  int32_t counts[kMaxBins + 1];
+  for (int i = 0; i <= g->n_bins[p]; ++i) counts[i] = i < i0 ? g->bin_count[p][i] : 0;
+  const int32_t head = bins_before(g, p, i0), tail = bins_total(g, p) - head;
   rs->begin(st);
   rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
                                           (const SweepParams<T>*)w.prm, (T*)w.xw,
-                                          g->d_bin_edges[p], g->bin_count[p], g->n_bins[p], w.acc,
+                                          g->d_bin_edges[p], counts, g->n_bins[p], w.acc,
                                           (T*)w.yscr, (T*)w.rpscr, o.recover_sg, st);
+  if (sizeof(T) == 4 && tail > 0)
+    rs->launches += launch_recover_nodes<OutT>(
+        g->d, hn.L(), S, (const float*)b, (const SweepParams<float>*)w.prm, (const float*)w.xw,
+        g->d_bin_edges[p] + head, tail, out, st);
   if (spec)
     rs->launches += launch_spec_recover<OutT>(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
                                               g->spec_count, w.bhat, (const float*)w.xw, out, st);
@@ -740,7 +793,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
-                   gc.precond == o.precond && gc.spectral == o.spectral &&
+                   gc.precond == o.precond && gc.spectral == o.spectral && gc.sweep == o.sweep &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
                    gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
@@ -792,6 +845,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.precision = o.precision;
     gc.precond = o.precond;
     gc.spectral = o.spectral;
+    gc.sweep = o.sweep;
     gc.out_dtype = o.out_dtype;
     gc.pcg_layout = o.pcg_layout;
     gc.recover_sg = o.recover_sg;

@@ -105,6 +105,21 @@ int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t
                    const T* b, const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins,
                    double* acc, T* yscr, T* rpscr, int sg, cudaStream_t st);
+// ---- sweep.cu (FP32 interiors)
+// Node-parallel sweeps: one warp per (edge, 4 samples), each lane a set of
+// quadrature nodes (at most kNodeSweepMaxNL per lane, so L <= 32 kNodeSweepMaxNL).
+// condense: adds the listed edges' end values into gvec (after launch_condense's
+// vertex init); recover: writes the listed edges' interior DOFs of out.
+// Both need the sweep constants prm of launch_schur. Return the launch count.
+constexpr int kNodeSweepMaxNL = 8;
+bool node_sweep_fits(int32_t L);
+int launch_condense_nodes(const DevGraph& g, int32_t L, int64_t S, const float* b,
+                          const SweepParams<float>* prm, const int32_t* edges, int32_t n_edges,
+                          double* gvec, cudaStream_t st);
+template <typename OutT>
+int launch_recover_nodes(const DevGraph& g, int32_t L, int64_t S, const float* b,
+                         const SweepParams<float>* prm, const float* xw, const int32_t* edges,
+                         int32_t n_edges, OutT* out, cudaStream_t st);
 // [S][n] double -> [n][S] T, each DOF j scaled by scale[j] (or 1 when scale is null
 // and mass_scale is false; by M_L,j = sqrt_ml[j]^2 when mass_scale is true)
 template <typename T>

@@ -30,6 +30,8 @@
 // SG trades registers for shared work: pivots and the scans' multipliers are
 // computed once per lane for SG samples, while fewer samples per lane leave
 // room for more resident warps. It is a launch parameter picked by measurement.
+#include <type_traits>
+
 #include "grf_internal.h"
 
 namespace grf {
@@ -37,18 +39,46 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// FP32 pivots use the SFU reciprocal (relative error a few 1e-8): the sweeps
+// contract, so pivot errors of that size stay at that size.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+// K theta from which coth(K theta) = 1 in the working precision (2 exp(-2 K
+// theta) below half an ulp): the pivots of such nodes are the fixed point.
+// SG consecutive values of a shared-memory row (aligned to SG * sizeof(T)).
+template <typename T, int SG>
+__device__ __forceinline__ void load_vec(const T* p, T (&v)[SG]) {
+  if constexpr (std::is_same<T, float>::value && SG == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (std::is_same<T, float>::value && SG == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else if constexpr (std::is_same<T, double>::value && SG == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int s = 0; s < SG; ++s) v[s] = p[s];
+  }
+}
+
+template <typename T>
+constexpr T kConvTheta = sizeof(T) == 4 ? (T)9 : (T)19;
 __device__ __forceinline__ float tanh_t(float x) { return tanhf(x); }
 __device__ __forceinline__ double tanh_t(double x) { return tanh(x); }
 
 // Inclusive composition of affine maps y -> R + A y across the lanes of a warp.
 // forward: lane i ends with f_i o f_{i-1} o ... o f_0;
 // backward: lane i ends with f_i o f_{i+1} o ... o f_31.
-template <typename T, int SG, bool kForward>
+// Only the first SPAN lanes need the result (lanes from SPAN on hold the
+// identity when SPAN < 32).
+template <typename T, int SG, bool kForward, int SPAN = 32>
 __device__ __forceinline__ void warp_scan(T& a, T (&r)[SG], int lane) {
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
+  for (int d = 1; d < SPAN; d <<= 1) {
     T ap, rp[SG];
     if (kForward) {
       ap = __shfl_up_sync(kFull, a, d);
@@ -93,7 +123,10 @@ __device__ __forceinline__ void lane_carry(T a, const T (&r)[SG], int lane, int 
   T win[SG];
 #pragma unroll
   for (int s = 0; s < SG; ++s) win[s] = (T)0;
-  if (NW > 1) {
+  if constexpr (NW > 1) {
+    // One barrier per direction and node: the forward and backward totals
+    // live in separate rows, and a row is rewritten only after the other
+    // direction's barrier, which every warp passes after its last read.
     const int tot_lane = kForward ? 31 : 0;
     const int dir = kForward ? 0 : 1;
     if (lane == tot_lane) {
@@ -102,18 +135,24 @@ __device__ __forceinline__ void lane_carry(T a, const T (&r)[SG], int lane, int 
       for (int s = 0; s < SG; ++s) sh_r[dir][wi][s] = ir[s];
     }
     __syncthreads();
-    if (kForward) {
-      for (int j = 0; j < wi; ++j) {
+    // lane j < NW takes warp j's total, the other lanes the identity; one scan
+    // over them gives every warp the composition of the warps before (after) it
+    T ta = (T)1, tr[SG];
 #pragma unroll
-        for (int s = 0; s < SG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
-      }
-    } else {
-      for (int j = NW - 1; j > wi; --j) {
+    for (int s = 0; s < SG; ++s) tr[s] = (T)0;
+    if (lane < NW) {
+      ta = sh_a[dir][lane];
 #pragma unroll
-        for (int s = 0; s < SG; ++s) win[s] = fma(sh_a[dir][j], win[s], sh_r[dir][j][s]);
-      }
+      for (int s = 0; s < SG; ++s) tr[s] = sh_r[dir][lane][s];
     }
-    __syncthreads();
+    warp_scan<T, SG, kForward, NW>(ta, tr, lane);
+    const int src = kForward ? wi - 1 : wi + 1;
+    const bool none = kForward ? wi == 0 : wi == NW - 1;
+#pragma unroll
+    for (int s = 0; s < SG; ++s) {
+      const T t = __shfl_sync(kFull, tr[s], src & 31);
+      win[s] = none ? (T)0 : t;
+    }
   }
 #pragma unroll
   for (int s = 0; s < SG; ++s) carry[s] = fma(ea, win[s], er[s]);
@@ -173,48 +212,77 @@ __global__ void __launch_bounds__(32 * NW * UPC)
 #pragma unroll
       for (int s = 0; s < SG; ++s) accf[k][s] = (T)0;
 
-    for (int32_t l = 0; l < L; ++l) {
-      const SweepParams<T> pr = prm[(int64_t)l * g.ne + e];
+    // the boundary values enter only the lanes holding node 1 (x_a) and node m (x_b)
+    const bool has1 = live && K0 == 1;
+    const bool hasm = live && K0 <= m && m < K0 + B;
+    const int km = m - K0;  // slot of node m in this lane when hasm
+    const SweepParams<T>* pe = prm + e;
+    const T* xap = xw + (int64_t)va * S + s0;
+    const T* xbp = xw + (int64_t)vb * S + s0;
+    const int64_t xstep = (int64_t)g.nv * S;
+    for (int32_t l = 0; l < L; ++l, pe += g.ne, xap += xstep, xbp += xstep) {
+      const SweepParams<T> pr = *pe;
       const T dl = pr.delta, sc = pr.sc, shv = pr.sh, th = pr.theta;
+      // The sweeps run on the right-hand side divided by sc (b + (x_a / sc) e_1 +
+      // (x_b / sc) e_m); the factor sc is applied once, when summing over nodes.
       T xa[SG], xb[SG];
+      if (has1 || hasm) {
+        const T isc = rcp(sc);
 #pragma unroll
-      for (int s = 0; s < SG; ++s) {
-        const bool ok = live && (s0 + s < S);
-        const int64_t sj = ok ? s0 + s : 0;
-        xa[s] = ok ? xw[((int64_t)l * g.nv + va) * S + sj] : (T)0;
-        xb[s] = ok ? xw[((int64_t)l * g.nv + vb) * S + sj] : (T)0;
+        for (int s = 0; s < SG; ++s) {
+          const bool ok = s0 + s < S;
+          xa[s] = (has1 && ok) ? xap[s] * isc : (T)0;
+          xb[s] = (hasm && ok) ? xbp[s] * isc : (T)0;
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < SG; ++s) xa[s] = xb[s] = (T)0;
       }
       // pivots of this lane's nodes (rp[k] = 1 / p_{K0+k}) and of the node before
-      T q, rp_prev;
-      if (K0 >= 2) {
-        q = (T)0.5 * dl + shv / tanh_t((T)(K0 - 1) * th);
-        rp_prev = rcp((T)1 + q);
-        q = dl + q * rp_prev;
-      } else {
-        rp_prev = (T)0;
-        q = (T)1 + dl;
-      }
-      T rp[B];
+      T rp_prev, rp[B];
+      if (K0 >= 2 && (T)(K0 - 1) * th >= kConvTheta<T>) {
+        // every node of the lane is at the fixed point p* = 1 + delta / 2 + sinh(theta)
+        const T rps = rcp((T)1 + (T)0.5 * dl + shv);
+        rp_prev = rps;
+        if (hasm) {
 #pragma unroll
-      for (int k = 0; k < B; ++k) {
-        const T r_ = rcp((T)1 + q);
-        rp[k] = (K0 + k <= m) ? r_ : (T)0;
-        q = dl + q * r_;
+          for (int k = 0; k < B; ++k) rp[k] = k <= km ? rps : (T)0;
+        } else {
+          const T r_ = K0 <= m ? rps : (T)0;
+#pragma unroll
+          for (int k = 0; k < B; ++k) rp[k] = r_;
+        }
+      } else {
+        T q;
+        if (K0 >= 2) {
+          q = (T)0.5 * dl + quot(shv, tanh_t((T)(K0 - 1) * th));
+          rp_prev = rcp((T)1 + q);
+          q = dl + q * rp_prev;
+        } else {
+          rp_prev = (T)0;
+          q = (T)1 + dl;
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          const T r_ = rcp((T)1 + q);
+          rp[k] = (K0 + k <= m) ? r_ : (T)0;
+          q = dl + q * r_;
+        }
       }
       if (K0 > m) rp_prev = (T)0;
-      // right-hand side and forward elimination from a zero carry
+      // forward elimination from a zero carry
       T y[B][SG];
 #pragma unroll
       for (int k = 0; k < B; ++k) {
-        const int K = K0 + k;
+        T bv[SG];
+        if (kRbSmem)
+          load_vec<T, SG>(rbs + (k * 32 + lane) * SG, bv);
+        else
 #pragma unroll
-        for (int s = 0; s < SG; ++s) {
-          const T bv = kRbSmem ? rbs[(k * 32 + lane) * SG + s] : rb[kRbSmem ? 0 : k][s];
-          T r = bv * sc;
-          if (K == 1) r += xa[s];
-          if (K == m) r += xb[s];
-          y[k][s] = (k == 0) ? r : fma(rp[k - 1], y[k - 1][s], r);
-        }
+          for (int s = 0; s < SG; ++s) bv[s] = rb[kRbSmem ? 0 : k][s];
+#pragma unroll
+        for (int s = 0; s < SG; ++s)
+          y[k][s] = (k == 0) ? bv[s] + xa[s] : fma(rp[k - 1], y[k - 1][s], bv[s]);
       }
       T af = rp_prev;
 #pragma unroll
@@ -230,14 +298,20 @@ __global__ void __launch_bounds__(32 * NW * UPC)
           for (int s = 0; s < SG; ++s) y[k][s] = fma(c, yin[s], y[k][s]);
         }
       }
-      // back substitution from a zero carry: x_K = y_K / p_K + x_{K+1} / p_K
+      // x_b enters at node m: y_m is used only by the back substitution there
+      if (hasm) {
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+          if (k == km)
+#pragma unroll
+            for (int s = 0; s < SG; ++s) y[k][s] += xb[s];
+      }
+      // back substitution from a zero carry: x_K = (y_K + x_{K+1}) / p_K
 #pragma unroll
       for (int k = B - 1; k >= 0; --k) {
 #pragma unroll
-        for (int s = 0; s < SG; ++s) {
-          const T u = y[k][s] * rp[k];
-          y[k][s] = (k == B - 1) ? u : fma(rp[k], y[k + 1][s], u);
-        }
+        for (int s = 0; s < SG; ++s)
+          y[k][s] = (k == B - 1) ? y[k][s] * rp[k] : (y[k][s] + y[k + 1][s]) * rp[k];
       }
       T ab = (T)1;
 #pragma unroll
@@ -250,7 +324,7 @@ __global__ void __launch_bounds__(32 * NW * UPC)
         for (int k = B - 1; k >= 0; --k) {
           c *= rp[k];
 #pragma unroll
-          for (int s = 0; s < SG; ++s) accf[k][s] += fma(c, xin[s], y[k][s]);
+          for (int s = 0; s < SG; ++s) accf[k][s] = fma(sc, fma(c, xin[s], y[k][s]), accf[k][s]);
         }
       }
       if ((l + 1) % group == 0 || l + 1 == L) {

@@ -17,6 +17,8 @@
 // recover: U_I = sum_l w_l T^{-1} (b_I / c + u_a e_1 + u_b e_m) (Eq.
 //   internal_recovery) with the quadrature sum (Phase 5) fused: the weight is
 //   folded into the right-hand side and the sum over nodes is kept in FP64.
+#include <type_traits>
+
 #include "grf_internal.h"
 
 namespace grf {
@@ -42,34 +44,82 @@ __global__ void gvec_init_kernel(DevGraph g, int32_t L, int64_t S, const T* __re
   }
 }
 
+// Reciprocal of a pivot. FP32: the SFU approximation (relative error a few
+// 1e-8); the sweeps contract, so pivot errors of that size stay at that size.
+__device__ __forceinline__ float rcp_piv(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_piv(double x) { return 1.0 / x; }
+
+// q_K = delta / 2 + sinh(theta) coth(K theta) reaches q* = delta / 2 + sinh(theta)
+// in the working precision once 2 exp(-2 K theta) is below half an ulp:
+// K theta >= 9 in FP32, >= 19 in FP64. First node index from which q_K = q*
+// (clamped to [2, m + 1]).
+template <typename T>
+__device__ __forceinline__ int32_t converged_from(T delta, int32_t m) {
+  constexpr T kTheta = sizeof(T) == 4 ? (T)9 : (T)19;
+  const T th = (T)2 * asinh((T)0.5 * sqrt(delta));
+  const T k = th > (T)0 ? ceil(kTheta / th) : (T)(m + 1);
+  if (!(k < (T)(m + 1))) return m + 1;
+  return k < (T)2 ? 2 : (int32_t)k;
+}
+
 // One CTA per (edge, group of kSG samples): the edge's noise rows are staged in
 // shared memory once ([m][kSG]) and every thread runs the two end eliminations
 // of one quadrature node from there (all threads read the same row at the same
-// step: broadcast). The pivot recurrence of a node is shared by its kSG samples.
+// step: broadcast). The pivot recurrence of a node is shared by its kSG samples
+// and runs only until it has converged; from there on the pivot is the fixed
+// point 1 + q*.
 // The two end eliminations of one node over rows src[i * stride .. + kSG).
-// Only the first kv (<= kSG) samples of a row are read.
-template <typename T>
+// Only the first kv (<= kSG) samples of a row are read; kStaged: rows are
+// contiguous in shared memory (stride kSG, all kSG samples), read as vectors.
+template <typename T, bool kStaged>
+__device__ __forceinline__ void load_row(const T* p, int kv, T (&v)[kSG]) {
+  if constexpr (kStaged && std::is_same<T, float>::value) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (kStaged) {
+    const double2 t0 = *reinterpret_cast<const double2*>(p);
+    const double2 t1 = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = t0.x; v[1] = t0.y; v[2] = t1.x; v[3] = t1.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < kSG; ++k) v[k] = k < kv ? p[k] : (T)0;
+  }
+}
+
+template <typename T, bool kStaged>
 __device__ __forceinline__ void end_sweeps(const T* src, int64_t stride, int32_t m, T delta,
                                            int kv, T (&yf)[kSG], T (&yr)[kSG], T& rp_out) {
-#pragma unroll
-  for (int k = 0; k < kSG; ++k) {
-    yf[k] = k < kv ? src[k] : (T)0;
-    yr[k] = k < kv ? src[(int64_t)(m - 1) * stride + k] : (T)0;
-  }
+  load_row<T, kStaged>(src, kv, yf);
+  load_row<T, kStaged>(src + (int64_t)(m - 1) * stride, kv, yr);
   T q = (T)1 + delta;
-  T rp = (T)1 / ((T)1 + q);
-  for (int32_t i = 1; i < m; ++i) {
-    const T* rowf = src + (int64_t)i * stride;
-    const T* rowr = src + (int64_t)(m - 1 - i) * stride;
+  T rp = rcp_piv((T)1 + q);
+  const int32_t kc = converged_from<T>(delta, m);  // nodes >= kc have q = q*
+  int32_t i = 1;
+  for (; i < kc && i < m; ++i) {
+    T rf[kSG], rr[kSG];
+    load_row<T, kStaged>(src + (int64_t)i * stride, kv, rf);
+    load_row<T, kStaged>(src + (int64_t)(m - 1 - i) * stride, kv, rr);
 #pragma unroll
     for (int k = 0; k < kSG; ++k) {
-      if (k < kv) {
-        yf[k] = rowf[k] + rp * yf[k];
-        yr[k] = rowr[k] + rp * yr[k];
-      }
+      yf[k] = rf[k] + rp * yf[k];
+      yr[k] = rr[k] + rp * yr[k];
     }
     q = delta + q * rp;
-    rp = (T)1 / ((T)1 + q);
+    rp = rcp_piv((T)1 + q);
+  }
+  if (i < m) {
+    rp = rcp_piv((T)1 + (T)0.5 * delta + sqrt(delta * ((T)1 + (T)0.25 * delta)));
+#pragma unroll 4
+    for (; i < m; ++i) {
+      T rf[kSG], rr[kSG];
+      load_row<T, kStaged>(src + (int64_t)i * stride, kv, rf);
+      load_row<T, kStaged>(src + (int64_t)(m - 1 - i) * stride, kv, rr);
+#pragma unroll
+      for (int k = 0; k < kSG; ++k) {
+        yf[k] = rf[k] + rp * yf[k];
+        yr[k] = rr[k] + rp * yr[k];
+      }
+    }
   }
   rp_out = rp;
 }
@@ -110,9 +160,9 @@ __global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, 
       const T delta = (T)((nd.alpha[l] / nd.gamma[l] + kappa2) * h * h);
       T yf[kSG], yr[kSG], rp;
       if (staged)
-        end_sweeps<T>(sb, kSG, m, delta, kSG, yf, yr, rp);
+        end_sweeps<T, true>(sb, kSG, m, delta, kSG, yf, yr, rp);
       else
-        end_sweeps<T>(bI + s0, S, m, delta, kv, yf, yr, rp);
+        end_sweeps<T, false>(bI + s0, S, m, delta, kv, yf, yr, rp);
       double* gl = gvec + (int64_t)l * S * g.nv;
 #pragma unroll
       for (int k = 0; k < kSG; ++k) {

@@ -232,6 +232,51 @@ def test_sample_every_recovery_bin(precision, sg, interior):
     assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
 
 
+@pytest.mark.parametrize("sweep,interior", [("nodes", "thomas"), ("segments", "thomas"),
+                                            ("nodes", "spectral")])
+@pytest.mark.parametrize("S", [6, 8])
+@pytest.mark.parametrize("h", [1e-3, 2e-2])
+def test_sample_node_sweeps(sweep, interior, S, h):
+    """The node-parallel FP32 sweeps (one warp per edge and 4 samples, twisted
+    factorisation in the recovery) against the oracle: interiors of 1 to 2999
+    nodes, so that the 8-node output blocks end ragged and the two end zones of
+    unconverged pivots overlap (small h: j theta < 9 along whole edges) or
+    leave a long converged middle (large h); S = 6 leaves a group of 2 samples
+    (scalar row loads), S = 8 full groups (vector loads)."""
+    ne = [2, 3, 4, 8, 9, 10, 16, 17, 18, 300, 1025, 3000]
+    E = len(ne)
+    eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 0, 2, 4, 6])
+    ev = np.array([1, 2, 3, 4, 5, 6, 7, 0, 4, 6, 1, 3])
+    lengths = np.array(ne) * h
+    g = gi.Graph(8, eu, ev, lengths)
+    G, m = make(g, n_elems=ne)
+    kappa, beta, k, seed = 6.0, 0.6, 0.5, 23
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     interior=interior, sweep=sweep)
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, n_elems=ne)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
+@pytest.mark.parametrize("beta", [0.25, 0.75])
+def test_node_sweeps_many_nodes_per_lane(beta):
+    """k = 0.3 gives 148 quadrature nodes at beta = 0.25 and 0.75: five nodes per
+    lane; the node and segment sweeps agree, and both match the oracle."""
+    ne = [40, 600, 1500]
+    g = gi.Graph(3, np.array([0, 1, 2]), np.array([1, 2, 0]), np.array(ne) * 2.0 ** -9)
+    G, m = make(g, n_elems=ne)
+    kappa, k, seed, S = 8.0, 0.3, 5, 4
+    un, _ = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     interior="thomas", sweep="nodes")
+    us, _ = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     interior="thomas", sweep="segments")
+    ml = fem.lumped_mass(m)
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, n_elems=ne)
+    assert rel_l2(un.cpu().numpy(), ref, ml) < TOL["mixed"]
+    assert rel_l2(us.cpu().numpy(), ref, ml) < TOL["mixed"]
+    assert rel_l2(un.cpu().numpy(), us.cpu().numpy(), ml) < TOL["mixed"]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("beta", [1.0, 1.25, 2.0, 2.6])
 def test_sample_integer_powers(precision, beta):
@@ -308,6 +353,7 @@ def test_autotune_returns_working_knobs():
     knobs, ms = G.autotune(3.0, 0.7, 0.5, 8, precision="mixed")
     assert knobs["pcg_layout"] in ("per_system", "staged", "staged_pairs")
     assert knobs["recover_sg"] in (1, 2, 4) and knobs["interior"] in ("thomas", "spectral")
+    assert knobs["sweep"] in ("auto", "segments", "nodes")
     assert ms > 0
     u, _ = G.sample(3.0, 0.7, 0.5, 9, 8, precision="mixed", out_dtype="f64", **knobs)
     _, ref, _ = sampler.sample(g, 3.0, 0.7, 0.5, 9, 8, h=h)
