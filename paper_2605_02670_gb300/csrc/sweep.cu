@@ -41,6 +41,8 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 4;  // units (warps) per CTA
 constexpr int kS = 4;      // samples per unit
+// resident CTAs per SM the register budget aims at (128 or 168 registers, no spills)
+constexpr int min_blocks(int nl) { return nl <= 5 ? 4 : 3; }
 constexpr float kConvTheta = 9.0f;
 
 __device__ __forceinline__ float rcpf(float x) { return __fdividef(1.0f, x); }
@@ -107,6 +109,7 @@ __device__ __forceinline__ void chunked_sweep(float4* buf, int lane, const float
     const int32_t jn = c0 + 32 + lane;
     pf = fetch_row(rows, S, ri(jn), vec, kv, jn <= j1);
     const int32_t cnt = min(32, j1 - c0 + 1);
+#pragma unroll 1
     for (int32_t i = 0; i < cnt; ++i) step(c0 + i, buf[i]);
   }
 }
@@ -152,7 +155,7 @@ __device__ __forceinline__ Unit unit_of(const DevGraph& g, const int32_t* edges,
 // Step j carries the elimination into node j from node j - 1 (pivot 1 + q_{j-1}),
 // from node 1 forward (y) and from node m backward (z, rows m - j).
 template <int NL>
-__global__ void __launch_bounds__(32 * kWarps)
+__global__ void __launch_bounds__(32 * kWarps, min_blocks(NL))
     condense_nodes_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ b,
                           const SweepParams<float>* __restrict__ prm,
                           const int32_t* __restrict__ edges, int32_t n_edges,
@@ -167,17 +170,18 @@ __global__ void __launch_bounds__(32 * kWarps)
     const Unit t = unit_of(g, edges, nsg, u, n_units, S);
     const int32_t m = t.m;
     if (m <= 0) continue;  // uniform across the warp
-    NodeK k[NL];
-    float q[NL], rp[NL];
+    float dl[NL], rps[NL], q[NL], rp[NL];
     int kcw = 2;
 #pragma unroll
     for (int n = 0; n < NL; ++n) {
       const int l = lane + 32 * n;
       const bool on = l < L;
-      k[n] = node_consts(on ? prm[(int64_t)l * g.ne + t.e] : SweepParams<float>{}, m, on);
+      const NodeK k = node_consts(on ? prm[(int64_t)l * g.ne + t.e] : SweepParams<float>{}, m, on);
+      dl[n] = k.dl;
+      rps[n] = k.rps;
       q[n] = 0.f;
       rp[n] = 0.f;
-      kcw = max(kcw, k[n].kc);
+      kcw = max(kcw, k.kc);
     }
     kcw = __reduce_max_sync(kFull, kcw);
     const float* rows = b + (g.nv + t.off) * S + t.s0;
@@ -208,11 +212,11 @@ __global__ void __launch_bounds__(32 * kWarps)
           for (int n = 0; n < NL; ++n)
 #pragma unroll
             for (int s = 0; s < kS; ++s) {
-              yf[n][s] = fmaf(k[n].rps, yf[n][s], fv[s]);
-              yr[n][s] = fmaf(k[n].rps, yr[n][s], rv[s]);
+              yf[n][s] = fmaf(rps[n], yf[n][s], fv[s]);
+              yr[n][s] = fmaf(rps[n], yr[n][s], rv[s]);
             }
         }
-      } else {
+      } else {  // the recurrence runs on past convergence: its fixed point attracts
         for (int32_t i = 0; i < cnt; ++i) {
           const int32_t j = c0 + i;
           const float4 f = bf[i], r = br[i];
@@ -225,9 +229,8 @@ __global__ void __launch_bounds__(32 * kWarps)
               yr[n][s] = fmaf(rp[n], yr[n][s], rv[s]);
             }
             // pivot of node j for the next step
-            const float qj = j == 1 ? 1.0f + k[n].dl : fmaf(q[n], rp[n], k[n].dl);
-            q[n] = j < k[n].kc ? qj : k[n].qs;
-            rp[n] = j < k[n].kc ? rcpf(1.0f + q[n]) : k[n].rps;
+            q[n] = j == 1 ? 1.0f + dl[n] : fmaf(q[n], rp[n], dl[n]);
+            rp[n] = rcpf(1.0f + q[n]);
           }
         }
       }
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(32 * kWarps)
     for (int n = 0; n < NL; ++n) {
       const int l = lane + 32 * n;
       if (l >= L) continue;
-      const float rpm = m >= k[n].kc ? k[n].rps : rp[n];
+      const float rpm = m > kcw ? rps[n] : rp[n];
       double* gl = gvec + (int64_t)l * S * g.nv;
 #pragma unroll
       for (int s = 0; s < kS; ++s) {
@@ -256,30 +259,43 @@ __global__ void __launch_bounds__(32 * kWarps)
 // 1 / gamma_K is the diagonal of T^{-1} in closed form,
 //   1 / gamma = F(j) F(m + 1 - j) / (2 sinh(theta) F(m + 1)),  F(i) = 1 - exp(-2 i theta),
 // so the factor of a node is sc / (2 sinh(theta)) times F of the distances to
-// both ends. Three regions: near the start (j <= kcw: own pivots by the
-// recurrence, F(j) by its recurrence F(j+1) = F(j) + exp(-2 j theta) F(1)),
-// the middle (both pivots at the fixed point, factor constant), near the other
-// end (j > m + 1 - kcw: F(m + 1 - j) from exp, re-anchored every 8 nodes and
-// at the last 8). Edges shorter than 2 kcw take the first kind of step
-// throughout, with F of the far end from its closed form.
+// both ends. Regions: the two boundary nodes (x_a, x_b enter there), near the
+// start (j <= kcw: own pivots by the recurrence, F(j) by F(j+1) = F(j) +
+// exp(-2 j theta) F(1)), the middle (both pivots at the fixed point, constant
+// factor), near the other end (j > m + 1 - kcw: F(m + 1 - j) from exp,
+// re-anchored every 8 nodes and at the last 8). Edges shorter than 2 kcw take
+// the near kind of step throughout, with F of the far end from its closed form.
+// Each region loads the constants it needs, so few stay live across regions.
 // Results go to out at node K for sample s in lane 8 s + ((K - 1) & 7), stored
 // in aligned blocks of 8 nodes; pass B reads back what the same lane wrote in
 // pass A and adds to it.
 template <int NL, bool kB, typename OutT>
 __device__ __forceinline__ void twisted_pass(const Unit& t, int lane, int64_t S, int64_t n_dofs,
-                                             int32_t nv, const float* rows, bool vec,
-                                             const NodeK (&k)[NL], const float* xs,
-                                             const float* xe, int64_t xstride, int kcw,
-                                             float4* buf, OutT* out) {
+                                             int32_t nv, int32_t L, const float* rows, bool vec,
+                                             const SweepParams<float>* pe, int64_t pstride,
+                                             const float* xs, const float* xe, int64_t xstride,
+                                             int kcw, float4* buf, OutT* out) {
   const int32_t m = t.m;
   const int sl = lane >> 3;  // this lane's sample in the sums
   const bool store_lane = t.live && sl < t.kv;
   OutT* orow = out + (t.s0 + (sl < t.kv ? sl : 0)) * n_dofs + nv + t.off;  // + K - 1
-  float y[NL][kS];
+  auto prm_of = [&](int n) {
+    const int l = lane + 32 * n;
+    SweepParams<float> p;
+    if (l < L) {
+      p = pe[(int64_t)l * pstride];
+    } else {  // an empty slot: contributes nothing
+      p.delta = 1.f; p.sc = 0.f; p.sh = 1.f; p.theta = 1.f;
+    }
+    return p;
+  };
+  float y[NL][kS], rp[NL];
 #pragma unroll
-  for (int n = 0; n < NL; ++n)
+  for (int n = 0; n < NL; ++n) {
+    rp[n] = 0.f;
 #pragma unroll
     for (int s = 0; s < kS; ++s) y[n][s] = 0.f;
+  }
   float keep = 0.f;  // this lane's node of the current block of 8
   auto finish = [&](int j, float (&c)[kS]) {
     const float v = warp_sum4(c, lane);
@@ -298,135 +314,181 @@ __device__ __forceinline__ void twisted_pass(const Unit& t, int lane, int64_t S,
       }
     }
   };
-  // x_s / sc at j = 1, x_e / sc at j = m (uniform branch)
-  auto boundary = [&](int j, int n, float (&add)[kS]) {
-#pragma unroll
-    for (int s = 0; s < kS; ++s) add[s] = 0.f;
-    if (j == 1 || j == m) {
-      if (k[n].sc != 0.f) {
-        const float isc = rcpf(k[n].sc);
-        const int l = lane + 32 * n;
-#pragma unroll
-        for (int s = 0; s < kS; ++s) {
-          if (s < t.kv) {
-            if (j == 1) add[s] += xs[(int64_t)l * xstride + s] * isc;
-            if (j == m) add[s] += xe[(int64_t)l * xstride + s] * isc;
-          }
-        }
-      }
-    }
-  };
   auto row_of = [&](int j) { return kB ? m - j : j - 1; };
   const bool overlap = m + 1 < 2 * kcw;
-  const int e1 = overlap ? m : min(kcw, m);  // last near step
-  const int s3 = overlap ? m + 1 : m + 2 - kcw;  // first far step
-  // near region: own pivots and F(j) by their recurrences
-  {
-    float q[NL], rp[NL], eo[NL], fo[NL], ed[NL], d1[NL], nrm[NL];
+  // a boundary node (j = 1 or j = m): the factor from its closed form; the
+  // carry rp[] holds 1 / p_{j-1} and on return 1 / p_1
+  auto edge_step = [&](int j, float4 r4) {
+    const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
+    float c[kS] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int n = 0; n < NL; ++n) {
-      q[n] = 1.0f + k[n].dl;
-      rp[n] = 0.f;
-      d1[n] = one_minus_exp(2.0f * k[n].th);  // F(1)
-      ed[n] = 1.0f - d1[n];                   // exp(-2 theta)
-      eo[n] = ed[n];
-      fo[n] = d1[n];
-      nrm[n] = overlap ? rcpf(one_minus_exp(2.0f * (float)(m + 1) * k[n].th)) : 1.0f;
+      const SweepParams<float> p = prm_of(n);
+      const int l = lane + 32 * n;
+      const float isc = p.sc != 0.f ? rcpf(p.sc) : 0.f;
+      float add[kS] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int s = 0; s < kS; ++s) {
+        if (p.sc != 0.f && s < t.kv) {
+          if (j == 1) add[s] += xs[(int64_t)l * xstride + s] * isc;
+          if (j == m) add[s] += xe[(int64_t)l * xstride + s] * isc;
+        }
+      }
+      const float two = 2.0f * p.theta;
+      const float g = p.sc * rcpf(2.0f * p.sh) * one_minus_exp(two * (float)j) *
+                      one_minus_exp(two * (float)(m + 1 - j)) *
+                      rcpf(one_minus_exp(two * (float)(m + 1)));
+#pragma unroll
+      for (int s = 0; s < kS; ++s) {
+        const float tc = rp[n] * y[n][s];
+        y[n][s] = r[s] + add[s] + tc;
+        c[s] = fmaf(g, kB ? tc : y[n][s], c[s]);
+      }
+      // 1 / p_1 for the carry into node 2 (q_1 = 1 + delta); after node m no carry
+      rp[n] = rcpf(2.0f + p.delta);
+      asm volatile("" ::: "memory");  // one slot's loads at a time: fewer live registers
     }
-    chunked_sweep(buf, lane, rows, S, vec, t.kv, 1, e1, row_of, [&](int j, float4 r4) {
+    finish(j, c);
+  };
+  chunked_sweep(buf, lane, rows, S, vec, t.kv, 1, 1, row_of, edge_step);
+  if (m == 1) return;
+  // near region j = 2 .. e1. The pivot recurrence runs on past the nodes whose
+  // pivot has converged: the fixed point is attracting, so it stays there.
+  const int e1 = overlap ? m - 1 : min(kcw, m - 1);
+  {
+    // gf = sc F(j) / (2 sinh(theta)) and its increment w = sc F(1) exp(-2 j theta) / (2 sinh(theta))
+    float q[NL], gf[NL], w[NL], ed[NL], dl[NL], thn[NL], nrm[NL];
+#pragma unroll
+    for (int n = 0; n < NL; ++n) {
+      const SweepParams<float> p = prm_of(n);
+      dl[n] = p.delta;
+      const float cs = p.sc * rcpf(2.0f * p.sh);
+      const float d1 = one_minus_exp(2.0f * p.theta);  // F(1)
+      ed[n] = 1.0f - d1;                               // exp(-2 theta)
+      // state at j = 2: q_2, F(2), exp(-4 theta)
+      const float q1 = 1.0f + p.delta;
+      q[n] = fmaf(q1, rp[n], p.delta);
+      gf[n] = cs * fmaf(ed[n], d1, d1);
+      w[n] = cs * d1 * ed[n] * ed[n];
+      thn[n] = p.theta;
+      nrm[n] = overlap ? rcpf(one_minus_exp(2.0f * (float)(m + 1) * p.theta)) : 1.0f;
+    }
+    chunked_sweep(buf, lane, rows, S, vec, t.kv, 2, e1, row_of, [&](int j, float4 r4) {
       const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
       float c[kS] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int n = 0; n < NL; ++n) {
-        float add[kS];
-        boundary(j, n, add);
-        const int jf = m + 1 - j;
-        const float ff =
-            overlap && jf < k[n].kc ? one_minus_exp(2.0f * (float)jf * k[n].th) * nrm[n] : 1.0f;
-        const float gsc = k[n].cs * fo[n] * ff;
+        float gsc = gf[n];
+        if (overlap)  // uniform; F(m + 1 - j) rounds to 1 away from the far end
+          gsc *= one_minus_exp(2.0f * (float)(m + 1 - j) * thn[n]) * nrm[n];
+        if (kB) {
+          const float gr = gsc * rp[n];
 #pragma unroll
-        for (int s = 0; s < kS; ++s) {
-          const float tc = rp[n] * y[n][s];  // carried from the previous node
-          y[n][s] = r[s] + add[s] + tc;
-          c[s] = fmaf(gsc, kB ? tc : y[n][s], c[s]);
+          for (int s = 0; s < kS; ++s) {
+            c[s] = fmaf(gr, y[n][s], c[s]);
+            y[n][s] = fmaf(rp[n], y[n][s], r[s]);
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < kS; ++s) {
+            y[n][s] = fmaf(rp[n], y[n][s], r[s]);
+            c[s] = fmaf(gsc, y[n][s], c[s]);
+          }
         }
-        const float qo = q[n];
-        rp[n] = j < k[n].kc ? rcpf(1.0f + qo) : k[n].rps;
-        q[n] = j + 1 < k[n].kc ? fmaf(qo, rp[n], k[n].dl) : k[n].qs;
-        fo[n] = fmaf(eo[n], d1[n], fo[n]);
-        eo[n] *= ed[n];
+        // pivot of node j for the carry into j + 1, then q_{j+1}, F(j+1)
+        rp[n] = rcpf(1.0f + q[n]);
+        q[n] = fmaf(q[n], rp[n], dl[n]);
+        gf[n] += w[n];
+        w[n] *= ed[n];
       }
       finish(j, c);
     });
   }
   // middle: both pivots at the fixed point, constant factor
-  {
-    float cf[NL];
-#pragma unroll
-    for (int n = 0; n < NL; ++n) cf[n] = kB ? k[n].cs * k[n].rps : k[n].cs;
-    chunked_sweep(buf, lane, rows, S, vec, t.kv, e1 + 1, min(s3 - 1, m - 1), row_of,
-                  [&](int j, float4 r4) {
-                    const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
-                    float c[kS] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int n = 0; n < NL; ++n) {
-#pragma unroll
-                      for (int s = 0; s < kS; ++s) {
-                        if (kB) {  // the carried part rps z_{j-1} enters the sum
-                          c[s] = fmaf(cf[n], y[n][s], c[s]);
-                          y[n][s] = fmaf(k[n].rps, y[n][s], r[s]);
-                        } else {
-                          y[n][s] = fmaf(k[n].rps, y[n][s], r[s]);
-                          c[s] = fmaf(cf[n], y[n][s], c[s]);
-                        }
-                      }
-                    }
-                    finish(j, c);
-                  });
-  }
-  // far region: own pivot at the fixed point, F(m + 1 - j) from exp
-  if (!overlap) {
-    float ef[NL], e2[NL];
+  const int s3 = overlap ? m : max(m + 2 - kcw, e1 + 1);  // first far step
+  if (s3 - 1 >= e1 + 1) {
+    float rps[NL], cf[NL];
 #pragma unroll
     for (int n = 0; n < NL; ++n) {
-      ef[n] = 0.f;
-      // exp(2 theta), capped: where it would overflow, exp(-2 jf theta) is 0 already
-      e2[n] = __expf(fminf(2.0f * k[n].th, 80.0f));
+      const SweepParams<float> p = prm_of(n);
+      rps[n] = rcpf(1.0f + 0.5f * p.delta + p.sh);
+      const float cs = p.sc * rcpf(2.0f * p.sh);
+      cf[n] = kB ? cs * rps[n] : cs;
+      rp[n] = rps[n];
     }
-    chunked_sweep(buf, lane, rows, S, vec, t.kv, max(s3, e1 + 1), m, row_of,
-                  [&](int j, float4 r4) {
-                    const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
-                    float c[kS] = {0.f, 0.f, 0.f, 0.f};
-                    const int jf = m + 1 - j;
-                    const bool anchor = (jf & 7) == 0 || jf <= 8 || j == s3;
+    chunked_sweep(buf, lane, rows, S, vec, t.kv, e1 + 1, s3 - 1, row_of, [&](int j, float4 r4) {
+      const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
+      float c[kS] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int n = 0; n < NL; ++n) {
-                      float add[kS];
-                      boundary(j, n, add);
-                      float ff;
-                      if (anchor) {  // uniform branch
-                        const float a = 2.0f * (float)jf * k[n].th;
-                        ef[n] = __expf(-a);
-                        ff = one_minus_exp(a);
-                      } else {
-                        ef[n] *= e2[n];
-                        ff = 1.0f - ef[n];
-                      }
-                      const float gsc = k[n].cs * ff;
+      for (int n = 0; n < NL; ++n) {
 #pragma unroll
-                      for (int s = 0; s < kS; ++s) {
-                        const float tc = k[n].rps * y[n][s];
-                        y[n][s] = r[s] + add[s] + tc;
-                        c[s] = fmaf(gsc, kB ? tc : y[n][s], c[s]);
-                      }
-                    }
-                    finish(j, c);
-                  });
+        for (int s = 0; s < kS; ++s) {
+          if (kB) {  // the carried part rps z_{j-1} enters the sum
+            c[s] = fmaf(cf[n], y[n][s], c[s]);
+            y[n][s] = fmaf(rps[n], y[n][s], r[s]);
+          } else {
+            y[n][s] = fmaf(rps[n], y[n][s], r[s]);
+            c[s] = fmaf(cf[n], y[n][s], c[s]);
+          }
+        }
+      }
+      finish(j, c);
+    });
   }
+  // far region j = s3 .. m - 1: own pivot at the fixed point, F(m + 1 - j) from exp
+  if (!overlap && s3 <= m - 1) {
+    float rps[NL], cs[NL], thn[NL], e2[NL], ef[NL];
+#pragma unroll
+    for (int n = 0; n < NL; ++n) {
+      const SweepParams<float> p = prm_of(n);
+      rps[n] = rcpf(1.0f + 0.5f * p.delta + p.sh);
+      cs[n] = p.sc * rcpf(2.0f * p.sh);
+      thn[n] = p.theta;
+      // exp(2 theta), capped: where it would overflow, exp(-2 jf theta) is 0 already
+      e2[n] = __expf(fminf(2.0f * p.theta, 80.0f));
+      ef[n] = 0.f;
+      rp[n] = rps[n];
+    }
+    chunked_sweep(buf, lane, rows, S, vec, t.kv, s3, m - 1, row_of, [&](int j, float4 r4) {
+      const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
+      float c[kS] = {0.f, 0.f, 0.f, 0.f};
+      const int jf = m + 1 - j;
+      const bool anchor = (jf & 7) == 0 || jf <= 8 || j == s3;
+#pragma unroll
+      for (int n = 0; n < NL; ++n) {
+        float ff;
+        if (anchor) {  // uniform branch
+          const float a = 2.0f * (float)jf * thn[n];
+          ef[n] = __expf(-a);
+          ff = one_minus_exp(a);
+        } else {
+          ef[n] *= e2[n];
+          ff = 1.0f - ef[n];
+        }
+        const float gsc = cs[n] * ff;
+        if (kB) {
+          const float gr = gsc * rps[n];
+#pragma unroll
+          for (int s = 0; s < kS; ++s) {
+            c[s] = fmaf(gr, y[n][s], c[s]);
+            y[n][s] = fmaf(rps[n], y[n][s], r[s]);
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < kS; ++s) {
+            y[n][s] = fmaf(rps[n], y[n][s], r[s]);
+            c[s] = fmaf(gsc, y[n][s], c[s]);
+          }
+        }
+      }
+      finish(j, c);
+    });
+  }
+  chunked_sweep(buf, lane, rows, S, vec, t.kv, m, m, row_of, edge_step);
 }
 
 template <int NL, typename OutT>
-__global__ void __launch_bounds__(32 * kWarps)
+__global__ void __launch_bounds__(32 * kWarps, min_blocks(NL))
     recover_nodes_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ b,
                          const SweepParams<float>* __restrict__ prm,
                          const float* __restrict__ xw, const int32_t* __restrict__ edges,
@@ -440,14 +502,16 @@ __global__ void __launch_bounds__(32 * kWarps)
        u += (int64_t)gridDim.x * kWarps) {
     const Unit t = unit_of(g, edges, nsg, u, n_units, S);
     if (t.m <= 0) continue;  // uniform across the warp
-    NodeK k[NL];
+    const SweepParams<float>* pe = prm + t.e;
     int kcw = 2;
 #pragma unroll
     for (int n = 0; n < NL; ++n) {
       const int l = lane + 32 * n;
-      const bool on = l < L;
-      k[n] = node_consts(on ? prm[(int64_t)l * g.ne + t.e] : SweepParams<float>{}, t.m, on);
-      kcw = max(kcw, k[n].kc);
+      if (l < L) {
+        const float kcf = ceilf(kConvTheta / pe[(int64_t)l * g.ne].theta);
+        const int kc = kcf < (float)(t.m + 1) ? (kcf < 2.f ? 2 : (int)kcf) : t.m + 1;
+        kcw = max(kcw, kc);
+      }
     }
     kcw = __reduce_max_sync(kFull, kcw);
     const float* rows = b + (g.nv + t.off) * S + t.s0;
@@ -455,10 +519,10 @@ __global__ void __launch_bounds__(32 * kWarps)
     const int64_t xstride = (int64_t)g.nv * S;
     const float* xa = xw + (int64_t)t.va * S + t.s0;
     const float* xb = xw + (int64_t)t.vb * S + t.s0;
-    twisted_pass<NL, false, OutT>(t, lane, S, g.n, g.nv, rows, vec, k, xa, xb, xstride, kcw,
-                                  stage[wid], out);
-    twisted_pass<NL, true, OutT>(t, lane, S, g.n, g.nv, rows, vec, k, xb, xa, xstride, kcw,
-                                 stage[wid], out);
+    twisted_pass<NL, false, OutT>(t, lane, S, g.n, g.nv, L, rows, vec, pe, g.ne, xa, xb, xstride,
+                                  kcw, stage[wid], out);
+    twisted_pass<NL, true, OutT>(t, lane, S, g.n, g.nv, L, rows, vec, pe, g.ne, xb, xa, xstride,
+                                 kcw, stage[wid], out);
   }
 }
 
