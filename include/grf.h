@@ -111,8 +111,7 @@ typedef struct grf_options {
  *     (at most 256 nodes) swept along the whole edge; the recovery uses the
  *     twisted factorisation x_K = (y_K + z_K - r_K) / gamma_K (one elimination
  *     from each end, no back substitution) and sums over nodes across lanes;
- *   AUTO: NODES for the condensation of edges with more than 64 interior nodes
- *     and the recovery of edges with more than 1024, SEGMENTS otherwise. */
+ *   AUTO: NODES for edges with more than 64 interior nodes, SEGMENTS below. */
 #define GRF_SWEEP_AUTO 0
 #define GRF_SWEEP_SEGMENTS 1
 #define GRF_SWEEP_NODES 2

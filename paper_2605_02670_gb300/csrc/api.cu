@@ -358,19 +358,18 @@ int read_opts(const grf_options* o, Opts* r) {
 // FP32 tridiagonal edges of path p (0: every edge, 2: the edges the spectral
 // path leaves over) are grouped by recovery bin in increasing length. The edges
 // from bin node_bin0 on (and those beyond every bin) are swept by the
-// node-parallel kernels. AUTO (measured on GB300 with 148 nodes): the node
-// kernels condense faster from about 100 interior nodes on, and recover faster
-// beyond 1024 (2.2x at 3072; segments are ahead between 256 and 1024).
-int node_bin0(const grf_graph* g, int p, const Opts& o, int32_t L, bool recover) {
+// node-parallel kernels. AUTO (measured on GB300 with 148 nodes and 64
+// samples): from about 100 interior nodes on they condense 1.5-3x and recover
+// 1.7-3.6x faster than the segment kernels.
+int node_bin0(const grf_graph* g, int p, const Opts& o, int32_t L) {
   const int nb = g->n_bins[p];
   if (o.sweep == GRF_SWEEP_SEGMENTS || !node_sweep_fits(L)) return nb + 1;
   if (o.sweep == GRF_SWEEP_NODES) return 0;
-  const int32_t above = recover ? 1024 : 64;
   int32_t B[kMaxBins], NW[kMaxBins];
   recover_bins(false, B, NW);
   int32_t lo = 0;  // bin i holds lo < m <= 32 NW B
   for (int i = 0; i < nb; ++i) {
-    if (lo >= above) return i;
+    if (lo >= 64) return i;
     lo = 32 * NW[i] * B[i];
   }
   return nb;
@@ -586,7 +585,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       launch_node_consts(nd, kappa2, w.nshift, w.nwgam, st);
       rs->launches += 1;
     }
-    const int32_t head = bins_before(g, p, node_bin0(g, p, o, L, false));
+    const int32_t head = bins_before(g, p, node_bin0(g, p, o, L));
     const int32_t tail = bins_total(g, p) - head;
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head);
     if (tail > 0)
@@ -660,7 +659,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   const bool spec = sizeof(T) == 4 && o.spectral;
   const int p = sizeof(T) == 8 ? 1 : (spec ? 2 : 0);
   // FP32: bins from i0 on (and the edges beyond every bin) by the node sweeps
-  const int i0 = sizeof(T) == 4 ? node_bin0(g, p, o, hn.L(), true) : g->n_bins[p] + 1;
+  const int i0 = sizeof(T) == 4 ? node_bin0(g, p, o, hn.L()) : g->n_bins[p] + 1;
   int32_t counts[kMaxBins + 1];
   for (int i = 0; i <= g->n_bins[p]; ++i) counts[i] = i < i0 ? g->bin_count[p][i] : 0;
   const int32_t head = bins_before(g, p, i0), tail = bins_total(g, p) - head;

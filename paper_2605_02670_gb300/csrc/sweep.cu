@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(32 * kWarps, min_blocks(NL))
 // exp(-2 j theta) F(1)), the middle (both pivots at the fixed point, constant
 // factor), near the other end (j > m + 1 - kcw: F(m + 1 - j) from exp,
 // re-anchored every 8 nodes and at the last 8). Edges shorter than 2 kcw take
-// the near kind of step throughout, with F of the far end from its closed form.
+// the near kind of step throughout, with F of the far end from the same
+// anchored exp products as the far region.
 // Each region loads the constants it needs, so few stay live across regions.
 // Results go to out at node K for sample s in lane 8 s + ((K - 1) & 7), stored
 // in aligned blocks of 8 nodes; pass B reads back what the same lane wrote in
@@ -357,7 +358,7 @@ __device__ __forceinline__ void twisted_pass(const Unit& t, int lane, int64_t S,
   const int e1 = overlap ? m - 1 : min(kcw, m - 1);
   {
     // gf = sc F(j) / (2 sinh(theta)) and its increment w = sc F(1) exp(-2 j theta) / (2 sinh(theta))
-    float q[NL], gf[NL], w[NL], ed[NL], dl[NL], thn[NL], nrm[NL];
+    float q[NL], gf[NL], w[NL], ed[NL], dl[NL], thn[NL], nrm[NL], ef[NL], e2[NL];
 #pragma unroll
     for (int n = 0; n < NL; ++n) {
       const SweepParams<float> p = prm_of(n);
@@ -372,6 +373,8 @@ __device__ __forceinline__ void twisted_pass(const Unit& t, int lane, int64_t S,
       w[n] = cs * d1 * ed[n] * ed[n];
       thn[n] = p.theta;
       nrm[n] = overlap ? rcpf(one_minus_exp(2.0f * (float)(m + 1) * p.theta)) : 1.0f;
+      ef[n] = 0.f;  // exp(-2 (m + 1 - j) theta), anchored at the first step
+      e2[n] = __expf(fminf(2.0f * p.theta, 80.0f));
     }
     chunked_sweep(buf, lane, rows, S, vec, t.kv, 2, e1, row_of, [&](int j, float4 r4) {
       const float r[kS] = {r4.x, r4.y, r4.z, r4.w};
@@ -379,8 +382,19 @@ __device__ __forceinline__ void twisted_pass(const Unit& t, int lane, int64_t S,
 #pragma unroll
       for (int n = 0; n < NL; ++n) {
         float gsc = gf[n];
-        if (overlap)  // uniform; F(m + 1 - j) rounds to 1 away from the far end
-          gsc *= one_minus_exp(2.0f * (float)(m + 1 - j) * thn[n]) * nrm[n];
+        if (overlap) {  // uniform: the far factor F(m + 1 - j) / F(m + 1)
+          const int jf = m + 1 - j;
+          float ff;
+          if ((jf & 7) == 0 || jf <= 8 || j == 2) {  // re-anchor
+            const float a = 2.0f * (float)jf * thn[n];
+            ef[n] = __expf(-a);
+            ff = one_minus_exp(a);
+          } else {
+            ef[n] *= e2[n];
+            ff = 1.0f - ef[n];
+          }
+          gsc *= ff * nrm[n];
+        }
         if (kB) {
           const float gr = gsc * rp[n];
 #pragma unroll
