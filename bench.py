@@ -255,6 +255,10 @@ def run_grf(args, w, graph):
         knobs, tune_ms = G.autotune(w.kappa, w.beta, w.k_step, S, precision=prec,
                                     out_dtype=out_dtype, reps=2, precond=args.precond)
     knobs["precond"] = args.precond
+    if args.interior:
+        knobs["interior"] = args.interior
+    if args.sweep:
+        knobs["sweep"] = args.sweep
 
     def step(i, timing=True):
         return G.sample(w.kappa, w.beta, w.k_step, seed0 + i, S, precision=prec,
@@ -336,9 +340,12 @@ def run_grf(args, w, graph):
     work, bound = algorithmic(w, G, st, dom, S, tsize, osz)
     dur_s = mean_ph[dom] / 1000.0
     spectral = knobs.get("interior", "spectral" if prec == "mixed" else "thomas") == "spectral"
+    segments = knobs.get("sweep") == "segments"
     kernel_file = {"noise": "noise.cu", "schur": "schur.cu",
-                   "condense": "spectral.cu" if spectral else "thomas.cu",
-                   "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else "recover.cu",
+                   "condense": "spectral.cu" if spectral else
+                   ("thomas.cu" if segments else "sweep.cu"),
+                   "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else
+                   ("recover.cu" if segments else "sweep.cu"),
                    "precond_net": "learned.cu"}.get(dom, "api.cu")
     if bound == "hbm":
         ach = work / dur_s / 1e9
@@ -392,6 +399,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
+    ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral"],
+                    help="edge-interior solver (default: the autotuner's or the library's)")
+    ap.add_argument("--sweep", default=None, choices=[None, "segments", "nodes"],
+                    help="layout of the FP32 tridiagonal sweeps (default: the library's)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-graph", dest="use_graph", action="store_false",
                     help="direct calls instead of replaying each call as a captured CUDA graph")

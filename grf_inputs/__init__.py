@@ -154,6 +154,18 @@ def grid_deleted(nx: int = 300, ny: int = 300, frac: float = 0.15,
     return Graph(int(inside.sum()), eu, ev, lengths)
 
 
+def long_edges(n_vertices: int = 200, n_edges: int = 300, n_elems: int = 3072,
+               spread: int = 64, h: float = 2.0 ** -9, seed: int = 0) -> Graph:
+    """Edges of about n_elems uniform elements each (n_elems +- spread), edge i
+    from vertex i mod n_vertices to a uniformly drawn other vertex; length =
+    elements x h, so that ceil(length / h) gives the element count back."""
+    rng = np.random.default_rng(seed)
+    eu = np.arange(n_edges, dtype=np.int64) % n_vertices
+    ev = (eu + 1 + rng.integers(n_vertices - 1, size=n_edges)) % n_vertices
+    ne = n_elems + rng.integers(-spread, spread, size=n_edges)
+    return Graph(n_vertices, eu, ev, ne.astype(np.float64) * h)
+
+
 def _components(n: int, eu: np.ndarray, ev: np.ndarray) -> np.ndarray:
     parent = np.arange(n)
 
@@ -209,7 +221,7 @@ class Workload:
         args = {k: v for k, v in self.graph_args.items() if k != "kind"}
         return {"square_diagonal": square_diagonal, "rgg": random_geometric,
                 "ba": barabasi_albert, "grid": grid_deleted,
-                "interval": interval}[kind](**args)
+                "interval": interval, "long": long_edges}[kind](**args)
 
 
 WORKLOADS = {
@@ -226,6 +238,13 @@ WORKLOADS = {
     "ba20000": Workload("ba20000", kappa=8.0, beta=0.75, k_step=0.3, h=2.0 ** -9,
                         n_samples=64, seed=1, clip=(2, 4096), precision="mixed",
                         graph_args={"kind": "ba", "n": 20000, "m": 3, "seed": 0}),
+    # 300 edges of about 3072 elements (the long edges of ba20000: h = 2^-9,
+    # 148 quadrature nodes): the case of the node-parallel sweep profiles.
+    "long300": Workload("long300", kappa=8.0, beta=0.75, k_step=0.3, h=2.0 ** -9,
+                        n_samples=64, seed=1, precision="mixed",
+                        graph_args={"kind": "long", "n_vertices": 200, "n_edges": 300,
+                                    "n_elems": 3072, "spread": 64, "h": 2.0 ** -9,
+                                    "seed": 0}),
     # 300x300 grid, 15% edges deleted, largest component.
     "grid300": Workload("grid300", kappa=2.0, beta=0.75, k_step=0.25, h=2.0 ** -9,
                         n_samples=32, seed=1, precision="mixed",
