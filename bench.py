@@ -339,11 +339,12 @@ def run_grf(args, w, graph):
     roof = {}
     work, bound = algorithmic(w, G, st, dom, S, tsize, osz)
     dur_s = mean_ph[dom] / 1000.0
-    spectral = knobs.get("interior", "spectral" if prec == "mixed" else "thomas") == "spectral"
+    interior = knobs.get("interior", "spectral" if prec == "mixed" else "thomas")
+    spectral = interior in ("spectral", "spectral_tc")
     segments = knobs.get("sweep") == "segments"
     kernel_file = {"noise": "noise.cu", "schur": "schur.cu",
-                   "condense": "spectral.cu" if spectral else
-                   ("thomas.cu" if segments else "sweep.cu"),
+                   "condense": ("spectral_mma.cu" if interior == "spectral_tc" else "spectral.cu")
+                   if spectral else ("thomas.cu" if segments else "sweep.cu"),
                    "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else
                    ("recover.cu" if segments else "sweep.cu"),
                    "precond_net": "learned.cu"}.get(dom, "api.cu")
@@ -399,7 +400,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
-    ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral"],
+    ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral", "spectral_tc"],
                     help="edge-interior solver (default: the autotuner's or the library's)")
     ap.add_argument("--sweep", default=None, choices=[None, "segments", "nodes"],
                     help="layout of the FP32 tridiagonal sweeps (default: the library's)")

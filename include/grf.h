@@ -84,7 +84,8 @@ typedef struct grf_options {
                           options, sample count or output pointer change) and replays it;
                           phase timing is then not reported */
   int32_t interior;    /* edge-interior solver of the condensation and recovery steps:
-                          GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS or GRF_INTERIOR_SPECTRAL */
+                          GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL or
+                          GRF_INTERIOR_SPECTRAL_TC */
   int32_t sweep;       /* how FP32 edges left to the tridiagonal solves are swept:
                           GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS or GRF_SWEEP_NODES */
 } grf_options;
@@ -101,6 +102,10 @@ typedef struct grf_options {
 #define GRF_INTERIOR_AUTO 0
 #define GRF_INTERIOR_THOMAS 1
 #define GRF_INTERIOR_SPECTRAL 2
+#define GRF_INTERIOR_SPECTRAL_TC 3  /* SPECTRAL with the condensation's sine transform
+                                       and end-value contraction on the tensor cores
+                                       (mma.sync, TF32 operands in three terms); the
+                                       recovery as SPECTRAL */
 
 /* Parallel layouts of the FP32 tridiagonal edge solves (same results up to
  * rounding; FP64 sweeps always use SEGMENTS):

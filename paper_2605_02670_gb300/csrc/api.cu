@@ -123,7 +123,7 @@ struct grf_graph {
   struct GraphCache {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
-    bool spectral = false;
+    bool spectral = false, spec_tc = false;
     int sweep = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
     int64_t S = 0;
@@ -313,6 +313,7 @@ struct Opts {
   int recover_sg;  // 1, 2 or 4
   bool use_graph;
   bool spectral;   // edge interiors in the sine basis (mixed precision)
+  bool spec_tc;    // ... with the transforms and contractions on the tensor cores
   int sweep;       // GRF_SWEEP_* of the FP32 tridiagonal edges
 };
 
@@ -344,11 +345,12 @@ int read_opts(const grf_options* o, Opts* r) {
   if (r->out_dtype != GRF_OUT_F64 && r->out_dtype != GRF_OUT_F32)
     return fail(GRF_EINVAL, "unknown out_dtype %d", r->out_dtype);
   const int in = o ? o->interior : GRF_INTERIOR_AUTO;
-  if (in < GRF_INTERIOR_AUTO || in > GRF_INTERIOR_SPECTRAL)
+  if (in < GRF_INTERIOR_AUTO || in > GRF_INTERIOR_SPECTRAL_TC)
     return fail(GRF_EINVAL, "unknown interior solver %d", in);
-  if (in == GRF_INTERIOR_SPECTRAL && r->precision != GRF_MIXED)
+  if ((in == GRF_INTERIOR_SPECTRAL || in == GRF_INTERIOR_SPECTRAL_TC) && r->precision != GRF_MIXED)
     return fail(GRF_ENOTSUP, "the spectral interior solver needs precision GRF_MIXED");
   r->spectral = r->precision == GRF_MIXED && in != GRF_INTERIOR_THOMAS;
+  r->spec_tc = r->spectral && in == GRF_INTERIOR_SPECTRAL_TC;
   r->sweep = o ? o->sweep : GRF_SWEEP_AUTO;
   if (r->sweep < GRF_SWEEP_AUTO || r->sweep > GRF_SWEEP_NODES)
     return fail(GRF_EINVAL, "unknown sweep layout %d", r->sweep);
@@ -592,7 +594,10 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
                                             g->d_bin_edges[p] + head, tail, gvec, st);
-    if (spec)
+    if (spec && o.spec_tc)
+      rs->launches += launch_spec_condense_mma(g->d, nd, S, (const float*)b, g->d_spec_edges,
+                                               g->spec_count, w.bhat, gvec, st);
+    else if (spec)
       rs->launches += launch_spec_condense(g->d, nd, kappa2, S, (const float*)b, g->d_spec_edges,
                                            g->spec_count, w.bhat, gvec, st);
   } else {
@@ -793,6 +798,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
                    gc.precond == o.precond && gc.spectral == o.spectral && gc.sweep == o.sweep &&
+                   gc.spec_tc == o.spec_tc &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
                    gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
@@ -844,6 +850,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.precision = o.precision;
     gc.precond = o.precond;
     gc.spectral = o.spectral;
+    gc.spec_tc = o.spec_tc;
     gc.sweep = o.sweep;
     gc.out_dtype = o.out_dtype;
     gc.pcg_layout = o.pcg_layout;
@@ -1630,6 +1637,7 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
       for (int sg : {1, 2, 4}) cands.push_back({GRF_INTERIOR_SPECTRAL, sg});
     else
       cands.push_back({GRF_INTERIOR_SPECTRAL, 4});
+    cands.push_back({GRF_INTERIOR_SPECTRAL_TC, 4});
   } else {
     cands.push_back({GRF_INTERIOR_THOMAS, 0});
   }

@@ -209,6 +209,10 @@ int spec_bins(int32_t* mmax);
 int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                          const float* b, const int32_t* bin_edges, const int32_t* bin_count,
                          float* bhat, double* gvec, cudaStream_t st);
+// The same on the tensor cores (spectral_mma.cu): mma.sync TF32 in three terms.
+int launch_spec_condense_mma(const DevGraph& g, const DevNodes& nd, int64_t S, const float* b,
+                             const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
+                             double* gvec, cudaStream_t st);
 // Interior field of the binned edges from bhat and xw = w_l u_v^(l).
 template <typename OutT>
 int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,

@@ -159,7 +159,7 @@ def test_apply_matches_oracle(precision, name):
 
 
 @pytest.mark.parametrize("precision,interior", [("fp64", "auto"), ("mixed", "thomas"),
-                                                ("mixed", "spectral")])
+                                                ("mixed", "spectral"), ("mixed", "spectral_tc")])
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("beta", [0.3, 0.75])
 def test_sample_matches_oracle(precision, interior, name, beta):
@@ -211,7 +211,7 @@ def test_sample_group_pcg_every_vertex_split(nx, layout):
 
 @pytest.mark.parametrize("precision,sg,interior", [
     ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
-    ("mixed", 1, "spectral"), ("mixed", 4, "spectral")])
+    ("mixed", 1, "spectral"), ("mixed", 4, "spectral"), ("mixed", 4, "spectral_tc")])
 def test_sample_every_recovery_bin(precision, sg, interior):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
     Thomas recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps),
@@ -352,7 +352,8 @@ def test_autotune_returns_working_knobs():
     G, m = make(g, h)
     knobs, ms = G.autotune(3.0, 0.7, 0.5, 8, precision="mixed")
     assert knobs["pcg_layout"] in ("per_system", "staged", "staged_pairs")
-    assert knobs["recover_sg"] in (1, 2, 4) and knobs["interior"] in ("thomas", "spectral")
+    assert knobs["recover_sg"] in (1, 2, 4)
+    assert knobs["interior"] in ("thomas", "spectral", "spectral_tc")
     assert knobs["sweep"] in ("auto", "segments", "nodes")
     assert ms > 0
     u, _ = G.sample(3.0, 0.7, 0.5, 9, 8, precision="mixed", out_dtype="f64", **knobs)
