@@ -1663,7 +1663,9 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
       cudaEventRecord(e1, st);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&ms, e0, e1);
-      const double t = ms / reps;
+      // the tensor-core condensation has to win by 3 %: on par, keep the
+      // FP32 kernels (ties would otherwise flip from run to run)
+      const double t = ms / reps * (c.interior == GRF_INTERIOR_SPECTRAL_TC ? 1.03 : 1.0);
       if (t < best_t) {
         best_t = t;
         best_o = c;
