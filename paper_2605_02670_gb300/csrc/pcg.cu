@@ -390,13 +390,16 @@ __device__ __forceinline__ void report(int64_t sys, const SysResult& r, int32_t*
 }
 
 constexpr int kThreadsA = 256;
+// per-system CTAs with the vectors in global memory (measured on GB300: 128 and
+// 512 threads per system both slower than 256 on 20 000- and 90 000-vertex graphs)
+constexpr int kThreadsL = 256;
 
 // dscale: FP64 mode 1 / D; mixed mode 1 / sqrt(D).
 // offv_t: FP64 mode the blocks; mixed mode the Jacobi-scaled blocks.
 // pre / pc / pn: preconditioner kind and its per-node coefficients
 // ([L][V] and [L][2E]; see launch_pcg).
-template <typename VT, bool kSmem>
-__global__ void __launch_bounds__(kThreadsA) pcg_kernel(
+template <typename VT, bool kSmem, int NT>
+__global__ void __launch_bounds__(NT) pcg_kernel(
     DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const VT* __restrict__ dscale_t,
     const VT* __restrict__ offv_t, int pre, const VT* __restrict__ pc,
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
     VT* __restrict__ gy, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
     PcgStatus* status) {
   constexpr bool kRefine = sizeof(VT) == 4;
-  __shared__ Shared<kThreadsA, VT> shs;
+  __shared__ Shared<NT, VT> shs;
   extern __shared__ __align__(16) unsigned char vec_sm[];
   const int64_t nsys = (int64_t)L * S;
   const int32_t nv = g.nv;
@@ -441,9 +444,9 @@ __global__ void __launch_bounds__(kThreadsA) pcg_kernel(
       v.q = gq + sys * nv;
       v.y = gy + sys * nv;
     }
-    const SysResult res = solve_system<kThreadsA, VT>(nv, M, gvec + sys * nv, xo, v, !kSmem,
-                                                      rtol, max_iter, shs);
-    report<kThreadsA>(sys, res, iters, status);
+    const SysResult res = solve_system<NT, VT>(nv, M, gvec + sys * nv, xo, v, !kSmem, rtol,
+                                               max_iter, shs);
+    report<NT>(sys, res, iters, status);
     __syncthreads();
   }
 }
@@ -1501,15 +1504,18 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
                       (pre == kPreLearned ? 5 : 4) * sizeof(VT) * (size_t)g.nv;
   if (smem <= kSmemMax - 16 * 1024) {
     // dynamic + static may pass the 48 KB default; per device: set at every launch
-    cudaFuncSetAttribute(pcg_kernel<VT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    pcg_kernel<VT, true><<<blocks, kThreadsA, smem, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                          pre, pc, pn, gvec, x, d, r, p, q, y,
-                                                          rtol, max_iter, iters, status);
+    cudaFuncSetAttribute(pcg_kernel<VT, true, kThreadsA>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    pcg_kernel<VT, true, kThreadsA><<<blocks, kThreadsA, smem, st>>>(
+        g, L, S, diag, offv, dscale_t, offv_t, pre, pc, pn, gvec, x, d, r, p, q, y, rtol, max_iter,
+        iters, status);
   } else {
-    pcg_kernel<VT, false><<<blocks, kThreadsA, 0, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                        pre, pc, pn, gvec, x, d, r, p, q, y,
-                                                        rtol, max_iter, iters, status);
+    constexpr int kNT = kThreadsL;
+    int gb = (int)(nsys < 152 * (2048 / kNT) * 2 ? nsys : 152 * (2048 / kNT) * 2);
+    if (gb < 1) gb = 1;
+    pcg_kernel<VT, false, kNT><<<gb, kNT, 0, st>>>(g, L, S, diag, offv, dscale_t, offv_t, pre, pc,
+                                                  pn, gvec, x, d, r, p, q, y, rtol, max_iter,
+                                                  iters, status);
   }
 }
 #define GRF_INST(VT)                                                                          \

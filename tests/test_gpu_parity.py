@@ -209,6 +209,22 @@ def test_sample_group_pcg_every_vertex_split(nx, layout):
     assert rel_l2(u.cpu().numpy(), u1.cpu().numpy(), fem.lumped_mass(m)) < TOL["mixed"] / 10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_large_graph_global_vectors(precision):
+    """About 9 000 kept vertices: the per-system PCG keeps its vectors in global
+    memory (they do not fit shared memory), in both precisions; the group layout
+    falls back to it too."""
+    g = gi.grid_deleted(105, 105, 0.15, 4)
+    G, m = make(g, 0.45)
+    assert G.n_kept > 8600
+    kappa, beta, k, seed, S = 1.5, 0.7, 0.5, 19, 3
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     pcg_layout="per_system")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.45)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
 @pytest.mark.parametrize("precision,sg,interior", [
     ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
     ("mixed", 1, "spectral"), ("mixed", 4, "spectral"), ("mixed", 4, "spectral_tc")])
