@@ -131,3 +131,24 @@ def test_learned_options_rejected_without_weights_or_in_fp64():
     with pytest.raises(grf.GrfError) as ei:
         G.precond_get()
     assert ei.value.code == grf.GRF_EINVAL
+
+
+def test_interior_and_sweep_options_checked_before_device_work():
+    G = grf.Graph([0, 1], [1, 2], [1.0, 0.5], 3, h=0.1)
+    bad_sweep = grf.make_options("mixed")
+    bad_sweep.sweep = 7
+    with pytest.raises(grf.GrfError) as ei:
+        grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad_sweep, stream=0)
+    assert ei.value.code == grf.GRF_EINVAL
+    bad_interior = grf.make_options("mixed")
+    bad_interior.interior = 9
+    with pytest.raises(grf.GrfError) as ei:
+        grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad_interior, stream=0)
+    assert ei.value.code == grf.GRF_EINVAL
+    for interior in ("spectral", "spectral_tc"):  # sine-basis interiors are FP32 only
+        with pytest.raises(grf.GrfError) as ei:
+            grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0,
+                           grf.make_options("fp64", interior=interior), stream=0)
+        assert ei.value.code == grf.GRF_ENOTSUP
+    assert grf.make_options("mixed", interior="spectral_tc", sweep="nodes").knobs() == {
+        "pcg_layout": "auto", "recover_sg": 0, "interior": "spectral_tc", "sweep": "nodes"}
