@@ -51,6 +51,27 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of a rank's replica: ranks draw disjoint sample streams (the noise
+    counter runs over (DOF, sample) under a per-seed key)."""
+    return seed + 1000003 * rank
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest of the ranks' values (the job ends with its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
@@ -234,7 +255,7 @@ def run_grf(args, w, graph):
                       device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    seed0 = w.seed + 1000003 * rank
+    seed0 = rank_seed(w.seed, rank)
 
     train = None
     if args.precond == "learned":
@@ -289,15 +310,11 @@ def run_grf(args, w, graph):
     if dist:
         dist.barrier()
     ms = statistics.mean(times)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist)
     st = iters[-1]
     L = st["n_nodes"]
-    value = S * world / (ms_max / 1000.0)
-    dof_solves = G.n_dofs * L * S * world / (ms_max / 1000.0)
+    value = job_rate(S, world, ms_max / 1000.0)
+    dof_solves = job_rate(G.n_dofs * L * S, world, ms_max / 1000.0)
 
     # end to end through the C ABI with a host output buffer
     host = torch.empty((S, G.n_dofs), dtype=out.dtype, pin_memory=True)
@@ -312,11 +329,7 @@ def run_grf(args, w, graph):
         grf.grf_sample_host(G.handle, w.kappa, w.beta, w.k_step, seed0 + 10_000 + i, S,
                             host.numpy(), e2e_opts, stream)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.mean(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(statistics.mean(e2e_t), dist)
 
     phase_source = "timed steps"
     if args.use_graph:
@@ -378,7 +391,7 @@ def run_grf(args, w, graph):
         "roofline": roof,
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
-        "e2e": {"value": S * world / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_rate(S, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * 8 * L,
                 "d2h_bytes_per_step": S * G.n_dofs * osz},
     }
