@@ -405,7 +405,7 @@ def run_grf(args, w, graph):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grf", choices=["grf", "reference"])
     ap.add_argument("--workload", default="rgg2000", choices=sorted(gi.WORKLOADS))
