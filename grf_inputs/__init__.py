@@ -202,6 +202,20 @@ def random_small_graph(n_vertices: int, n_edges: int, seed: int,
     return Graph(n_vertices, np.array(us, np.int64), np.array(vs, np.int64), lengths)
 
 
+def disjoint_union(*graphs: Graph, seed: int = 0) -> Graph:
+    """The graphs side by side as one graph with several connected components;
+    vertex ids are offset per part and then shuffled by a seeded permutation so
+    that the components interleave in the numbering."""
+    eu, ev, ln, off = [], [], [], 0
+    for g in graphs:
+        eu.append(np.asarray(g.edge_u, np.int64) + off)
+        ev.append(np.asarray(g.edge_v, np.int64) + off)
+        ln.append(np.asarray(g.lengths, np.float64))
+        off += g.n_vertices
+    perm = np.random.default_rng(seed).permutation(off)
+    return Graph(off, perm[np.concatenate(eu)], perm[np.concatenate(ev)], np.concatenate(ln))
+
+
 @dataclass
 class Workload:
     """A named sampling workload: a graph recipe plus the SPDE parameters."""

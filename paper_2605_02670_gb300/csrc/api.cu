@@ -88,6 +88,10 @@ struct grf_graph {
   int64_t n = 0;
   std::vector<int64_t> vertex_map;
   std::vector<int32_t> eu, ev, nel, vptr, adj_edge, adj_nbr, adj_rev;
+  // the vertices in reverse Cuthill-McKee order (slot -> vertex) and the
+  // incidence lists in that order: neighbour slot and original incidence index
+  std::vector<int32_t> rperm, rvptr, rnbr, rinc;
+  VertexOrder d_order{};
   std::vector<double> he;
   std::vector<int64_t> ioff;
   std::vector<double> ml_vertex;  // lumped mass at kept vertices
@@ -206,6 +210,7 @@ int ensure_device(grf_graph* g) {
   c.take<double>((size_t)g->n); c.take<double>(V);
   c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1);
   c.take<int32_t>(2 * E);
+  c.take<int32_t>(V); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -245,6 +250,14 @@ int ensure_device(grf_graph* g) {
   CUDA_TRY(cudaMemcpy(an, g->adj_nbr.data(), 2 * E * 4, cudaMemcpyHostToDevice));
   int32_t* arev = k.take<int32_t>(2 * E);
   CUDA_TRY(cudaMemcpy(arev, g->adj_rev.data(), 2 * E * 4, cudaMemcpyHostToDevice));
+  int32_t* rperm = k.take<int32_t>(V);
+  int32_t* rvptr = k.take<int32_t>(V + 1);
+  int32_t* rnbr = k.take<int32_t>(2 * E);
+  int32_t* rinc = k.take<int32_t>(2 * E);
+  CUDA_TRY(cudaMemcpy(rperm, g->rperm.data(), V * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(rvptr, g->rvptr.data(), (V + 1) * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(rnbr, g->rnbr.data(), 2 * E * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(rinc, g->rinc.data(), 2 * E * 4, cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(mlv, g->ml_vertex.data(), V * 8, cudaMemcpyHostToDevice));
   DevGraph& d = g->d;
   d.nv = g->nv; d.ne = g->ne; d.ni = g->ni; d.n = g->n;
@@ -252,6 +265,7 @@ int ensure_device(grf_graph* g) {
   for (int32_t e = 0; e < g->ne; ++e) d.max_m = std::max(d.max_m, g->nel[e] - 1);
   d.eu = eu; d.ev = ev; d.nel = nel; d.he = he; d.ioff = ioff;
   d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.adj_rev = arev; d.sqrt_ml = sml;
+  g->d_order = VertexOrder{rperm, rvptr, rnbr, rinc};
   int64_t blocks = (g->n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml);
@@ -634,7 +648,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   }
   rs->begin(st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
-  launch_pcg<T>(g->d, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
+  launch_pcg<T>(g->d, g->d_order, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
                 (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st);
   rs->end(3, st);
@@ -1396,6 +1410,62 @@ int grf_precond_train(grf_graph* g, double kappa, double beta, double k_step,
   return GRF_OK;
 }
 
+// Reverse Cuthill-McKee order of the kept vertices: a breadth-first search
+// from a vertex of smallest degree in each component, the new neighbours of
+// every vertex taken by increasing degree, the whole order reversed. Adjacent
+// vertices end up in nearby slots, so the shared-memory PCG that stores its
+// system in this order gathers neighbour rows from a narrow band.
+static void rcm_order(grf_graph& g) {
+  const int32_t nv = g.nv;
+  std::vector<int32_t> deg(nv);
+  for (int32_t v = 0; v < nv; ++v) deg[v] = g.vptr[v + 1] - g.vptr[v];
+  const auto by_degree = [&deg](int32_t a, int32_t b) {
+    return deg[a] != deg[b] ? deg[a] < deg[b] : a < b;
+  };
+  std::vector<int32_t> roots(nv);
+  for (int32_t v = 0; v < nv; ++v) roots[v] = v;
+  std::sort(roots.begin(), roots.end(), by_degree);
+  std::vector<int32_t> order;
+  order.reserve(nv);
+  std::vector<char> seen(nv, 0);
+  std::vector<int32_t> fresh;
+  for (const int32_t r : roots) {
+    if (seen[r]) continue;
+    seen[r] = 1;
+    size_t head = order.size();
+    order.push_back(r);
+    while (head < order.size()) {
+      const int32_t v = order[head++];
+      fresh.clear();
+      for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
+        const int32_t w = g.adj_nbr[k];
+        if (!seen[w]) {
+          seen[w] = 1;
+          fresh.push_back(w);
+        }
+      }
+      std::sort(fresh.begin(), fresh.end(), by_degree);
+      order.insert(order.end(), fresh.begin(), fresh.end());
+    }
+  }
+  std::reverse(order.begin(), order.end());
+  std::vector<int32_t> slot(nv);
+  for (int32_t i = 0; i < nv; ++i) slot[order[i]] = i;
+  g.rperm = order;
+  g.rvptr.assign(nv + 1, 0);
+  for (int32_t i = 0; i < nv; ++i) g.rvptr[i + 1] = g.rvptr[i] + deg[order[i]];
+  g.rnbr.resize(g.adj_nbr.size());
+  g.rinc.resize(g.adj_nbr.size());
+  for (int32_t i = 0; i < nv; ++i) {
+    const int32_t v = order[i];
+    for (int32_t j = 0; j < deg[v]; ++j) {
+      const int32_t k = g.vptr[v] + j;
+      g.rnbr[g.rvptr[i] + j] = slot[g.adj_nbr[k]];
+      g.rinc[g.rvptr[i] + j] = k;
+    }
+  }
+}
+
 int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
                      const int64_t* edge_v, const double* lengths, const int32_t* n_elems,
                      double h, grf_graph** out) {
@@ -1539,6 +1609,7 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
       }
     }
   }
+  rcm_order(*g);
   *out = g;
   return GRF_OK;
 }

@@ -26,6 +26,16 @@ struct DevGraph {
   const double* sqrt_ml;    // [n] sqrt of the lumped mass per DOF
 };
 
+// A renumbering of the vertices into slots (reverse Cuthill-McKee order,
+// computed once per graph) and the incidence lists in slot order. Kept apart
+// from DevGraph: only the shared-memory vertex PCG uses it.
+struct VertexOrder {
+  const int32_t* perm;  // [nv] slot -> vertex
+  const int32_t* vptr;  // [nv + 1] slot -> incidence list
+  const int32_t* nbr;   // [2 ne] slot of the vertex at the other end
+  const int32_t* inc;   // [2 ne] index of the same incidence in DevGraph's lists
+};
+
 // Per-call node list: A_l = alpha_l M_L + gamma_l K, weight w_l.
 struct DevNodes {
   int32_t L;
@@ -132,15 +142,16 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 // VT = float: FP32 Jacobi-scaled CG inside FP64 refinement (dscale = 1 / sqrt(D),
 // offv_t = scaled blocks). d, r, p, q: [L][S][nv] scratch used when a system's
 // vectors do not fit in shared memory. layout: 1 one CTA per system, 2 staged
-// matrix per (node, sample group) when it fits (mixed only), else layout 1.
+// matrix per (node, sample group) when it fits (mixed only), else layout 1;
+// the sample-group Jacobi kernel stores its system in the slot order ord.
 // Preconditioner: pre = kPreJacobi (pc, pn unused), kPreNeumann (pc [L][V] and
 // pn [L][2E] in VT: z_v = pc_v r_v + sum_k pn_k r_nbr(k)) or kPreLearned (mixed
 // only, float es = pc and N = pn per node: z = B B^T r, B = diag(es) + N);
 // y: one more [L][S][nv] scratch for the learned form.
 constexpr int kPreJacobi = 0, kPreNeumann = 1, kPreLearned = 2;
 template <typename VT>
-void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
+void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
+                const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
                 cudaStream_t st);

@@ -564,25 +564,29 @@ __device__ __forceinline__ void load_xrow(const double* p, double (&v)[SGP]) {
   }
 }
 
-// FP64 residual res[s] = g_s - (S x_s)_v of an owned vertex v for the group's
-// samples, from the shared FP64 iterates X [nv][SGP] and the node's FP64 blocks:
-// every incidence's coefficient and neighbour are loaded once for all samples,
-// two incidences per step so that their loads are in flight together.
+// FP64 residual res[s] = g_s - (S x_s)_v of an owned vertex for the group's
+// samples, from the shared FP64 iterates X [nv][SGP] and the node's FP64 blocks.
+// The shared arrays are in slot order (slot v holds vertex ov), the global ones
+// in vertex order: the incidences of slot v are vp[v] .. vp[v + 1] in NO and
+// obeg onwards in O. Every incidence's coefficient and neighbour are loaded
+// once for all samples, two incidences per step so that their loads are in
+// flight together.
 template <int SGP>
-__device__ __forceinline__ void group_residual(int32_t v, int32_t nv, const int32_t* vp,
-                                               const int2* NO, const double* D, const double* O,
-                                               const double* X, const double* gl,
+__device__ __forceinline__ void group_residual(int32_t v, int32_t ov, int32_t obeg, int32_t nv,
+                                               const int32_t* vp, const int2* NO, const double* D,
+                                               const double* O, const double* X, const double* gl,
                                                const bool (&act)[SGP], double (&res)[SGP]) {
   double y[SGP], xv[SGP];
   load_xrow<SGP>(X + (size_t)v * SGP, xv);
-  const double dv = D[v];
+  const double dv = D[ov];
 #pragma unroll
   for (int s = 0; s < SGP; ++s) y[s] = dv * xv[s];
-  const int32_t kend = vp[v + 1];
-  int32_t kk = vp[v];
+  const int32_t kbeg = vp[v], kend = vp[v + 1];
+  const double* Ov = O + obeg;
+  int32_t kk = kbeg;
   for (; kk + 1 < kend; kk += 2) {
     const int32_t w0 = NO[kk].x, w1 = NO[kk + 1].x;
-    const double o0 = O[kk], o1 = O[kk + 1];
+    const double o0 = Ov[kk - kbeg], o1 = Ov[kk + 1 - kbeg];
     double x0[SGP], x1[SGP];
     load_xrow<SGP>(X + (size_t)w0 * SGP, x0);
     load_xrow<SGP>(X + (size_t)w1 * SGP, x1);
@@ -592,7 +596,7 @@ __device__ __forceinline__ void group_residual(int32_t v, int32_t nv, const int3
   }
   if (kk < kend) {
     const int32_t w0 = NO[kk].x;
-    const double o0 = O[kk];
+    const double o0 = Ov[kk - kbeg];
     double x0[SGP];
     load_xrow<SGP>(X + (size_t)w0 * SGP, x0);
 #pragma unroll
@@ -600,7 +604,7 @@ __device__ __forceinline__ void group_residual(int32_t v, int32_t nv, const int3
       if (act[s]) y[s] = fma(o0, x0[s], y[s]);
   }
 #pragma unroll
-  for (int s = 0; s < SGP; ++s) res[s] = act[s] ? gl[(int64_t)s * nv + v] - y[s] : 0.0;
+  for (int s = 0; s < SGP; ++s) res[s] = act[s] ? gl[(int64_t)s * nv + ov] - y[s] : 0.0;
 }
 
 // Block sums of N floats (N = 2, 4 or 8) for NT <= 1024 threads: a warp
@@ -639,14 +643,16 @@ __device__ __forceinline__ void group_sum(float (&v)[N], float* shw) {
 // Mixed-precision PCG for one node and a group of SGP samples at a time: the
 // same FP32 Jacobi-scaled inner CG inside FP64 refinement as solve_system,
 // run for the group's samples together so that every load of the node's
-// matrix serves SGP samples. Thread t owns vertices t + k * kThreadsG
+// matrix serves SGP samples. Thread t owns slots t + k * NT
 // (k < VPT): their r, q and d stay in registers; only the search directions,
 // which neighbours read, are shared. Each sample keeps its own scalars,
 // stopping tests and iteration count; the CTA iterates while any sample of the
-// group is still working (every loop bounded by max_iter).
+// group is still working (every loop bounded by max_iter). The shared arrays
+// hold the vertices in reverse Cuthill-McKee order (slot i is vertex
+// ord.perm[i]), so that the rows a warp gathers lie in a narrow band of P.
 template <int NT, int VPT, int SGP>
 __global__ void __launch_bounds__(NT) pcg_group_kernel(
-    DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
+    DevGraph g, VertexOrder ord, int32_t L, int64_t S, const double* __restrict__ diag,
     const double* __restrict__ offv, const float* __restrict__ dscale_t,
     const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
     double rtol, int32_t max_iter, int32_t* __restrict__ iters, PcgStatus* status) {
@@ -668,7 +674,7 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
   int2* NO = reinterpret_cast<int2*>(P + (size_t)nv * SGP);  // [2E] (neighbour, bits of o)
   float* Ds = reinterpret_cast<float*>(NO + ne2);  // [nv]
   int32_t* vp = reinterpret_cast<int32_t*>(Ds + nv);  // [nv + 1] incidence offsets
-  for (int32_t v = threadIdx.x; v <= nv; v += NT) vp[v] = g.vptr[v];
+  for (int32_t v = threadIdx.x; v <= nv; v += NT) vp[v] = ord.vptr[v];
   const int64_t ngrp = (S + SGP - 1) / SGP;
   const int64_t units = (int64_t)L * ngrp;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
@@ -679,8 +685,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
     const int kv = (int)(S - s0 < SGP ? S - s0 : SGP);
     __syncthreads();  // the previous unit is done with the shared arrays
     for (int64_t k = threadIdx.x; k < ne2; k += NT)
-      NO[k] = make_int2(g.adj_nbr[k], __float_as_int(offv_t[l * ne2 + k]));
-    for (int32_t v = threadIdx.x; v < nv; v += NT) Ds[v] = dscale_t[l * nv + v];
+      NO[k] = make_int2(ord.nbr[k], __float_as_int(offv_t[l * ne2 + ord.inc[k]]));
+    for (int32_t v = threadIdx.x; v < nv; v += NT) Ds[v] = dscale_t[l * nv + ord.perm[v]];
     __syncthreads();
     const double* D = diag + l * nv;
     const double* O = offv + l * ne2;
@@ -693,10 +699,11 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
     for (int k = 0; k < VPT; ++k) {
       const int32_t v = threadIdx.x + k * NT;
       if (v < nv) {
+        const int32_t ov = ord.perm[v];
 #pragma unroll
         for (int s = 0; s < SGP; ++s) {
           if (s < kv) {
-            const double gv = gl[(int64_t)s * nv + v];
+            const double gv = gl[(int64_t)s * nv + ov];
             const double sv = gv * (double)Ds[v];
             nrm[s] += gv * gv;
             nrm[SGP + s] += sv * sv;
@@ -744,7 +751,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
           const int32_t v = threadIdx.x + k * NT;
           if (v < nv) {
             double res[SGP];
-            group_residual<SGP>(v, nv, vp, NO, D, O, X, gl, act, res);
+            const int32_t ov = ord.perm[v];
+            group_residual<SGP>(v, ov, g.vptr[ov], nv, vp, NO, D, O, X, gl, act, res);
 #pragma unroll
             for (int s = 0; s < SGP; ++s) {
               float rs = 0.f;
@@ -791,10 +799,11 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
           const int32_t v = threadIdx.x + k * NT;
+          const int32_t ov = v < nv ? ord.perm[v] : 0;
 #pragma unroll
           for (int s = 0; s < SGP; ++s)
             r[k][s] = (act[s] && v < nv)
-                          ? (float)(gl[(int64_t)s * nv + v] * (double)Ds[v] * isg0[s])
+                          ? (float)(gl[(int64_t)s * nv + ov] * (double)Ds[v] * isg0[s])
                           : 0.f;
         }
       }
@@ -973,7 +982,8 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
         const int32_t v = threadIdx.x + k * NT;
         if (v < nv) {
           double res[SGP];
-          group_residual<SGP>(v, nv, vp, NO, D, O, X, gl, act, res);
+          const int32_t ov = ord.perm[v];
+          group_residual<SGP>(v, ov, g.vptr[ov], nv, vp, NO, D, O, X, gl, act, res);
 #pragma unroll
           for (int s = 0; s < SGP; ++s) {
             if (act[s]) {
@@ -993,9 +1003,10 @@ __global__ void __launch_bounds__(NT) pcg_group_kernel(
     for (int k = 0; k < VPT; ++k) {
       const int32_t v = threadIdx.x + k * NT;
       if (v < nv) {
+        const int32_t ov = ord.perm[v];
 #pragma unroll
         for (int s = 0; s < SGP; ++s)
-          if (s < kv) xl[(int64_t)s * nv + v] = X[(size_t)v * SGP + s];
+          if (s < kv) xl[(int64_t)s * nv + ov] = X[(size_t)v * SGP + s];
       }
     }
     if (threadIdx.x == 0) {
@@ -1429,8 +1440,9 @@ bool group_pre_fits(const DevGraph& g, int pre) {
 }
 
 template <int NT, int VPT, int SGP>
-void launch_group(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                  const float* dscale_t, const float* offv_t, const double* gvec, double* x,
+void launch_group(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
+                  const double* diag, const double* offv, const float* dscale_t,
+                  const float* offv_t, const double* gvec, double* x,
                   double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
                   cudaStream_t st) {
   const size_t dyn = group_bytes<SGP>(g.nv, g.ne);
@@ -1438,8 +1450,8 @@ void launch_group(const DevGraph& g, int32_t L, int64_t S, const double* diag, c
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
   const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
-  pcg_group_kernel<NT, VPT, SGP><<<blocks, NT, dyn, st>>>(g, L, S, diag, offv, dscale_t, offv_t,
-                                                          gvec, x, rtol, max_iter, iters, status);
+  pcg_group_kernel<NT, VPT, SGP><<<blocks, NT, dyn, st>>>(
+      g, ord, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter, iters, status);
 }
 
 // The group layout applies when every vertex fits the per-thread register
@@ -1453,8 +1465,8 @@ bool group_fits(const DevGraph& g) {
 }  // namespace
 
 template <typename VT>
-void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, const double* offv,
-                const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
+void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
+                const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
                 cudaStream_t st) {
@@ -1462,8 +1474,8 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
   if constexpr (sizeof(VT) == 4) {
     if ((layout == 2 || layout == 3) && pre == kPreJacobi && group_fits(g)) {
 #define GRF_GROUP(NT, VPT, SGP)                                                               \
-  launch_group<NT, VPT, SGP>(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter,  \
-                             iters, status, st)
+  launch_group<NT, VPT, SGP>(g, ord, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol,      \
+                             max_iter, iters, status, st)
       if (layout == 2) {  // 512 threads, groups of 4 samples
         if (g.nv <= kThreadsG) GRF_GROUP(512, 1, 4);
         else if (g.nv <= 2 * kThreadsG) GRF_GROUP(512, 2, 4);
@@ -1519,10 +1531,11 @@ void launch_pcg(const DevGraph& g, int32_t L, int64_t S, const double* diag, con
   }
 }
 #define GRF_INST(VT)                                                                          \
-  template void launch_pcg<VT>(const DevGraph&, int32_t, int64_t, const double*, const double*, \
-                               const VT*, const VT*, int, const VT*, const VT*, const double*,    \
-                               double*, VT*, VT*, VT*, VT*, VT*, double, int32_t, int32_t*,      \
-                               PcgStatus*, int, cudaStream_t);
+  template void launch_pcg<VT>(const DevGraph&, const VertexOrder&, int32_t, int64_t,      \
+                               const double*, const double*, const VT*, const VT*, int,      \
+                               const VT*, const VT*, const double*, double*, VT*, VT*, VT*,  \
+                               VT*, VT*, double, int32_t, int32_t*, PcgStatus*, int,         \
+                               cudaStream_t);
 GRF_INST(float)
 GRF_INST(double)
 #undef GRF_INST

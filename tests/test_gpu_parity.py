@@ -209,6 +209,26 @@ def test_sample_group_pcg_every_vertex_split(nx, layout):
     assert rel_l2(u.cpu().numpy(), u1.cpu().numpy(), fem.lumped_mass(m)) < TOL["mixed"] / 10
 
 
+@pytest.mark.parametrize("layout", ["staged", "staged_pairs", "per_system"])
+@pytest.mark.parametrize("parts", [(12, 30, 60), (20, 40, 300)])
+def test_sample_pcg_disconnected_multigraph(layout, parts):
+    """Several connected components whose vertex ids interleave, with parallel
+    edges, in the sample-group layouts (which renumber the vertices component by
+    component) and one CTA per system: 236 and 742 kept vertices."""
+    nx, n_small, n_rand = parts
+    g = gi.disjoint_union(gi.grid_deleted(nx, nx, 0.15, 3),
+                          gi.random_small_graph(n_rand, 2 * n_rand, 4),
+                          gi.random_small_graph(n_small, n_small + 6, 5),
+                          gi.interval(0.8), seed=nx)
+    G, m = make(g, 0.2)
+    kappa, beta, k, seed, S = 2.0, 0.65, 0.5, 23, 6
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     pcg_layout=layout)
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.2)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL["mixed"]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_sample_large_graph_global_vectors(precision):
     """About 9 000 kept vertices: the per-system PCG keeps its vectors in global
