@@ -245,6 +245,24 @@ def test_sample_large_graph_global_vectors(precision):
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sample_large_disconnected_graph_global_vectors(precision):
+    """10 554 kept vertices in three components with interleaved ids (two grids
+    with deleted edges and a small multigraph with parallel edges): the
+    per-system PCG with its vectors in global memory, which in mixed precision
+    keeps them in vertex order (the group layouts renumber, this one does not)."""
+    g = gi.disjoint_union(gi.grid_deleted(75, 75, 0.15, 6), gi.grid_deleted(70, 70, 0.15, 7),
+                          gi.random_small_graph(40, 50, 9), seed=5)
+    G, m = make(g, 0.45)
+    assert G.n_kept > 10000
+    kappa, beta, k, seed, S = 1.5, 0.7, 0.5, 19, 3
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     pcg_layout="per_system")
+    _, ref, _ = sampler.sample(g, kappa, beta, k, seed, S, h=0.45)
+    assert rel_l2(u.cpu().numpy(), ref, fem.lumped_mass(m)) < TOL[precision]
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
 @pytest.mark.parametrize("precision,sg,interior", [
     ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
     ("mixed", 1, "spectral"), ("mixed", 4, "spectral"), ("mixed", 4, "spectral_tc")])
