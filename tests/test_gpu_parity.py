@@ -61,6 +61,45 @@ def test_noise_words_bit_exact(name, seed):
     np.testing.assert_array_equal(words, philox.noise_words(seed, m.n_dofs, 5))
 
 
+def test_noise_words_match_curand_philox(tmp_path):
+    """The noise words against a second Philox4x32-10: cuRAND's device
+    generator (run through a small test-only kernel, tests/curand_philox_words.cu)
+    started at the same key (seed) and counter (block q, sample s). Both follow
+    the published Random123 definition; this pins the key and counter layout
+    on the GPU independently of the oracle."""
+    import ctypes
+    import subprocess
+    from pathlib import Path
+
+    from paper_2605_02670_gb300 import build as grf_build
+
+    src = Path(__file__).with_name("curand_philox_words.cu")
+    lib = tmp_path / "libcurand_blocks.so"
+    subprocess.run([grf_build.nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O2",
+                    "-shared", "-Xcompiler", "-fPIC", "-o", str(lib), str(src)], check=True)
+    cl = ctypes.CDLL(str(lib))
+    cl.curand_philox_blocks.restype = ctypes.c_int
+    cl.curand_philox_blocks.argtypes = [ctypes.c_ulonglong, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int64, ctypes.c_void_p]
+    g, h = GRAPHS["square5"]()
+    G, m = make(g, h)
+    S = 7
+    nq = m.n_dofs // 4  # whole blocks only
+    for seed in (1, 0xDEADBEEF12345678):
+        words = G.noise(seed, S, raw=True).cpu().numpy().view(np.uint32)
+        s_idx = np.repeat(np.arange(S, dtype=np.int32), nq)
+        q_idx = np.tile(np.arange(nq, dtype=np.int64), S)
+        d_s = torch.from_numpy(s_idx).cuda()
+        d_q = torch.from_numpy(q_idx).cuda()
+        d_out = torch.empty((s_idx.size, 4), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        rc = cl.curand_philox_blocks(seed, d_s.data_ptr(), d_q.data_ptr(), s_idx.size,
+                                     d_out.data_ptr())
+        assert rc == 0
+        ref = d_out.cpu().numpy().view(np.uint32).reshape(S, nq * 4)
+        np.testing.assert_array_equal(words[:, :nq * 4], ref)
+
+
 @pytest.mark.parametrize("name", ["square5", "random12", "isolated"])
 def test_noise_values(name):
     g, h = GRAPHS[name]()
