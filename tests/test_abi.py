@@ -29,9 +29,13 @@ def test_every_declared_symbol_is_exported():
     assert set(names) == set(grf.C_SYMBOLS)
 
 
-@pytest.mark.parametrize("name", ["square5", "rgg_small", "grid_small", "ba_small"])
+@pytest.mark.parametrize("name", ["square5", "rgg_small", "grid_small", "ba_small", "parts"])
 def test_mesh_and_dof_map_match_oracle(name):
-    if name == "square5":
+    if name == "parts":
+        g = gi.disjoint_union(gi.grid_deleted(12, 12, 0.15, seed=3),
+                              gi.random_small_graph(30, 40, 5), gi.interval(0.8), seed=3)
+        h, clip = 2.0 ** -4, None
+    elif name == "square5":
         g, h, clip = gi.square_diagonal(0), 2.0 ** -7, None
     elif name == "rgg_small":
         g, h, clip = gi.random_geometric(300, 0.07, seed=2), 2.0 ** -6, None
@@ -48,6 +52,22 @@ def test_mesh_and_dof_map_match_oracle(name):
     G2 = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h)
     if clip is None:
         assert G2.n_dofs == m.n_dofs
+
+
+def test_disjoint_union_keeps_the_parts_as_components():
+    parts = [gi.grid_deleted(10, 10, 0.15, seed=2), gi.random_small_graph(25, 35, 4),
+             gi.interval(0.8)]
+    g = gi.disjoint_union(*parts, seed=11)
+    assert g.n_vertices == sum(p.n_vertices for p in parts)
+    assert g.edge_u.shape[0] == sum(p.edge_u.shape[0] for p in parts)
+    np.testing.assert_array_equal(np.sort(g.lengths),
+                                  np.sort(np.concatenate([p.lengths for p in parts])))
+    comp = gi._components(g.n_vertices, g.edge_u, g.edge_v)
+    sizes = sorted(np.unique(comp, return_counts=True)[1].tolist())
+    assert sizes == sorted(p.n_vertices for p in parts)
+    # the parts' ids interleave: the smallest part is not a block of consecutive ids
+    small = np.flatnonzero(comp == comp[g.edge_u[-1]])
+    assert small.size == 2 and small[1] - small[0] > 1
 
 
 @pytest.mark.parametrize("case,msg", [
