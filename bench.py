@@ -281,13 +281,24 @@ def run_grf(args, w, graph):
     if args.sweep:
         knobs["sweep"] = args.sweep
 
-    def step(i, timing=True):
+    def step(i, timing):
+        # phase events (in a replayed graph: event record nodes, recorded by
+        # every replay): True = every phase, or a list of phase names
         return G.sample(w.kappa, w.beta, w.k_step, seed0 + i, S, precision=prec,
-                        out_dtype=out_dtype, out=out, timing=timing and not args.use_graph,
+                        out_dtype=out_dtype, out=out, timing=timing,
                         use_graph=args.use_graph, **knobs)
 
+    # warm-up with every phase timed: the per-phase report and the dominant phase
+    warm = []
     for i in range(args.warmup):
-        step(i)
+        flush.zero_()
+        warm.append(step(i, True)[1]["phase_ms"])
+    warm = warm[1:] if len(warm) > 1 else warm
+    mean_ph = {k: statistics.mean(p[k] for p in warm) for k in warm[0]}
+    dom = max(mean_ph, key=mean_ph.get)
+    # the timed steps carry the events of the dominant phase only (two event
+    # records per call); this untimed call captures that graph
+    step(args.warmup, [dom])
     torch.cuda.synchronize()
     times, phases, launches, iters = [], [], [], []
     if dist:
@@ -299,7 +310,7 @@ def run_grf(args, w, graph):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            _, st = step(args.warmup + i)
+            _, st = step(args.warmup + 1 + i, [dom])
             b.record(stream)
             b.synchronize()
             times.append(a.elapsed_time(b))
@@ -331,22 +342,14 @@ def run_grf(args, w, graph):
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_t), dist)
 
-    phase_source = "timed steps"
-    if args.use_graph:
-        # graph replays carry no per-phase events: time the same kernels in
-        # direct calls (after the timed region) for the per-kernel roofline
-        phases = []
-        for i in range(3):
-            flush.zero_()
-            phases.append(G.sample(w.kappa, w.beta, w.k_step, seed0 + 20_000 + i, S,
-                                   precision=prec, out_dtype=out_dtype, out=out, timing=True,
-                                   **knobs)[1]["phase_ms"])
-        phase_source = "direct calls after the timed graph replays"
+    # the roofline phase from the timed steps, the others from the warm-up calls
+    mean_ph[dom] = statistics.mean(p[dom] for p in phases)
+    how = "event record nodes of the replayed graph" if args.use_graph else "direct calls"
+    phase_source = (f"CUDA events on the call's stream ({how}): '{dom}' over the timed "
+                    "steps, the other phases over the warm-up calls")
     if rank != 0:
         dist.destroy_process_group()
         return
-    mean_ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
-    dom = max(mean_ph, key=mean_ph.get)
     hbm_peak, peak_kind = peaks()
     clocks = clk.summary()
     roof = {}

@@ -75,14 +75,17 @@ typedef struct grf_options {
   int32_t out_dtype;   /* GRF_OUT_F64 or GRF_OUT_F32 */
   int32_t max_iter;    /* PCG iteration cap per system; <= 0: 1000 */
   double rtol;         /* PCG stop: ||r||_2 <= rtol ||g||_2; <= 0: 1e-12 (FP64) / 1e-8 (mixed) */
-  int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms) */
+  int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms);
+                          GRF_TIMING_ONLY | mask: only around the phases whose bit p
+                          (p = the phase_ms index, bits 0-7) is set; other bits: GRF_EINVAL */
   int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
   int32_t recover_sg;  /* samples per lane in the interior recovery: 0 = auto, or 1, 2, 4
                           (FP32 sweeps; FP64 sweeps always use 2) */
   int32_t use_graph;   /* grf_sample only: nonzero captures the call's launch sequence into a
                           CUDA graph cached on the handle (re-captured when the parameters,
                           options, sample count or output pointer change) and replays it;
-                          phase timing is then not reported */
+                          with timing, the phase events are event record nodes of the
+                          graph and every replay reports its own phase_ms */
   int32_t interior;    /* edge-interior solver of the condensation and recovery steps:
                           GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL or
                           GRF_INTERIOR_SPECTRAL_TC */
@@ -129,6 +132,10 @@ typedef struct grf_options {
  *     samples) stages the node's matrix in shared memory and iterates the
  *     group's samples together (per-sample scalars, stopping tests and counts);
  *   AUTO: the library's choice. */
+/* grf_options.timing: time only the phases of the mask in bits 0-7 (bit p is
+ * grf_stats.phase_ms[p]); each timed phase adds two event records to the call */
+#define GRF_TIMING_ONLY (1 << 30)
+
 #define GRF_PCG_AUTO 0
 #define GRF_PCG_PER_SYSTEM 1
 #define GRF_PCG_STAGED 2

@@ -33,6 +33,7 @@ INTERIORS = {"auto": GRF_INTERIOR_AUTO, "thomas": GRF_INTERIOR_THOMAS,
              "spectral": GRF_INTERIOR_SPECTRAL, "spectral_tc": GRF_INTERIOR_SPECTRAL_TC}
 GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS, GRF_SWEEP_NODES = 0, 1, 2
 SWEEPS = {"auto": GRF_SWEEP_AUTO, "segments": GRF_SWEEP_SEGMENTS, "nodes": GRF_SWEEP_NODES}
+GRF_TIMING_ONLY = 1 << 30
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
@@ -150,15 +151,27 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def timing_flag(timing) -> int:
+    """grf_options.timing from False/True (no phases / every phase) or an
+    iterable of phase names (only those: GRF_TIMING_ONLY | their bits)."""
+    if isinstance(timing, (bool, int)):
+        return 1 if timing else 0
+    names = list(timing)
+    if not names:
+        return 0
+    return GRF_TIMING_ONLY | sum(1 << grf_stats.PHASES.index(n) for n in set(names))
+
+
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
                  timing=False, pcg_layout="auto", recover_sg=0, use_graph=False,
                  precond="jacobi", interior="auto", sweep="auto") -> grf_options:
+    """timing: False, True (every phase) or phase names to time only those."""
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
         out_dtype = "f64" if prec == GRF_FP64 else "f32"
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, PRECONDS[precond], od, int(max_iter), float(rtol),
-                       1 if timing else 0, PCG_LAYOUTS[pcg_layout], int(recover_sg),
+                       timing_flag(timing), PCG_LAYOUTS[pcg_layout], int(recover_sg),
                        1 if use_graph else 0, INTERIORS[interior], SWEEPS[sweep])
 
 

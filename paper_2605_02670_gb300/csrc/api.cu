@@ -80,6 +80,13 @@ struct LearnedModel {
 
 }  // namespace
 
+// One timed phase of a call: CUDA events recorded on the call's stream before
+// and after it (phase index as in grf_stats.phase_ms).
+struct PhaseSpan {
+  int phase;
+  cudaEvent_t a, b;
+};
+
 struct grf_graph {
   int64_t nv_in = 0;
   int32_t nv = 0;
@@ -127,7 +134,8 @@ struct grf_graph {
   struct GraphCache {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
-    bool spectral = false, spec_tc = false;
+    bool spectral = false, spec_tc = false, timing = false;
+    uint32_t phase_mask = 0;
     int sweep = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
     int64_t S = 0;
@@ -141,6 +149,9 @@ struct grf_graph {
     int h_status_cap = 0;
     std::vector<int32_t> stage_L;
     int launches = 0;
+    // with phase timing: the phase events, nodes of the graph that every
+    // replay records again
+    std::vector<PhaseSpan> spans;
   } gc;
   cudaStream_t cap_stream = nullptr;
   LearnedModel lm;
@@ -152,6 +163,11 @@ struct grf_graph {
   void drop_graph() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
     if (gc.nodes_dev) cudaFree(gc.nodes_dev);
+    for (auto& sp : gc.spans) {
+      cudaEventDestroy(sp.a);
+      cudaEventDestroy(sp.b);
+    }
+    gc.spans.clear();
     gc.exec = nullptr;
     gc.nodes_dev = nullptr;
     gc.d_seed = nullptr;
@@ -323,6 +339,7 @@ struct Opts {
   int precision, precond, out_dtype, max_iter;
   double rtol;
   bool timing;
+  uint32_t phase_mask;  // phases timed (bit p = grf_stats.phase_ms[p]) when timing
   int pcg_layout;  // 1 per system, 2 staged
   int recover_sg;  // 1, 2 or 4
   bool use_graph;
@@ -333,7 +350,15 @@ struct Opts {
 
 int read_opts(const grf_options* o, Opts* r) {
   r->use_graph = o && o->use_graph != 0;
-  r->timing = o && o->timing != 0 && !r->use_graph;
+  r->timing = o && o->timing != 0;
+  r->phase_mask = 0xFFu;
+  if (r->timing && (o->timing & GRF_TIMING_ONLY)) {
+    const uint32_t t = (uint32_t)o->timing;
+    if ((t & ~(uint32_t)GRF_TIMING_ONLY & ~0xFFu) != 0 || (t & 0xFFu) == 0)
+      return fail(GRF_EINVAL, "timing: GRF_TIMING_ONLY needs a phase mask in bits 0-7 (got 0x%x)",
+                  t);
+    r->phase_mask = t & 0xFFu;
+  }
   const int sg = o ? o->recover_sg : 0;
   if (sg != 0 && sg != 1 && sg != 2 && sg != 4)
     return fail(GRF_EINVAL, "recover_sg must be 0, 1, 2 or 4 (got %d)", sg);
@@ -493,28 +518,31 @@ struct RunStats {
   int64_t nodes = 0, systems = 0, iters_total = 0;
   int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0, fallback = 0;
   bool timing = false;
+  uint32_t mask = 0xFFu;  // the phases timed
   // graph capture: status words are copied to pinned host slots, no syncs
   bool capturing = false;
   PcgStatus* h_status = nullptr;
   int stage_idx = 0;
-  struct Span {
-    int phase;
-    cudaEvent_t a, b;
-  };
-  std::vector<Span> spans;
+  std::vector<PhaseSpan> spans;
   cudaEvent_t open = nullptr;
   double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 
-  void begin(cudaStream_t st) {
-    if (!timing) return;
+  // Under stream capture an event record becomes a node of the graph (an
+  // external event record), so each replay records the event again.
+  void record(cudaEvent_t e, cudaStream_t st) const {
+    if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+  }
+  void begin(int phase, cudaStream_t st) {
+    if (!timing || !((mask >> phase) & 1u)) return;
     cudaEventCreate(&open);
-    cudaEventRecord(open, st);
+    record(open, st);
   }
   void end(int phase, cudaStream_t st) {
-    if (!timing || !open) return;
+    if (!timing || !open || !((mask >> phase) & 1u)) return;
     cudaEvent_t b;
     cudaEventCreate(&b);
-    cudaEventRecord(b, st);
+    record(b, st);
     spans.push_back({phase, open, b});
     open = nullptr;
   }
@@ -583,14 +611,14 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                  const T* b, double* gvec, double* xv, const Opts& o, cudaStream_t st,
                  RunStats* rs) {
   const DevNodes nd = dev_nodes(w, L);
-  rs->begin(st);
+  rs->begin(1, st);
   // the Thomas sweep constants are needed only where an edge is left to Thomas
   SweepParams<T>* prm = (SweepParams<T>*)w.prm;
   if (sizeof(T) == 4 && o.spectral && w.bhat && g->thomas_rest() == 0) prm = nullptr;
   rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, prm,
                                   (T*)w.dscale, (T*)w.offv_t, st);
   rs->end(1, st);
-  rs->begin(st);
+  rs->begin(2, st);
   if (sizeof(T) == 4) {
     // FP32: the tridiagonal edges (all of them, or those the spectral path
     // leaves over), short ones by segments and long ones by nodes; then the
@@ -634,7 +662,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   if (learned) {
     if (!g->lm.ready || w.lp_chunk < 1 || L > kRamp)
       return fail(GRF_EINVAL, "learned preconditioner not set up for this call");
-    rs->begin(st);
+    rs->begin(6, st);
     const int64_t ne2 = 2 * (int64_t)g->ne;
     for (int32_t l0 = 0; l0 < L; l0 += w.lp_chunk) {
       LpActs a = w.lpa;
@@ -646,7 +674,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     }
     rs->end(6, st);
   }
-  rs->begin(st);
+  rs->begin(3, st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
   launch_pcg<T>(g->d, g->d_order, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
@@ -682,7 +710,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   int32_t counts[kMaxBins + 1];
   for (int i = 0; i <= g->n_bins[p]; ++i) counts[i] = i < i0 ? g->bin_count[p][i] : 0;
   const int32_t head = bins_before(g, p, i0), tail = bins_total(g, p) - head;
-  rs->begin(st);
+  rs->begin(4, st);
   rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
                                           (const SweepParams<T>*)w.prm, (T*)w.xw,
                                           g->d_bin_edges[p], counts, g->n_bins[p], w.acc,
@@ -767,7 +795,7 @@ int enqueue_sample(grf_graph* g, const std::vector<HostNodes>& stages, double ka
   T* b = c.take<T>((size_t)g->n * S);
   double* tmp = multi ? c.take<double>((size_t)g->n * S) : nullptr;
   void* ws_tail = g->ws ? (char*)g->ws + c.off : nullptr;
-  rs->begin(st);
+  rs->begin(0, st);
   launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev);
   rs->end(0, st);
   rs->launches += 1;
@@ -776,7 +804,7 @@ int enqueue_sample(grf_graph* g, const std::vector<HostNodes>& stages, double ka
     const bool last = i + 1 == stages.size();
     const double* nd = nodes_dev ? (*nodes_dev)[i] : nullptr;
     if (i > 0) {
-      rs->begin(st);
+      rs->begin(5, st);
       launch_to_minor<T>(g->d, S, tmp, b, true, st);
       rs->end(5, st);
       rs->launches += 1;
@@ -802,7 +830,9 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
 // The same call through a captured CUDA graph: captured once per configuration
 // (on an internal stream), then replayed on the caller's stream with the seed
 // copied in from pinned memory. Iteration statistics come back through pinned
-// status slots; per-phase timing is not available on this path.
+// status slots. With phase timing the phase events are captured as event
+// record nodes (a separate capture from the untimed one), and every replay
+// adds their elapsed times to the call's phase_ms.
 template <typename T, typename OutT>
 int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
                       int64_t S, OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
@@ -812,7 +842,8 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
                    gc.precond == o.precond && gc.spectral == o.spectral && gc.sweep == o.sweep &&
-                   gc.spec_tc == o.spec_tc &&
+                   gc.spec_tc == o.spec_tc && gc.timing == o.timing &&
+                   gc.phase_mask == (o.timing ? o.phase_mask : 0u) &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
                    gc.beta == beta && gc.k == k_step && gc.S == S && gc.out == (void*)out &&
@@ -844,6 +875,8 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     if (!g->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     RunStats cap;
     cap.capturing = true;
+    cap.timing = o.timing;
+    cap.mask = o.phase_mask;
     cap.h_status = gc.h_status;
     CUDA_TRY(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed));
     const int r = enqueue_sample<T, OutT>(g, stages, kappa, 0, S, out, o, g->cap_stream, &cap,
@@ -858,6 +891,8 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     const cudaError_t ei = cudaGraphInstantiate(&gc.exec, graph, 0);
     cudaGraphDestroy(graph);
     if (ei != cudaSuccess) return fail(GRF_ECUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+    gc.spans = std::move(cap.spans);  // owned by the cache from here on
+    cap.spans.clear();
     gc.stage_L.clear();
     for (auto& s : stages) gc.stage_L.push_back(s.L());
     gc.launches = cap.launches;
@@ -865,6 +900,8 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.precond = o.precond;
     gc.spectral = o.spectral;
     gc.spec_tc = o.spec_tc;
+    gc.timing = o.timing;
+    gc.phase_mask = o.timing ? o.phase_mask : 0u;
     gc.sweep = o.sweep;
     gc.out_dtype = o.out_dtype;
     gc.pcg_layout = o.pcg_layout;
@@ -883,6 +920,10 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   CUDA_TRY(cudaMemcpyAsync(gc.d_seed, gc.h_seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
   CUDA_TRY(cudaGraphLaunch(gc.exec, st));
   CUDA_TRY(cudaStreamSynchronize(st));
+  for (const auto& sp : gc.spans) {  // this replay's phase events
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, sp.a, sp.b) == cudaSuccess) rs->phase_ms[sp.phase] += ms;
+  }
   for (size_t i = 0; i < gc.stage_L.size(); ++i) {
     add_status(gc.h_status[i], rs);
     rs->nodes += gc.stage_L[i];
@@ -1663,6 +1704,7 @@ int grf_sample(grf_graph* g, double kappa, double beta, double k_step, uint64_t 
   cudaStream_t st = (cudaStream_t)stream;
   RunStats rs;
   rs.timing = o.timing;
+  rs.mask = o.phase_mask;
   int r;
 #define GRF_RUN(T, O)                                                                      \
   (o.use_graph ? sample_graph_impl<T, O>(g, kappa, beta, k_step, seed, n_samples, (O*)out, o, \
@@ -1826,6 +1868,7 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   cudaStream_t st = (cudaStream_t)stream;
   RunStats rs;
   rs.timing = o.timing;
+  rs.mask = o.phase_mask;
   void* tail = (char*)g->ws + head;
   int r;
   if (o.precision == GRF_FP64) {
@@ -1893,6 +1936,7 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
   const double k2 = kappa * kappa;
   RunStats rs;
   rs.timing = o.timing;
+  rs.mask = o.phase_mask;
   rs.launches += 1;
   if (o.precision == GRF_FP64) {
     double* b = (double*)g->ws;

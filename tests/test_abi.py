@@ -172,3 +172,29 @@ def test_interior_and_sweep_options_checked_before_device_work():
         assert ei.value.code == grf.GRF_ENOTSUP
     assert grf.make_options("mixed", interior="spectral_tc", sweep="nodes").knobs() == {
         "pcg_layout": "auto", "recover_sg": 0, "interior": "spectral_tc", "sweep": "nodes"}
+
+
+def test_timing_mask_checked_before_device_work():
+    G = grf.Graph([0, 1], [1, 2], [1.0, 0.5], 3, h=0.1)
+    assert grf.make_options("mixed", timing=True).timing == 1
+    assert grf.make_options("mixed", timing=False).timing == 0
+    assert grf.make_options("mixed", timing=["pcg"]).timing == grf.GRF_TIMING_ONLY | (1 << 3)
+    assert grf.make_options("mixed", timing=("noise", "recover")).timing == (
+        grf.GRF_TIMING_ONLY | 1 | (1 << 4))
+    for flag in (grf.GRF_TIMING_ONLY, grf.GRF_TIMING_ONLY | (1 << 8) | 1):
+        bad = grf.make_options("mixed")
+        bad.timing = flag
+        with pytest.raises(grf.GrfError) as ei:
+            grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad, stream=0)
+        assert ei.value.code == grf.GRF_EINVAL and "timing" in str(ei.value)
+
+
+def test_header_constants_match_the_binding():
+    src = open(os.path.join(ROOT, "include", "grf.h")).read()
+    found = 0
+    for name, shift, val in re.findall(r"^#define (GRF_\w+) (?:\(1 << (\d+)\)|(-?\d+))", src,
+                                       re.M):
+        if hasattr(grf, name):
+            assert getattr(grf, name) == (1 << int(shift) if shift else int(val)), name
+            found += 1
+    assert found >= 20

@@ -426,6 +426,38 @@ def test_cuda_graph_replay_matches_direct_calls(precision):
         assert rel_l2(graphed.cpu().numpy(), ref, ml) < TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_reports_phase_times(precision):
+    """With phase timing a replayed graph records the phase events as event
+    record nodes: every replay reports its own device time per phase, and the
+    field agrees with the untimed replay's."""
+    g, h = GRAPHS["random12"]()
+    G, m = make(g, h)
+    ml = fem.lumped_mass(m)
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    out = torch.empty((4, G.n_dofs), dtype=torch.float64, device="cuda")
+    plain = {}
+    for seed in (8, 9):
+        u, _ = G.sample(2.5, 0.6, 0.45, seed, 4, precision=precision, out_dtype="f64", out=out,
+                        use_graph=True)
+        plain[seed] = u.cpu().numpy()
+    for seed in (8, 9):  # the timed graph: captured, then replayed
+        u, st = G.sample(2.5, 0.6, 0.45, seed, 4, precision=precision, out_dtype="f64", out=out,
+                         use_graph=True, timing=True)
+        assert rel_l2(u.cpu().numpy(), plain[seed], ml) < tol
+        ph = st["phase_ms"]
+        for k in ("noise", "schur", "condense", "pcg", "recover"):
+            assert 0.0 < ph[k] < 1e3, (k, ph)
+        assert ph["precond_net"] == 0.0
+    for seed in (8, 9):  # only the PCG phase timed: its two events alone
+        u, st = G.sample(2.5, 0.6, 0.45, seed, 4, precision=precision, out_dtype="f64", out=out,
+                         use_graph=True, timing=["pcg"])
+        assert rel_l2(u.cpu().numpy(), plain[seed], ml) < tol
+        ph = st["phase_ms"]
+        assert 0.0 < ph["pcg"] < 1e3
+        assert all(v == 0.0 for k, v in ph.items() if k != "pcg"), ph
+
+
 def test_sample_host_graph_replay_across_calls():
     """grf_sample_host keeps its device output on the handle, so a captured
     graph is replayed (not re-captured) by later calls and still follows the
