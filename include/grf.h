@@ -184,6 +184,13 @@ int grf_graph_destroy(grf_graph* g);
 int grf_graph_info(const grf_graph* g, int64_t* n_dofs, int64_t* n_kept_vertices,
                    int64_t* n_interior, int64_t* vertex_map, int64_t* interior_offsets);
 
+/* The order in which the sample-group vertex PCG (Sec. 3, Phase 4) stores a
+ * system in shared memory: reverse Cuthill-McKee, each connected component
+ * in a contiguous range of slots (a launch detail: results do not depend on it).
+ *   perm_out: host int64 [n_kept_vertices], slot i -> kept vertex id.
+ *   GRF_EINVAL on a NULL handle or output. Host-only; no device work. */
+int grf_graph_vertex_order(const grf_graph* g, int64_t* perm_out);
+
 /* Draw n_samples fields of (kappa^2 - Delta)^beta u = W (Eq. 1) by the
  * lumped-mass, domain-decomposed sinc quadrature (Eq. 4, Eq. spde_approx_fem,
  * Sec. 3 Phases 2-5).

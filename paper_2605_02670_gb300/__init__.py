@@ -35,7 +35,8 @@ GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS, GRF_SWEEP_NODES = 0, 1, 2
 SWEEPS = {"auto": GRF_SWEEP_AUTO, "segments": GRF_SWEEP_SEGMENTS, "nodes": GRF_SWEEP_NODES}
 GRF_TIMING_ONLY = 1 << 30
 
-C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info", "grf_sample",
+C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info",
+             "grf_graph_vertex_order", "grf_sample",
              "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
              "grf_vertex_solve_noalloc", "grf_autotune", "grf_workspace_bytes",
              "grf_precond_init", "grf_precond_set", "grf_precond_get", "grf_precond_save",
@@ -98,6 +99,7 @@ def _load() -> ctypes.CDLL:
         "grf_graph_create": [I64, I64, P, P, P, P, D, ctypes.POINTER(P)],
         "grf_graph_destroy": [P],
         "grf_graph_info": [P, P, P, P, P, P],
+        "grf_graph_vertex_order": [P, P],
         "grf_sample": [P, D, D, D, U64, I64, P, P, P, P],
         "grf_sample_host": [P, D, D, D, U64, I64, P, P, P, P],
         "grf_noise": [P, U64, I64, P, I32, P],
@@ -205,6 +207,12 @@ def grf_graph_info(handle, n_vertices_in: int, n_edges: int) -> dict:
                                _ptr(vmap), _ptr(offs)))
     return {"n_dofs": n.value, "n_kept_vertices": nk.value, "n_interior": ni.value,
             "vertex_map": vmap, "interior_offsets": offs}
+
+
+def grf_graph_vertex_order(handle, n_kept: int) -> np.ndarray:
+    perm = np.empty(n_kept, np.int64)
+    _check(_lib.grf_graph_vertex_order(handle, _ptr(perm)))
+    return perm
 
 
 def grf_sample(handle, kappa, beta, k_step, seed, n_samples, out_ptr: int, opts: grf_options,
@@ -362,6 +370,11 @@ class Graph:
         self.n_interior = info["n_interior"]
         self.vertex_map = info["vertex_map"]
         self.interior_offsets = info["interior_offsets"]
+
+    @property
+    def vertex_order(self) -> np.ndarray:
+        """Slot -> kept vertex id of the sample-group PCG's shared-memory layout."""
+        return grf_graph_vertex_order(self.handle, self.n_kept)
 
     def close(self):
         if getattr(self, "handle", None) is not None:

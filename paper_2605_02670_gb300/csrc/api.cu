@@ -1655,6 +1655,13 @@ int grf_graph_create(int64_t n_vertices, int64_t n_edges, const int64_t* edge_u,
   return GRF_OK;
 }
 
+int grf_graph_vertex_order(const grf_graph* g, int64_t* perm_out) {
+  GRF_TRY(check_graph(g));
+  if (!perm_out) return fail(GRF_EINVAL, "perm_out is null");
+  for (int32_t i = 0; i < g->nv; ++i) perm_out[i] = g->rperm[i];
+  return GRF_OK;
+}
+
 int grf_graph_destroy(grf_graph* g) {
   delete g;
   return GRF_OK;

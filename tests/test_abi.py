@@ -54,6 +54,31 @@ def test_mesh_and_dof_map_match_oracle(name):
         assert G2.n_dofs == m.n_dofs
 
 
+@pytest.mark.parametrize("name", ["rgg", "parts"])
+def test_vertex_order_is_a_banded_permutation(name):
+    """The sample-group PCG's slot order (reverse Cuthill-McKee): a permutation
+    of the kept vertices, a narrower bandwidth than the input numbering, and
+    every connected component in one contiguous range of slots."""
+    if name == "rgg":
+        g = gi.random_geometric(400, 0.06, seed=3)
+    else:
+        g = gi.disjoint_union(gi.grid_deleted(15, 15, 0.15, seed=1),
+                              gi.random_small_graph(40, 60, 2), gi.interval(0.5), seed=4)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.1)
+    perm = G.vertex_order
+    n = G.n_kept
+    np.testing.assert_array_equal(np.sort(perm), np.arange(n))
+    slot = np.empty(n, np.int64)
+    slot[perm] = np.arange(n)
+    u, v = G.vertex_map[g.edge_u], G.vertex_map[g.edge_v]
+    assert (u >= 0).all() and (v >= 0).all()
+    assert np.abs(slot[u] - slot[v]).max() < np.abs(u - v).max() / 2
+    comp = gi._components(n, u, v)
+    for c in np.unique(comp):
+        s = np.sort(slot[comp == c])
+        assert s[-1] - s[0] + 1 == s.size
+
+
 def test_disjoint_union_keeps_the_parts_as_components():
     parts = [gi.grid_deleted(10, 10, 0.15, seed=2), gi.random_small_graph(25, 35, 4),
              gi.interval(0.8)]
