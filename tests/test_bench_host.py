@@ -1,0 +1,68 @@
+"""Host-side arithmetic of bench.py's roofline object, on CPU: the FP32 peak
+from the unit counts and clock, the algorithmic work of each phase from its
+per-unit figure, and the traffic record that is valid only for the kernel
+source it was measured on. The expected values are worked out here by hand
+from the per-unit figures (not by calling the same expressions)."""
+import hashlib
+import json
+import os
+from types import SimpleNamespace
+
+import pytest
+
+import bench
+
+
+def test_fp32_peak_from_unit_counts():
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA at 2070 MHz = 80.54784 TFLOP/s
+    assert bench.fp32_peak_tflops(2070) == pytest.approx(80.54784, rel=1e-12)
+    assert bench.fp32_peak_tflops(1000) == pytest.approx(38.912, rel=1e-12)
+
+
+def _workload(V=1980, E=4990, NI=957_699):
+    return SimpleNamespace(n_dofs=V + NI, n_kept=V, n_edges=E, n_interior=NI)
+
+
+def test_pcg_work_on_chip_counts_flops():
+    G = _workload()
+    stats = {"n_nodes": 148, "pcg_iters_total": 90_592}
+    work, bound = bench.algorithmic(None, G, stats, "pcg", 16, 4, 4)
+    # per iteration: SpMV 2 (1980 + 2 * 4990) = 23 920 flops, vector work 10 * 1980
+    assert bound == "alu"
+    assert work == 90_592 * (23_920 + 19_800)
+
+
+def test_pcg_work_off_chip_counts_bytes():
+    G = _workload(V=20_000, E=59_991, NI=48_000_000)
+    stats = {"n_nodes": 148, "pcg_iters_total": 145_235}
+    S = 64  # 148 x 64 x 20 000 x 8 B = 1.5 GB of vertex vectors: larger than L2
+    work, bound = bench.algorithmic(None, G, stats, "pcg", S, 4, 4)
+    vectors = 145_235 * 10 * 20_000 * 8
+    matrix = (145_235 / 64) * ((20_000 + 2 * 59_991) * 8 + 2 * 59_991 * 4)
+    assert bound == "hbm"
+    assert work == pytest.approx(vectors + matrix, rel=1e-12)
+
+
+def test_noise_recovery_condensation_and_schur_work():
+    G = _workload(V=10, E=12, NI=1000)
+    stats = {"n_nodes": 7, "pcg_iters_total": 0}
+    S = 3
+    assert bench.algorithmic(None, G, stats, "noise", S, 4, 4) == (1010 * 3 * 4 + 1010 * 8, "hbm")
+    assert bench.algorithmic(None, G, stats, "recover", S, 4, 4) == (6.0 * 1000 * 7 * 3, "alu")
+    assert bench.algorithmic(None, G, stats, "condense", S, 4, 4) == (4.0 * 1000 * 7 * 3, "alu")
+    # per node: 2 FP64 words per edge block pair, the vertex diagonal, 2 off-diagonals per edge
+    assert bench.algorithmic(None, G, stats, "schur", S, 4, 4) == (7 * (12 * 16 + 10 * 8 + 24 * 8),
+                                                                    "hbm")
+
+
+def test_traffic_record_only_for_the_measured_source():
+    p = os.path.join(bench.ROOT, "profiles", "traffic.json")
+    recs = json.load(open(p))
+    assert bench.traffic_record("pcg.cu", "no_such_workload") is None
+    for key, rec in recs.items():
+        kernel_file, workload = key.split(":")
+        src = os.path.join(bench.ROOT, "paper_2605_02670_gb300", "csrc", kernel_file)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        expect = rec["bytes_per_launch"] if sha == rec["sha256"] else None
+        assert bench.traffic_record(kernel_file, workload) == expect
+        assert rec["bytes_per_launch"] > 0
