@@ -2,7 +2,8 @@
 from the unit counts and clock, the algorithmic work of each phase from its
 per-unit figure, and the traffic record that is valid only for the kernel
 source it was measured on. The expected values are worked out here by hand
-from the per-unit figures (not by calling the same expressions)."""
+from the per-unit figures (not by calling the same expressions). Also the
+reference arm's contract line (it runs the oracle on the host cores only)."""
 import hashlib
 import json
 import os
@@ -66,3 +67,43 @@ def test_traffic_record_only_for_the_measured_source():
         expect = rec["bytes_per_launch"] if sha == rec["sha256"] else None
         assert bench.traffic_record(kernel_file, workload) == expect
         assert rec["bytes_per_launch"] > 0
+
+
+def _run_bench(args, env_extra=None):
+    import subprocess
+    import sys
+
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py")] + args,
+                          capture_output=True, text=True, env=env, timeout=300)
+
+
+def test_reference_arm_prints_one_contract_line():
+    """The reference arm (the FP64 oracle on the host cores, bounded samples):
+    one JSON line with the keys of the bench contract, its e2e equal to its
+    value with no host-device copies."""
+    r = _run_bench(["--impl", "reference", "--workload", "square5", "--steps", "2",
+                    "--warmup", "1"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["ms_per_step"] == pytest.approx(1000.0 * bench.gi.WORKLOADS["square5"].n_samples
+                                             / d["value"])
+    assert d["config"]["workload"] == "square5"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    r = _run_bench(["--impl", "reference", "--workload", "square5", "--steps", "1",
+                    "--warmup", "1"], {"RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
