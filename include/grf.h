@@ -158,7 +158,9 @@ typedef struct grf_stats {
    * events on the call's stream: [0] noise, [1] Schur blocks, [2] condensed
    * right-hand side, [3] vertex PCG, [4] recovery + quadrature sum,
    * [5] layout/mass scaling between stages, [6] learned-preconditioner network,
-   * [7] unused; zero otherwise */
+   * [7] unused; zero for the phases outside a GRF_TIMING_ONLY mask, and
+   * without timing. With use_graph the events are nodes of the replayed graph
+   * and the times are this call's replay. */
   double phase_ms[8];
 } grf_stats;
 
