@@ -223,3 +223,19 @@ def test_header_constants_match_the_binding():
             assert getattr(grf, name) == (1 << int(shift) if shift else int(val)), name
             found += 1
     assert found >= 20
+
+
+def test_binding_without_the_library_fails_loudly(tmp_path):
+    """No CPU fallback: a copy of the package without libgrf.so refuses to import."""
+    import shutil
+    import subprocess
+    import sys
+
+    pkg = tmp_path / "paper_2605_02670_gb300"
+    pkg.mkdir()
+    shutil.copy(os.path.join(ROOT, "paper_2605_02670_gb300", "__init__.py"), pkg / "__init__.py")
+    env = {k: v for k, v in os.environ.items() if k != "PYTHONPATH"}
+    r = subprocess.run([sys.executable, "-c", "import paper_2605_02670_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "no CPU fallback" in r.stderr
