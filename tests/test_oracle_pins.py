@@ -197,6 +197,29 @@ def test_random_graph_against_dense_eigendecomposition(seed):
     assert np.abs(u - exact).max() < 2e-2 * np.abs(exact).max()
 
 
+def test_half_powers_compose_to_the_stiffness_solve():
+    """Two applications of the beta = 1/2 quadrature with the lumped mass between
+    them give one solve with K: with L = M_L^-1 K, each application is
+    L^-1/2 M_L^-1 up to q(lambda) lambda^1/2 - 1 per mode, so the composition is
+    K^-1 b up to q(lambda)^2 lambda - 1, below about 2e-7 here (k = 0.2, spectrum
+    inside [2.25, 713] for kappa = 1.5 and elements of at least 0.075). The
+    consistent mass in place of M_L between the two breaks it."""
+    g = gi.random_small_graph(9, 14, 5)
+    mesh = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.1)
+    ml, _, kmat = sampler.assemble(mesh, 1.5)
+    b = np.random.default_rng(3).standard_normal((2, mesh.n_dofs))
+    ref = sampler.stiff_solve(kmat, b)
+
+    def rel(u):
+        return np.sqrt((ml * (u - ref) ** 2).sum()) / np.sqrt((ml * ref ** 2).sum())
+
+    half = sampler.fractional_apply(ml, kmat, b, 0.5, 0.2)
+    assert rel(sampler.fractional_apply(ml, kmat, ml[None, :] * half, 0.5, 0.2)) < 3e-7
+    mc = fem.consistent_mass(mesh)
+    wrong = sampler.fractional_apply(ml, kmat, np.asarray((mc @ half.T).T), 0.5, 0.2)
+    assert rel(wrong) > 1e-3
+
+
 def test_kirchhoff_and_continuity_at_vertices():
     """u is continuous by construction (one DOF per vertex). The vertex rows
     of (M_L + t K) u - b are the discrete Kirchhoff balance: zero flux sum up
