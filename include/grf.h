@@ -264,9 +264,10 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
  *   The graph must already be resident on the current device: a call that may
  *   allocate (grf_vertex_solve, grf_sample, grf_noise, ...) must have used the
  *   graph on that device before; otherwise GRF_EINVAL, with no device work.
- *   Sizes whose scratch (about 8 n_dofs n_rhs bytes in FP64, plus the Schur
- *   system and three PCG vectors per right-hand side) exceeds 16 MiB are
- *   rejected with GRF_EINVAL and a message naming the limit.
+ *   Sizes whose scratch (about 8 n_dofs n_rhs bytes in FP64, 4 in mixed
+ *   precision, plus the Schur system, the per-edge sweep constants and four
+ *   PCG vectors per right-hand side) exceeds 16 MiB are rejected with
+ *   GRF_EINVAL and a message naming the limit and the bytes needed.
  *   The first call on a device looks up the device address of the static array
  *   (once per device, with that device current); make that first call before
  *   any stream capture. All calls share the one array and it keeps the last

@@ -632,6 +632,9 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     const int32_t head = bins_before(g, p, node_bin0(g, p, o, L));
     const int32_t tail = bins_total(g, p) - head;
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head);
+    if (tail > 0 && !prm)
+      return fail(GRF_EINVAL, "node-parallel condensation of %d edges without sweep constants",
+                  (int)tail);
     if (tail > 0)
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
@@ -991,9 +994,12 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->offv_t = tsize == 4 ? c.take<char>(2 * E * 4) : nullptr;
   w->iters = c.take<int32_t>(Ss);
   w->status = c.take<PcgStatus>(1);
+  // sweep constants of the one node: launch_schur fills them and the
+  // node-parallel condensation of the long FP32 edges reads them
+  w->prm = c.take<char>(E * 4 * tsize);
   w->gvec = w->x = w->acc = nullptr;
   w->yscr = w->rpscr = nullptr;
-  w->prm = w->xw = nullptr;
+  w->xw = nullptr;
   w->bhat = nullptr;
   w->nshift = w->nwgam = nullptr;
 }
