@@ -523,22 +523,6 @@ def test_rgg2000_full_size_sampled_nodes():
     _sampled_node_check("rgg2000", [t[0], t[len(t) // 2], t[-1]], 4, "mixed")
 
 
-def test_rgg2000_full_size_sample_properties():
-    """Whole sampler at full size: finite, the vertex values of a mixed and an
-    FP64 run agree, and the sample mean / variance of the noise-driven field
-    behave (mean ~ 0 over DOFs)."""
-    w = gi.WORKLOADS["rgg2000"]
-    g = w.graph()
-    G, m = make(g, w.h)
-    u32, st = G.sample(w.kappa, w.beta, w.k_step, w.seed, w.n_samples, precision="mixed",
-                       out_dtype="f64")
-    u64, _ = G.sample(w.kappa, w.beta, w.k_step, w.seed, 2, precision="fp64")
-    ml = fem.lumped_mass(m)
-    a = u32.cpu().numpy()
-    assert np.isfinite(a).all() and st["n_unconverged"] == 0
-    assert rel_l2(a[:2], u64.cpu().numpy(), ml) < TOL["mixed"]
-
-
 # ---------------------------------------------------------------- preconditioners
 
 
