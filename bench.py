@@ -33,6 +33,7 @@ import grf_inputs as gi  # noqa: E402
 
 METRIC = "field samples/s and DOF-solves/s at rel L2 ≤1e-4 vs FP64 oracle; HBM % of peak"
 UNIT = "samples/s"
+# L2 size used by the CPU-side work model when no device is there to ask
 L2_BYTES = 129 * 1024 * 1024
 
 
@@ -143,35 +144,105 @@ def traffic_record(kernel_file: str, workload: str):
 
 # ----------------------------------------------------------------- CPU oracle
 
+# Above this many DOFs the oracle is timed on a smaller graph of the same family
+# (same parameters, edge statistics and mesh size) and its cost scaled by the
+# DOF ratio: one sparse LU of the 78 M-DOF lattice takes minutes.
+ORACLE_MAX_DOFS = 2_000_000
+ORACLE_SUBGRAPHS = {"grid": {"nx": 20, "ny": 20}, "ba": {"n": 1000}}
 
-def oracle_sample(w, graph, n_nodes_sample=4):
-    """Time the FP64 oracle on a bounded sample of the workload: mesh and
-    assembly, noise for all samples, and `n_nodes_sample` of the L quadrature
-    nodes (spread over the range), each factorised once and solved for every
-    sample. Extrapolated linearly in the node count."""
+
+def oracle_graph(w, graph):
+    """(graph, mesh of it, scale): the graph the oracle is timed on and the
+    factor N_workload / N_timed that takes its cost to the workload."""
+    from oracle import fem
+    mesh = _oracle_mesh(w, graph)
+    if mesh.n_dofs <= ORACLE_MAX_DOFS or w.graph_args["kind"] not in ORACLE_SUBGRAPHS:
+        return graph, mesh, 1.0
+    args = dict(w.graph_args)
+    args.update(ORACLE_SUBGRAPHS[args["kind"]])
+    kind = args.pop("kind")
+    sub = {"grid": gi.grid_deleted, "ba": gi.barabasi_albert}[kind](**args)
+    sm = _oracle_mesh(w, sub)
+    return sub, sm, mesh.n_dofs / sm.n_dofs
+
+
+def _oracle_mesh(w, graph):
+    from oracle import fem
+    ne = np.clip(np.ceil(graph.lengths / w.h), *w.clip) if w.clip else None
+    return fem.build_mesh(graph.edge_u, graph.edge_v, graph.lengths, graph.n_vertices, h=w.h,
+                          n_elems=ne)
+
+
+def _oracle_nodes(wdict, graph, node_ids):
+    """One worker's share: assembly and noise, then the listed quadrature
+    nodes (each one sparse LU and S solves). Returns (fixed s, per-node s)."""
+    import math as _m
+
     from oracle import fem, noise, quadrature, sampler
     t0 = time.perf_counter()
-    ne = None
-    if w.clip:
-        ne = np.clip(np.ceil(graph.lengths / w.h), *w.clip)
-    mesh = fem.build_mesh(graph.edge_u, graph.edge_v, graph.lengths, graph.n_vertices, h=w.h,
-                          n_elems=ne)
-    ml, _, kmat = sampler.assemble(mesh, w.kappa)
-    b = noise.white_noise(ml, w.seed, w.n_samples)
+    ne = np.clip(np.ceil(graph.lengths / wdict["h"]), *wdict["clip"]) if wdict["clip"] else None
+    mesh = fem.build_mesh(graph.edge_u, graph.edge_v, graph.lengths, graph.n_vertices,
+                          h=wdict["h"], n_elems=ne)
+    ml, _, kmat = sampler.assemble(mesh, wdict["kappa"])
+    b = noise.white_noise(ml, wdict["seed"], wdict["n_samples"])
     t_fixed = time.perf_counter() - t0
-    f = w.beta - math.floor(w.beta)
-    t, wt = quadrature.nodes(f, w.k_step)
-    pick = np.linspace(0, len(t) - 1, n_nodes_sample).round().astype(int)
+    f = wdict["beta"] - _m.floor(wdict["beta"])
+    t, wt = quadrature.nodes(f, wdict["k_step"])
     t1 = time.perf_counter()
-    for i in pick:
+    for i in node_ids:
         sampler.shifted_sum(ml, kmat, b, [t[i]], [wt[i]])
-    t_nodes = time.perf_counter() - t1
-    total = t_fixed + t_nodes * len(t) / len(pick)
-    return {"value": w.n_samples / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{w.name}: mesh+assembly+noise for {w.n_samples} samples, then "
-                       f"{len(pick)} of {len(t)} quadrature nodes (SuperLU factorisation + "
-                       f"{w.n_samples} solves each, single thread), extrapolated linearly "
-                       f"to all nodes; measured {t_fixed + t_nodes:.1f} s")}
+    return t_fixed, (time.perf_counter() - t1) / max(1, len(node_ids))
+
+
+def _wdict(w):
+    return {"h": w.h, "clip": w.clip, "kappa": w.kappa, "beta": w.beta, "k_step": w.k_step,
+            "seed": w.seed, "n_samples": w.n_samples}
+
+
+def oracle_sample(w, graph, n_nodes_sample=2, parallel=False):
+    """Time the FP64 oracle on a bounded sample of the workload: mesh, assembly
+    and noise for all samples, then `n_nodes_sample` of the L quadrature nodes
+    (spread over the range), each factorised once and solved for every sample;
+    extrapolated linearly in the node count (and by the DOF ratio when a
+    smaller graph of the family stands in). parallel: the paper's
+    parallelisation, quadrature nodes spread over every host core (one process
+    each, started with spawn); each core's share is then ceil(L / cores)
+    nodes after its own assembly."""
+    import math as _m
+    g, mesh, scale = oracle_graph(w, graph)
+    # beta >= 1: one more factorisation per integer power, timed like a node
+    Lq = quad_count(w.beta, w.k_step)
+    L = Lq + int(math.floor(w.beta))
+    t0 = time.perf_counter()
+    if not parallel:
+        pick = np.linspace(0, Lq - 1, n_nodes_sample).round().astype(int).tolist()
+        t_fixed, t_node = _oracle_nodes(_wdict(w), g, pick)
+        cores = 1
+        total = (t_fixed + t_node * L) * scale
+        how = f"{len(pick)} of {L} quadrature nodes, single thread"
+    else:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        pick = np.linspace(0, Lq - 1, cores).round().astype(int).tolist()
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        # a worker that dies raises BrokenProcessPool here instead of hanging
+        with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(_oracle_nodes, _wdict(w), g, [i]) for i in pick]
+            res = [f.result(timeout=600) for f in futs]
+        t_fixed = max(r[0] for r in res)
+        t_node = max(r[1] for r in res)
+        total = (t_fixed + t_node * _m.ceil(L / cores)) * scale
+        how = f"{cores} of {L} quadrature nodes at once, one per core (spawned processes)"
+    wall = time.perf_counter() - t0
+    where = (f"{w.name}" if scale == 1.0 else
+             f"a {mesh.n_dofs}-DOF graph of the {w.name} family (same parameters and mesh "
+             f"size), scaled by the DOF ratio {scale:.1f}")
+    return {"value": w.n_samples / total, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"{where}: mesh+assembly+noise for {w.n_samples} samples, then {how} "
+                       f"(SuperLU factorisation + {w.n_samples} solves each), extrapolated "
+                       f"linearly to all {L} nodes; measured {wall:.1f} s"),
+            "wall_s": wall}
 
 
 def run_reference(args, w, graph):
@@ -180,16 +251,20 @@ def run_reference(args, w, graph):
         return
     # the oracle keeps no state between calls, so it needs no warm-up;
     # every step is one timed bounded sample
-    vals = []
+    vals, walls = [], []
     cb = None
     for _ in range(args.steps):
-        cb = oracle_sample(w, graph, n_nodes_sample=2)
+        cb = oracle_sample(w, graph, parallel=True)
         vals.append(cb["value"])
+        walls.append(cb.pop("wall_s"))
     v = statistics.median(vals)
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * w.n_samples / v, "higher_is_better": True,
+            "ms_per_step": 1000.0 * statistics.mean(walls),
+            "ms_per_step_is": "wall time of one bounded oracle sample (cpu_baseline.sample); "
+                              "value is that sample extrapolated to the whole workload",
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name}, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -199,27 +274,29 @@ def run_reference(args, w, graph):
 # ----------------------------------------------------------------- GPU path
 
 
-def algorithmic(w, G, stats, phase, S, tsize, out_size):
+def algorithmic(w, G, stats, phase, S, tsize, out_size, l2_bytes=L2_BYTES):
     """Algorithmic bytes (or flops) of one launch of a phase, from the
-    per-unit figures: noise writes N S values and reads N mass factors; one
-    PCG iteration of one system moves ~10 |V| FP64 vector values and each
-    (node, sample-batch) reads the Schur matrix ((|V| + 2|E|) values + 2|E|
-    indices); recovery reads the noise, the vertex solutions and writes U."""
+    method's per-unit figures (b = bytes per value of the phase's arithmetic:
+    4 in mixed precision, 8 in FP64):
+    noise: writes N S b and reads the N FP64 mass factors;
+    PCG, per system-iteration: 4 (|V| + 2|E|) + 10 |V| flops; when the vertex
+    vectors of all systems exceed L2, 10 |V| b bytes of vector traffic plus the
+    node's matrix, (|V| + |E|) (8 + 4) bytes, shared over the S samples;
+    condensation + recovery: 12 flops per (interior node, node, sample),
+    4 of them in the two end sweeps of the condensation and 8 in the recovery
+    (forward/back sweep and the weighted accumulation);
+    Schur blocks: the FP64 words written per node."""
     N, V, E, NI = G.n_dofs, G.n_kept, G.n_edges, G.n_interior
     L = stats["n_nodes"]
     if phase == "noise":
         return N * S * tsize + N * 8, "hbm"
     if phase == "pcg":
         it = stats["pcg_iters_total"]
-        if L * S * V * 8 <= L2_BYTES:
-            # the vertex vectors of every system stay on chip (shared memory and
-            # registers of the sample-group layout): bounded by the FP32 work,
-            # SpMV 2 (|V| + 2|E|) + dots and updates ~10 |V| flops per iteration
-            return it * (2 * (V + 2 * E) + 10 * V), "alu"
-        return it * 10 * V * 8 + (it / S) * ((V + 2 * E) * 8 + 2 * E * 4), "hbm"
+        if L * S * V * 8 <= l2_bytes:
+            return it * (4 * (V + 2 * E) + 10 * V), "alu"
+        return it * 10 * V * tsize + (it / S) * (V + E) * 12, "hbm"
     if phase == "recover":
-        # FP32 FMA work: ~6 flops per (interior node, quadrature node, sample)
-        return 6.0 * NI * L * S, "alu"
+        return 8.0 * NI * L * S, "alu"
     if phase == "condense":
         return 4.0 * NI * L * S, "alu"
     if phase == "schur":
@@ -227,9 +304,91 @@ def algorithmic(w, G, stats, phase, S, tsize, out_size):
     return 0, "hbm"
 
 
-def fp32_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flops (FMA) per clock
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz, n_sm=152):
+    # SMs x 128 FP32 lanes x 2 flops (FMA) per clock
+    return n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# Same family and parameters, small enough for the oracle to solve every node
+# in seconds: the accuracy of the bench's configuration against the oracle.
+CHECK_GRAPHS = {
+    "grid": lambda a: gi.grid_deleted(6, 6, a.get("frac", 0.15), seed=a.get("seed", 7)),
+    "rgg": lambda a: gi.random_geometric(300, a.get("radius", 0.0285) * math.sqrt(2000 / 300),
+                                         seed=a.get("seed", 0)),
+    "ba": lambda a: gi.barabasi_albert(80, a.get("m", 3), seed=a.get("seed", 0)),
+    "long": lambda a: gi.long_edges(20, 20, a.get("n_elems", 3072), a.get("spread", 64),
+                                    a.get("h", 2.0 ** -9), seed=a.get("seed", 0)),
+}
+
+
+def ml_weights(graph, ne, G):
+    """Lumped-mass diagonal in the library's DOF order ([kept vertices], then
+    the interior nodes edge by edge): h_e on an edge's interior nodes, the sum
+    of h_e / 2 over the incident edges on a vertex."""
+    he = np.asarray(graph.lengths, np.float64) / ne
+    vm = np.asarray(G.vertex_map)
+    wv = np.zeros(G.n_kept)
+    np.add.at(wv, vm[np.asarray(graph.edge_u)], he / 2)
+    np.add.at(wv, vm[np.asarray(graph.edge_v)], he / 2)
+    return np.concatenate([wv, np.repeat(he, np.asarray(ne, np.int64) - 1)])
+
+
+def accuracy_checks(args, w, graph, G, out, seed, prec, knobs):
+    """GPU side of the accuracy figures of the benchmarked configuration:
+    (1) the same parameters, mesh size and launch knobs on a small graph of
+    the workload's family (4 samples), kept for the CPU leg's oracle;
+    (2) at full size, the last timed call's first two samples against the
+    plain FP64 form on the same GPU (same seed), whose rate is timed too."""
+    import torch
+    import paper_2605_02670_gb300 as grf
+
+    res = {}
+    kind = w.graph_args["kind"]
+    cg = CHECK_GRAPHS[kind](w.graph_args) if kind in CHECK_GRAPHS else graph
+    ne = grf.mesh_elements(cg.lengths, w.h, w.clip)
+    Gc = grf.Graph(cg.edge_u, cg.edge_v, cg.lengths, cg.n_vertices, n_elems=ne)
+    Sc = min(4, w.n_samples)
+    uc, _ = Gc.sample(w.kappa, w.beta, w.k_step, w.seed, Sc, precision=prec, out_dtype="f64",
+                      use_graph=args.use_graph, **knobs)
+    res["_check"] = (cg, ne, Sc, uc.cpu().numpy(), Gc.n_dofs)
+    if prec == "mixed":
+        S2 = 2
+        u64, _ = G.sample(w.kappa, w.beta, w.k_step, seed, S2, precision="fp64")
+        mlf = ml_weights(graph, grf.mesh_elements(graph.lengths, w.h, w.clip), G)
+        res["full_vs_fp64_form"] = {
+            "rel_l2": _rel_l2(out[:S2].double().cpu().numpy(), u64.cpu().numpy(), mlf),
+            "samples": S2}
+        del u64
+        # the plain FP64 form (FP64 Thomas interiors, FP64 Jacobi-PCG), timed
+        st = torch.cuda.current_stream()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        G.sample(w.kappa, w.beta, w.k_step, seed + 1, S2, precision="fp64")
+        b.record(st)
+        b.synchronize()
+        res["fp64_form"] = {"value": S2 / (a.elapsed_time(b) / 1000.0), "unit": UNIT,
+                            "samples_per_call": S2}
+        torch.cuda.empty_cache()
+    return res
+
+
+def oracle_check(w, check):
+    """CPU leg: the oracle's field on the small check graph and the relative
+    M_L-weighted L2 error of the GPU's field there."""
+    from oracle import fem, sampler
+    cg, ne, Sc, uc, n = check
+    m, ref, _ = sampler.sample(cg, w.kappa, w.beta, w.k_step, w.seed, Sc, n_elems=ne)
+    return {"rel_l2": _rel_l2(uc, ref, fem.lumped_mass(m)),
+            "graph": f"{w.graph_args['kind']} family, {n} DOFs, {Sc} samples, every node"}
+
+
+def _rel_l2(u, ref, ml):
+    u = np.atleast_2d(u)
+    ref = np.atleast_2d(ref)
+    num = np.sqrt((ml[None, :] * (u - ref) ** 2).sum(axis=1))
+    den = np.sqrt((ml[None, :] * ref ** 2).sum(axis=1))
+    return float((num / den).max())
 
 
 def run_grf(args, w, graph):
@@ -253,7 +412,10 @@ def run_grf(args, w, graph):
     osz = 4 if out_dtype == "f32" else 8
     out = torch.empty((S, G.n_dofs), dtype=torch.float32 if osz == 4 else torch.float64,
                       device="cuda")
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    props = torch.cuda.get_device_properties(local)
+    l2_bytes = int(getattr(props, "L2_cache_size", 0) or L2_BYTES)
+    n_sm = int(props.multi_processor_count)
+    flush = torch.empty(2 * l2_bytes // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     seed0 = rank_seed(w.seed, rank)
 
@@ -322,6 +484,10 @@ def run_grf(args, w, graph):
         dist.barrier()
     ms = statistics.mean(times)
     ms_max = max_over_ranks(ms, dist)
+    last_seed = seed0 + args.warmup + args.steps
+    accuracy = None
+    if not args.no_accuracy:
+        accuracy = accuracy_checks(args, w, graph, G, out, last_seed, prec, knobs)
     st = iters[-1]
     L = st["n_nodes"]
     value = job_rate(S, world, ms_max / 1000.0)
@@ -353,8 +519,21 @@ def run_grf(args, w, graph):
     hbm_peak, peak_kind = peaks()
     clocks = clk.summary()
     roof = {}
-    work, bound = algorithmic(w, G, st, dom, S, tsize, osz)
+    work, bound = algorithmic(w, G, st, dom, S, tsize, osz, l2_bytes)
     dur_s = mean_ph[dom] / 1000.0
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp32_pk = fp32_peak_tflops(sm_mhz, n_sm)
+    phases = {}
+    for ph, t_ms in mean_ph.items():
+        wk, bd = algorithmic(w, G, st, ph, S, tsize, osz, l2_bytes)
+        if not wk or not t_ms:
+            continue
+        if bd == "hbm":
+            phases[ph] = {"ms": t_ms, "bound": "hbm", "GB/s": wk / t_ms / 1e6,
+                          "frac": wk / t_ms / 1e6 / hbm_peak}
+        else:
+            phases[ph] = {"ms": t_ms, "bound": "alu", "TFLOP/s": wk / t_ms / 1e9,
+                          "frac": wk / t_ms / 1e9 / fp32_pk}
     interior = knobs.get("interior", "spectral" if prec == "mixed" else "thomas")
     spectral = interior in ("spectral", "spectral_tc")
     segments = knobs.get("sweep") == "segments"
@@ -370,11 +549,11 @@ def run_grf(args, w, graph):
                 "frac": ach / hbm_peak, "peak_source": peak_kind,
                 "traffic": traffic_record(kernel_file, w.name)}
     else:
-        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-        pk = fp32_peak_tflops(mhz)
         ach = work / dur_s / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_pk,
+                "unit": "TFLOP/s", "frac": ach / fp32_pk,
+                "peak_source": (f"{n_sm} SMs (device properties) x 128 FP32 lanes x 2 x "
+                                f"{sm_mhz:.0f} MHz (median sampled SM clock)"),
                 "traffic": traffic_record(kernel_file, w.name)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -392,14 +571,34 @@ def run_grf(args, w, graph):
         "pcg_iters_total": st["pcg_iters_total"], "pcg_iters_max": st["pcg_iters_max"],
         "phase_ms": mean_ph, "phase_ms_source": phase_source,
         "roofline": roof,
+        "phase_roofline": phases,
+        "accuracy": accuracy,
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
         "e2e": {"value": job_rate(S, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 3 * 8 * L,
                 "d2h_bytes_per_step": S * G.n_dofs * osz},
     }
+    if accuracy and accuracy.get("fp64_form"):
+        line["speedup_vs_fp64_form"] = value / accuracy["fp64_form"]["value"]
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_sample(w, graph)
+        # the paper's parallelisation (quadrature nodes over every host core),
+        # and beside it the single-thread figure (its instruction counts are
+        # single-threaded)
+        cb1 = oracle_sample(w, graph)
+        cb1.pop("wall_s", None)
+        cbp = oracle_sample(w, graph, parallel=True)
+        cbp.pop("wall_s", None)
+        line["cpu_baseline"] = cbp
+        line["cpu_baseline_1core"] = cb1
+        if accuracy and "_check" in accuracy:
+            accuracy["reduced_vs_oracle"] = oracle_check(w, accuracy["_check"])
+            line["rel_l2"] = {"vs_oracle_small_graph": accuracy["reduced_vs_oracle"]["rel_l2"]}
+            if "full_vs_fp64_form" in accuracy:
+                line["rel_l2"]["vs_fp64_form_full_size"] = \
+                    accuracy["full_vs_fp64_form"]["rel_l2"]
+    if accuracy:
+        accuracy.pop("_check", None)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -408,12 +607,14 @@ def run_grf(args, w, graph):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grf", choices=["grf", "reference"])
-    ap.add_argument("--workload", default="rgg2000", choices=sorted(gi.WORKLOADS))
+    ap.add_argument("--workload", default="grid300", choices=sorted(gi.WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the accuracy checks (oracle on a small graph, FP64 form)")
     ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
     ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral", "spectral_tc"],
