@@ -535,10 +535,11 @@ def run_grf(args, w, graph):
             phases[ph] = {"ms": t_ms, "bound": "alu", "TFLOP/s": wk / t_ms / 1e9,
                           "frac": wk / t_ms / 1e9 / fp32_pk}
     interior = knobs.get("interior", "spectral" if prec == "mixed" else "thomas")
-    spectral = interior in ("spectral", "spectral_tc")
+    spectral = interior in ("spectral", "spectral_tc", "spectral_umma")
     segments = knobs.get("sweep") == "segments"
     kernel_file = {"noise": "noise.cu", "schur": "schur.cu",
-                   "condense": ("spectral_mma.cu" if interior == "spectral_tc" else "spectral.cu")
+                   "condense": ("spectral_mma.cu" if interior == "spectral_tc" else
+                                ("dst_gemm.cu" if interior == "spectral_umma" else "spectral.cu"))
                    if spectral else ("thomas.cu" if segments else "sweep.cu"),
                    "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else
                    ("recover.cu" if segments else "sweep.cu"),
@@ -615,9 +616,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the accuracy checks (oracle on a small graph, FP64 form)")
-    ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs"])
+    ap.add_argument("--pcg-layout", default="auto", choices=["auto", "per_system", "staged", "staged_pairs",
+                                                          "batched"])
     ap.add_argument("--recover-sg", type=int, default=0, choices=[0, 1, 2, 4])
-    ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral", "spectral_tc"],
+    ap.add_argument("--interior", default=None, choices=[None, "thomas", "spectral", "spectral_tc", "spectral_umma"],
                     help="edge-interior solver (default: the autotuner's or the library's)")
     ap.add_argument("--sweep", default=None, choices=[None, "segments", "nodes"],
                     help="layout of the FP32 tridiagonal sweeps (default: the library's)")

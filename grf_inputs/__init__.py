@@ -259,6 +259,13 @@ WORKLOADS = {
                         graph_args={"kind": "long", "n_vertices": 200, "n_edges": 300,
                                     "n_elems": 3072, "spread": 64, "h": 2.0 ** -9,
                                     "seed": 0}),
+    # 120x120 grid with the 300x300 lattice's parameters and a coarser mesh:
+    # more than 4096 vertices and vectors larger than L2 at a few GB on the
+    # device (profiles of the vertex PCG).
+    "grid120": Workload("grid120", kappa=2.0, beta=0.75, k_step=0.25, h=2.0 ** -6,
+                        n_samples=32, seed=1, precision="mixed",
+                        graph_args={"kind": "grid", "nx": 120, "ny": 120,
+                                    "frac": 0.15, "seed": 7}),
     # 300x300 grid, 15% edges deleted, largest component.
     "grid300": Workload("grid300", kappa=2.0, beta=0.75, k_step=0.25, h=2.0 ** -9,
                         n_samples=32, seed=1, precision="mixed",

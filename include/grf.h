@@ -78,7 +78,7 @@ typedef struct grf_options {
   int32_t timing;      /* nonzero: record CUDA events around each phase (grf_stats.phase_ms);
                           GRF_TIMING_ONLY | mask: only around the phases whose bit p
                           (p = the phase_ms index, bits 0-7) is set; other bits: GRF_EINVAL */
-  int32_t pcg_layout;  /* GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM or GRF_PCG_STAGED (see below) */
+  int32_t pcg_layout;  /* GRF_PCG_AUTO, _PER_SYSTEM, _STAGED, _STAGED_PAIRS, _BATCHED (below) */
   int32_t recover_sg;  /* samples per lane in the interior recovery: 0 = auto, or 1, 2, 4
                           (FP32 sweeps; FP64 sweeps always use 2) */
   int32_t use_graph;   /* grf_sample only: nonzero captures the call's launch sequence into a
@@ -87,8 +87,8 @@ typedef struct grf_options {
                           with timing, the phase events are event record nodes of the
                           graph and every replay reports its own phase_ms */
   int32_t interior;    /* edge-interior solver of the condensation and recovery steps:
-                          GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL or
-                          GRF_INTERIOR_SPECTRAL_TC */
+                          GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL,
+                          GRF_INTERIOR_SPECTRAL_TC or GRF_INTERIOR_SPECTRAL_UMMA */
   int32_t sweep;       /* how FP32 edges left to the tridiagonal solves are swept:
                           GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS or GRF_SWEEP_NODES */
 } grf_options;
@@ -109,6 +109,14 @@ typedef struct grf_options {
                                        and end-value contraction on the tensor cores
                                        (mma.sync, TF32 operands in three terms); the
                                        recovery as SPECTRAL */
+#define GRF_INTERIOR_SPECTRAL_UMMA 4 /* SPECTRAL with both sine transforms of every edge
+                                        as tcgen05 tensor-core products: the edges are
+                                        grouped by interior-node count m and each group's
+                                        transforms are one product with Phi_m (BF16 hi/lo
+                                        operands in three terms, FP32 accumulation in
+                                        tensor memory); the end values and the sine-basis
+                                        coefficients as SPECTRAL. Needs n_samples <= 256
+                                        (larger sample counts run as SPECTRAL) */
 
 /* Parallel layouts of the FP32 tridiagonal edge solves (same results up to
  * rounding; FP64 sweeps always use SEGMENTS):
@@ -141,6 +149,10 @@ typedef struct grf_options {
 #define GRF_PCG_STAGED 2
 #define GRF_PCG_STAGED_PAIRS 3  /* as STAGED with 256-thread CTAs and groups of 2 samples:
                                    more resident CTAs per SM, half the matrix reuse */
+#define GRF_PCG_BATCHED 4       /* mixed precision, Jacobi: one CTA per (node, 8 samples)
+                                   with the group's vectors in global memory as rows of 8
+                                   samples per vertex; what STAGED and STAGED_PAIRS fall
+                                   back to when a node's system does not fit on chip */
 
 typedef struct grf_stats {
   int64_t n_dofs;          /* N = |V_kept| + sum_e (n_e - 1) */
@@ -280,9 +292,12 @@ int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double ga
 
 /* Launch-schedule autotuner (the paper has no counterpart; it picks GPU launch
  * knobs only and does not change the computed field beyond rounding): times
- * grf_sample with CUDA events on `stream` for every candidate
- * (pcg_layout in {PER_SYSTEM, STAGED where it applies} x recover_sg in {1, 2, 4}
- * for FP32 sweeps) after one warm-up call each, `reps` timed calls each.
+ * grf_sample with CUDA events on `stream`, after one warm-up call each and
+ * `reps` timed calls each, in two passes: first the edge-interior solvers
+ * (mixed precision: THOMAS and SPECTRAL with recover_sg in {1, 2, 4} where
+ * tridiagonal edges remain, SPECTRAL_TC, and SPECTRAL_UMMA for n_samples <= 256;
+ * FP64: THOMAS) with the default PCG layout, then every PCG layout (PER_SYSTEM,
+ * and in mixed precision STAGED, STAGED_PAIRS, BATCHED) with the fastest solver.
  *   out: device buffer [n_samples][n_dofs] of base->out_dtype for the trials;
  *   base: options whose precision, out_dtype, rtol and max_iter are kept (NULL:
  *     defaults); best: receives base with the fastest knobs; best_ms: its mean

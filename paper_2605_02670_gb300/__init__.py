@@ -25,12 +25,14 @@ PRECONDS = {"jacobi": GRF_PRECOND_JACOBI, "learned": GRF_PRECOND_LEARNED,
             "neumann": GRF_PRECOND_NEUMANN}
 GRF_LP_PARAMS = 25538
 GRF_OUT_F64, GRF_OUT_F32 = 0, 1
-GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED, GRF_PCG_STAGED_PAIRS = 0, 1, 2, 3
+GRF_PCG_AUTO, GRF_PCG_PER_SYSTEM, GRF_PCG_STAGED, GRF_PCG_STAGED_PAIRS, GRF_PCG_BATCHED = \
+    0, 1, 2, 3, 4
 PCG_LAYOUTS = {"auto": GRF_PCG_AUTO, "per_system": GRF_PCG_PER_SYSTEM, "staged": GRF_PCG_STAGED,
-               "staged_pairs": GRF_PCG_STAGED_PAIRS}
+               "staged_pairs": GRF_PCG_STAGED_PAIRS, "batched": GRF_PCG_BATCHED}
 GRF_INTERIOR_AUTO, GRF_INTERIOR_THOMAS, GRF_INTERIOR_SPECTRAL, GRF_INTERIOR_SPECTRAL_TC = 0, 1, 2, 3
+GRF_INTERIOR_SPECTRAL_UMMA = 4
 INTERIORS = {"auto": GRF_INTERIOR_AUTO, "thomas": GRF_INTERIOR_THOMAS,
-             "spectral": GRF_INTERIOR_SPECTRAL, "spectral_tc": GRF_INTERIOR_SPECTRAL_TC}
+             "spectral": GRF_INTERIOR_SPECTRAL, "spectral_tc": GRF_INTERIOR_SPECTRAL_TC, "spectral_umma": GRF_INTERIOR_SPECTRAL_UMMA}
 GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS, GRF_SWEEP_NODES = 0, 1, 2
 SWEEPS = {"auto": GRF_SWEEP_AUTO, "segments": GRF_SWEEP_SEGMENTS, "nodes": GRF_SWEEP_NODES}
 GRF_TIMING_ONLY = 1 << 30

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -123,7 +124,15 @@ struct grf_graph {
   }
 
   int device = -1;
+  int n_sm = 0;  // multiprocessors of that device
+  const float* d_sqrt_ml_f = nullptr;  // FP32 copy of DevGraph::sqrt_ml (FP32 noise)
   void* dev_block = nullptr;
+  // sine-transform plan of the tensor-core spectral path (built on first use,
+  // for one sample padding at a time)
+  struct DstPlan {
+    void* blk = nullptr;
+    DstPlanDev dev{};
+  } dst;
   DevGraph d{};
   void* ws = nullptr;
   size_t ws_bytes = 0;
@@ -134,7 +143,7 @@ struct grf_graph {
   struct GraphCache {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
-    bool spectral = false, spec_tc = false, timing = false;
+    bool spectral = false, spec_tc = false, spec_umma = false, timing = false;
     uint32_t phase_mask = 0;
     int sweep = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
@@ -187,6 +196,7 @@ struct grf_graph {
       if (ws) cudaFree(ws);
       if (lm.blk) cudaFree(lm.blk);
       if (host_out) cudaFree(host_out);
+      if (dst.blk) cudaFree(dst.blk);
       cudaSetDevice(cur);
     }
   }
@@ -194,12 +204,13 @@ struct grf_graph {
 
 namespace {
 
-__global__ void sqrt_ml_kernel(DevGraph g, const double* mlv, double* out) {
+__global__ void sqrt_ml_kernel(DevGraph g, const double* mlv, double* out, float* out_f) {
   const int64_t total = g.n;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
        j += (int64_t)gridDim.x * blockDim.x) {
     if (j < g.nv) {
       out[j] = sqrt(mlv[j]);
+      out_f[j] = (float)out[j];
     } else {
       // interior DOF: find its edge by bisection over the interior offsets
       const int64_t i = j - g.nv;
@@ -209,6 +220,7 @@ __global__ void sqrt_ml_kernel(DevGraph g, const double* mlv, double* out) {
         if (g.ioff[mid] <= i) lo = mid; else hi = mid - 1;
       }
       out[j] = sqrt(g.he[lo]);
+      out_f[j] = (float)out[j];
     }
   }
 }
@@ -227,10 +239,12 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1); c.take<int32_t>(E + 1);
   c.take<int32_t>(2 * E);
   c.take<int32_t>(V); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
+  c.take<float>((size_t)g->n);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
   g->dev_block = blk;
+  CUDA_TRY(cudaDeviceGetAttribute(&g->n_sm, cudaDevAttrMultiProcessorCount, dev));
   Carve k(blk);
   int32_t* eu = k.take<int32_t>(E);
   int32_t* ev = k.take<int32_t>(E);
@@ -284,7 +298,9 @@ int ensure_device(grf_graph* g) {
   g->d_order = VertexOrder{rperm, rvptr, rnbr, rinc};
   int64_t blocks = (g->n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml);
+  float* smlf = k.take<float>((size_t)g->n);
+  g->d_sqrt_ml_f = smlf;
+  sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml, smlf);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaDeviceSynchronize());
   return GRF_OK;
@@ -301,6 +317,67 @@ int ensure_ws(grf_graph* g, size_t bytes) {
   }
   CUDA_TRY(cudaMalloc(&g->ws, bytes));
   g->ws_bytes = bytes;
+  return GRF_OK;
+}
+
+// The tensor-core sine transforms (interior GRF_INTERIOR_SPECTRAL_UMMA): the
+// spectral edges grouped by interior-node count m, Phi_m's BF16 hi/lo planes
+// and the work items for sample padding sp. Built before any capture, for one
+// sp at a time (S > 256 has no plan: the call takes the FP32 spectral kernels).
+int ensure_dst_plan(grf_graph* g, int64_t S) {
+  const int32_t sp = dst_gemm_sample_pad(S);
+  if (sp == 0) return GRF_OK;
+  if (g->dst.blk && g->dst.dev.sp == sp) return GRF_OK;
+  if (g->dst.blk) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->drop_graph();  // a captured graph refers to the old plan
+    CUDA_TRY(cudaFree(g->dst.blk));
+    g->dst = grf_graph::DstPlan{};
+  }
+  const int32_t BM = dst_gemm_tile_rows(), BK = dst_gemm_tile_k(), BN = dst_gemm_tile_cols();
+  const int32_t ept = BN / sp;
+  std::map<int32_t, std::vector<int32_t>> by_m;
+  for (int32_t e : g->spec_edges) by_m[g->nel[e] - 1].push_back(e);
+  std::vector<DstGroup> groups;
+  std::vector<DstItem> items;
+  std::vector<int32_t> edges;
+  int64_t phi_total = 0;
+  for (auto& kv : by_m) {
+    const int32_t m = kv.first;
+    const std::vector<int32_t>& list = kv.second;
+    DstGroup G{phi_total, m, (m + BM - 1) / BM * BM, (m + BK - 1) / BK * BK, 0};
+    groups.push_back(G);
+    const int32_t e0 = (int32_t)edges.size();
+    edges.insert(edges.end(), list.begin(), list.end());
+    for (int32_t t = 0; t < (int32_t)list.size(); t += ept)
+      for (int32_t mt = 0; mt < G.mp / BM; ++mt)
+        items.push_back(DstItem{G.phi_off, m, G.kp, e0 + t,
+                                std::min<int32_t>(ept, (int32_t)list.size() - t), mt, 0});
+    phi_total += (int64_t)G.mp * G.kp;
+  }
+  if (items.empty()) return GRF_OK;
+  Carve dry(nullptr);
+  dry.take<__nv_bfloat16>(phi_total);
+  dry.take<__nv_bfloat16>(phi_total);
+  dry.take<int32_t>(edges.size());
+  dry.take<DstGroup>(groups.size());
+  dry.take<DstItem>(items.size());
+  void* blk = nullptr;
+  CUDA_TRY(cudaMalloc(&blk, dry.off));
+  Carve c(blk);
+  __nv_bfloat16* hi = c.take<__nv_bfloat16>(phi_total);
+  __nv_bfloat16* lo = c.take<__nv_bfloat16>(phi_total);
+  int32_t* de = c.take<int32_t>(edges.size());
+  DstGroup* dg = c.take<DstGroup>(groups.size());
+  DstItem* di = c.take<DstItem>(items.size());
+  CUDA_TRY(cudaMemcpy(de, edges.data(), edges.size() * 4, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(dg, groups.data(), groups.size() * sizeof(DstGroup), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(di, items.data(), items.size() * sizeof(DstItem), cudaMemcpyHostToDevice));
+  launch_phi_planes(dg, (int32_t)groups.size(), hi, lo, 0);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaDeviceSynchronize());
+  g->dst.blk = blk;
+  g->dst.dev = DstPlanDev{hi, lo, de, di, (int32_t)items.size(), sp};
   return GRF_OK;
 }
 
@@ -345,6 +422,7 @@ struct Opts {
   bool use_graph;
   bool spectral;   // edge interiors in the sine basis (mixed precision)
   bool spec_tc;    // ... with the transforms and contractions on the tensor cores
+  bool spec_umma;  // ... with the sine transforms as tcgen05 products per edge length
   int sweep;       // GRF_SWEEP_* of the FP32 tridiagonal edges
 };
 
@@ -364,7 +442,7 @@ int read_opts(const grf_options* o, Opts* r) {
     return fail(GRF_EINVAL, "recover_sg must be 0, 1, 2 or 4 (got %d)", sg);
   r->recover_sg = sg == 0 ? 4 : sg;
   const int lay = o ? o->pcg_layout : GRF_PCG_AUTO;
-  if (lay < GRF_PCG_AUTO || lay > GRF_PCG_STAGED_PAIRS)
+  if (lay < GRF_PCG_AUTO || lay > GRF_PCG_BATCHED)
     return fail(GRF_EINVAL, "unknown pcg_layout %d", lay);
   // AUTO: the sample-group layout where it applies (launch_pcg falls back to
   // one CTA per system otherwise)
@@ -384,16 +462,24 @@ int read_opts(const grf_options* o, Opts* r) {
   if (r->out_dtype != GRF_OUT_F64 && r->out_dtype != GRF_OUT_F32)
     return fail(GRF_EINVAL, "unknown out_dtype %d", r->out_dtype);
   const int in = o ? o->interior : GRF_INTERIOR_AUTO;
-  if (in < GRF_INTERIOR_AUTO || in > GRF_INTERIOR_SPECTRAL_TC)
+  if (in < GRF_INTERIOR_AUTO || in > GRF_INTERIOR_SPECTRAL_UMMA)
     return fail(GRF_EINVAL, "unknown interior solver %d", in);
-  if ((in == GRF_INTERIOR_SPECTRAL || in == GRF_INTERIOR_SPECTRAL_TC) && r->precision != GRF_MIXED)
+  if ((in == GRF_INTERIOR_SPECTRAL || in == GRF_INTERIOR_SPECTRAL_TC ||
+       in == GRF_INTERIOR_SPECTRAL_UMMA) && r->precision != GRF_MIXED)
     return fail(GRF_ENOTSUP, "the spectral interior solver needs precision GRF_MIXED");
   r->spectral = r->precision == GRF_MIXED && in != GRF_INTERIOR_THOMAS;
   r->spec_tc = r->spectral && in == GRF_INTERIOR_SPECTRAL_TC;
+  r->spec_umma = r->spectral && in == GRF_INTERIOR_SPECTRAL_UMMA;
   r->sweep = o ? o->sweep : GRF_SWEEP_AUTO;
   if (r->sweep < GRF_SWEEP_AUTO || r->sweep > GRF_SWEEP_NODES)
     return fail(GRF_EINVAL, "unknown sweep layout %d", r->sweep);
   return GRF_OK;
+}
+
+// The tensor-core transforms run for this call (the plan exists for its S).
+bool umma_ready(const grf_graph* g, const Opts& o, int64_t S) {
+  return o.spec_umma && g->dst.blk && g->dst.dev.sp == dst_gemm_sample_pad(S) &&
+         g->dst.dev.n_items > 0;
 }
 
 // FP32 tridiagonal edges of path p (0: every edge, 2: the edges the spectral
@@ -480,10 +566,12 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->offv = c.take<double>(Ls * 2 * E);
   w->gvec = c.take<double>(Ls * Ss * V);
   w->x = c.take<double>(Ls * Ss * V);
-  w->r = c.take<char>(Ls * Ss * V * tsize);
-  w->p = c.take<char>(Ls * Ss * V * tsize);
-  w->q = c.take<char>(Ls * Ss * V * tsize);
-  w->d = c.take<char>(Ls * Ss * V * tsize);
+  // FP32: samples padded to the batched PCG's groups of 8
+  const size_t Sv = tsize == 4 ? (size_t)pcg_batch_padded_samples(S) : Ss;
+  w->r = c.take<char>(Ls * Sv * V * tsize);
+  w->p = c.take<char>(Ls * Sv * V * tsize);
+  w->q = c.take<char>(Ls * Sv * V * tsize);
+  w->d = c.take<char>(Ls * Sv * V * tsize);
   w->lpa = LpActs{};
   w->lp_chunk = 0;
   w->y = nullptr;
@@ -516,7 +604,7 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
 // Per-call statistics, kernel-launch count and (optional) CUDA-event phase timing.
 struct RunStats {
   int64_t nodes = 0, systems = 0, iters_total = 0;
-  int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0, fallback = 0;
+  int32_t iters_max = 0, unconverged = 0, numeric = 0, launches = 0, fallback = 0, timeouts = 0;
   bool timing = false;
   uint32_t mask = 0xFFu;  // the phases timed
   // graph capture: status words are copied to pinned host slots, no syncs
@@ -584,6 +672,7 @@ void add_status(const PcgStatus& h, RunStats* rs) {
   rs->unconverged += h.n_unconverged;
   rs->numeric += h.numeric_flag;
   rs->fallback += h.n_fallback;
+  rs->timeouts += h.device_timeout;
 }
 
 int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* rs) {
@@ -611,6 +700,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                  const T* b, double* gvec, double* xv, const Opts& o, cudaStream_t st,
                  RunStats* rs) {
   const DevNodes nd = dev_nodes(w, L);
+  CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
   rs->begin(1, st);
   // the Thomas sweep constants are needed only where an edge is left to Thomas
   SweepParams<T>* prm = (SweepParams<T>*)w.prm;
@@ -639,7 +729,12 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
                                             g->d_bin_edges[p] + head, tail, gvec, st);
-    if (spec && o.spec_tc)
+    if (spec && umma_ready(g, o, S)) {
+      rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
+                                                    w.status, g->n_sm, st);
+      rs->launches += launch_spec_ends(g->d, nd, kappa2, S, g->d_spec_edges, g->spec_count,
+                                       w.bhat, gvec, st);
+    } else if (spec && o.spec_tc)
       rs->launches += launch_spec_condense_mma(g->d, nd, S, (const float*)b, g->d_spec_edges,
                                                g->spec_count, w.bhat, gvec, st);
     else if (spec)
@@ -649,7 +744,6 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
   }
   rs->end(2, st);
-  CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
   // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
   const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
   const bool learned = sizeof(T) == 4 && o.precond == GRF_PRECOND_LEARNED;
@@ -722,9 +816,15 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
     rs->launches += launch_recover_nodes<OutT>(
         g->d, hn.L(), S, (const float*)b, (const SweepParams<float>*)w.prm, (const float*)w.xw,
         g->d_bin_edges[p] + head, tail, out, st);
-  if (spec)
+  if (spec && umma_ready(g, o, S)) {
+    rs->launches += launch_spec_coef(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
+                                     g->spec_count, w.bhat, (const float*)w.xw, st);
+    rs->launches += launch_dst_gemm<true, OutT>(g->d, g->dst.dev, S, w.bhat, out, w.status,
+                                                g->n_sm, st);
+  } else if (spec) {
     rs->launches += launch_spec_recover<OutT>(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
                                               g->spec_count, w.bhat, (const float*)w.xw, out, st);
+  }
   rs->end(4, st);
   CUDA_TRY(cudaGetLastError());
   return collect(w, st, hn.L(), S, rs);
@@ -751,6 +851,8 @@ int finish(const RunStats& rs, grf_graph* g, grf_stats* stats) {
     stats->reserved = 0;
     for (int i = 0; i < 8; ++i) stats->phase_ms[i] = rs.phase_ms[i];
   }
+  if (rs.timeouts)
+    return fail(GRF_ECUDA, "%d tensor-core kernels gave up waiting for their MMAs", rs.timeouts);
   if (rs.numeric) return fail(GRF_ENUMERIC, "NaN/Inf or non-positive p.Sp in %d PCG systems", rs.numeric);
   if (rs.unconverged)
     return fail(GRF_ENOCONV, "%d PCG systems did not converge", rs.unconverged);
@@ -799,7 +901,7 @@ int enqueue_sample(grf_graph* g, const std::vector<HostNodes>& stages, double ka
   double* tmp = multi ? c.take<double>((size_t)g->n * S) : nullptr;
   void* ws_tail = g->ws ? (char*)g->ws + c.off : nullptr;
   rs->begin(0, st);
-  launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev);
+  launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev, g->d_sqrt_ml_f);
   rs->end(0, st);
   rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
@@ -827,6 +929,7 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
+  if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
   return enqueue_sample<T, OutT>(g, stages, kappa, seed, S, out, o, st, rs);
 }
 
@@ -842,10 +945,12 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
+  if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
                    gc.precond == o.precond && gc.spectral == o.spectral && gc.sweep == o.sweep &&
-                   gc.spec_tc == o.spec_tc && gc.timing == o.timing &&
+                   gc.spec_tc == o.spec_tc && gc.spec_umma == o.spec_umma &&
+                   gc.timing == o.timing &&
                    gc.phase_mask == (o.timing ? o.phase_mask : 0u) &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
                    gc.max_iter == o.max_iter && gc.rtol == o.rtol && gc.kappa == kappa &&
@@ -903,6 +1008,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.precond = o.precond;
     gc.spectral = o.spectral;
     gc.spec_tc = o.spec_tc;
+    gc.spec_umma = o.spec_umma;
     gc.timing = o.timing;
     gc.phase_mask = o.timing ? o.phase_mask : 0u;
     gc.sweep = o.sweep;
@@ -984,10 +1090,11 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->sab = c.take<double>(E);
   w->diag = c.take<double>(V);
   w->offv = c.take<double>(2 * E);
-  w->r = c.take<char>(Ss * V * tsize);
-  w->p = c.take<char>(Ss * V * tsize);
-  w->q = c.take<char>(Ss * V * tsize);
-  w->d = c.take<char>(Ss * V * tsize);
+  const size_t Sv = tsize == 4 ? (size_t)pcg_batch_padded_samples(S) : Ss;
+  w->r = c.take<char>(Sv * V * tsize);
+  w->p = c.take<char>(Sv * V * tsize);
+  w->q = c.take<char>(Sv * V * tsize);
+  w->d = c.take<char>(Sv * V * tsize);
   w->y = nullptr;
   w->pre_c = w->pre_n = nullptr;
   w->dscale = c.take<char>(V * tsize);
@@ -1362,7 +1469,7 @@ int grf_precond_train(grf_graph* g, double kappa, double beta, double k_step,
   }
   GRF_TRY(lp_node_setup(g, hn, kappa, nn, st));
   DevNodes nd{L, nn.alpha, nn.gamma, nn.weight};
-  launch_noise_minor<float>(g->d, o.seed, St, b, st);
+  launch_noise_minor<float>(g->d, o.seed, St, b, st, nullptr, g->d_sqrt_ml_f);
   launch_condense<float>(g->d, nd, kappa * kappa, St, b, gvec, st);
   lp_record_pairs(g->d, (int64_t)nsys, St, nn.diag, nn.offv, gvec, work, xrec, R, E, rinv, count,
                   per, stride, rtol, max_iter, rec_ctas, st);
@@ -1753,6 +1860,7 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   if (fp32) {
     layouts.push_back(GRF_PCG_STAGED);
     layouts.push_back(GRF_PCG_STAGED_PAIRS);
+    layouts.push_back(GRF_PCG_BATCHED);
   }
   // candidates (interior solver, recover_sg); recover_sg only matters for the
   // edges a solver leaves to the Thomas bins
@@ -1764,6 +1872,7 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
     else
       cands.push_back({GRF_INTERIOR_SPECTRAL, 4});
     cands.push_back({GRF_INTERIOR_SPECTRAL_TC, 4});
+    if (dst_gemm_sample_pad(n_samples) > 0) cands.push_back({GRF_INTERIOR_SPECTRAL_UMMA, 4});
   } else {
     cands.push_back({GRF_INTERIOR_THOMAS, 0});
   }
@@ -1773,8 +1882,20 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   double best_t = 1e300;
   grf_options best_o = b0;
   int rc = GRF_OK;
-  for (int lay : layouts) {
-    for (auto cand : cands) {
+  // two passes: the interior solvers with the default PCG layout, then the PCG
+  // layouts with the best interior solver (the two phases hardly interact)
+  std::vector<std::pair<int, std::pair<int, int>>> trials;
+  for (auto cand : cands) trials.push_back({GRF_PCG_STAGED, cand});
+  const size_t n_first = trials.size();
+  for (size_t ti = 0;; ++ti) {
+    if (ti == n_first)
+      for (int lay : layouts)
+        if (lay != GRF_PCG_STAGED)
+          trials.push_back({lay, {best_o.interior, best_o.recover_sg}});
+    if (ti >= trials.size()) break;
+    {
+      const int lay = trials[ti].first;
+      const auto cand = trials[ti].second;
       grf_options c = b0;
       c.pcg_layout = lay;
       c.interior = cand.first;
@@ -1878,6 +1999,7 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
   GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts, o)));
+  if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, n_rhs));
   cudaStream_t st = (cudaStream_t)stream;
   RunStats rs;
   rs.timing = o.timing;

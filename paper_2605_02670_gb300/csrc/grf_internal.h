@@ -54,15 +54,18 @@ struct PcgStatus {
   int32_t numeric_flag;
   int32_t iters_max;
   int32_t n_fallback;  // systems whose learned preconditioner fell back to Jacobi
+  int32_t device_timeout;  // tensor-core kernels whose bounded waits ran out
+  int32_t pad;
   unsigned long long iters_total;
 };
 
 // ---- noise.cu
 // b[j][s] (sample-minor, T = float or double) = sqrt(M_L,j) xi_{s,j};
-// the seed is read from seed_dev when it is not null (graph replays).
+// the seed is read from seed_dev when it is not null (graph replays); the FP32
+// form scales by sqrt_ml_f (an FP32 copy of g.sqrt_ml) when it is given.
 template <typename T>
 void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st,
-                        const uint64_t* seed_dev = nullptr);
+                        const uint64_t* seed_dev = nullptr, const float* sqrt_ml_f = nullptr);
 // sample-major output: raw words (uint32) or b in double
 void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
                         cudaStream_t st);
@@ -149,6 +152,17 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 // only, float es = pc and N = pn per node: z = B B^T r, B = diag(es) + N);
 // y: one more [L][S][nv] scratch for the learned form.
 constexpr int kPreJacobi = 0, kPreNeumann = 1, kPreLearned = 2;
+
+// ---- pcg_batch.cu
+// Mixed-precision Jacobi-PCG with one CTA per (node, 8 samples) and the
+// group's FP32 vectors as [nv][8] rows in global memory (graphs whose vectors
+// do not fit on chip). R, PA, PB, Dv: [L][ceil(S / 8)][nv][8] floats each.
+int64_t pcg_batch_padded_samples(int64_t S);
+void launch_pcg_batch(const DevGraph& g, int32_t L, int64_t S, const double* diag,
+                      const double* offv, const float* dscale, const float* offv_t,
+                      const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
+                      double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
+                      cudaStream_t st);
 template <typename VT>
 void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
@@ -229,6 +243,52 @@ template <typename OutT>
 int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                         const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
                         const float* xw, OutT* out, cudaStream_t st);
+// The two halves around tensor-core transforms (dst_gemm.cu): end values of
+// every node from bhat (already transformed) added into gvec; the sine-basis
+// coefficients c of the recovery written over bhat (the inverse transform of
+// c is then the interior field).
+int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
+                     double* gvec, cudaStream_t st);
+int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
+                     const float* xw, cudaStream_t st);
+
+// ---- dst_gemm.cu: sine transforms of edges grouped by interior-node count m,
+// as BF16-split products on the tcgen05 tensor cores.
+// A group: edges with m interior nodes; Phi_m's hi and lo planes start at
+// phi_off ([mp][kp], mp, kp rounded up to the tile rows and K).
+struct DstGroup {
+  int64_t phi_off;
+  int32_t m, mp, kp, pad;
+};
+// A work item: rows [128 mt, 128 mt + 128) of Phi_m times ne <= 256 / sp edges
+// (edges[e0 .. e0 + ne)).
+struct DstItem {
+  int64_t phi_off;
+  int32_t m, kp, e0, ne, mt, pad;
+};
+struct DstPlanDev {
+  const __nv_bfloat16* phi_hi = nullptr;
+  const __nv_bfloat16* phi_lo = nullptr;
+  const int32_t* edges = nullptr;
+  const DstItem* items = nullptr;
+  int32_t n_items = 0;
+  int32_t sp = 0;
+};
+// Samples padded to a power of two >= 8 (0 if S > 256: no tensor-core path).
+int32_t dst_gemm_sample_pad(int64_t S);
+int32_t dst_gemm_tile_rows();
+int32_t dst_gemm_tile_k();
+int32_t dst_gemm_tile_cols();
+void launch_phi_planes(const DstGroup* groups, int32_t n_groups, __nv_bfloat16* hi,
+                       __nv_bfloat16* lo, cudaStream_t st);
+// kInv = false: dst = bhat [n_interior][S] from src = b [n][S] (noise rows);
+// kInv = true: dst = out [S][n] (interior DOFs) from src = c [n_interior][S].
+// A timed-out wait adds to status->device_timeout.
+template <bool kInv, typename OutT>
+int launch_dst_gemm(const DevGraph& g, const DstPlanDev& p, int64_t S, const float* src,
+                    OutT* dst, PcgStatus* status, int n_sm, cudaStream_t st);
 
 // ---- recover.cu
 // Edge bins of the register-resident recovery: bin i takes edges with

@@ -61,9 +61,12 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& n0, 
 // group: a CTA covers SB = min(S, 1024) samples (blockIdx.y picks the sample
 // chunk) and blockDim / SB rows, so a warp writes whole rows b[j][s0..s0+31]
 // and no thread divides per block.
+// sml_f: the FP32 mass factors for T = float (one FP64 -> FP32 conversion per
+// element would run on GB300's narrow FP64 pipe and bound the kernel).
 template <typename T>
 __global__ void noise_minor_kernel(DevGraph g, uint64_t seed, const uint64_t* seed_dev, int64_t S,
-                                   int32_t SB, T* __restrict__ b) {
+                                   int32_t SB, T* __restrict__ b,
+                                   const float* __restrict__ sml_f) {
   if (seed_dev) seed = *seed_dev;
   const int64_t nq = (g.n + 3) / 4;
   const int32_t rows = blockDim.x / SB;  // Philox blocks per CTA pass
@@ -78,7 +81,12 @@ __global__ void noise_minor_kernel(DevGraph g, uint64_t seed, const uint64_t* se
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int64_t j = 4 * q + k;
-      if (j < g.n) b[j * S + s] = (T)g.sqrt_ml[j] * n[k];
+      if (j < g.n) {
+        if (sizeof(T) == 4 && sml_f)
+          b[j * S + s] = (T)(sml_f[j] * (float)n[k]);
+        else
+          b[j * S + s] = (T)g.sqrt_ml[j] * n[k];
+      }
     }
   }
 }
@@ -119,7 +127,7 @@ int grid_for(int64_t total, int threads) {
 
 template <typename T>
 void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaStream_t st,
-                        const uint64_t* seed_dev) {
+                        const uint64_t* seed_dev, const float* sqrt_ml_f) {
   // SB samples per CTA, blockDim a multiple of SB (at least 256 threads when S allows)
   const int32_t SB = (int32_t)(S < 1024 ? S : 1024);
   const int32_t rows = SB >= 256 ? 1 : (256 + SB - 1) / SB;
@@ -131,13 +139,13 @@ void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaS
   if (cap < 1) cap = 1;
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
-  noise_minor_kernel<T><<<dim3((unsigned)bx, (unsigned)by), threads, 0, st>>>(g, seed, seed_dev,
-                                                                             S, SB, b);
+  noise_minor_kernel<T><<<dim3((unsigned)bx, (unsigned)by), threads, 0, st>>>(
+      g, seed, seed_dev, S, SB, b, sqrt_ml_f);
 }
 template void launch_noise_minor<float>(const DevGraph&, uint64_t, int64_t, float*, cudaStream_t,
-                                        const uint64_t*);
+                                        const uint64_t*, const float*);
 template void launch_noise_minor<double>(const DevGraph&, uint64_t, int64_t, double*,
-                                         cudaStream_t, const uint64_t*);
+                                         cudaStream_t, const uint64_t*, const float*);
 
 void launch_noise_major(const DevGraph& g, uint64_t seed, int64_t S, void* out, bool raw,
                         cudaStream_t st) {

@@ -1472,6 +1472,11 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
                 cudaStream_t st) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
+    if (layout == 4 && pre == kPreJacobi) {
+      launch_pcg_batch(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
+                       max_iter, iters, status, st);
+      return;
+    }
     if ((layout == 2 || layout == 3) && pre == kPreJacobi && group_fits(g)) {
 #define GRF_GROUP(NT, VPT, SGP)                                                               \
   launch_group<NT, VPT, SGP>(g, ord, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol,      \
@@ -1507,6 +1512,15 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
       }
 #undef GRF_GROUP_PRE_ALL
 #undef GRF_GROUP_PRE
+      return;
+    }
+  }
+  if constexpr (sizeof(VT) == 4) {
+    // larger graphs: samples batched in rows of 8 (the vectors are carved with
+    // the sample count padded to a multiple of 8)
+    if (layout != 1 && pre == kPreJacobi) {
+      launch_pcg_batch(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
+                       max_iter, iters, status, st);
       return;
     }
   }

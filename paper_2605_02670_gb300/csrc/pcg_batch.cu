@@ -1,0 +1,491 @@
+// Jacobi-PCG on the vertex Schur systems S^(l) u = g (Eq. global_schur; Sec. 3,
+// Phase 4) for graphs whose vectors do not fit on chip: one CTA per (node l,
+// group of 8 samples), the group's vectors stored as rows of 8 samples per
+// vertex ([V][8], one 32-byte sector), so that every load of the node's matrix
+// (incidence list, scaled block) serves the 8 samples and every vector access
+// is a whole sector.
+//
+// Mixed precision, as in the other layouts: FP32 CG on the Jacobi-scaled system
+// (D^-1/2 S D^-1/2) e = D^-1/2 r inside FP64 iterative refinement; the
+// refinement residual r = g - S x uses the FP64 blocks and the FP64 iterate.
+// The dot products are accumulated in FP64 (FP32 partial sums over at most 16
+// vertices per thread, then FP64 across the vector and the CTA) and the CG
+// scalars alpha, beta are FP64; the vector updates are FP32.
+//
+// A thread owns 4 of the group's samples (one 16-byte half row) of two
+// vertices per step, so every dependent load chain (incidence list, then the
+// neighbour's row) moves 16 bytes and each thread keeps two chains in flight.
+// The per-sample CG state lives in shared memory; after each CTA reduction one
+// thread per sample takes its decisions in FP64.
+//
+// One inner iteration is two passes over the vertices with one CTA reduction
+// each, and moves 8 vector rows per vertex (instead of 10-11 for the textbook
+// ordering):
+//   pass A: p' = r + beta p (double-buffered: the neighbours' p' are formed
+//           from their r and p, nothing is read that this pass writes),
+//           q = S p' for the own vertex, partial p'.q;
+//   pass B: q = S p' again (gathers of p', which stay in L1/L2), d += alpha p',
+//           r -= alpha q, partial r.r.
+// Every loop is bounded by max_iter; no CTA waits on another.
+#include "grf_internal.h"
+
+namespace grf {
+namespace {
+
+constexpr int kBT = 256;          // threads per CTA
+constexpr int kSG = 8;            // samples per group: one 32-byte row per vertex
+constexpr int kVP = kBT / 2;      // vertices per half-step (two threads per vertex row)
+constexpr int kU = 2;             // vertices per thread per step
+constexpr int kWarps = kBT / 32;
+constexpr int kChunk = 16;        // FP32 partial sums over this many vertices
+constexpr double kInnerRtol = 1e-5;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Per-sample state of the group (one entry per sample, written by thread j).
+struct SampleState {
+  double rz, rz0, best, stop2, inner_e, rho, inv_g;
+  int32_t it, since;
+  int32_t done, bad, cg, has_d, first;
+  float af, bf, ig;  // FP32 alpha, beta, 1 / rho for the vector passes
+};
+
+struct BatchShared {
+  double red[kWarps][kSG][2];
+  SampleState st[kSG];
+};
+
+// FP32 partial sums of 4 samples x N values, flushed into FP64 every kChunk
+// vertices.
+template <int N>
+struct Acc4 {
+  double d[4][N];
+  float f[4][N];
+  int c;
+  __device__ __forceinline__ void init() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < N; ++k) d[i][k] = 0.0, f[i][k] = 0.f;
+    c = 0;
+  }
+  __device__ __forceinline__ void tick() {
+    if (++c == kChunk) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < N; ++k) d[i][k] += (double)f[i][k], f[i][k] = 0.f;
+      c = 0;
+    }
+  }
+  __device__ __forceinline__ void finish() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < N; ++k) d[i][k] += (double)f[i][k], f[i][k] = 0.f;
+  }
+};
+
+// Per-sample CTA sums: lanes of equal parity share a half row (4 samples).
+// After the call thread j < 8 holds the sums of sample j in out[k].
+template <int N>
+__device__ __forceinline__ void group_sum(Acc4<N>& a, BatchShared& sh, double (&out)[N]) {
+  a.finish();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double v = a.d[i][k];
+#pragma unroll
+      for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
+      a.d[i][k] = v;
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < 2) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int k = 0; k < N; ++k) sh.red[warp][4 * lane + i][k] = a.d[i][k];
+  }
+  __syncthreads();
+  if (threadIdx.x < kSG) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double v = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) v += sh.red[w][threadIdx.x][k];
+      out[k] = v;
+    }
+  }
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 fma4(float4 a, float4 x, float4 y) {  // a * x + y per lane
+  return make_float4(fmaf(a.x, x.x, y.x), fmaf(a.y, x.y, y.y), fmaf(a.z, x.z, y.z),
+                     fmaf(a.w, x.w, y.w));
+}
+__device__ __forceinline__ float4 fma1(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 sel4(const bool (&c)[4], float4 a, float4 b) {
+  return make_float4(c[0] ? a.x : b.x, c[1] ? a.y : b.y, c[2] ? a.z : b.z, c[3] ? a.w : b.w);
+}
+__device__ __forceinline__ float get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+}  // namespace
+
+// gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out; xout also
+// holds the FP64 iterate). R, PA, PB, Dv: [L][ceil(S / 8)][nv][8] FP32 scratch.
+__global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
+    DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
+    const double* __restrict__ offv, const float* __restrict__ dscale,
+    const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
+    float* __restrict__ R, float* __restrict__ PA, float* __restrict__ PB,
+    float* __restrict__ Dv, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
+    PcgStatus* __restrict__ status) {
+  __shared__ BatchShared sh;
+  const int32_t nv = g.nv;
+  const int64_t ne2 = 2 * (int64_t)g.ne;
+  const int64_t nsg = (S + kSG - 1) / kSG;
+  const int64_t n_items = (int64_t)L * nsg;
+  const int hh = threadIdx.x & 1;            // half row: samples 4 hh .. 4 hh + 3
+  const int32_t vs = threadIdx.x >> 1;       // vertex lane
+  const int32_t* __restrict__ vptr = g.vptr;
+  const int32_t* __restrict__ nbr = g.adj_nbr;
+  const double rtol2 = rtol * rtol;
+  for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int64_t l = L - 1 - item / nsg;  // largest shifts first (longest solves)
+    const int64_t s0 = (item % nsg) * kSG;
+    const double* __restrict__ D = diag + l * nv;
+    const double* __restrict__ O = offv + l * ne2;
+    const float* __restrict__ Ds = dscale + l * nv;
+    const float* __restrict__ Ot = offv_t + l * ne2;
+    const int64_t base = (l * nsg + (item % nsg)) * (int64_t)nv * kSG + 4 * hh;
+    float* __restrict__ r = R + base;
+    float* __restrict__ pa = PA + base;
+    float* __restrict__ pb = PB + base;
+    float* __restrict__ dv = Dv + base;
+    // this thread's 4 samples: FP64 rows of g and x
+    const double* gs[4];
+    double* xs[4];
+    bool live[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t s = s0 + 4 * hh + i;
+      live[i] = s < S;
+      const int64_t sys = l * S + (live[i] ? s : 0);
+      gs[i] = gvec + sys * nv;
+      xs[i] = xout + sys * nv;
+    }
+
+    // ---- ||g||^2, ||D^-1/2 g||^2 (FP64); x = 0
+    {
+      Acc4<2> a;
+      a.init();
+      for (int32_t v = vs; v < nv; v += kVP) {
+        const double dsv = (double)Ds[v];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const double gv = live[i] ? gs[i][v] : 0.0;
+          const double sv = gv * dsv;
+          a.d[i][0] = fma(gv, gv, a.d[i][0]);
+          a.d[i][1] = fma(sv, sv, a.d[i][1]);
+          if (live[i]) xs[i][v] = 0.0;
+        }
+      }
+      double out[2] = {0.0, 0.0};
+      group_sum<2>(a, sh, out);
+      if (threadIdx.x < kSG) {
+        SampleState& q = sh.st[threadIdx.x];
+        const bool lv = s0 + threadIdx.x < S;
+        q.bad = lv && (!isfinite(out[0]) || !isfinite(out[1]));
+        q.done = !lv || q.bad || !(out[0] > 0.0) || !(out[1] > 0.0);
+        q.inv_g = q.done ? 0.0 : 1.0 / sqrt(out[0]);
+        // the inner FP32 solve runs on r = D^-1/2 r64 / rho, O(1) whatever the
+        // node's scale: rho = ||D^-1/2 g|| first, then the estimate of the
+        // refinement residual's norm from the previous inner solve
+        q.rho = q.done ? 1.0 : sqrt(out[1]);
+        q.rz0 = q.done ? 0.0 : out[1] / (q.rho * q.rho);
+        q.inner_e = kInnerRtol;
+        q.it = 0;
+        q.ig = (float)(1.0 / q.rho);
+        q.cg = 0;
+      }
+      __syncthreads();
+      bool dn[4];
+      float ig[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dn[i] = sh.st[4 * hh + i].done, ig[i] = sh.st[4 * hh + i].ig;
+      for (int32_t v = vs; v < nv; v += kVP) {
+        const float dsv = Ds[v];
+        float rv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) rv[i] = dn[i] ? 0.f : ((float)gs[i][v] * ig[i]) * dsv;
+        st4(r + (int64_t)v * kSG, make_float4(rv[0], rv[1], rv[2], rv[3]));
+      }
+      __syncthreads();
+    }
+
+    for (int32_t round = 0; round <= max_iter; ++round) {
+      if (round > 0) {
+        // ---- FP64 refinement residual r64 = g - S x; stored r = D^-1/2 r64 / rho
+        bool dn[4];
+        double ir[4], ivg[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const SampleState& q = sh.st[4 * hh + i];
+          dn[i] = q.done;
+          ir[i] = 1.0 / q.rho;
+          ivg[i] = q.inv_g;
+        }
+        Acc4<2> a;
+        a.init();
+        for (int32_t v = vs; v < nv; v += kVP) {
+          const int32_t k0 = vptr[v], k1 = vptr[v + 1];
+          const double dd = D[v];
+          const float dsv = Ds[v];
+          float sv4[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            sv4[i] = 0.f;
+            if (dn[i]) continue;
+            double y = dd * xs[i][v];
+            for (int32_t k = k0; k < k1; ++k) y = fma(O[k], xs[i][nbr[k]], y);
+            const double rv = gs[i][v] - y;
+            const float rel = (float)(rv * ivg[i]);
+            sv4[i] = (float)(rv * ir[i]) * dsv;
+            a.f[i][0] = fmaf(rel, rel, a.f[i][0]);
+            a.f[i][1] = fmaf(sv4[i], sv4[i], a.f[i][1]);
+          }
+          a.tick();
+          st4(r + (int64_t)v * kSG, make_float4(sv4[0], sv4[1], sv4[2], sv4[3]));
+        }
+        double out[2] = {0.0, 0.0};
+        group_sum<2>(a, sh, out);
+        if (threadIdx.x < kSG) {
+          SampleState& q = sh.st[threadIdx.x];
+          if (!q.done) {
+            if (!isfinite(out[0]) || !isfinite(out[1])) {
+              q.bad = q.done = 1;
+            } else if (out[0] <= rtol2) {
+              q.done = 1;
+            } else {
+              q.rz0 = out[1];
+              q.inner_e = fmax(kInnerRtol, 0.1 * sqrt(rtol2 / out[0]));
+            }
+          }
+        }
+      }
+      // start an inner CG on the scaled system from d = 0, p = r
+      int cgj = 0;
+      if (threadIdx.x < kSG) {
+        SampleState& q = sh.st[threadIdx.x];
+        q.cg = !q.done && q.it < max_iter && q.rz0 > 0.0;
+        q.rz = q.rz0;
+        q.best = q.rz0;
+        q.stop2 = q.inner_e * q.inner_e * q.rz0;
+        q.since = 0;
+        q.has_d = 0;
+        q.first = 1;
+        q.bf = 0.f;
+        cgj = q.cg;
+      }
+      if (!__syncthreads_or(cgj)) break;
+      for (int32_t inner = 0; inner < max_iter; ++inner) {
+        bool cg[4], fs[4], any = false;
+        float bf[4];
+        const bool fst = sh.st[4 * hh].first;  // the group's samples start together
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const SampleState& q = sh.st[4 * hh + i];
+          cg[i] = q.cg;
+          fs[i] = q.first || !q.cg;
+          bf[i] = q.bf;
+          any |= cg[i];
+        }
+        const float* pold = (inner & 1) ? pb : pa;
+        float* pnew = (inner & 1) ? pa : pb;
+        // ---- pass A: p' = r + beta p (p' = r at the start), q = S p', p'.q
+        {
+          Acc4<1> a;
+          a.init();
+          if (any) {
+            for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
+#pragma unroll
+              for (int u = 0; u < kU; ++u) {
+                const int32_t v = v0 + u * kVP;
+                if (v >= nv) break;
+                const int32_t k0 = vptr[v], k1 = vptr[v + 1];
+                const float4 rv = ld4(r + (int64_t)v * kSG);
+                float4 pv = rv;
+                if (!fst) pv = sel4(fs, rv, fma4(make_float4(bf[0], bf[1], bf[2], bf[3]),
+                                                 ld4(pold + (int64_t)v * kSG), rv));
+                float4 q = pv;
+                for (int32_t k = k0; k < k1; ++k) {
+                  const int64_t w = (int64_t)nbr[k] * kSG;
+                  const float o = Ot[k];
+                  const float4 rw = ld4(r + w);
+                  float4 pw = rw;
+                  if (!fst) pw = sel4(fs, rw, fma4(make_float4(bf[0], bf[1], bf[2], bf[3]),
+                                                   ld4(pold + w), rw));
+                  q = fma1(o, pw, q);
+                }
+                st4(pnew + (int64_t)v * kSG, pv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a.f[i][0] = fmaf(get(pv, i), get(q, i), a.f[i][0]);
+              }
+              a.tick();
+            }
+          }
+          double out[1] = {0.0};
+          group_sum<1>(a, sh, out);
+          if (threadIdx.x < kSG) {
+            SampleState& q = sh.st[threadIdx.x];
+            q.af = 0.f;
+            if (q.cg) {
+              const double pq = out[0];
+              if (!isfinite(pq)) {
+                q.bad = q.done = 1;
+                q.cg = 0;
+              } else if (!(pq > 0.0)) {
+                q.cg = 0;  // p vanished: the FP32 recurrence is at its floor
+              } else {
+                q.af = (float)(q.rz / pq);
+              }
+            }
+          }
+          __syncthreads();
+        }
+        // ---- pass B: q = S p' again, d += alpha p', r -= alpha q, r.r
+        {
+          bool hd[4];
+          float af[4];
+          any = false;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const SampleState& q = sh.st[4 * hh + i];
+            cg[i] = q.cg;
+            hd[i] = q.has_d;
+            af[i] = cg[i] ? q.af : 0.f;
+            any |= cg[i];
+          }
+          const float4 af4 = make_float4(af[0], af[1], af[2], af[3]);
+          const float4 naf4 = make_float4(-af[0], -af[1], -af[2], -af[3]);
+          Acc4<1> a;
+          a.init();
+          if (any) {
+            for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
+#pragma unroll
+              for (int u = 0; u < kU; ++u) {
+                const int32_t v = v0 + u * kVP;
+                if (v >= nv) break;
+                const int32_t k0 = vptr[v], k1 = vptr[v + 1];
+                const int64_t iv = (int64_t)v * kSG;
+                const float4 pv = ld4(pnew + iv);
+                float4 q = pv;
+                for (int32_t k = k0; k < k1; ++k)
+                  q = fma1(Ot[k], ld4(pnew + (int64_t)nbr[k] * kSG), q);
+                const float4 d0 = ld4(dv + iv);
+                const float4 r0 = ld4(r + iv);
+                const float4 dn = fma4(af4, pv, make_float4(hd[0] ? d0.x : 0.f, hd[1] ? d0.y : 0.f,
+                                                            hd[2] ? d0.z : 0.f, hd[3] ? d0.w : 0.f));
+                const float4 rn = fma4(naf4, q, r0);
+                st4(dv + iv, sel4(cg, dn, d0));
+                st4(r + iv, rn);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a.f[i][0] = fmaf(get(rn, i), get(rn, i), a.f[i][0]);
+              }
+              a.tick();
+            }
+          }
+          double out[1] = {0.0};
+          group_sum<1>(a, sh, out);
+          int cgj2 = 0;
+          if (threadIdx.x < kSG) {
+            SampleState& q = sh.st[threadIdx.x];
+            q.first = 0;
+            if (q.cg) {
+              q.has_d = 1;
+              ++q.it;
+              const double rr = out[0];
+              if (!isfinite(rr)) {
+                q.bad = q.done = 1;
+                q.cg = 0;
+              } else {
+                const double rz_prev = q.rz;
+                q.rz = rr;
+                if (rr <= q.stop2) {
+                  q.cg = 0;
+                } else {
+                  if (rr < 0.98 * q.best) {
+                    q.best = rr;
+                    q.since = 0;
+                  } else if (++q.since >= 32) {
+                    q.cg = 0;  // the FP32 recurrence has reached its rounding floor
+                  }
+                  q.bf = (float)(rr / rz_prev);
+                  if (q.it >= max_iter) q.cg = 0;
+                }
+              }
+            }
+            cgj2 = q.cg;
+          }
+          if (!__syncthreads_or(cgj2)) break;
+        }
+      }
+      // ---- x += rho D^-1/2 d for the samples that ran a correction this round
+      {
+        bool up[4];
+        double rh[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const SampleState& q = sh.st[4 * hh + i];
+          up[i] = q.has_d && !q.bad;
+          rh[i] = q.rho;
+        }
+        for (int32_t v = vs; v < nv; v += kVP) {
+          const float4 d4 = ld4(dv + (int64_t)v * kSG);
+          const double dsv = (double)Ds[v];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (up[i]) xs[i][v] = fma(rh[i] * dsv, (double)get(d4, i), xs[i][v]);
+        }
+      }
+      __syncthreads();  // x complete, every thread done with the state
+      if (threadIdx.x < kSG) {
+        SampleState& q = sh.st[threadIdx.x];
+        if (q.has_d && !q.bad) q.rho *= sqrt(fmax(q.rz, 1e-24 * q.rz0));
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < kSG && s0 + threadIdx.x < S) {
+      const SampleState& q = sh.st[threadIdx.x];
+      const int64_t sys = l * S + s0 + threadIdx.x;
+      iters[sys] = q.it;
+      atomicAdd(&status->iters_total, (unsigned long long)q.it);
+      atomicMax(&status->iters_max, q.it);
+      if (q.bad) atomicAdd(&status->numeric_flag, 1);
+      else if (!q.done) atomicAdd(&status->n_unconverged, 1);
+    }
+    __syncthreads();
+  }
+}
+
+// Vectors of the batched layout need [L][ceil(S / 8) * 8][nv] floats each.
+int64_t pcg_batch_padded_samples(int64_t S) { return (S + kSG - 1) / kSG * kSG; }
+
+void launch_pcg_batch(const DevGraph& g, int32_t L, int64_t S, const double* diag,
+                      const double* offv, const float* dscale, const float* offv_t,
+                      const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
+                      double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
+                      cudaStream_t st) {
+  const int64_t items = (int64_t)L * ((S + kSG - 1) / kSG);
+  if (items <= 0) return;
+  const int blocks = (int)(items < (int64_t)1 << 30 ? items : (int64_t)1 << 30);
+  pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, L, S, diag, offv, dscale, offv_t, gvec, x, R, PA,
+                                           PB, Dv, rtol, max_iter, iters, status);
+}
+
+}  // namespace grf

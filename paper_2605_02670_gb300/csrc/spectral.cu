@@ -169,7 +169,9 @@ __host__ __device__ constexpr size_t spec_condense_floats(int32_t mmax) {
 
 // Forward transform of the edge's noise (written to bhat, rows like b) and
 // the two end values of T_l^-1 b_I for every node, added into gvec.
-template <int SG, int QJ>
+// kFromBhat: bhat already holds the forward transform (tensor-core path);
+// only the end values are formed.
+template <int SG, int QJ, bool kFromBhat = false>
 __global__ void __launch_bounds__(256)
     spec_condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                          const float* __restrict__ b, const int32_t* __restrict__ edges,
@@ -191,12 +193,19 @@ __global__ void __launch_bounds__(256)
     const int kv = (int)(S - s0 < SG ? S - s0 : SG);
     __syncthreads();  // the previous unit is done with the shared arrays
     spec_tables(m, tab, ctab, sig);
-    stage_rows<SG>(b + (g.nv + off) * S + s0, S, kv, m, bs);
-    __syncthreads();
     const float scale = sqrtf(2.f / (float)(m + 1));
+    if (kFromBhat) {
+      stage_rows<SG>(bhat + off * S + s0, S, kv, m, bt);
+      __syncthreads();
+      for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x)
+        bt[t] *= scale * tab[t / SG + 1];
+    } else {
+      stage_rows<SG>(b + (g.nv + off) * S + s0, S, kv, m, bs);
+    }
+    __syncthreads();
     // forward transform: modes t + q blockDim (q < QJ) per thread share every
     // row load; the bin's QJ blockDim >= m, so one pass covers the edge
-    for (int32_t jb = 0; jb < m; jb += QJ * blockDim.x) {
+    for (int32_t jb = 0; jb < (kFromBhat ? 0 : m); jb += QJ * blockDim.x) {
       int32_t jj[QJ];
 #pragma unroll
       for (int q = 0; q < QJ; ++q) {
@@ -263,12 +272,14 @@ __host__ __device__ constexpr size_t spec_recover_floats(int32_t mmax) {
 }
 
 // U_I = Phi c with c from bhat and the weighted vertex values xw[l][v][s] = w_l u_v^(l).
-template <int SG, int QJ, typename OutT>
+// kCoef: write c over the edge's bhat rows (cout) instead of transforming it
+// back (the tensor-core path transforms all edges of a length at once).
+template <int SG, int QJ, typename OutT, bool kCoef = false>
 __global__ void __launch_bounds__(256)
     spec_recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                         const int32_t* __restrict__ edges, int32_t n_edges, int32_t mmax,
-                        const float* __restrict__ bhat, const float* __restrict__ xw,
-                        OutT* __restrict__ out) {
+                        const float* bhat, const float* __restrict__ xw,
+                        OutT* __restrict__ out, float* cout) {
   extern __shared__ __align__(16) float spec_sm[];
   float* cs = spec_sm;                            // [mmax][SG] bh, then c
   float* xp = cs + (size_t)mmax * SG;             // [chunk][SG] xa + xb
@@ -351,6 +362,13 @@ __global__ void __launch_bounds__(256)
       }
     }
     __syncthreads();
+    if (kCoef) {
+      for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
+        const int32_t j = t / SG, sc = t - j * SG;
+        if (sc < kv) cout[(off + j) * S + s0 + sc] = cs[t];
+      }
+      continue;
+    }
     // inverse transform: output nodes t + q blockDim (q < QJ) per thread
     for (int32_t ib = 0; ib < m; ib += QJ * blockDim.x) {
       int32_t ii[QJ];
@@ -411,32 +429,34 @@ int spec_bins(int32_t* mmax) {
   return kNumSpecBins;
 }
 
-template <int QJ>
+template <int QJ, bool kFromBhat>
 void spec_condense_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                        const float* b, const int32_t* e, int32_t n, const SpecBin& bin,
                        float* bhat, double* gvec, cudaStream_t st) {
   const size_t smem = spec_condense_floats<kSpecSG>(bin.mmax) * sizeof(float);
-  cudaFuncSetAttribute(spec_condense_kernel<kSpecSG, QJ>,
+  cudaFuncSetAttribute(spec_condense_kernel<kSpecSG, QJ, kFromBhat>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  spec_condense_kernel<kSpecSG, QJ><<<grid_units(units), bin.threads, smem, st>>>(
+  spec_condense_kernel<kSpecSG, QJ, kFromBhat><<<grid_units(units), bin.threads, smem, st>>>(
       g, nd, kappa2, S, b, e, n, bin.mmax, bhat, gvec);
 }
 
-int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                         const float* b, const int32_t* bin_edges, const int32_t* bin_count,
-                         float* bhat, double* gvec, cudaStream_t st) {
+template <bool kFromBhat>
+int spec_condense_all(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                      const float* b, const int32_t* bin_edges, const int32_t* bin_count,
+                      float* bhat, double* gvec, cudaStream_t st) {
   const int32_t* e = bin_edges;
   int launches = 0;
   for (int i = 0; i < kNumSpecBins; ++i) {
     const int32_t n = bin_count[i];
     if (n > 0) {
       const SpecBin& bn = kSpecBins[i];
-      switch (bn.qj) {
-        case 1: spec_condense_bin<1>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        case 2: spec_condense_bin<2>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        case 3: spec_condense_bin<3>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        default: spec_condense_bin<4>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+      // (transform-free: QJ only sizes the unused transform loop)
+      switch (kFromBhat ? 1 : bn.qj) {
+        case 1: spec_condense_bin<1, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 2: spec_condense_bin<2, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 3: spec_condense_bin<3, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        default: spec_condense_bin<4, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
       }
       ++launches;
     }
@@ -445,16 +465,52 @@ int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, i
   return launches;
 }
 
-template <int QJ, typename OutT>
+int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                         const float* b, const int32_t* bin_edges, const int32_t* bin_count,
+                         float* bhat, double* gvec, cudaStream_t st) {
+  return spec_condense_all<false>(g, nd, kappa2, S, b, bin_edges, bin_count, bhat, gvec, st);
+}
+
+int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
+                     double* gvec, cudaStream_t st) {
+  return spec_condense_all<true>(g, nd, kappa2, S, nullptr, bin_edges, bin_count,
+                                 const_cast<float*>(bhat), gvec, st);
+}
+
+template <int QJ, typename OutT, bool kCoef = false>
 void spec_recover_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                       const int32_t* e, int32_t n, const SpecBin& bin, const float* bhat,
-                      const float* xw, OutT* out, cudaStream_t st) {
+                      const float* xw, OutT* out, cudaStream_t st, float* cout = nullptr) {
   const size_t smem = spec_recover_floats<kSpecSG>(bin.mmax) * sizeof(float);
-  cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, QJ, OutT>,
+  cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, QJ, OutT, kCoef>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  spec_recover_kernel<kSpecSG, QJ, OutT><<<grid_units(units), bin.threads, smem, st>>>(
-      g, nd, kappa2, S, e, n, bin.mmax, bhat, xw, out);
+  spec_recover_kernel<kSpecSG, QJ, OutT, kCoef><<<grid_units(units), bin.threads, smem, st>>>(
+      g, nd, kappa2, S, e, n, bin.mmax, bhat, xw, out, cout);
+}
+
+int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
+                     const float* xw, cudaStream_t st) {
+  const int32_t* e = bin_edges;
+  int launches = 0;
+  for (int i = 0; i < kNumSpecBins; ++i) {
+    const int32_t n = bin_count[i];
+    if (n > 0) {
+      const SpecBin& bn = kSpecBins[i];
+      float* no = nullptr;
+      switch (bn.qj) {
+        case 1: spec_recover_bin<1, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
+        case 2: spec_recover_bin<2, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
+        case 3: spec_recover_bin<3, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
+        default: spec_recover_bin<4, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
+      }
+      ++launches;
+    }
+    e += n;
+  }
+  return launches;
 }
 
 template <typename OutT>

@@ -190,7 +190,7 @@ def test_interior_and_sweep_options_checked_before_device_work():
     with pytest.raises(grf.GrfError) as ei:
         grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad_interior, stream=0)
     assert ei.value.code == grf.GRF_EINVAL
-    for interior in ("spectral", "spectral_tc"):  # sine-basis interiors are FP32 only
+    for interior in ("spectral", "spectral_tc", "spectral_umma"):  # FP32 only
         with pytest.raises(grf.GrfError) as ei:
             grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0,
                            grf.make_options("fp64", interior=interior), stream=0)

@@ -82,7 +82,7 @@ def test_lattice_edges_quadrature_k025(kappa, beta):
     assert rel_l2(u.cpu().numpy(), ref, ml) < TOL["mixed"]
 
 
-@pytest.mark.parametrize("interior", ["thomas", "spectral", "spectral_tc"])
+@pytest.mark.parametrize("interior", ["thomas", "spectral", "spectral_tc", "spectral_umma"])
 @pytest.mark.parametrize("kappa,beta", [(2.0, 0.75), (20.0, 0.25)])
 def test_lattice_edges_every_interior_solver(interior, kappa, beta):
     g = small_lattice()
@@ -109,20 +109,23 @@ def test_lattice_edges_fp64(kappa, beta):
 # ------------------------------------------- more than 4096 vertices: per-system PCG
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision,layout", [("mixed", "auto"), ("mixed", "per_system"),
+                                              ("fp64", "auto")])
 @pytest.mark.parametrize("kappa,beta", [(2.0, 0.75), (20.0, 0.25)])
-def test_large_lattice_global_vector_pcg_k025(precision, kappa, beta):
-    """68 x 68 grid with 15 % of the edges deleted (> 4096 kept vertices, so
-    the PCG runs one CTA per system with its vectors in global memory), the
-    quadrature of the large-lattice workload (k = 0.25), short edge meshes
-    (h = 2^-3) so that the oracle stays fast."""
+def test_large_lattice_global_vector_pcg_k025(precision, layout, kappa, beta):
+    """68 x 68 grid with 15 % of the edges deleted (> 4096 kept vertices: the
+    mixed PCG runs with its vectors in global memory, batched in rows of 8
+    samples by default, or one CTA per system), the quadrature of the
+    large-lattice workload (k = 0.25), short edge meshes (h = 2^-3) so that the
+    oracle stays fast."""
     g = gi.grid_deleted(68, 68, 0.15, seed=7)
     assert g.n_vertices > 4096
     h = 2.0 ** -3
     G = _graph(g, h=h)
     k, seed, S = 0.25, 5, 2
     ml, ref = _oracle("lattice68", g, kappa, beta, k, seed, S, h=h)
-    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64")
+    u, st = G.sample(kappa, beta, k, seed, S, precision=precision, out_dtype="f64",
+                     pcg_layout=layout)
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
     assert rel_l2(u.cpu().numpy(), ref, ml) < TOL[precision]
 
@@ -187,3 +190,94 @@ def test_rgg2000_whole_sample_against_oracle():
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
     ml, ref = _oracle("rgg2000", g, w.kappa, w.beta, w.k_step, w.seed, S, h=w.h)
     assert rel_l2(u.double().cpu().numpy(), ref, ml) < TOL["mixed"]
+
+
+# ------------------------------------------- batched PCG: ragged sample groups
+
+
+@pytest.mark.parametrize("S", [1, 8, 11])
+@pytest.mark.parametrize("gamma", [1e-12, 0.05, 3.0, 1e7])
+def test_batched_pcg_vertex_solve_matches_oracle(S, gamma):
+    """The batched layout (rows of 8 samples per vertex) on a small multigraph:
+    one sample, a full group and a ragged second group; shifts from nearly the
+    mass matrix to nearly the stiffness matrix; condensed right-hand side and
+    vertex solution against the oracle's global blocks."""
+    from oracle import noise
+    g = gi.random_small_graph(40, 70, 9)
+    h = 0.05
+    G = _graph(g, h=h)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h)
+    kappa = 1.7
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = noise.white_noise(ml, 4, S)
+    opts = grf.make_options("mixed", pcg_layout="batched")
+    gv = torch.empty((S, G.n_kept), dtype=torch.float64, device="cuda")
+    uv = torch.empty_like(gv)
+    rt = torch.tensor(rhs, device="cuda")
+    st = grf.grf_vertex_solve(G.handle, kappa, 1.0, gamma, S, rt.data_ptr(), gv.data_ptr(),
+                              uv.data_ptr(), opts, None)
+    g_ref, u_ref = sampler.vertex_condensation(m, ml, kmat, gamma, rhs)
+    for got, ref in ((gv, g_ref), (uv, u_ref)):
+        got = got.cpu().numpy()
+        err = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert err.max() < 1e-5, err
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+
+
+def test_batched_pcg_whole_sample_ragged_groups():
+    g = gi.random_small_graph(40, 70, 9)
+    h = 0.05
+    G = _graph(g, h=h)
+    kappa, beta, k, seed, S = 2.5, 0.6, 0.45, 3, 11
+    ml, ref = _oracle("random40", g, kappa, beta, k, seed, S, h=h)
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     pcg_layout="batched")
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    assert rel_l2(u.cpu().numpy(), ref, ml) < TOL["mixed"]
+
+
+# ------------------------------------------- tensor-core sine transforms
+
+
+@pytest.mark.parametrize("S", [1, 4, 16, 32, 40])
+def test_umma_transforms_sample_counts(S):
+    """The tcgen05 sine transforms with 1 to 40 samples (sample padding 8 to 64,
+    4 to 32 edges per 256-column tile, ragged last tiles), edges of 1 to 1024
+    interior nodes (several 128-row blocks of Phi_m, one and many edges per
+    length), against the oracle."""
+    ne = [2, 3, 3, 17, 64, 65, 128, 129, 200, 200, 200, 383, 700, 1025, 5, 9]
+    eu = np.array([0, 1, 2, 3, 4, 5, 6, 7, 0, 2, 4, 6, 1, 3, 5, 7])
+    ev = np.array([1, 2, 3, 4, 5, 6, 7, 0, 4, 6, 1, 3, 5, 7, 0, 2])
+    lengths = np.array(ne) * 1e-3 * np.linspace(0.9, 1.1, len(ne))
+    g = gi.Graph(8, eu, ev, lengths)
+    G = _graph(g, n_elems=ne)
+    kappa, beta, k, seed = 6.0, 0.6, 0.5, 21
+    ml, ref = _oracle("umma8", g, kappa, beta, k, seed, S, n_elems=ne)
+    for out_dtype in ("f64", "f32"):
+        u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype=out_dtype,
+                         interior="spectral_umma")
+        assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+        assert rel_l2(u.double().cpu().numpy(), ref, ml) < TOL["mixed"]
+
+
+def test_umma_transforms_graph_replay_and_apply():
+    """The tensor-core path inside a captured CUDA graph (replayed twice with
+    different seeds) and through the general right-hand-side entry point."""
+    g = small_lattice()
+    G = _graph(g, h=H9)
+    kappa, beta, k, S = 2.0, 0.75, 0.25, 8
+    out = torch.empty((S, G.n_dofs), dtype=torch.float32, device="cuda")
+    for seed in (3, 4):
+        ml, ref = _oracle("lattice6", g, kappa, beta, k, seed, S, h=H9)
+        u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f32", out=out,
+                         use_graph=True, interior="spectral_umma")
+        assert st["n_unconverged"] == 0
+        assert rel_l2(u.double().cpu().numpy(), ref, ml) < TOL["mixed"]
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=H9)
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = np.random.default_rng(5).standard_normal((3, m.n_dofs))
+    t = np.array([1e-6, 0.01, 1.0, 30.0, 1e6])
+    w = np.array([0.3, 1.0, 2.0, 0.5, 1e-3])
+    o, _ = G.apply(kappa, np.ones_like(t), t, w, torch.tensor(rhs, device="cuda"),
+                   precision="mixed", out_dtype="f64", interior="spectral_umma")
+    assert rel_l2(o.cpu().numpy(), sampler.shifted_sum(ml, kmat, rhs, t, w), ml) < 1e-5

@@ -198,7 +198,8 @@ def test_apply_matches_oracle(precision, name):
 
 
 @pytest.mark.parametrize("precision,interior", [("fp64", "auto"), ("mixed", "thomas"),
-                                                ("mixed", "spectral"), ("mixed", "spectral_tc")])
+                                                ("mixed", "spectral"), ("mixed", "spectral_tc"),
+                                                ("mixed", "spectral_umma")])
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("beta", [0.3, 0.75])
 def test_sample_matches_oracle(precision, interior, name, beta):
@@ -304,7 +305,8 @@ def test_sample_large_disconnected_graph_global_vectors(precision):
 
 @pytest.mark.parametrize("precision,sg,interior", [
     ("fp64", 0, "thomas"), ("mixed", 1, "thomas"), ("mixed", 2, "thomas"), ("mixed", 4, "thomas"),
-    ("mixed", 1, "spectral"), ("mixed", 4, "spectral"), ("mixed", 4, "spectral_tc")])
+    ("mixed", 1, "spectral"), ("mixed", 4, "spectral"), ("mixed", 4, "spectral_tc"),
+    ("mixed", 4, "spectral_umma")])
 def test_sample_every_recovery_bin(precision, sg, interior):
     """Edge interiors from 1 to 4999 nodes: every register-resident bin of the
     Thomas recovery (one warp with 1, 2, 4, 8 nodes per lane; 2 to 16 warps),

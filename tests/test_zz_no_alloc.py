@@ -44,7 +44,8 @@ def _scratch_bytes(n_dofs, n_kept, n_edges, n_rhs, ts):
     edges' node-parallel condensation reads."""
     up = lambda x: (x + 255) // 256 * 256
     E, V, S = n_edges, n_kept, n_rhs
-    parts = [n_dofs * S * ts, 8, 8, 8, 8 * E, 8 * E, 8 * V, 16 * E] + [S * V * ts] * 4
+    Sv = (S + 7) // 8 * 8 if ts == 4 else S  # FP32 PCG vectors: samples padded to 8
+    parts = [n_dofs * S * ts, 8, 8, 8, 8 * E, 8 * E, 8 * V, 16 * E] + [Sv * V * ts] * 4
     parts += [V * ts] + ([8 * E] if ts == 4 else []) + [4 * S, 24, 4 * ts * E]
     return sum(up(x) for x in parts)
 
