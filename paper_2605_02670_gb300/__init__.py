@@ -365,6 +365,8 @@ class Graph:
                  n_elems=None):
         self.n_vertices_in = int(n_vertices)
         self.n_edges = int(np.asarray(edge_u).shape[0])
+        self.edge_u_in = np.asarray(edge_u, np.int64).copy()
+        self.edge_v_in = np.asarray(edge_v, np.int64).copy()
         self.handle = grf_graph_create(edge_u, edge_v, lengths, n_vertices, h, n_elems)
         info = grf_graph_info(self.handle, self.n_vertices_in, self.n_edges)
         self.n_dofs = info["n_dofs"]
