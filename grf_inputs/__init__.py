@@ -266,6 +266,12 @@ WORKLOADS = {
                         n_samples=32, seed=1, precision="mixed",
                         graph_args={"kind": "grid", "nx": 120, "ny": 120,
                                     "frac": 0.15, "seed": 7}),
+    # 40x40 grid with the 300x300 lattice's parameters and mesh (edges of
+    # 410-615 elements, 212 nodes, 32 samples): profiles of its edge kernels.
+    "grid40": Workload("grid40", kappa=2.0, beta=0.75, k_step=0.25, h=2.0 ** -9,
+                       n_samples=32, seed=1, precision="mixed",
+                       graph_args={"kind": "grid", "nx": 40, "ny": 40,
+                                   "frac": 0.15, "seed": 7}),
     # 300x300 grid, 15% edges deleted, largest component.
     "grid300": Workload("grid300", kappa=2.0, beta=0.75, k_step=0.25, h=2.0 ** -9,
                         n_samples=32, seed=1, precision="mixed",

@@ -230,9 +230,24 @@ __global__ void __launch_bounds__(kGT, 1)
     const __nv_bfloat16* al = phi_lo + it.phi_off + (int64_t)it.mt * kBM * it.kp;
     const int nk = it.kp / kBK;
     int last = 0;
+    // B values of the next stage are loaded into registers one stage ahead,
+    // so their latency overlaps the previous stage's MMAs and barrier wait
+    float xb[8][8];
+    auto load_b = [&](int kb, float (&x)[8][8]) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = kb * kBK + c * 8 + q;
+          x[c][q] = (col_ok && k < it.m) ? __ldg(colp + (int64_t)k * S) : 0.f;
+        }
+    };
+    load_b(0, xb);
     for (int kb = 0; kb < nk; ++kb) {
       const int st = kb & 1;
       last = st;
+      float xn[8][8];
+      if (kb + 1 < nk) load_b(kb + 1, xn);
       if (uses[st] > 0 && !mbar_wait(&mbar[st], (uses[st] - 1) & 1)) failed = true;
       if (__syncthreads_or(failed)) {
         failed = true;
@@ -242,31 +257,35 @@ __global__ void __launch_bounds__(kGT, 1)
       unsigned char* A_lo = A_hi + kATile;
       unsigned char* B_hi = A_lo + kATile;
       unsigned char* B_lo = B_hi + kBTile;
-      // A: 128 rows x 8 chunks of 16 bytes per plane
+      // A: 128 rows x 8 chunks of 16 bytes per plane, copied asynchronously
 #pragma unroll
       for (int u = 0; u < (kBM * 8) / kGT; ++u) {
         const int idx = tid + u * kGT;
         const int r = idx >> 3, c = idx & 7;
         const int64_t go = (int64_t)r * it.kp + kb * kBK + c * 8;
-        const uint4 vh = __ldg(reinterpret_cast<const uint4*>(ah + go));
-        const uint4 vl = __ldg(reinterpret_cast<const uint4*>(al + go));
-        *reinterpret_cast<uint4*>(A_hi + swz(r, c)) = vh;
-        *reinterpret_cast<uint4*>(A_lo + swz(r, c)) = vl;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(A_hi + swz(r, c))),
+                     "l"(ah + go)
+                     : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(A_lo + swz(r, c))),
+                     "l"(al + go)
+                     : "memory");
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
       // B: column tid, 64 K values in 8 chunks of 8, split into hi/lo
-#pragma unroll 2
-      for (int c = 0; c < 8; ++c) {
-        float x[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int k = kb * kBK + c * 8 + q;
-          x[q] = (col_ok && k < it.m) ? __ldg(colp + (int64_t)k * S) : 0.f;
-        }
+      for (int c = 0; c < 8; ++c) {
         uint4 hi, lo;
-        split8(x, hi, lo);
+        split8(xb[c], hi, lo);
         *reinterpret_cast<uint4*>(B_hi + swz(tid, c)) = hi;
         *reinterpret_cast<uint4*>(B_lo + swz(tid, c)) = lo;
       }
+      if (kb + 1 < nk) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) xb[c][q] = xn[c][q];
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
       // make the generic-proxy stores visible to the tensor core
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -303,6 +322,19 @@ __global__ void __launch_bounds__(kGT, 1)
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)col0, v);
       if (jrow >= it.m) continue;
+      if (!kInv && sizeof(OutT) == 4 && sp >= 32 && (S & 3) == 0) {
+        // the 32 columns are 32 consecutive samples of one edge: 8 vector stores
+        const int e_t = col0 / sp, sc0 = col0 % sp;
+        if (e_t < it.ne && sc0 + 32 <= S) {
+          const int32_t e = edges[it.e0 + e_t];
+          float4* row = reinterpret_cast<float4*>(
+              reinterpret_cast<float*>(dst) + (g.ioff[e] + jrow) * S + sc0);
+#pragma unroll
+          for (int t = 0; t < 8; ++t)
+            row[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+          continue;
+        }
+      }
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
         const int n = col0 + t;

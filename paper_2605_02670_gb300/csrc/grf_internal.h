@@ -86,10 +86,11 @@ struct alignas(4 * sizeof(T)) SweepParams {
 //   dscale[l][v] (if not null): 1 / S_vv (T = double) or 1 / sqrt(S_vv) (T = float);
 //   offv_t (T = float, if not null): offv / sqrt(S_vv S_ww).
 // Returns the number of kernels launched.
+// consistent: blocks of the consistent-mass operator (no sweep constants).
 template <typename T>
 int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa,
                  double* sab, double* diag, double* offv, SweepParams<T>* prm, T* dscale,
-                 T* offv_t, cudaStream_t st);
+                 T* offv_t, cudaStream_t st, bool consistent = false);
 
 // Neumann-Neumann preconditioner coefficients per node: pc[l][v] (diagonal) and
 // pn[l][k] (incidence k), for the Jacobi-scaled system (scaled) or S itself.

@@ -167,18 +167,15 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     float* __restrict__ pa = PA + base;
     float* __restrict__ pb = PB + base;
     float* __restrict__ dv = Dv + base;
-    // this thread's 4 samples: FP64 rows of g and x
-    const double* gs[4];
-    double* xs[4];
-    bool live[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t s = s0 + 4 * hh + i;
-      live[i] = s < S;
-      const int64_t sys = l * S + (live[i] ? s : 0);
-      gs[i] = gvec + sys * nv;
-      xs[i] = xout + sys * nv;
-    }
+    // this thread's 4 samples: FP64 rows of g and x (row i at + i nv; only
+    // the first nlive exist)
+    const int64_t sfirst = s0 + 4 * hh;
+    const int nlive = (int)(S - sfirst < 0 ? 0 : (S - sfirst > 4 ? 4 : S - sfirst));
+    const double* __restrict__ g0 = gvec + (l * S + (nlive > 0 ? sfirst : 0)) * nv;
+    double* __restrict__ x0 = xout + (l * S + (nlive > 0 ? sfirst : 0)) * nv;
+#define GS(i) (g0 + (int64_t)(i) * nv)
+#define XS(i) (x0 + (int64_t)(i) * nv)
+#define LIVE(i) ((i) < nlive)
 
     // ---- ||g||^2, ||D^-1/2 g||^2 (FP64); x = 0
     {
@@ -188,11 +185,11 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         const double dsv = (double)Ds[v];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const double gv = live[i] ? gs[i][v] : 0.0;
+          const double gv = LIVE(i) ? GS(i)[v] : 0.0;
           const double sv = gv * dsv;
           a.d[i][0] = fma(gv, gv, a.d[i][0]);
           a.d[i][1] = fma(sv, sv, a.d[i][1]);
-          if (live[i]) xs[i][v] = 0.0;
+          if (LIVE(i)) XS(i)[v] = 0.0;
         }
       }
       double out[2] = {0.0, 0.0};
@@ -222,7 +219,7 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         const float dsv = Ds[v];
         float rv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rv[i] = dn[i] ? 0.f : ((float)gs[i][v] * ig[i]) * dsv;
+        for (int i = 0; i < 4; ++i) rv[i] = dn[i] ? 0.f : ((float)GS(i)[v] * ig[i]) * dsv;
         st4(r + (int64_t)v * kSG, make_float4(rv[0], rv[1], rv[2], rv[3]));
       }
       __syncthreads();
@@ -251,9 +248,9 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           for (int i = 0; i < 4; ++i) {
             sv4[i] = 0.f;
             if (dn[i]) continue;
-            double y = dd * xs[i][v];
-            for (int32_t k = k0; k < k1; ++k) y = fma(O[k], xs[i][nbr[k]], y);
-            const double rv = gs[i][v] - y;
+            double y = dd * XS(i)[v];
+            for (int32_t k = k0; k < k1; ++k) y = fma(O[k], XS(i)[nbr[k]], y);
+            const double rv = GS(i)[v] - y;
             const float rel = (float)(rv * ivg[i]);
             sv4[i] = (float)(rv * ir[i]) * dsv;
             a.f[i][0] = fmaf(rel, rel, a.f[i][0]);
@@ -450,7 +447,7 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           const double dsv = (double)Ds[v];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
-            if (up[i]) xs[i][v] = fma(rh[i] * dsv, (double)get(d4, i), xs[i][v]);
+            if (up[i]) XS(i)[v] = fma(rh[i] * dsv, (double)get(d4, i), XS(i)[v]);
         }
       }
       __syncthreads();  // x complete, every thread done with the state
@@ -472,6 +469,10 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     __syncthreads();
   }
 }
+
+#undef GS
+#undef XS
+#undef LIVE
 
 // Vectors of the batched layout need [L][ceil(S / 8) * 8][nv] floats each.
 int64_t pcg_batch_padded_samples(int64_t S) { return (S + kSG - 1) / kSG * kSG; }

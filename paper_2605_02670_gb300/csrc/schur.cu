@@ -16,6 +16,16 @@
 // costs O(1) per (node, edge) instead of O(n_e). sinh(theta) =
 // sqrt(delta (1 + delta / 4)) and theta = log1p(delta / 2 + sinh(theta)) avoid
 // cancellation for small delta; expm1 keeps large n theta finite.
+//
+// Consistent mass (the paper's comparison system, Sec. 3 Phase 2 consistent
+// case): with a = alpha + gamma kappa^2 the interior block is tridiag(o, d, o),
+// d = 2 a h / 3 + 2 gamma / h, o = a h / 6 - gamma / h, the couplings are o and
+// the edge's share of A_vv is d / 2. With r = |o| and 2 cosh(theta) = d / r
+// (> 2: the block is diagonally dominant) the same algebra gives
+//   S^(e) = r sinh(theta) [[coth(n theta), -s csch(n theta)], [..., coth(n theta)]],
+// s = 1 for o < 0 and (-1)^n for o > 0 (tridiag(o, d, o) with o > 0 is
+// D tridiag(-o, d, -o) D, D = diag((-1)^i)). d / r - 2 is formed without
+// cancellation: a h / r for o < 0, (a h / 3 + 4 gamma / h) / r for o > 0.
 #include "grf_internal.h"
 
 namespace grf {
@@ -23,7 +33,8 @@ namespace {
 
 template <typename T>
 __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, double* __restrict__ saa,
-                                   double* __restrict__ sab, SweepParams<T>* __restrict__ prm) {
+                                   double* __restrict__ sab, SweepParams<T>* __restrict__ prm,
+                                   int consistent) {
   const int64_t total = (int64_t)nd.L * g.ne;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -31,8 +42,23 @@ __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, doubl
     const int32_t e = (int32_t)(t - l * g.ne);
     const double h = g.he[e];
     const double gam = nd.gamma[l];
-    const double c = gam / h;
-    const double delta = (nd.alpha[l] / gam + kappa2) * h * h;
+    double c = gam / h;
+    double delta = (nd.alpha[l] / gam + kappa2) * h * h;
+    double sgn = 1.0;
+    if (consistent) {
+      const double a = nd.alpha[l] + gam * kappa2;
+      const double o = a * h / 6.0 - gam / h;
+      const double r = fabs(o);
+      if (!(r > 1e-300)) {  // no coupling through the interior
+        const double d2 = a * h / 3.0 + gam / h;
+        saa[t] = d2;
+        sab[t] = g.nel[e] == 1 ? o : 0.0;
+        continue;
+      }
+      c = r;
+      delta = o < 0.0 ? a * h / r : (a * h / 3.0 + 4.0 * gam / h) / r;
+      sgn = (o < 0.0 || (g.nel[e] & 1) == 0) ? 1.0 : -1.0;
+    }
     // sinh(theta) and theta = acosh(1 + delta/2) = log1p(delta/2 + sinh(theta));
     // with u = expm1(-n theta): exp(-n theta) = 1 + u and
     // 1 - exp(-2 n theta) = -u (2 + u), both free of cancellation
@@ -43,7 +69,7 @@ __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, doubl
     const double e1 = 1.0 + u;
     const double e2 = -u * (2.0 + u);  // 1 - exp(-2 n theta)
     saa[t] = c * sh * ((2.0 - e2) / e2);
-    sab[t] = -c * sh * (2.0 * e1 / e2);
+    sab[t] = -sgn * c * sh * (2.0 * e1 / e2);
     if (prm) {
       SweepParams<T> p;
       p.delta = (T)delta;
@@ -143,9 +169,9 @@ int grid_for(int64_t total, int threads) {
 template <typename T>
 int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa, double* sab,
                  double* diag, double* offv, SweepParams<T>* prm, T* dscale, T* offv_t,
-                 cudaStream_t st) {
-  edge_blocks_kernel<T><<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(g, nd, kappa2, saa,
-                                                                            sab, prm);
+                 cudaStream_t st, bool consistent) {
+  edge_blocks_kernel<T><<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(
+      g, nd, kappa2, saa, sab, consistent ? nullptr : prm, consistent ? 1 : 0);
   vertex_diag_kernel<T><<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, saa, sab,
                                                                              diag, offv, dscale);
   if constexpr (sizeof(T) == 4) {
@@ -170,9 +196,9 @@ template void launch_nn_coeffs<double>(const DevGraph&, int32_t, const double*, 
 
 template int launch_schur<float>(const DevGraph&, const DevNodes&, double, double*, double*,
                                  double*, double*, SweepParams<float>*, float*, float*,
-                                 cudaStream_t);
+                                 cudaStream_t, bool);
 template int launch_schur<double>(const DevGraph&, const DevNodes&, double, double*, double*,
                                   double*, double*, SweepParams<double>*, double*, double*,
-                                  cudaStream_t);
+                                  cudaStream_t, bool);
 
 }  // namespace grf

@@ -169,9 +169,7 @@ __host__ __device__ constexpr size_t spec_condense_floats(int32_t mmax) {
 
 // Forward transform of the edge's noise (written to bhat, rows like b) and
 // the two end values of T_l^-1 b_I for every node, added into gvec.
-// kFromBhat: bhat already holds the forward transform (tensor-core path);
-// only the end values are formed.
-template <int SG, int QJ, bool kFromBhat = false>
+template <int SG, int QJ>
 __global__ void __launch_bounds__(256)
     spec_condense_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                          const float* __restrict__ b, const int32_t* __restrict__ edges,
@@ -193,19 +191,12 @@ __global__ void __launch_bounds__(256)
     const int kv = (int)(S - s0 < SG ? S - s0 : SG);
     __syncthreads();  // the previous unit is done with the shared arrays
     spec_tables(m, tab, ctab, sig);
-    const float scale = sqrtf(2.f / (float)(m + 1));
-    if (kFromBhat) {
-      stage_rows<SG>(bhat + off * S + s0, S, kv, m, bt);
-      __syncthreads();
-      for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x)
-        bt[t] *= scale * tab[t / SG + 1];
-    } else {
-      stage_rows<SG>(b + (g.nv + off) * S + s0, S, kv, m, bs);
-    }
+    stage_rows<SG>(b + (g.nv + off) * S + s0, S, kv, m, bs);
     __syncthreads();
+    const float scale = sqrtf(2.f / (float)(m + 1));
     // forward transform: modes t + q blockDim (q < QJ) per thread share every
     // row load; the bin's QJ blockDim >= m, so one pass covers the edge
-    for (int32_t jb = 0; jb < (kFromBhat ? 0 : m); jb += QJ * blockDim.x) {
+    for (int32_t jb = 0; jb < m; jb += QJ * blockDim.x) {
       int32_t jj[QJ];
 #pragma unroll
       for (int q = 0; q < QJ; ++q) {
@@ -272,14 +263,12 @@ __host__ __device__ constexpr size_t spec_recover_floats(int32_t mmax) {
 }
 
 // U_I = Phi c with c from bhat and the weighted vertex values xw[l][v][s] = w_l u_v^(l).
-// kCoef: write c over the edge's bhat rows (cout) instead of transforming it
-// back (the tensor-core path transforms all edges of a length at once).
-template <int SG, int QJ, typename OutT, bool kCoef = false>
+template <int SG, int QJ, typename OutT>
 __global__ void __launch_bounds__(256)
     spec_recover_kernel(DevGraph g, DevNodes nd, double kappa2, int64_t S,
                         const int32_t* __restrict__ edges, int32_t n_edges, int32_t mmax,
-                        const float* bhat, const float* __restrict__ xw,
-                        OutT* __restrict__ out, float* cout) {
+                        const float* __restrict__ bhat, const float* __restrict__ xw,
+                        OutT* __restrict__ out) {
   extern __shared__ __align__(16) float spec_sm[];
   float* cs = spec_sm;                            // [mmax][SG] bh, then c
   float* xp = cs + (size_t)mmax * SG;             // [chunk][SG] xa + xb
@@ -362,13 +351,6 @@ __global__ void __launch_bounds__(256)
       }
     }
     __syncthreads();
-    if (kCoef) {
-      for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x) {
-        const int32_t j = t / SG, sc = t - j * SG;
-        if (sc < kv) cout[(off + j) * S + s0 + sc] = cs[t];
-      }
-      continue;
-    }
     // inverse transform: output nodes t + q blockDim (q < QJ) per thread
     for (int32_t ib = 0; ib < m; ib += QJ * blockDim.x) {
       int32_t ii[QJ];
@@ -406,6 +388,161 @@ int grid_units(int64_t units) {
   return b < 1 ? 1 : (int)b;
 }
 
+// The two halves around the tensor-core transforms (dst_gemm.cu): they only
+// contract bhat with 1 / mu_jl, so one node (ends) or one mode (coefficients)
+// per thread and a shared-memory footprint of one edge's rows keep several
+// CTAs per SM.
+constexpr int kEndsThreads = 256;
+
+// End values of every node from the transformed rows: thread l accumulates
+// O_l (odd modes) and E_l (even modes) over the edge's modes, rows
+// phi_j bh_j staged once per (edge, sample group).
+constexpr int kEndsCta = 128;  // threads of the end-value kernel (two nodes each)
+
+template <int SG>
+__global__ void __launch_bounds__(kEndsCta, 4)
+    spec_ends_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
+                     int32_t n_edges, const float* __restrict__ bhat, double* __restrict__ gvec) {
+  extern __shared__ __align__(16) float ends_sm[];
+  const int64_t nsg = (S + SG - 1) / SG;
+  const int64_t units = (int64_t)n_edges * nsg;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int32_t e = edges[u / nsg];
+    const int64_t s0 = (u % nsg) * SG;
+    const int32_t m = g.nel[e] - 1;
+    const int64_t off = g.ioff[e];
+    const int kv = (int)(S - s0 < SG ? S - s0 : SG);
+    float* bt = ends_sm;                  // [m][SG] phi_j bh_j
+    float* sig = bt + (size_t)m * SG;     // [m] 4 sin^2(pi j / (2 (m + 1)))
+    __syncthreads();  // the previous unit is done with the shared arrays
+    stage_rows<SG>(bhat + off * S + s0, S, kv, m, bt);
+    for (int32_t j = threadIdx.x; j < m; j += blockDim.x) {
+      const float sh = 2.f * sinpif((float)(j + 1) / (float)(2 * (m + 1)));
+      sig[j] = sh * sh;
+    }
+    __syncthreads();
+    const float scale = sqrtf(2.f / (float)(m + 1));
+    for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x)
+      bt[t] *= scale * sinpif((float)(t / SG + 1) / (float)(m + 1));
+    __syncthreads();
+    const double h = g.he[e];
+    const float h2f = (float)(h * h);
+    const int32_t va = g.eu[e], vb = g.ev[e];
+    // nodes l and l + ceil(L / 2) per thread: every staged row serves both
+    const int32_t half = (nd.L + 1) / 2;
+    for (int32_t l0 = threadIdx.x; l0 < half; l0 += blockDim.x) {
+      const int32_t l1 = l0 + half;
+      const bool two = l1 < nd.L;
+      const float dl0 = nd.shift[l0] * h2f;
+      const float dl1 = two ? nd.shift[l1] * h2f : 1.f;
+      float od0[SG], ev0[SG], od1[SG], ev1[SG];
+#pragma unroll
+      for (int s = 0; s < SG; ++s) od0[s] = ev0[s] = od1[s] = ev1[s] = 0.f;
+      int32_t j = 0;
+      for (; j + 1 < m; j += 2) {  // odd mode j + 1 into od, even mode j + 2 into ev
+        const float sa = sig[j], sb = sig[j + 1];
+        spec_acc2<SG>(__fdividef(1.f, dl0 + sa), __fdividef(1.f, dl1 + sa), bt + (size_t)j * SG,
+                      od0, od1);
+        spec_acc2<SG>(__fdividef(1.f, dl0 + sb), __fdividef(1.f, dl1 + sb),
+                      bt + (size_t)(j + 1) * SG, ev0, ev1);
+      }
+      if (j < m)
+        spec_acc2<SG>(__fdividef(1.f, dl0 + sig[j]), __fdividef(1.f, dl1 + sig[j]),
+                      bt + (size_t)j * SG, od0, od1);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
+        double* gl = gvec + ((int64_t)(q ? l1 : l0) * S + s0) * g.nv;
+#pragma unroll
+        for (int s = 0; s < SG; ++s) {
+          if (s < kv) {
+            const float o = q ? od1[s] : od0[s], v = q ? ev1[s] : ev0[s];
+            atomicAdd(gl + (int64_t)s * g.nv + va, (double)(o + v));
+            atomicAdd(gl + (int64_t)s * g.nv + vb, (double)(o - v));
+          }
+        }
+      }
+    }
+  }
+}
+
+// Sine-basis coefficients of the recovery, written over the edge's bhat rows:
+// c_j = D_j bh_j + phi_j sum_l (xa_l + (-1)^(j+1) xb_l) / mu_jl with
+// D_j = sum_l sc_l / mu_jl; thread j owns mode j, the nodes' weighted vertex
+// values (xa +- xb) and constants are staged once per (edge, sample group).
+template <int SG>
+__global__ void __launch_bounds__(kEndsThreads)
+    spec_coef_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
+                     int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw) {
+  extern __shared__ __align__(16) float coef_sm[];
+  const int32_t L = nd.L;
+  float* xp = coef_sm;                     // [L][SG] xa + xb
+  float* xm = xp + (size_t)L * SG;         // [L][SG] xa - xb
+  float* dls = xm + (size_t)L * SG;        // [L] delta_l
+  float* scs = dls + L;                    // [L] sc_l
+  const int64_t nsg = (S + SG - 1) / SG;
+  const int64_t units = (int64_t)n_edges * nsg;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int32_t e = edges[u / nsg];
+    const int64_t s0 = (u % nsg) * SG;
+    const int32_t m = g.nel[e] - 1;
+    const int64_t off = g.ioff[e];
+    const int kv = (int)(S - s0 < SG ? S - s0 : SG);
+    const double h = g.he[e];
+    const float hf = (float)h, h2f = (float)(h * h);
+    const int32_t va = g.eu[e], vb = g.ev[e];
+    __syncthreads();
+    for (int32_t l = threadIdx.x; l < L; l += blockDim.x) {
+      dls[l] = nd.shift[l] * h2f;
+      scs[l] = nd.wgam[l] * hf;
+    }
+    for (int32_t t = threadIdx.x; t < L * SG; t += blockDim.x) {
+      const int32_t l = t / SG, s = t - l * SG;
+      float a = 0.f, c = 0.f;
+      if (s < kv) {
+        a = xw[((int64_t)l * g.nv + va) * S + s0 + s];
+        c = xw[((int64_t)l * g.nv + vb) * S + s0 + s];
+      }
+      xp[t] = a + c;
+      xm[t] = a - c;
+    }
+    __syncthreads();
+    const float scale = sqrtf(2.f / (float)(m + 1));
+    // modes 4 b + p and 4 b + p + 2 (equal parity p) per thread: every staged
+    // row of (xa +- xb) serves both
+    for (int32_t t = threadIdx.x; 2 * t < m + 1; t += blockDim.x) {
+      const int32_t j0 = 4 * (t >> 1) + (t & 1), j1 = j0 + 2;
+      if (j0 >= m) continue;
+      const bool two = j1 < m;
+      float sh = 2.f * sinpif((float)(j0 + 1) / (float)(2 * (m + 1)));
+      const float s0f = sh * sh;
+      sh = 2.f * sinpif((float)(j1 + 1) / (float)(2 * (m + 1)));
+      const float s1f = two ? sh * sh : s0f;
+      const float* X = (j0 & 1) ? xm : xp;  // mode j + 1 odd <=> j even
+      float C0[SG], C1[SG], D0 = 0.f, D1 = 0.f;
+#pragma unroll
+      for (int s = 0; s < SG; ++s) C0[s] = C1[s] = 0.f;
+      for (int32_t l = 0; l < L; ++l) {
+        const float dl = dls[l], sc = scs[l];
+        const float r0 = __fdividef(1.f, dl + s0f), r1 = __fdividef(1.f, dl + s1f);
+        D0 = fmaf(sc, r0, D0);
+        D1 = fmaf(sc, r1, D1);
+        spec_acc2<SG>(r0, r1, X + (size_t)l * SG, C0, C1);
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (q == 1 && !two) break;
+        const int32_t j = q ? j1 : j0;
+        const float phi = scale * sinpif((float)(j + 1) / (float)(m + 1));
+        float* row = bhat + (off + j) * S + s0;
+#pragma unroll
+        for (int s = 0; s < SG; ++s)
+          if (s < kv) row[s] = fmaf(q ? D1 : D0, row[s], phi * (q ? C1[s] : C0[s]));
+      }
+    }
+  }
+}
+
 }  // namespace
 
 // Spectral bins: interior-node limit, threads per CTA and modes per thread
@@ -429,88 +566,50 @@ int spec_bins(int32_t* mmax) {
   return kNumSpecBins;
 }
 
-template <int QJ, bool kFromBhat>
+template <int QJ>
 void spec_condense_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                        const float* b, const int32_t* e, int32_t n, const SpecBin& bin,
                        float* bhat, double* gvec, cudaStream_t st) {
   const size_t smem = spec_condense_floats<kSpecSG>(bin.mmax) * sizeof(float);
-  cudaFuncSetAttribute(spec_condense_kernel<kSpecSG, QJ, kFromBhat>,
+  cudaFuncSetAttribute(spec_condense_kernel<kSpecSG, QJ>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  spec_condense_kernel<kSpecSG, QJ, kFromBhat><<<grid_units(units), bin.threads, smem, st>>>(
+  spec_condense_kernel<kSpecSG, QJ><<<grid_units(units), bin.threads, smem, st>>>(
       g, nd, kappa2, S, b, e, n, bin.mmax, bhat, gvec);
-}
-
-template <bool kFromBhat>
-int spec_condense_all(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                      const float* b, const int32_t* bin_edges, const int32_t* bin_count,
-                      float* bhat, double* gvec, cudaStream_t st) {
-  const int32_t* e = bin_edges;
-  int launches = 0;
-  for (int i = 0; i < kNumSpecBins; ++i) {
-    const int32_t n = bin_count[i];
-    if (n > 0) {
-      const SpecBin& bn = kSpecBins[i];
-      // (transform-free: QJ only sizes the unused transform loop)
-      switch (kFromBhat ? 1 : bn.qj) {
-        case 1: spec_condense_bin<1, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        case 2: spec_condense_bin<2, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        case 3: spec_condense_bin<3, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-        default: spec_condense_bin<4, kFromBhat>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
-      }
-      ++launches;
-    }
-    e += n;
-  }
-  return launches;
 }
 
 int launch_spec_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                          const float* b, const int32_t* bin_edges, const int32_t* bin_count,
                          float* bhat, double* gvec, cudaStream_t st) {
-  return spec_condense_all<false>(g, nd, kappa2, S, b, bin_edges, bin_count, bhat, gvec, st);
-}
-
-int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
-                     double* gvec, cudaStream_t st) {
-  return spec_condense_all<true>(g, nd, kappa2, S, nullptr, bin_edges, bin_count,
-                                 const_cast<float*>(bhat), gvec, st);
-}
-
-template <int QJ, typename OutT, bool kCoef = false>
-void spec_recover_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                      const int32_t* e, int32_t n, const SpecBin& bin, const float* bhat,
-                      const float* xw, OutT* out, cudaStream_t st, float* cout = nullptr) {
-  const size_t smem = spec_recover_floats<kSpecSG>(bin.mmax) * sizeof(float);
-  cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, QJ, OutT, kCoef>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  spec_recover_kernel<kSpecSG, QJ, OutT, kCoef><<<grid_units(units), bin.threads, smem, st>>>(
-      g, nd, kappa2, S, e, n, bin.mmax, bhat, xw, out, cout);
-}
-
-int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
-                     const float* xw, cudaStream_t st) {
   const int32_t* e = bin_edges;
   int launches = 0;
   for (int i = 0; i < kNumSpecBins; ++i) {
     const int32_t n = bin_count[i];
     if (n > 0) {
       const SpecBin& bn = kSpecBins[i];
-      float* no = nullptr;
       switch (bn.qj) {
-        case 1: spec_recover_bin<1, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
-        case 2: spec_recover_bin<2, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
-        case 3: spec_recover_bin<3, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
-        default: spec_recover_bin<4, float, true>(g, nd, kappa2, S, e, n, bn, bhat, xw, no, st, bhat); break;
+        case 1: spec_condense_bin<1>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 2: spec_condense_bin<2>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        case 3: spec_condense_bin<3>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
+        default: spec_condense_bin<4>(g, nd, kappa2, S, b, e, n, bn, bhat, gvec, st); break;
       }
       ++launches;
     }
     e += n;
   }
   return launches;
+}
+
+template <int QJ, typename OutT>
+void spec_recover_bin(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                      const int32_t* e, int32_t n, const SpecBin& bin, const float* bhat,
+                      const float* xw, OutT* out, cudaStream_t st) {
+  const size_t smem = spec_recover_floats<kSpecSG>(bin.mmax) * sizeof(float);
+  cudaFuncSetAttribute(spec_recover_kernel<kSpecSG, QJ, OutT>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
+  spec_recover_kernel<kSpecSG, QJ, OutT><<<grid_units(units), bin.threads, smem, st>>>(
+      g, nd, kappa2, S, e, n, bin.mmax, bhat, xw, out);
 }
 
 template <typename OutT>
@@ -541,5 +640,41 @@ template int launch_spec_recover<float>(const DevGraph&, const DevNodes&, double
 template int launch_spec_recover<double>(const DevGraph&, const DevNodes&, double, int64_t,
                                          const int32_t*, const int32_t*, const float*,
                                          const float*, double*, cudaStream_t);
+
+int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
+                     double* gvec, cudaStream_t st) {
+  (void)kappa2;
+  int32_t n = 0;
+  for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
+  if (n <= 0) return 0;
+  const int32_t mmax = g.max_m < kSpecBins[kNumSpecBins - 1].mmax ? g.max_m
+                                                                   : kSpecBins[kNumSpecBins - 1].mmax;
+  const size_t smem = ((size_t)mmax * kSpecSG + mmax) * sizeof(float);
+  cudaFuncSetAttribute(spec_ends_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
+  const int64_t cap = (int64_t)152 * 16;
+  spec_ends_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsCta, smem, st>>>(
+      g, nd, S, bin_edges, n, bhat, gvec);
+  return 1;
+}
+
+int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
+                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
+                     const float* xw, cudaStream_t st) {
+  (void)kappa2;
+  int32_t n = 0;
+  for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
+  if (n <= 0) return 0;
+  const size_t smem = ((size_t)nd.L * (2 * kSpecSG + 2)) * sizeof(float);
+  cudaFuncSetAttribute(spec_coef_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
+  const int64_t cap = (int64_t)152 * 8;
+  spec_coef_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsThreads, smem, st>>>(
+      g, nd, S, bin_edges, n, bhat, xw);
+  return 1;
+}
 
 }  // namespace grf

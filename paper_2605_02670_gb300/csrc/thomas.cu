@@ -178,22 +178,53 @@ __global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, 
 // U_v = sum_l w_l u_v^(l) in FP64; also leaves xw[l][v][s] = w_l u_v^(l) in the
 // sweep precision for the interior recovery (sample-minor: an edge end's
 // samples are one contiguous row).
+// One CTA per tile of 32 vertices and up to 64 samples: for each node l the
+// tile's FP64 solutions are read along the vertices ([l][s][v] rows) and the
+// weighted values written along the samples ([l][v][s] rows) through a
+// shared-memory transpose, so both sides stay coalesced; the FP64 node sum of
+// every (s, v) stays in the registers of its thread.
+constexpr int kAccTile = 32, kAccRows = 8, kAccS = 64;
+
 template <typename T, typename OutT>
-__global__ void vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
-                                    OutT* __restrict__ out, T* __restrict__ xw) {
-  const int64_t total = S * g.nv;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = t / g.nv;
-    const int64_t v = t - s * g.nv;
-    double acc = 0.0;
+__global__ void __launch_bounds__(kAccTile * kAccRows)
+    vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
+                        OutT* __restrict__ out, T* __restrict__ xw) {
+  __shared__ T tile[kAccS][kAccTile + 1];
+  const int tx = threadIdx.x % kAccTile, ty = threadIdx.x / kAccTile;
+  const int64_t n_vt = (g.nv + kAccTile - 1) / kAccTile;
+  const int64_t n_sc = (S + kAccS - 1) / kAccS;
+  for (int64_t b = blockIdx.x; b < n_vt * n_sc; b += gridDim.x) {
+    const int64_t v0 = (b % n_vt) * kAccTile, s0 = (b / n_vt) * kAccS;
+    const int vn = (int)(g.nv - v0 < kAccTile ? g.nv - v0 : kAccTile);
+    const int sn = (int)(S - s0 < kAccS ? S - s0 : kAccS);
+    double acc[kAccS / kAccRows];
+#pragma unroll
+    for (int q = 0; q < kAccS / kAccRows; ++q) acc[q] = 0.0;
     for (int32_t l = 0; l < nd.L; ++l) {
-      const int64_t i = ((int64_t)l * S + s) * g.nv + v;
-      const double wx = nd.weight[l] * xv[i];
-      acc += wx;
-      xw[((int64_t)l * g.nv + v) * S + s] = (T)wx;
+      const double wl = nd.weight[l];
+#pragma unroll
+      for (int q = 0; q < kAccS / kAccRows; ++q) {
+        const int s = ty + q * kAccRows;
+        if (s < sn && tx < vn) {
+          const double wx = wl * xv[((int64_t)l * S + s0 + s) * g.nv + v0 + tx];
+          acc[q] += wx;
+          tile[s][tx] = (T)wx;
+        }
+      }
+      __syncthreads();
+      // the tile's rows xw[l][v0 + j][s0 .. s0 + sn) follow each other when
+      // sn == S; write them along the samples
+      for (int idx = threadIdx.x; idx < vn * sn; idx += blockDim.x) {
+        const int j = idx / sn, s = idx - j * sn;
+        xw[((int64_t)l * g.nv + v0 + j) * S + s0 + s] = tile[s][j];
+      }
+      __syncthreads();
     }
-    out[s * g.n + v] = (OutT)acc;
+#pragma unroll
+    for (int q = 0; q < kAccS / kAccRows; ++q) {
+      const int s = ty + q * kAccRows;
+      if (s < sn && tx < vn) out[(s0 + s) * g.n + v0 + tx] = (OutT)acc[q];
+    }
   }
 }
 
@@ -334,7 +365,11 @@ int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t
                    const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins, double* acc,
                    T* yscr, T* rpscr, int sg, cudaStream_t st) {
-  vertex_accum_kernel<T, OutT><<<grid_for(S * g.nv, 256), 256, 0, st>>>(g, nd, S, xv, out, xw);
+  {
+    const int64_t tiles = ((g.nv + kAccTile - 1) / kAccTile) * ((S + kAccS - 1) / kAccS);
+    vertex_accum_kernel<T, OutT><<<grid_for(tiles * 256, 256), kAccTile * kAccRows, 0, st>>>(
+        g, nd, S, xv, out, xw);
+  }
   int launches = 1;
   if (g.ni == 0) return launches;
   launches +=
