@@ -91,7 +91,22 @@ typedef struct grf_options {
                           GRF_INTERIOR_SPECTRAL_TC or GRF_INTERIOR_SPECTRAL_UMMA */
   int32_t sweep;       /* how FP32 edges left to the tridiagonal solves are swept:
                           GRF_SWEEP_AUTO, GRF_SWEEP_SEGMENTS or GRF_SWEEP_NODES */
+  int32_t mass;        /* GRF_MASS_LUMPED (the method) or GRF_MASS_CONSISTENT (the paper's
+                          comparison system, below) */
 } grf_options;
+
+/* Mass matrix of the noise and the operator:
+ *   LUMPED: M_L (Sec. 2.5 mass lumping), noise b = M_L^{1/2} xi;
+ *   CONSISTENT: the consistent mass of Sec. 3 Phase 2 in the noise, W = R xi
+ *     with M = R R^T the Cholesky factor in the order interiors (edge by edge),
+ *     then vertices by kept id, and in the operator, A_l = M + t_l (kappa^2 M + G).
+ *     Runs with GRF_MIXED, GRF_PRECOND_JACOBI, interior AUTO or SPECTRAL_UMMA,
+ *     0 < beta < 1, at most 256 samples per call and every edge within 1024
+ *     interior nodes (else GRF_ENOTSUP). Its first use on a graph factors the
+ *     vertex Schur complement of the mass on the host (envelope Cholesky in
+ *     kept-vertex order; GRF_ENOTSUP above 2^27 envelope entries). */
+#define GRF_MASS_LUMPED 0
+#define GRF_MASS_CONSISTENT 1
 
 /* Edge-interior solvers (same results up to rounding):
  *   THOMAS: per node l a tridiagonal elimination along the edge (Sec. 3, Phases
@@ -232,7 +247,10 @@ int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint
  *     counter = (q lo32, q hi32, s, 0)), q = j div 4;
  *   raw_words == 0: out is double [n_samples][n_dofs], b = sqrt(M_L) xi with
  *     u = (word + 1/2) 2^-32 and Box-Muller on the word pairs (0,1), (2,3):
- *     xi_a = sqrt(-2 ln u_a) cos(2 pi u_b), xi_b = sqrt(-2 ln u_a) sin(2 pi u_b).
+ *     xi_a = sqrt(-2 ln u_a) cos(2 pi u_b), xi_b = sqrt(-2 ln u_a) sin(2 pi u_b);
+ *   raw_words == 2: out is double [n_samples][n_dofs], the consistent-mass
+ *     noise W = R xi (see GRF_MASS_CONSISTENT; computed in FP32; at most 256
+ *     samples; uses the handle's workspace and synchronises nothing).
  * Asynchronous on `stream`. */
 int grf_noise(grf_graph* g, uint64_t seed, int64_t n_samples, void* out, int32_t raw_words,
               void* stream);

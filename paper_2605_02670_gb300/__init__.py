@@ -58,7 +58,7 @@ class grf_options(ctypes.Structure):
                 ("rtol", ctypes.c_double), ("timing", ctypes.c_int32),
                 ("pcg_layout", ctypes.c_int32), ("recover_sg", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("interior", ctypes.c_int32),
-                ("sweep", ctypes.c_int32)]
+                ("sweep", ctypes.c_int32), ("mass", ctypes.c_int32)]
 
     def knobs(self) -> dict:
         inv = {v: k for k, v in PCG_LAYOUTS.items()}
@@ -166,9 +166,13 @@ def timing_flag(timing) -> int:
     return GRF_TIMING_ONLY | sum(1 << grf_stats.PHASES.index(n) for n in set(names))
 
 
+GRF_MASS_LUMPED, GRF_MASS_CONSISTENT = 0, 1
+MASSES = {"lumped": GRF_MASS_LUMPED, "consistent": GRF_MASS_CONSISTENT}
+
+
 def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
                  timing=False, pcg_layout="auto", recover_sg=0, use_graph=False,
-                 precond="jacobi", interior="auto", sweep="auto") -> grf_options:
+                 precond="jacobi", interior="auto", sweep="auto", mass="lumped") -> grf_options:
     """timing: False, True (every phase) or phase names to time only those."""
     prec = {"fp64": GRF_FP64, "mixed": GRF_MIXED}[precision]
     if out_dtype is None:
@@ -176,7 +180,7 @@ def make_options(precision="fp64", out_dtype=None, rtol=0.0, max_iter=0,
     od = {"f64": GRF_OUT_F64, "f32": GRF_OUT_F32}[out_dtype]
     return grf_options(prec, PRECONDS[precond], od, int(max_iter), float(rtol),
                        timing_flag(timing), PCG_LAYOUTS[pcg_layout], int(recover_sg),
-                       1 if use_graph else 0, INTERIORS[interior], SWEEPS[sweep])
+                       1 if use_graph else 0, INTERIORS[interior], SWEEPS[sweep], MASSES[mass])
 
 
 # ------------------------------------------------------------ C-named functions
@@ -236,9 +240,11 @@ def grf_sample_host(handle, kappa, beta, k_step, seed, n_samples, out: np.ndarra
     return st.as_dict()
 
 
-def grf_noise(handle, seed, n_samples, out_ptr: int, raw_words: bool, stream=None) -> None:
+def grf_noise(handle, seed, n_samples, out_ptr: int, raw_words, stream=None) -> None:
+    """raw_words: 0 (or False) lumped noise in FP64, 1 (or True) the uint32
+    words, 2 the consistent-mass noise in FP64."""
     _check(_lib.grf_noise(handle, int(seed), int(n_samples), ctypes.c_void_p(out_ptr),
-                          1 if raw_words else 0, _stream(stream)))
+                          int(raw_words), _stream(stream)))
 
 
 def grf_apply(handle, kappa, alpha, gamma, weight, n_rhs, rhs_ptr: int, out_ptr: int,
@@ -394,10 +400,10 @@ class Graph:
     def sample(self, kappa, beta, k_step, seed, n_samples, precision="fp64", out_dtype=None,
                rtol=0.0, max_iter=0, out=None, stream=None, allow_noconv=False, timing=False,
                pcg_layout="auto", recover_sg=0, use_graph=False, precond="jacobi",
-               interior="auto", sweep="auto"):
+               interior="auto", sweep="auto", mass="lumped"):
         import torch
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            use_graph, precond, interior, sweep)
+                            use_graph, precond, interior, sweep, mass)
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         if out is None:
             out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
@@ -431,17 +437,21 @@ class Graph:
                                 stream, reps)
         return best.knobs(), ms
 
-    def noise(self, seed, n_samples, raw=False, stream=None):
+    def noise(self, seed, n_samples, raw=False, stream=None, mass="lumped"):
+        """raw: the uint32 Philox words; mass="consistent": W = R xi of the
+        consistent mass (FP64 output of the FP32 computation)."""
         import torch
         dt = torch.int32 if raw else torch.float64
         out = torch.empty((n_samples, self.n_dofs), dtype=dt, device="cuda")
-        grf_noise(self.handle, seed, n_samples, out.data_ptr(), raw, stream)
+        grf_noise(self.handle, seed, n_samples, out.data_ptr(),
+                  2 if mass == "consistent" else (1 if raw else 0), stream)
         return out
 
     def apply(self, kappa, alpha, gamma, weight, rhs, precision="fp64", out_dtype=None,
-              rtol=0.0, max_iter=0, stream=None, interior="auto", sweep="auto"):
+              rtol=0.0, max_iter=0, stream=None, interior="auto", sweep="auto", mass="lumped"):
         import torch
-        opts = make_options(precision, out_dtype, rtol, max_iter, interior=interior, sweep=sweep)
+        opts = make_options(precision, out_dtype, rtol, max_iter, interior=interior, sweep=sweep,
+                            mass=mass)
         rhs = rhs.to(dtype=torch.float64).contiguous()
         dt = torch.float64 if opts.out_dtype == GRF_OUT_F64 else torch.float32
         out = torch.empty(tuple(rhs.shape), dtype=dt, device="cuda")

@@ -127,6 +127,15 @@ struct grf_graph {
   int n_sm = 0;  // multiprocessors of that device
   const float* d_sqrt_ml_f = nullptr;  // FP32 copy of DevGraph::sqrt_ml (FP32 noise)
   void* dev_block = nullptr;
+  // Cholesky factor of the consistent mass's vertex Schur complement (CSR,
+  // FP32 on the device; built on first use of the consistent mass)
+  struct ConsPlan {
+    void* blk = nullptr;
+    const int64_t* rp = nullptr;
+    const int32_t* rc = nullptr;
+    const float* rv = nullptr;
+    const float* ones = nullptr;  // unit mass factors: the noise kernel's raw normals
+  } cons;
   // sine-transform plan of the tensor-core spectral path (built on first use,
   // for one sample padding at a time)
   struct DstPlan {
@@ -143,7 +152,7 @@ struct grf_graph {
   struct GraphCache {
     bool valid = false;
     int precision = 0, precond = 0, out_dtype = 0, pcg_layout = 0, recover_sg = 0, max_iter = 0;
-    bool spectral = false, spec_tc = false, spec_umma = false, timing = false;
+    bool spectral = false, spec_tc = false, spec_umma = false, consistent = false, timing = false;
     uint32_t phase_mask = 0;
     int sweep = 0;
     double rtol = 0, kappa = 0, beta = 0, k = 0;
@@ -197,6 +206,7 @@ struct grf_graph {
       if (lm.blk) cudaFree(lm.blk);
       if (host_out) cudaFree(host_out);
       if (dst.blk) cudaFree(dst.blk);
+      if (cons.blk) cudaFree(cons.blk);
       cudaSetDevice(cur);
     }
   }
@@ -423,6 +433,7 @@ struct Opts {
   bool spectral;   // edge interiors in the sine basis (mixed precision)
   bool spec_tc;    // ... with the transforms and contractions on the tensor cores
   bool spec_umma;  // ... with the sine transforms as tcgen05 products per edge length
+  bool consistent; // the consistent-mass comparison system (noise and operator)
   int sweep;       // GRF_SWEEP_* of the FP32 tridiagonal edges
 };
 
@@ -470,9 +481,124 @@ int read_opts(const grf_options* o, Opts* r) {
   r->spectral = r->precision == GRF_MIXED && in != GRF_INTERIOR_THOMAS;
   r->spec_tc = r->spectral && in == GRF_INTERIOR_SPECTRAL_TC;
   r->spec_umma = r->spectral && in == GRF_INTERIOR_SPECTRAL_UMMA;
+  const int mass = o ? o->mass : GRF_MASS_LUMPED;
+  if (mass != GRF_MASS_LUMPED && mass != GRF_MASS_CONSISTENT)
+    return fail(GRF_EINVAL, "unknown mass %d", mass);
+  r->consistent = mass == GRF_MASS_CONSISTENT;
+  if (r->consistent) {
+    if (r->precision != GRF_MIXED || r->precond != GRF_PRECOND_JACOBI ||
+        (in != GRF_INTERIOR_AUTO && in != GRF_INTERIOR_SPECTRAL_UMMA))
+      return fail(GRF_ENOTSUP,
+                  "the consistent mass runs with precision GRF_MIXED, GRF_PRECOND_JACOBI and "
+                  "the interior solver AUTO or SPECTRAL_UMMA");
+    r->spec_umma = r->spectral;
+  }
   r->sweep = o ? o->sweep : GRF_SWEEP_AUTO;
   if (r->sweep < GRF_SWEEP_AUTO || r->sweep > GRF_SWEEP_NODES)
     return fail(GRF_EINVAL, "unknown sweep layout %d", r->sweep);
+  return GRF_OK;
+}
+
+// Consistent-mass noise, set-up (once per graph): the vertex Schur complement
+// of the consistent mass, S_M = M_GG - M_GI M_II^-1 M_IG, from per-edge 2x2
+// blocks (on an edge M_II = tridiag(h/6, 2h/3, h/6) with the vertex couplings
+// h/6 and the edge's share h/3 of M_vv; with r = h/6 and cosh(theta) = 2 the
+// block is r sinh(theta) [[coth(n theta), (-1)^(n+1) csch(n theta)], ...]),
+// then its Cholesky factor in kept-vertex order by an envelope (skyline)
+// factorisation: row i holds columns first(i) .. i, first(i) its lowest
+// neighbour, and the fill stays inside the envelope. Refused above 2^27
+// envelope entries (the consistent mass of a graph without a narrow vertex
+// numbering: what makes the comparison system expensive).
+int ensure_cons_plan(grf_graph* g) {
+  if (g->cons.blk) return GRF_OK;
+  GRF_TRY(ensure_device(g));
+  const int32_t V = g->nv;
+  std::vector<double> diag(V, 0.0);
+  std::vector<int32_t> first(V);
+  for (int32_t v = 0; v < V; ++v) first[v] = v;
+  const double th = std::acosh(2.0), sh = std::sinh(th);
+  std::map<std::pair<int32_t, int32_t>, double> off;
+  for (int32_t e = 0; e < g->ne; ++e) {
+    const double r = g->he[e] / 6.0;
+    const int32_t n = g->nel[e];
+    const double q = std::exp(-(double)n * th);  // e^{-n theta}
+    const double coth = (1.0 + q * q) / (1.0 - q * q), csch = 2.0 * q / (1.0 - q * q);
+    const int32_t u = g->eu[e], v = g->ev[e];
+    diag[u] += r * sh * coth;
+    diag[v] += r * sh * coth;
+    const double b = ((n & 1) ? 1.0 : -1.0) * r * sh * csch;
+    const int32_t lo = std::min(u, v), hi = std::max(u, v);
+    off[{hi, lo}] += b;
+    first[hi] = std::min(first[hi], lo);
+  }
+  std::vector<int64_t> rp(V + 1, 0);
+  for (int32_t i = 0; i < V; ++i) rp[i + 1] = rp[i] + (i - first[i] + 1);
+  const int64_t nnz = rp[V];
+  if (nnz > ((int64_t)1 << 27))
+    return fail(GRF_ENOTSUP,
+                "the consistent-mass factor of this graph needs %lld envelope entries "
+                "(limit 2^27); number the vertices with a narrower band",
+                (long long)nnz);
+  std::vector<double> L((size_t)nnz, 0.0);
+  auto at = [&](int32_t i, int32_t j) -> double& { return L[(size_t)(rp[i] + (j - first[i]))]; };
+  for (int32_t i = 0; i < V; ++i) at(i, i) = diag[i];
+  for (auto& kv : off) at(kv.first.first, kv.first.second) = kv.second;
+  for (int32_t i = 0; i < V; ++i) {
+    for (int32_t j = first[i]; j < i; ++j) {
+      double acc = at(i, j);
+      const int32_t k0 = std::max(first[i], first[j]);
+      const double* li = &L[(size_t)(rp[i] + (k0 - first[i]))];
+      const double* lj = &L[(size_t)(rp[j] + (k0 - first[j]))];
+      for (int32_t k = 0; k < j - k0; ++k) acc -= li[k] * lj[k];
+      at(i, j) = acc / at(j, j);
+    }
+    double acc = at(i, i);
+    for (int32_t k = first[i]; k < i; ++k) acc -= at(i, k) * at(i, k);
+    if (!(acc > 0.0)) return fail(GRF_ENUMERIC, "consistent-mass factor: pivot %d is %g", i, acc);
+    at(i, i) = std::sqrt(acc);
+  }
+  std::vector<int32_t> rc((size_t)nnz);
+  std::vector<float> rv((size_t)nnz);
+  for (int32_t i = 0; i < V; ++i)
+    for (int32_t j = first[i]; j <= i; ++j) {
+      rc[(size_t)(rp[i] + (j - first[i]))] = j;
+      rv[(size_t)(rp[i] + (j - first[i]))] = (float)at(i, j);
+    }
+  Carve dry(nullptr);
+  dry.take<int64_t>(V + 1);
+  dry.take<int32_t>((size_t)nnz);
+  dry.take<float>((size_t)nnz);
+  dry.take<float>((size_t)g->n);
+  void* blk = nullptr;
+  CUDA_TRY(cudaMalloc(&blk, dry.off));
+  Carve c(blk);
+  int64_t* drp = c.take<int64_t>(V + 1);
+  int32_t* drc = c.take<int32_t>((size_t)nnz);
+  float* drv = c.take<float>((size_t)nnz);
+  float* ones = c.take<float>((size_t)g->n);
+  CUDA_TRY(cudaMemcpy(drp, rp.data(), sizeof(int64_t) * (V + 1), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(drc, rc.data(), sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(drv, rv.data(), sizeof(float) * (size_t)nnz, cudaMemcpyHostToDevice));
+  std::vector<float> one((size_t)g->n, 1.0f);
+  CUDA_TRY(cudaMemcpy(ones, one.data(), sizeof(float) * (size_t)g->n, cudaMemcpyHostToDevice));
+  g->cons.blk = blk;
+  g->cons.rp = drp;
+  g->cons.rc = drc;
+  g->cons.rv = drv;
+  g->cons.ones = ones;
+  return GRF_OK;
+}
+
+// The consistent mass needs every edge on the sine-basis path and a
+// fractional beta (the integer part would need the consistent mass between
+// the stiffness solves).
+int check_consistent(const grf_graph* g, const Opts& o, double beta, int64_t S) {
+  if (!o.consistent) return GRF_OK;
+  if (g->thomas_rest() > 0)
+    return fail(GRF_ENOTSUP, "the consistent mass needs every edge within 1024 interior nodes");
+  if (beta >= 1.0) return fail(GRF_ENOTSUP, "the consistent mass runs with 0 < beta < 1");
+  if (dst_gemm_sample_pad(S) == 0)
+    return fail(GRF_ENOTSUP, "the consistent mass runs with at most 256 samples per call");
   return GRF_OK;
 }
 
@@ -706,7 +832,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   SweepParams<T>* prm = (SweepParams<T>*)w.prm;
   if (sizeof(T) == 4 && o.spectral && w.bhat && g->thomas_rest() == 0) prm = nullptr;
   rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, prm,
-                                  (T*)w.dscale, (T*)w.offv_t, st);
+                                  (T*)w.dscale, (T*)w.offv_t, st, o.consistent);
   rs->end(1, st);
   rs->begin(2, st);
   if (sizeof(T) == 4) {
@@ -729,11 +855,13 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
                                             g->d_bin_edges[p] + head, tail, gvec, st);
+    if (o.consistent && !(spec && umma_ready(g, o, S)))
+      return fail(GRF_ENOTSUP, "the consistent mass needs the tensor-core sine transforms");
     if (spec && umma_ready(g, o, S)) {
       rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
                                                     w.status, g->n_sm, st);
       rs->launches += launch_spec_ends(g->d, nd, kappa2, S, g->d_spec_edges, g->spec_count,
-                                       w.bhat, gvec, st);
+                                       w.bhat, gvec, st, o.consistent);
     } else if (spec && o.spec_tc)
       rs->launches += launch_spec_condense_mma(g->d, nd, S, (const float*)b, g->d_spec_edges,
                                                g->spec_count, w.bhat, gvec, st);
@@ -818,7 +946,8 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
         g->d_bin_edges[p] + head, tail, out, st);
   if (spec && umma_ready(g, o, S)) {
     rs->launches += launch_spec_coef(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
-                                     g->spec_count, w.bhat, (const float*)w.xw, st);
+                                     g->spec_count, w.bhat, (const float*)w.xw, st,
+                                     o.consistent);
     rs->launches += launch_dst_gemm<true, OutT>(g->d, g->dst.dev, S, w.bhat, out, w.status,
                                                 g->n_sm, st);
   } else if (spec) {
@@ -884,6 +1013,7 @@ size_t sample_ws_bytes(const grf_graph* g, const std::vector<HostNodes>& stages,
   size_t tail = 0;
   for (auto& s : stages) tail = std::max(tail, apply_bytes(g, s.L(), S, tsize, o));
   if (stages.size() > 1) need += align_up((size_t)g->n * S * sizeof(double));
+  if (o.consistent) need += align_up((size_t)g->nv * S * sizeof(float));  // vertex noise
   return need + tail;
 }
 
@@ -899,9 +1029,17 @@ int enqueue_sample(grf_graph* g, const std::vector<HostNodes>& stages, double ka
   Carve c(g->ws);
   T* b = c.take<T>((size_t)g->n * S);
   double* tmp = multi ? c.take<double>((size_t)g->n * S) : nullptr;
+  float* wv = o.consistent ? c.take<float>((size_t)g->nv * S) : nullptr;
   void* ws_tail = g->ws ? (char*)g->ws + c.off : nullptr;
   rs->begin(0, st);
-  launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev, g->d_sqrt_ml_f);
+  if (sizeof(T) == 4 && o.consistent) {
+    // W = R xi of the consistent mass: unit-mass normals, then the factor
+    launch_noise_minor<float>(g->d, seed, S, (float*)b, st, seed_dev, g->cons.ones);
+    rs->launches += launch_cons_noise(g->d, S, (float*)b, wv, g->cons.rp, g->cons.rc,
+                                      g->cons.rv, g->n_sm, st);
+  } else {
+    launch_noise_minor<T>(g->d, seed, S, b, st, seed_dev, g->d_sqrt_ml_f);
+  }
   rs->end(0, st);
   rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
@@ -928,8 +1066,10 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
                 OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
+  GRF_TRY(check_consistent(g, o, beta, S));
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
+  if (o.consistent) GRF_TRY(ensure_cons_plan(g));
   return enqueue_sample<T, OutT>(g, stages, kappa, seed, S, out, o, st, rs);
 }
 
@@ -944,12 +1084,15 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
                       int64_t S, OutT* out, const Opts& o, cudaStream_t st, RunStats* rs) {
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
+  GRF_TRY(check_consistent(g, o, beta, S));
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
+  if (o.consistent) GRF_TRY(ensure_cons_plan(g));
   auto& gc = g->gc;
   const bool hit = gc.valid && gc.precision == o.precision && gc.out_dtype == o.out_dtype &&
                    gc.precond == o.precond && gc.spectral == o.spectral && gc.sweep == o.sweep &&
                    gc.spec_tc == o.spec_tc && gc.spec_umma == o.spec_umma &&
+                   gc.consistent == o.consistent &&
                    gc.timing == o.timing &&
                    gc.phase_mask == (o.timing ? o.phase_mask : 0u) &&
                    gc.pcg_layout == o.pcg_layout && gc.recover_sg == o.recover_sg &&
@@ -1009,6 +1152,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
     gc.spectral = o.spectral;
     gc.spec_tc = o.spec_tc;
     gc.spec_umma = o.spec_umma;
+    gc.consistent = o.consistent;
     gc.timing = o.timing;
     gc.phase_mask = o.timing ? o.phase_mask : 0u;
     gc.sweep = o.sweep;
@@ -1970,6 +2114,23 @@ int grf_noise(grf_graph* g, uint64_t seed, int64_t n_samples, void* out, int32_t
   if (n_samples == 0) return GRF_OK;
   if (!out) return fail(GRF_EINVAL, "out is null");
   GRF_TRY(ensure_device(g));
+  if (raw_words == 2) {  // consistent-mass noise W = R xi, FP32, written as double
+    if (n_samples > 256) return fail(GRF_EINVAL, "at most 256 samples of consistent noise");
+    GRF_TRY(ensure_cons_plan(g));
+    const size_t need = align_up((size_t)g->n * n_samples * 4) +
+                        align_up((size_t)g->nv * n_samples * 4);
+    GRF_TRY(ensure_ws(g, need));
+    Carve c(g->ws);
+    float* b = c.take<float>((size_t)g->n * n_samples);
+    float* wv = c.take<float>((size_t)g->nv * n_samples);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_noise_minor<float>(g->d, seed, n_samples, b, st, nullptr, g->cons.ones);
+    launch_cons_noise(g->d, n_samples, b, wv, g->cons.rp, g->cons.rc, g->cons.rv, g->n_sm, st);
+    launch_minor_to_major(g->n, n_samples, b, (double*)out, st);
+    CUDA_TRY(cudaGetLastError());
+    return GRF_OK;
+  }
+  if (raw_words != 0 && raw_words != 1) return fail(GRF_EINVAL, "raw_words must be 0, 1 or 2");
   launch_noise_major(g->d, seed, n_samples, out, raw_words != 0, (cudaStream_t)stream);
   CUDA_TRY(cudaGetLastError());
   return GRF_OK;
@@ -1998,6 +2159,9 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   hn.weight.assign(weight, weight + n_nodes);
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
+  if (o.consistent && (g->thomas_rest() > 0 || dst_gemm_sample_pad(n_rhs) == 0))
+    return fail(GRF_ENOTSUP, "the consistent mass needs every edge within 1024 interior nodes "
+                             "and at most 256 right-hand sides");
   GRF_TRY(ensure_ws(g, head + apply_bytes(g, hn.L(), n_rhs, ts, o)));
   if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, n_rhs));
   cudaStream_t st = (cudaStream_t)stream;

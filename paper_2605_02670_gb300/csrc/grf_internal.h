@@ -248,12 +248,23 @@ int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, in
 // every node from bhat (already transformed) added into gvec; the sine-basis
 // coefficients c of the recovery written over bhat (the inverse transform of
 // c is then the interior field).
+// consistent: the consistent-mass operator (interior constants transformed).
 int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                      const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
-                     double* gvec, cudaStream_t st);
+                     double* gvec, cudaStream_t st, bool consistent = false);
 int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                      const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
-                     const float* xw, cudaStream_t st);
+                     const float* xw, cudaStream_t st, bool consistent = false);
+
+// ---- consistent.cu: white noise of the consistent mass, W = R xi with the
+// Cholesky order interiors (edge by edge) then vertices. On entry b [n][S]
+// holds unit-mass standard normals; on return W. wv: [nv][S] scratch;
+// (rp, rc, rv): the lower factor of the vertex Schur complement of the mass
+// (CSR, kept-vertex order). Returns the launch count.
+int launch_cons_noise(const DevGraph& g, int64_t S, float* b, float* wv, const int64_t* rp,
+                      const int32_t* rc, const float* rv, int n_sm, cudaStream_t st);
+// out[s][j] = b[j][s] (FP32 sample-minor to FP64 sample-major)
+void launch_minor_to_major(int64_t n, int64_t S, const float* b, double* out, cudaStream_t st);
 
 // ---- dst_gemm.cu: sine transforms of edges grouped by interior-node count m,
 // as BF16-split products on the tcgen05 tensor cores.

@@ -402,7 +402,8 @@ constexpr int kEndsCta = 128;  // threads of the end-value kernel (two nodes eac
 template <int SG>
 __global__ void __launch_bounds__(kEndsCta, 4)
     spec_ends_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
-                     int32_t n_edges, const float* __restrict__ bhat, double* __restrict__ gvec) {
+                     int32_t n_edges, const float* __restrict__ bhat, double* __restrict__ gvec,
+                     int consistent) {
   extern __shared__ __align__(16) float ends_sm[];
   const int64_t nsg = (S + SG - 1) / SG;
   const int64_t units = (int64_t)n_edges * nsg;
@@ -435,20 +436,26 @@ __global__ void __launch_bounds__(kEndsCta, 4)
       const bool two = l1 < nd.L;
       const float dl0 = nd.shift[l0] * h2f;
       const float dl1 = two ? nd.shift[l1] * h2f : 1.f;
+      // consistent mass: T' = tridiag(-1, 2 + delta', -1) with
+      // delta' = delta / eps, eps = 1 - delta / 6, so
+      // 1 / (delta' + sig) = eps / (delta + sig eps) (no pole: delta (1 - sig/6)
+      // + sig > 0 for sig <= 4); the lumped case is eps = 1
+      const float ep0 = consistent ? 1.f - dl0 * (1.f / 6.f) : 1.f;
+      const float ep1 = consistent ? 1.f - dl1 * (1.f / 6.f) : 1.f;
       float od0[SG], ev0[SG], od1[SG], ev1[SG];
 #pragma unroll
       for (int s = 0; s < SG; ++s) od0[s] = ev0[s] = od1[s] = ev1[s] = 0.f;
       int32_t j = 0;
       for (; j + 1 < m; j += 2) {  // odd mode j + 1 into od, even mode j + 2 into ev
         const float sa = sig[j], sb = sig[j + 1];
-        spec_acc2<SG>(__fdividef(1.f, dl0 + sa), __fdividef(1.f, dl1 + sa), bt + (size_t)j * SG,
-                      od0, od1);
-        spec_acc2<SG>(__fdividef(1.f, dl0 + sb), __fdividef(1.f, dl1 + sb),
+        spec_acc2<SG>(__fdividef(ep0, fmaf(sa, ep0, dl0)), __fdividef(ep1, fmaf(sa, ep1, dl1)),
+                      bt + (size_t)j * SG, od0, od1);
+        spec_acc2<SG>(__fdividef(ep0, fmaf(sb, ep0, dl0)), __fdividef(ep1, fmaf(sb, ep1, dl1)),
                       bt + (size_t)(j + 1) * SG, ev0, ev1);
       }
       if (j < m)
-        spec_acc2<SG>(__fdividef(1.f, dl0 + sig[j]), __fdividef(1.f, dl1 + sig[j]),
-                      bt + (size_t)j * SG, od0, od1);
+        spec_acc2<SG>(__fdividef(ep0, fmaf(sig[j], ep0, dl0)),
+                      __fdividef(ep1, fmaf(sig[j], ep1, dl1)), bt + (size_t)j * SG, od0, od1);
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         if (q == 1 && !two) break;
@@ -473,13 +480,15 @@ __global__ void __launch_bounds__(kEndsCta, 4)
 template <int SG>
 __global__ void __launch_bounds__(kEndsThreads)
     spec_coef_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
-                     int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw) {
+                     int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw,
+                     int consistent) {
   extern __shared__ __align__(16) float coef_sm[];
   const int32_t L = nd.L;
   float* xp = coef_sm;                     // [L][SG] xa + xb
   float* xm = xp + (size_t)L * SG;         // [L][SG] xa - xb
   float* dls = xm + (size_t)L * SG;        // [L] delta_l
   float* scs = dls + L;                    // [L] sc_l
+  float* eps = scs + L;                    // [L] 1 - delta_l / 6 (consistent mass) or 1
   const int64_t nsg = (S + SG - 1) / SG;
   const int64_t units = (int64_t)n_edges * nsg;
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
@@ -495,6 +504,7 @@ __global__ void __launch_bounds__(kEndsThreads)
     for (int32_t l = threadIdx.x; l < L; l += blockDim.x) {
       dls[l] = nd.shift[l] * h2f;
       scs[l] = nd.wgam[l] * hf;
+      eps[l] = consistent ? 1.f - dls[l] * (1.f / 6.f) : 1.f;
     }
     for (int32_t t = threadIdx.x; t < L * SG; t += blockDim.x) {
       const int32_t l = t / SG, s = t - l * SG;
@@ -522,12 +532,14 @@ __global__ void __launch_bounds__(kEndsThreads)
       float C0[SG], C1[SG], D0 = 0.f, D1 = 0.f;
 #pragma unroll
       for (int s = 0; s < SG; ++s) C0[s] = C1[s] = 0.f;
+      // consistent mass: sc' / mu' = sc / (delta + sig eps) and the couplings'
+      // 1 / mu' = eps / (delta + sig eps) (eps = 1: lumped)
       for (int32_t l = 0; l < L; ++l) {
-        const float dl = dls[l], sc = scs[l];
-        const float r0 = __fdividef(1.f, dl + s0f), r1 = __fdividef(1.f, dl + s1f);
+        const float dl = dls[l], sc = scs[l], ep = eps[l];
+        const float r0 = __fdividef(1.f, fmaf(s0f, ep, dl)), r1 = __fdividef(1.f, fmaf(s1f, ep, dl));
         D0 = fmaf(sc, r0, D0);
         D1 = fmaf(sc, r1, D1);
-        spec_acc2<SG>(r0, r1, X + (size_t)l * SG, C0, C1);
+        spec_acc2<SG>(r0 * ep, r1 * ep, X + (size_t)l * SG, C0, C1);
       }
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
@@ -643,7 +655,7 @@ template int launch_spec_recover<double>(const DevGraph&, const DevNodes&, doubl
 
 int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                      const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
-                     double* gvec, cudaStream_t st) {
+                     double* gvec, cudaStream_t st, bool consistent) {
   (void)kappa2;
   int32_t n = 0;
   for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
@@ -656,24 +668,24 @@ int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
   const int64_t cap = (int64_t)152 * 16;
   spec_ends_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsCta, smem, st>>>(
-      g, nd, S, bin_edges, n, bhat, gvec);
+      g, nd, S, bin_edges, n, bhat, gvec, consistent ? 1 : 0);
   return 1;
 }
 
 int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                      const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
-                     const float* xw, cudaStream_t st) {
+                     const float* xw, cudaStream_t st, bool consistent) {
   (void)kappa2;
   int32_t n = 0;
   for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
   if (n <= 0) return 0;
-  const size_t smem = ((size_t)nd.L * (2 * kSpecSG + 2)) * sizeof(float);
+  const size_t smem = ((size_t)nd.L * (2 * kSpecSG + 3)) * sizeof(float);
   cudaFuncSetAttribute(spec_coef_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
   const int64_t cap = (int64_t)152 * 8;
   spec_coef_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsThreads, smem, st>>>(
-      g, nd, S, bin_edges, n, bhat, xw);
+      g, nd, S, bin_edges, n, bhat, xw, consistent ? 1 : 0);
   return 1;
 }
 

@@ -195,6 +195,20 @@ def test_interior_and_sweep_options_checked_before_device_work():
             grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0,
                            grf.make_options("fp64", interior=interior), stream=0)
         assert ei.value.code == grf.GRF_ENOTSUP
+    # the consistent mass (the comparison system): mixed precision, Jacobi and
+    # the tensor-core sine path only; unknown mass values are invalid
+    bad_mass = grf.make_options("mixed")
+    bad_mass.mass = 5
+    with pytest.raises(grf.GrfError) as ei:
+        grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0, bad_mass, stream=0)
+    assert ei.value.code == grf.GRF_EINVAL
+    for kw in ({"precision": "fp64"}, {"precision": "mixed", "interior": "thomas"},
+               {"precision": "mixed", "interior": "spectral_tc"},
+               {"precision": "mixed", "precond": "neumann"}):
+        with pytest.raises(grf.GrfError) as ei:
+            grf.grf_sample(G.handle, 1.0, 0.5, 0.3, 1, 2, 0,
+                           grf.make_options(mass="consistent", **kw), stream=0)
+        assert ei.value.code == grf.GRF_ENOTSUP
     assert grf.make_options("mixed", interior="spectral_tc", sweep="nodes").knobs() == {
         "pcg_layout": "auto", "recover_sg": 0, "interior": "spectral_tc", "sweep": "nodes"}
 
