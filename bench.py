@@ -199,16 +199,16 @@ def _wdict(w):
             "seed": w.seed, "n_samples": w.n_samples}
 
 
-def oracle_sample(w, graph, n_nodes_sample=2, parallel=False):
+def oracle_sample(w, graph, n_nodes_sample=8, parallel=False):
     """Time the FP64 oracle on a bounded sample of the workload: mesh, assembly
     and noise for all samples, then `n_nodes_sample` of the L quadrature nodes
     (spread over the range), each factorised once and solved for every sample;
     extrapolated linearly in the node count (and by the DOF ratio when a
     smaller graph of the family stands in). parallel: the paper's
-    parallelisation, quadrature nodes spread over every host core (one process
-    each, started with spawn); each core's share is then ceil(L / cores)
-    nodes after its own assembly."""
-    import math as _m
+    parallelisation, every quadrature node, dealt round-robin over every host
+    core (one process each, started with spawn), each core after its own
+    assembly; the time is the slowest core's (only the DOF ratio is
+    extrapolated)."""
     g, mesh, scale = oracle_graph(w, graph)
     # beta >= 1: one more factorisation per integer power, timed like a node
     Lq = quad_count(w.beta, w.k_step)
@@ -223,17 +223,19 @@ def oracle_sample(w, graph, n_nodes_sample=2, parallel=False):
     else:
         import concurrent.futures as cf
         import multiprocessing as mp
-        cores = os.cpu_count() or 1
-        pick = np.linspace(0, Lq - 1, cores).round().astype(int).tolist()
+        cores = min(os.cpu_count() or 1, Lq)
+        shares = [list(range(c, Lq, cores)) for c in range(cores)]
         os.environ.setdefault("OMP_NUM_THREADS", "1")
         # a worker that dies raises BrokenProcessPool here instead of hanging
         with cf.ProcessPoolExecutor(cores, mp_context=mp.get_context("spawn")) as ex:
-            futs = [ex.submit(_oracle_nodes, _wdict(w), g, [i]) for i in pick]
-            res = [f.result(timeout=600) for f in futs]
-        t_fixed = max(r[0] for r in res)
+            futs = [ex.submit(_oracle_nodes, _wdict(w), g, ids) for ids in shares]
+            res = [f.result(timeout=900) for f in futs]
+        per_core = [r[0] + r[1] * len(ids) for r, ids in zip(res, shares)]
+        # beta >= 1: the integer powers run after the sum, one solve each
         t_node = max(r[1] for r in res)
-        total = (t_fixed + t_node * _m.ceil(L / cores)) * scale
-        how = f"{cores} of {L} quadrature nodes at once, one per core (spawned processes)"
+        total = (max(per_core) + t_node * (L - Lq)) * scale
+        how = (f"all {Lq} quadrature nodes dealt round-robin over {cores} cores (spawned "
+               f"processes; the slowest core's time)")
     wall = time.perf_counter() - t0
     where = (f"{w.name}" if scale == 1.0 else
              f"a {mesh.n_dofs}-DOF graph of the {w.name} family (same parameters and mesh "
@@ -278,7 +280,7 @@ def algorithmic(w, G, stats, phase, S, tsize, out_size, l2_bytes=L2_BYTES):
     """Algorithmic bytes (or flops) of one launch of a phase, from the
     method's per-unit figures (b = bytes per value of the phase's arithmetic:
     4 in mixed precision, 8 in FP64):
-    noise: writes N S b and reads the N FP64 mass factors;
+    noise: writes N S b and reads the N mass factors (b bytes each);
     PCG, per system-iteration: 4 (|V| + 2|E|) + 10 |V| flops; when the vertex
     vectors of all systems exceed L2, 10 |V| b bytes of vector traffic plus the
     node's matrix, (|V| + |E|) (8 + 4) bytes, shared over the S samples;
@@ -289,7 +291,7 @@ def algorithmic(w, G, stats, phase, S, tsize, out_size, l2_bytes=L2_BYTES):
     N, V, E, NI = G.n_dofs, G.n_kept, G.n_edges, G.n_interior
     L = stats["n_nodes"]
     if phase == "noise":
-        return N * S * tsize + N * 8, "hbm"
+        return N * S * tsize + N * tsize, "hbm"
     if phase == "pcg":
         it = stats["pcg_iters_total"]
         if L * S * V * 8 <= l2_bytes:
@@ -350,8 +352,9 @@ def accuracy_checks(args, w, graph, G, out, seed, prec, knobs):
     Sc = min(4, w.n_samples)
     uc, _ = Gc.sample(w.kappa, w.beta, w.k_step, w.seed, Sc, precision=prec, out_dtype="f64",
                       use_graph=args.use_graph, **knobs)
-    res["_check"] = (cg, ne, Sc, uc.cpu().numpy(), Gc.n_dofs)
-    if prec == "mixed":
+    mass = knobs.get("mass", "lumped")
+    res["_check"] = (cg, ne, Sc, uc.cpu().numpy(), Gc.n_dofs, mass)
+    if prec == "mixed" and mass == "lumped":
         S2 = 2
         u64, _ = G.sample(w.kappa, w.beta, w.k_step, seed, S2, precision="fp64")
         mlf = ml_weights(graph, grf.mesh_elements(graph.lengths, w.h, w.clip), G)
@@ -376,10 +379,13 @@ def accuracy_checks(args, w, graph, G, out, seed, prec, knobs):
 def oracle_check(w, check):
     """CPU leg: the oracle's field on the small check graph and the relative
     M_L-weighted L2 error of the GPU's field there."""
-    from oracle import fem, sampler
-    cg, ne, Sc, uc, n = check
-    m, ref, _ = sampler.sample(cg, w.kappa, w.beta, w.k_step, w.seed, Sc, n_elems=ne)
-    return {"rel_l2": _rel_l2(uc, ref, fem.lumped_mass(m)),
+    from oracle import consistent, fem, sampler
+    cg, ne, Sc, uc, n, mass = check
+    if mass == "consistent":
+        m, ref, _ = consistent.sample(cg, w.kappa, w.beta, w.k_step, w.seed, Sc, n_elems=ne)
+    else:
+        m, ref, _ = sampler.sample(cg, w.kappa, w.beta, w.k_step, w.seed, Sc, n_elems=ne)
+    return {"rel_l2": _rel_l2(uc, ref, fem.lumped_mass(m)), "mass": mass,
             "graph": f"{w.graph_args['kind']} family, {n} DOFs, {Sc} samples, every node"}
 
 
@@ -433,11 +439,20 @@ def run_grf(args, w, graph):
                  "loss_first": float(hist[0]), "loss_last": float(hist[-1])}
     knobs = {"pcg_layout": args.pcg_layout, "recover_sg": args.recover_sg}
     tune_ms = None
+    if args.mass == "consistent":
+        # the comparison system runs only on the tensor-core sine-basis
+        # interiors; the autotuner times lumped-mass calls, so it is skipped
+        if prec != "mixed":
+            raise SystemExit("--mass consistent needs mixed precision")
+        args.autotune = False
+        args.interior = args.interior or "spectral_umma"
     if args.autotune and args.pcg_layout == "auto" and args.recover_sg == 0:
         # launch-schedule autotuner (setup, outside the timed region)
         knobs, tune_ms = G.autotune(w.kappa, w.beta, w.k_step, S, precision=prec,
                                     out_dtype=out_dtype, reps=2, precond=args.precond)
     knobs["precond"] = args.precond
+    if args.mass != "lumped":
+        knobs["mass"] = args.mass
     if args.interior:
         knobs["interior"] = args.interior
     if args.sweep:
@@ -541,7 +556,9 @@ def run_grf(args, w, graph):
                    "condense": ("spectral_mma.cu" if interior == "spectral_tc" else
                                 ("dst_gemm.cu" if interior == "spectral_umma" else "spectral.cu"))
                    if spectral else ("thomas.cu" if segments else "sweep.cu"),
-                   "pcg": "pcg.cu", "recover": "spectral.cu" if spectral else
+                   "pcg": ("pcg_batch.cu" if G.n_kept > 4096 and args.precond == "jacobi" and
+                           knobs.get("pcg_layout") != "per_system" else "pcg.cu"),
+                   "recover": "spectral.cu" if spectral else
                    ("recover.cu" if segments else "sweep.cu"),
                    "precond_net": "learned.cu"}.get(dom, "api.cu")
     if bound == "hbm":
@@ -582,7 +599,9 @@ def run_grf(args, w, graph):
     }
     if accuracy and accuracy.get("fp64_form"):
         line["speedup_vs_fp64_form"] = value / accuracy["fp64_form"]["value"]
-    if not args.no_cpu_baseline and world == 1:
+    if args.mass != "lumped":
+        line["config"]["mass"] = args.mass
+    if not args.no_cpu_baseline and world == 1 and args.mass == "lumped":
         # the paper's parallelisation (quadrature nodes over every host core),
         # and beside it the single-thread figure (its instruction counts are
         # single-threaded)
@@ -626,6 +645,9 @@ def main():
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--no-graph", dest="use_graph", action="store_false",
                     help="direct calls instead of replaying each call as a captured CUDA graph")
+    ap.add_argument("--mass", default="lumped", choices=["lumped", "consistent"],
+                    help="mass matrix of noise and operator: the method's lumped mass, or "
+                         "the consistent-mass comparison system (mixed precision)")
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "neumann", "learned"],
                     help="vertex PCG preconditioner (mixed precision for learned; the "
                          "learned network is trained on the workload before timing)")

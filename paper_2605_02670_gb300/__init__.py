@@ -416,9 +416,9 @@ class Graph:
     def sample_host(self, kappa, beta, k_step, seed, n_samples, precision="fp64",
                     out_dtype=None, rtol=0.0, max_iter=0, out=None, stream=None, timing=False,
                     precond="jacobi", pcg_layout="auto", recover_sg=0, interior="auto",
-                    use_graph=False, sweep="auto"):
+                    use_graph=False, sweep="auto", mass="lumped"):
         opts = make_options(precision, out_dtype, rtol, max_iter, timing, pcg_layout, recover_sg,
-                            use_graph, precond=precond, interior=interior, sweep=sweep)
+                            use_graph, precond=precond, interior=interior, sweep=sweep, mass=mass)
         dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
         if out is None:
             out = np.empty((n_samples, self.n_dofs), dtype=dt)

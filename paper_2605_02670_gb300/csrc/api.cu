@@ -307,7 +307,7 @@ int ensure_device(grf_graph* g) {
   d.vptr = vptr; d.adj_edge = ae; d.adj_nbr = an; d.adj_rev = arev; d.sqrt_ml = sml;
   g->d_order = VertexOrder{rperm, rvptr, rnbr, rinc};
   int64_t blocks = (g->n + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   float* smlf = k.take<float>((size_t)g->n);
   g->d_sqrt_ml_f = smlf;
   sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml, smlf);

@@ -106,7 +106,7 @@ __global__ void minor_to_major_kernel(int64_t n, int64_t S, const float* __restr
 }  // namespace
 
 void launch_minor_to_major(int64_t n, int64_t S, const float* b, double* out, cudaStream_t st) {
-  minor_to_major_kernel<<<blocks_for(n * S, 256, 152), 256, 0, st>>>(n, S, b, out);
+  minor_to_major_kernel<<<blocks_for(n * S, 256, sm_count()), 256, 0, st>>>(n, S, b, out);
 }
 
 int launch_cons_noise(const DevGraph& g, int64_t S, float* b, float* wv, const int64_t* rp,

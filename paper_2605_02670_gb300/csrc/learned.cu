@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) record_pairs_kernel(
 
 int grid_for(int64_t total, int threads) {
   int64_t blocks = (total + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   return blocks < 1 ? 1 : (int)blocks;
 }
 
@@ -591,7 +591,7 @@ int lp_forward(const DevGraph& g, int32_t Lb, const int32_t* lnode, const float*
                const double* alpha, const double* gamma, const float* P,
                const __nv_bfloat16* wb, const LpActs& a, cudaStream_t st) {
   const int64_t M = (int64_t)Lb * g.nv;
-  const int gb = (int)((M + 63) / 64 < 152 * 16 ? (M + 63) / 64 : 152 * 16);
+  const int gb = (int)((M + 63) / 64 < sm_count() * 16 ? (M + 63) / 64 : sm_count() * 16);
   features_kernel<<<grid_for(M, 256), 256, 0, st>>>(g, Lb, lnode, offv_t, alpha, gamma, a.X0);
   // h0 = relu(x W0 + b0), also the left half of the layer-1 input
   gemm_kernel<64><<<gb, 128, 0, st>>>(M, 16, a.X0, 16, wb, P + kOffB0, 1, a.H[0], 64, a.Xc[0],
@@ -626,7 +626,7 @@ void lp_backward(const DevGraph& g, int32_t Lb, const int32_t* lnode, const floa
                                             a.n, b.scratch, b.ds, b.dn, loss, inv_p);
   heads_bwd_kernel<<<grid_for(M * 32, 256), 256, 0, st>>>(g, Lb, lnode, offv_t, a.H[kLayers], P,
                                                         b.ds, b.dn, b.dH, G);
-  const int gb = (int)((M + 63) / 64 < 152 * 16 ? (M + 63) / 64 : 152 * 16);
+  const int gb = (int)((M + 63) / 64 < sm_count() * 16 ? (M + 63) / 64 : sm_count() * 16);
   const int64_t chunk = 1024;
   const int cb = (int)((M + chunk - 1) / chunk);
   for (int i = kLayers; i >= 1; --i) {

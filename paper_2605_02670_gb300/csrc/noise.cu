@@ -119,7 +119,7 @@ __global__ void noise_major_kernel(DevGraph g, uint64_t seed, int64_t S, void* o
 
 int grid_for(int64_t total, int threads) {
   int64_t blocks = (total + threads - 1) / threads;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > sm_count() * 64) blocks = sm_count() * 64;
   return blocks < 1 ? 1 : (int)blocks;
 }
 
@@ -135,7 +135,7 @@ void launch_noise_minor(const DevGraph& g, uint64_t seed, int64_t S, T* b, cudaS
   const int64_t nq = (g.n + 3) / 4;
   int64_t bx = (nq + rows - 1) / rows;
   const int64_t by = (S + SB - 1) / SB;
-  int64_t cap = 152 * 32 / by;
+  int64_t cap = sm_count() * 32 / by;
   if (cap < 1) cap = 1;
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;

@@ -17,7 +17,8 @@
 // entries offv_k / sqrt(D_v D_w) stored in FP32: every FP32 quantity is then
 // O(1) whatever the shift (the raw entries span 1e-30 .. 1e+34 over the
 // quadrature nodes). CG on the scaled matrix is Jacobi-PCG on S. The inner
-// solve stops at a relative 1e-4 or when the FP32 recurrence stops improving;
+// solve stops at a relative 1e-5 (or a tenth of the reduction still needed) or
+// when the FP32 recurrence stops improving;
 // the stopping test is always on the FP64 residual, whose norms are FP64 dot
 // products. The inner correction solve keeps its own dots and scalars (alpha,
 // beta) in FP32. On GB300 FP64 arithmetic runs at a small fraction of the FP32
@@ -1422,7 +1423,7 @@ void launch_group_pre(const DevGraph& g, int32_t L, int64_t S, const double* dia
   cudaFuncSetAttribute(pcg_group_pre_kernel<NT, VPT, SGP, PRE>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
-  const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
+  const int blocks = (int)(units < sm_count() * 8 ? units : sm_count() * 8);
   pcg_group_pre_kernel<NT, VPT, SGP, PRE><<<blocks, NT, dyn, st>>>(
       g, L, S, diag, offv, dscale_t, offv_t, pc, pn, gvec, x, rtol, max_iter, iters, status);
 }
@@ -1449,7 +1450,7 @@ void launch_group(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t 
   cudaFuncSetAttribute(pcg_group_kernel<NT, VPT, SGP>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   const int64_t units = (int64_t)L * ((S + SGP - 1) / SGP);
-  const int blocks = (int)(units < 152 * 8 ? units : 152 * 8);
+  const int blocks = (int)(units < sm_count() * 8 ? units : sm_count() * 8);
   pcg_group_kernel<NT, VPT, SGP><<<blocks, NT, dyn, st>>>(
       g, ord, L, S, diag, offv, dscale_t, offv_t, gvec, x, rtol, max_iter, iters, status);
 }
@@ -1524,7 +1525,7 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
       return;
     }
   }
-  int blocks = (int)(nsys < 152 * 16 ? nsys : 152 * 16);
+  int blocks = (int)(nsys < sm_count() * 16 ? nsys : sm_count() * 16);
   if (blocks < 1) blocks = 1;
   const size_t smem = (sizeof(VT) == 4 ? sizeof(double) : 0) * (size_t)g.nv +
                       (pre == kPreLearned ? 5 : 4) * sizeof(VT) * (size_t)g.nv;
@@ -1537,7 +1538,7 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
         iters, status);
   } else {
     constexpr int kNT = kThreadsL;
-    int gb = (int)(nsys < 152 * (2048 / kNT) * 2 ? nsys : 152 * (2048 / kNT) * 2);
+    int gb = (int)(nsys < sm_count() * (2048 / kNT) * 2 ? nsys : sm_count() * (2048 / kNT) * 2);
     if (gb < 1) gb = 1;
     pcg_kernel<VT, false, kNT><<<gb, kNT, 0, st>>>(g, L, S, diag, offv, dscale_t, offv_t, pre, pc,
                                                   pn, gvec, x, d, r, p, q, y, rtol, max_iter,

@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(32 * NW * UPC)
 
 int grid_for(int64_t units, int upc) {
   int64_t blocks = (units + upc - 1) / upc;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   return blocks < 1 ? 1 : (int)blocks;
 }
 

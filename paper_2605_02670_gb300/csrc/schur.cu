@@ -160,7 +160,7 @@ __global__ void nn_coeff_kernel(DevGraph g, int32_t L, const double* __restrict_
 
 int grid_for(int64_t total, int threads) {
   int64_t blocks = (total + threads - 1) / threads;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   return blocks < 1 ? 1 : (int)blocks;
 }
 

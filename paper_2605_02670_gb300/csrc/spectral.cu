@@ -384,7 +384,7 @@ __global__ void node_consts_kernel(DevNodes nd, double kappa2, float* __restrict
 }
 
 int grid_units(int64_t units) {
-  int64_t b = units < 152 * 16 ? units : 152 * 16;
+  int64_t b = units < sm_count() * 16 ? units : sm_count() * 16;
   return b < 1 ? 1 : (int)b;
 }
 
@@ -569,7 +569,7 @@ constexpr int kNumSpecBins = sizeof(kSpecBins) / sizeof(kSpecBins[0]);
 void launch_node_consts(const DevNodes& nd, double kappa2, float* shift, float* wgam,
                         cudaStream_t st) {
   int blocks = (nd.L + 255) / 256;
-  if (blocks > 152) blocks = 152;
+  if (blocks > sm_count()) blocks = sm_count();
   node_consts_kernel<<<blocks < 1 ? 1 : blocks, 256, 0, st>>>(nd, kappa2, shift, wgam);
 }
 
@@ -666,7 +666,7 @@ int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64
   cudaFuncSetAttribute(spec_ends_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  const int64_t cap = (int64_t)152 * 16;
+  const int64_t cap = (int64_t)sm_count() * 16;
   spec_ends_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsCta, smem, st>>>(
       g, nd, S, bin_edges, n, bhat, gvec, consistent ? 1 : 0);
   return 1;
@@ -683,7 +683,7 @@ int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64
   cudaFuncSetAttribute(spec_coef_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  const int64_t cap = (int64_t)152 * 8;
+  const int64_t cap = (int64_t)sm_count() * 8;
   spec_coef_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsThreads, smem, st>>>(
       g, nd, S, bin_edges, n, bhat, xw, consistent ? 1 : 0);
   return 1;

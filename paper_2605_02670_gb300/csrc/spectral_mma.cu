@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(32 * NW)
 }
 
 int grid_units(int64_t units) {
-  int64_t b = units < 152 * 16 ? units : 152 * 16;
+  int64_t b = units < sm_count() * 16 ? units : sm_count() * 16;
   return b < 1 ? 1 : (int)b;
 }
 

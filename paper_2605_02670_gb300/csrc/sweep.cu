@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(32 * kWarps, min_blocks(NL))
 
 int grid_units(int64_t units) {
   int64_t blocks = (units + kWarps - 1) / kWarps;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks > sm_count() * 16) blocks = sm_count() * 16;
   return blocks < 1 ? 1 : (int)blocks;
 }
 

@@ -28,7 +28,7 @@ constexpr int kSG = 4;  // samples per thread: pivots are shared across them
 
 int grid_for(int64_t total, int threads) {
   int64_t blocks = (total + threads - 1) / threads;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > sm_count() * 64) blocks = sm_count() * 64;
   return blocks < 1 ? 1 : (int)blocks;
 }
 
@@ -354,7 +354,7 @@ int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_
   const size_t smem = (size_t)(stage_max > 0 ? stage_max : 1) * kSG * sizeof(T);
   cudaFuncSetAttribute(condense_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (int64_t)n_edges * nsg;
-  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks > sm_count() * 64) blocks = sm_count() * 64;
   condense_kernel<T><<<(int)blocks, threads, smem, st>>>(g, nd, kappa2, S, b, gvec, stage_max,
                                                          edges, n_edges);
   return 2;

@@ -54,7 +54,7 @@ def test_noise_recovery_condensation_and_schur_work():
     G = _workload(V=10, E=12, NI=1000)
     stats = {"n_nodes": 7, "pcg_iters_total": 0}
     S = 3
-    assert bench.algorithmic(None, G, stats, "noise", S, 4, 4) == (1010 * 3 * 4 + 1010 * 8, "hbm")
+    assert bench.algorithmic(None, G, stats, "noise", S, 4, 4) == (1010 * 3 * 4 + 1010 * 4, "hbm")
     # condensation + recovery: 12 flops per (interior node, node, sample), 4 + 8
     assert bench.algorithmic(None, G, stats, "recover", S, 4, 4) == (8.0 * 1000 * 7 * 3, "alu")
     assert bench.algorithmic(None, G, stats, "condense", S, 4, 4) == (4.0 * 1000 * 7 * 3, "alu")

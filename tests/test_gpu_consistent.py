@@ -99,3 +99,12 @@ def test_consistent_refusals():
     with pytest.raises(grf.GrfError) as ei:  # an edge beyond the sine-basis path
         GL.sample(2.0, 0.6, 0.5, 1, 2, precision="mixed", mass="consistent")
     assert ei.value.code == grf.GRF_ENOTSUP
+
+
+def test_mass_comparison_harness_small_graph():
+    from paper_2605_02670_gb300 import mass_comparison as mc
+    row = mc.compare(100, S=4, reps=1)
+    assert row["n_dofs"] == 100 + 63 * row["n_edges"]
+    for mass in ("lumped", "consistent"):
+        assert row[mass]["call_ms"] > 0 and row[mass]["noise_ms"] > 0
+    assert row["consistent_over_lumped"]["full"] > 0
