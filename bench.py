@@ -14,6 +14,7 @@ replicas, seed offset by rank): weak scaling, no collective on the data path.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -579,7 +580,8 @@ def run_grf(args, w, graph):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if prec == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "n_dofs": G.n_dofs, "n_vertices": G.n_kept,
+        "config": {"workload": w.name, "kappa": w.kappa, "beta": w.beta, "k_step": w.k_step,
+                   "n_dofs": G.n_dofs, "n_vertices": G.n_kept,
                    "n_edges": G.n_edges, "quadrature_nodes": L, "samples_per_gpu": S,
                    "precision": prec, "l2": "flushed between timed steps",
                    "knobs": knobs, "autotune_ms": tune_ms, "cuda_graph": args.use_graph,
@@ -652,8 +654,15 @@ def main():
                     help="vertex PCG preconditioner (mixed precision for learned; the "
                          "learned network is trained on the workload before timing)")
     ap.add_argument("--train-epochs", type=int, default=40)
+    ap.add_argument("--kappa", type=float, default=None,
+                    help="override the workload's kappa (same graph and mesh)")
+    ap.add_argument("--beta", type=float, default=None,
+                    help="override the workload's beta (same graph and mesh)")
     args = ap.parse_args()
     w = gi.WORKLOADS[args.workload]
+    if args.kappa is not None or args.beta is not None:
+        w = dataclasses.replace(w, kappa=w.kappa if args.kappa is None else args.kappa,
+                                beta=w.beta if args.beta is None else args.beta)
     graph = w.graph()
     if args.impl == "reference":
         run_reference(args, w, graph)

@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrf.so")
 SOURCES = ["api.cu", "noise.cu", "schur.cu", "thomas.cu", "recover.cu", "sweep.cu", "pcg.cu", "pcg_batch.cu",
            "learned.cu", "spectral.cu", "spectral_mma.cu",
-           "dst_gemm.cu", "consistent.cu"]
+           "dst_gemm.cu", "consistent.cu", "spec_umma.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
          "--expt-relaxed-constexpr"]

@@ -126,6 +126,10 @@ struct grf_graph {
   int device = -1;
   int n_sm = 0;  // multiprocessors of that device
   const float* d_sqrt_ml_f = nullptr;  // FP32 copy of DevGraph::sqrt_ml (FP32 noise)
+  // per vertex its first four neighbours (int4, padded with itself), then per
+  // vertex the start of its incidence list and its degree (int2): the batched
+  // PCG's gathers
+  const int4* d_ell = nullptr;
   void* dev_block = nullptr;
   // Cholesky factor of the consistent mass's vertex Schur complement (CSR,
   // FP32 on the device; built on first use of the consistent mass)
@@ -250,6 +254,7 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(2 * E);
   c.take<int32_t>(V); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   c.take<float>((size_t)g->n);
+  c.take<int4>(2 * V);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -310,6 +315,21 @@ int ensure_device(grf_graph* g) {
   if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   float* smlf = k.take<float>((size_t)g->n);
   g->d_sqrt_ml_f = smlf;
+  {
+    // V int4 (neighbours) then V int2 (incidence-list start, degree)
+    int4* ell = k.take<int4>(2 * V);
+    std::vector<int4> h(2 * V);
+    int2* info = reinterpret_cast<int2*>(h.data() + V);
+    for (size_t v = 0; v < V; ++v) {
+      const int32_t k0 = g->vptr[v], deg = g->vptr[v + 1] - k0;
+      int32_t w[4];
+      for (int i = 0; i < 4; ++i) w[i] = i < deg ? g->adj_nbr[k0 + i] : (int32_t)v;
+      h[v] = make_int4(w[0], w[1], w[2], w[3]);
+      info[v] = make_int2(k0, deg);
+    }
+    CUDA_TRY(cudaMemcpy(ell, h.data(), 2 * V * sizeof(int4), cudaMemcpyHostToDevice));
+    g->d_ell = ell;
+  }
   sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml, smlf);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaDeviceSynchronize());
@@ -603,9 +623,9 @@ int check_consistent(const grf_graph* g, const Opts& o, double beta, int64_t S) 
 }
 
 // The tensor-core transforms run for this call (the plan exists for its S).
-bool umma_ready(const grf_graph* g, const Opts& o, int64_t S) {
+bool umma_ready(const grf_graph* g, const Opts& o, int64_t S, int32_t L) {
   return o.spec_umma && g->dst.blk && g->dst.dev.sp == dst_gemm_sample_pad(S) &&
-         g->dst.dev.n_items > 0;
+         g->dst.dev.n_items > 0 && spec_umma_fits(L);
 }
 
 // FP32 tridiagonal edges of path p (0: every edge, 2: the edges the spectral
@@ -648,6 +668,7 @@ struct ApplyWs {
   void* prm;  // SweepParams<T> [L][E]
   void* xw;   // T [L][V][S] (sample-minor)
   float* bhat;  // sine transform of the interior noise [n_interior][S] (spectral path)
+  float* ends;  // end values per edge [E][2][S][L] (tensor-core sine-basis path)
   float *nshift, *nwgam;  // FP32 node constants [L] (spectral path)
   int32_t* iters;
   PcgStatus* status;
@@ -680,7 +701,7 @@ void carve_lp_infer(Carve& c, const grf_graph* g, int32_t nodes, LpActs* a) {
 }
 
 void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w,
-                 int precond = GRF_PRECOND_JACOBI, bool spectral = false) {
+                 int precond = GRF_PRECOND_JACOBI, bool spectral = false, bool umma = false) {
   const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
   const size_t nsg = (Ss + recover_sample_group() - 1) / recover_sample_group();
   w->alpha = c.take<double>(Ls);
@@ -721,6 +742,7 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   w->prm = c.take<char>(Ls * E * 4 * tsize);
   w->xw = c.take<char>(Ls * Ss * V * tsize);
   w->bhat = spectral && tsize == 4 ? c.take<float>((size_t)g->ni * Ss) : nullptr;
+  w->ends = spectral && umma && tsize == 4 ? c.take<float>(2 * E * Ss * Ls) : nullptr;
   w->nshift = c.take<float>(Ls);
   w->nwgam = c.take<float>(Ls);
   w->iters = c.take<int32_t>(Ls * Ss);
@@ -855,13 +877,14 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
                                             g->d_bin_edges[p] + head, tail, gvec, st);
-    if (o.consistent && !(spec && umma_ready(g, o, S)))
+    if (o.consistent && !(spec && umma_ready(g, o, S, L)))
       return fail(GRF_ENOTSUP, "the consistent mass needs the tensor-core sine transforms");
-    if (spec && umma_ready(g, o, S)) {
+    if (spec && umma_ready(g, o, S, L)) {
       rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
                                                     w.status, g->n_sm, st);
-      rs->launches += launch_spec_ends(g->d, nd, kappa2, S, g->d_spec_edges, g->spec_count,
-                                       w.bhat, gvec, st, o.consistent);
+      rs->launches += launch_spec_ends_umma(g->d, nd, S, g->d_spec_edges, g->spec_count,
+                                            g->n_spec_bins, w.bhat, gvec, w.ends,
+                                            o.consistent, w.status, g->n_sm, st);
     } else if (spec && o.spec_tc)
       rs->launches += launch_spec_condense_mma(g->d, nd, S, (const float*)b, g->d_spec_edges,
                                                g->spec_count, w.bhat, gvec, st);
@@ -901,7 +924,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   }
   rs->begin(3, st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
-  launch_pcg<T>(g->d, g->d_order, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
+  launch_pcg<T>(g->d, g->d_order, g->d_ell, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
                 (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st);
   rs->end(3, st);
@@ -918,7 +941,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
              const double* nodes_dev = nullptr) {
   Carve c(ws_tail);
   ApplyWs w;
-  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond, o.spectral);
+  carve_apply(c, g, hn.L(), S, sizeof(T), &w, o.precond, o.spectral, o.spec_umma);
   const double k2 = kappa * kappa;
   if (nodes_dev) {
     w.alpha = const_cast<double*>(nodes_dev);
@@ -944,10 +967,11 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
     rs->launches += launch_recover_nodes<OutT>(
         g->d, hn.L(), S, (const float*)b, (const SweepParams<float>*)w.prm, (const float*)w.xw,
         g->d_bin_edges[p] + head, tail, out, st);
-  if (spec && umma_ready(g, o, S)) {
-    rs->launches += launch_spec_coef(g->d, dev_nodes(w, hn.L()), k2, S, g->d_spec_edges,
-                                     g->spec_count, w.bhat, (const float*)w.xw, st,
-                                     o.consistent);
+  if (spec && umma_ready(g, o, S, hn.L())) {
+    rs->launches += launch_spec_coef_umma(g->d, dev_nodes(w, hn.L()), S, g->d_spec_edges,
+                                          g->spec_count, g->n_spec_bins, w.bhat,
+                                          (const float*)w.xw, o.consistent, w.status, g->n_sm,
+                                          st);
     rs->launches += launch_dst_gemm<true, OutT>(g->d, g->dst.dev, S, w.bhat, out, w.status,
                                                 g->n_sm, st);
   } else if (spec) {
@@ -962,7 +986,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
 size_t apply_bytes(const grf_graph* g, int32_t L, int64_t S, size_t tsize, const Opts& o) {
   Carve c(nullptr);
   ApplyWs w;
-  carve_apply(c, g, L, S, tsize, &w, o.precond, o.spectral);
+  carve_apply(c, g, L, S, tsize, &w, o.precond, o.spectral, o.spec_umma);
   return c.off;
 }
 
@@ -1252,6 +1276,7 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->yscr = w->rpscr = nullptr;
   w->xw = nullptr;
   w->bhat = nullptr;
+  w->ends = nullptr;
   w->nshift = w->nwgam = nullptr;
 }
 

@@ -26,6 +26,7 @@
 // wait is bounded: on a timeout the CTA raises the error flag, waits (bounded)
 // for its MMAs, frees its tensor memory and stops.
 #include "grf_internal.h"
+#include "umma.cuh"
 
 namespace grf {
 namespace {
@@ -40,121 +41,9 @@ constexpr uint32_t kBTile = kBN * kBK * 2;                 // 32 KB
 constexpr uint32_t kStageBytes = 2 * kATile + 2 * kBTile;  // hi and lo planes
 constexpr uint32_t kSmemBytes = kStages * kStageBytes + 1024 + 128;
 constexpr uint32_t kTmemCols = 256;
-// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
-// N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-constexpr unsigned long long kWaitNs = 2000000000ull;  // give up a wait after 2 s
+constexpr uint32_t kIdesc = umma::idesc_bf16(kBM, kBN);  // N = 256, M = 128
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, rows of 128
-// bytes, 8-row groups 1024 bytes apart (the tile base is 1024-byte aligned).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused with this swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // 128-byte swizzle
-  return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Waits for the completion of the phase with the given parity; false once
-// kWaitNs have passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  const unsigned long long t0 = now_ns();
-  for (long long i = 0;; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if ((i & 255) == 255 && now_ns() - t0 > kWaitNs) return false;
-  }
-}
-
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // .x = a (low half)
-  return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// hi/lo BF16 split of 8 values into two 16-byte chunks
-__device__ __forceinline__ void split8(const float (&x)[8], uint4& hi, uint4& lo) {
-  float h[8], l[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(x[i]);
-    h[i] = __bfloat162float(b);
-    l[i] = x[i] - h[i];
-  }
-  hi = make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]),
-                  pack_bf16(h[6], h[7]));
-  lo = make_uint4(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]), pack_bf16(l[4], l[5]),
-                  pack_bf16(l[6], l[7]));
-}
-
-// byte offset of 16-byte chunk c of row r in a 128-byte-swizzled tile
-__device__ __forceinline__ uint32_t swz(int r, int c) {
-  return (uint32_t)r * 128u + (uint32_t)((c ^ (r & 7)) << 4);
-}
+using namespace umma;
 
 // Phi_m hi/lo planes: [mp][kp] row-major, zero outside j, i < m.
 __global__ void phi_planes_kernel(const DstGroup* __restrict__ groups, int32_t n_groups,
@@ -204,20 +93,15 @@ __global__ void __launch_bounds__(kGT, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tslot)),
-                 "r"(kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tmem_alloc(tslot, kTmemCols);
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
-  tc_fence_after();
+  fence_after();
   const uint32_t tmem = *tslot;
   uint32_t uses[kStages] = {0, 0};  // commits to each stage's barrier so far
   bool failed = false;
 
-  const int ept = kBN / sp;  // edges per tile
   for (int32_t item = blockIdx.x; item < n_items && !failed; item += gridDim.x) {
     const DstItem it = items[item];
     // this thread's B column: edge slot tid / sp, sample tid % sp
@@ -287,20 +171,14 @@ __global__ void __launch_bounds__(kGT, 1)
       }
       asm volatile("cp.async.wait_all;" ::: "memory");
       // make the generic-proxy stores visible to the tensor core
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      fence_proxy_async();
       __syncthreads();
       if (tid == 0) {
-        tc_fence_after();
+        fence_after();
         const uint64_t dah = sdesc(smem_u32(A_hi)), dal = sdesc(smem_u32(A_lo));
         const uint64_t dbh = sdesc(smem_u32(B_hi)), dbl = sdesc(smem_u32(B_lo));
-#pragma unroll
-        for (int kk = 0; kk < kBK / 16; ++kk) {
-          const uint64_t o = (uint64_t)(kk * 32) >> 4;  // 16 BF16 = 32 bytes along K
-          umma_bf16(tmem, dah + o, dbh + o, (kb | kk) != 0);
-          umma_bf16(tmem, dah + o, dbl + o, 1u);
-          umma_bf16(tmem, dal + o, dbh + o, 1u);
-        }
-        umma_commit(&mbar[st]);
+        mma_split_stage(tmem, dah, dal, dbh, dbl, kIdesc, kb != 0);
+        commit(&mbar[st]);
       }
       uses[st] += 1;
     }
@@ -311,7 +189,7 @@ __global__ void __launch_bounds__(kGT, 1)
       failed = true;
       break;
     }
-    tc_fence_after();
+    fence_after();
     // epilogue: warp w reads lanes 32 (w % 4) .. + 31, columns 128 (w / 4) .. + 127
     const int q4 = warp & 3, half = warp >> 2;
     const int row = 32 * q4 + lane;
@@ -347,9 +225,9 @@ __global__ void __launch_bounds__(kGT, 1)
           dst[(g.ioff[e] + jrow) * S + sc] = (OutT)v[t];
       }
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();  // accumulator read before the next item's first MMA
-    tc_fence_after();
+    fence_after();
   }
   if (failed) {
     if (tid == 0) atomicAdd(&status->device_timeout, 1);
@@ -357,12 +235,10 @@ __global__ void __launch_bounds__(kGT, 1)
     for (int s = 0; s < kStages; ++s)
       if (uses[s] > 0) mbar_wait(&mbar[s], (uses[s] - 1) & 1);
   }
-  tc_fence_before();
+  fence_before();
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols)
-                 : "memory");
+    tmem_dealloc(tmem, kTmemCols);
 }
 
 }  // namespace

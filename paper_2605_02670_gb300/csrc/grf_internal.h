@@ -175,14 +175,16 @@ constexpr int kPreJacobi = 0, kPreNeumann = 1, kPreLearned = 2;
 // Mixed-precision Jacobi-PCG with one CTA per (node, 8 samples) and the
 // group's FP32 vectors as [nv][8] rows in global memory (graphs whose vectors
 // do not fit on chip). R, PA, PB, Dv: [L][ceil(S / 8)][nv][8] floats each.
+// ell: nv int4 (each vertex's first four neighbours, padded with itself),
+// then nv int2 (incidence-list start, degree).
 int64_t pcg_batch_padded_samples(int64_t S);
-void launch_pcg_batch(const DevGraph& g, int32_t L, int64_t S, const double* diag,
+void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,
                       const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
                       double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
                       cudaStream_t st);
 template <typename VT>
-void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
+void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int32_t L, int64_t S,
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
@@ -261,17 +263,28 @@ template <typename OutT>
 int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                         const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
                         const float* xw, OutT* out, cudaStream_t st);
-// The two halves around tensor-core transforms (dst_gemm.cu): end values of
-// every node from bhat (already transformed) added into gvec; the sine-basis
-// coefficients c of the recovery written over bhat (the inverse transform of
-// c is then the interior field).
+// ---- spec_umma.cu: the two node contractions around the tensor-core sine
+// transforms (dst_gemm.cu) on the tensor cores (tcgen05, BF16 hi/lo operands
+// in three products, FP32 accumulation): the end values of every node from
+// bhat (already transformed) added into gvec, and the sine-basis coefficients
+// c of the recovery written over bhat (the inverse transform of c is then the
+// interior field). bin_edges / bin_count: the spectral edges over n_bins bins;
 // consistent: the consistent-mass operator (interior constants transformed).
-int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
-                     double* gvec, cudaStream_t st, bool consistent = false);
-int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
-                     const float* xw, cudaStream_t st, bool consistent = false);
+// Samples run in blocks of spec_umma_sample_block(S) (a multiple of 16, at
+// most 64; at most 32 for the coefficients); the shared memory of the
+// coefficient kernel grows with L (spec_umma_fits). ends: a scratch of
+// 2 E S L floats for the end values per edge, then added into gvec by a
+// gather over the vertices' incidences (null: FP64 atomics into gvec).
+int32_t spec_umma_sample_block(int64_t S);
+bool spec_umma_fits(int32_t L);
+int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
+                          const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
+                          const float* bhat, double* gvec, float* ends, bool consistent,
+                          PcgStatus* status, int n_sm, cudaStream_t st);
+int launch_spec_coef_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
+                          const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
+                          float* bhat, const float* xw, bool consistent, PcgStatus* status,
+                          int n_sm, cudaStream_t st);
 
 // ---- consistent.cu: white noise of the consistent mass, W = R xi with the
 // Cholesky order interiors (edge by edge) then vertices. On entry b [n][S]

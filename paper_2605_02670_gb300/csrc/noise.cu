@@ -44,13 +44,21 @@ __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, double& n0,
   n1 = r * sn;
 }
 
-// FP32 Box-Muller of the mixed-precision path: the hardware logarithm and
-// sine/cosine (absolute errors ~1e-6 on these arguments, far inside the FP32
-// sweeps' tolerance; the uint32 words stay bit-exact).
+// FP32 Box-Muller of the mixed-precision path: the hardware base-2
+// logarithm, square root and sine/cosine (one special-function instruction
+// each; their errors leave the normals within ~1e-6 relative in the L2 sense,
+// far inside the FP32 sweeps' tolerance; the uint32 words stay bit-exact).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void box_muller(uint32_t xa, uint32_t xb, float& n0, float& n1) {
   const float ua = fmaf((float)xa, 0x1p-32f, 0x1p-33f);
   const float ub = fmaf((float)xb, 0x1p-32f, 0x1p-33f);
-  const float r = sqrtf(-2.0f * __logf(ua));
+  // -2 ln u = (-2 ln 2) log2 u >= 0 (u <= 1 after rounding)
+  const float r = sqrt_approx(-1.3862943611198906f * __log2f(ua));
   float sn, cs;
   __sincosf(6.2831853071795865f * ub, &sn, &cs);
   n0 = r * cs;
@@ -73,19 +81,31 @@ __global__ void noise_minor_kernel(DevGraph g, uint64_t seed, const uint64_t* se
   const int32_t qi = threadIdx.x / SB;
   const int64_t s = (int64_t)blockIdx.y * SB + threadIdx.x % SB;
   if (qi >= rows || s >= S) return;
-  for (int64_t q = (int64_t)blockIdx.x * rows + qi; q < nq; q += (int64_t)gridDim.x * rows) {
+  const int64_t nfull = g.n / 4;  // blocks of four DOFs inside the vector
+  const int64_t step = (int64_t)gridDim.x * rows;
+  for (int64_t q = (int64_t)blockIdx.x * rows + qi; q < nq; q += step) {
     const uint4 w = noise_block(seed, (uint64_t)q, (uint32_t)s);
     T n[4];
     box_muller(w.x, w.y, n[0], n[1]);
     box_muller(w.z, w.w, n[2], n[3]);
+    T* p = b + 4 * q * S + s;
+    if (sizeof(T) == 4 && sml_f && q < nfull) {
+      // the block's four mass factors in one 16-byte load (4 q is a multiple of 4)
+      const float4 f = __ldg(reinterpret_cast<const float4*>(sml_f) + q);
+      p[0] = (T)(f.x * (float)n[0]);
+      p[S] = (T)(f.y * (float)n[1]);
+      p[2 * S] = (T)(f.z * (float)n[2]);
+      p[3 * S] = (T)(f.w * (float)n[3]);
+      continue;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int64_t j = 4 * q + k;
       if (j < g.n) {
         if (sizeof(T) == 4 && sml_f)
-          b[j * S + s] = (T)(sml_f[j] * (float)n[k]);
+          p[k * S] = (T)(sml_f[j] * (float)n[k]);
         else
-          b[j * S + s] = (T)g.sqrt_ml[j] * n[k];
+          p[k * S] = (T)g.sqrt_ml[j] * n[k];
       }
     }
   }

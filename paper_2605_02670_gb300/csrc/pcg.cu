@@ -1466,7 +1466,7 @@ bool group_fits(const DevGraph& g) {
 }  // namespace
 
 template <typename VT>
-void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
+void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int32_t L, int64_t S,
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
@@ -1474,7 +1474,7 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
     if (layout == 4 && pre == kPreJacobi) {
-      launch_pcg_batch(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
+      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
                        max_iter, iters, status, st);
       return;
     }
@@ -1520,7 +1520,7 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
     // larger graphs: samples batched in rows of 8 (the vectors are carved with
     // the sample count padded to a multiple of 8)
     if (layout != 1 && pre == kPreJacobi) {
-      launch_pcg_batch(g, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
+      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
                        max_iter, iters, status, st);
       return;
     }
@@ -1546,7 +1546,8 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, int32_t L, int64_t S,
   }
 }
 #define GRF_INST(VT)                                                                          \
-  template void launch_pcg<VT>(const DevGraph&, const VertexOrder&, int32_t, int64_t,      \
+  template void launch_pcg<VT>(const DevGraph&, const VertexOrder&, const int4*, int32_t,  \
+                               int64_t,                                                      \
                                const double*, const double*, const VT*, const VT*, int,      \
                                const VT*, const VT*, const double*, double*, VT*, VT*, VT*,  \
                                VT*, VT*, double, int32_t, int32_t*, PcgStatus*, int,         \

@@ -12,9 +12,11 @@
 // vertices per thread, then FP64 across the vector and the CTA) and the CG
 // scalars alpha, beta are FP64; the vector updates are FP32.
 //
-// A thread owns 4 of the group's samples (one 16-byte half row) of two
-// vertices per step, so every dependent load chain (incidence list, then the
-// neighbour's row) moves 16 bytes and each thread keeps two chains in flight.
+// A thread owns 4 of the group's samples (one 16-byte half row) of one vertex
+// per step. The vertex's first four neighbours and its incidence-list start
+// and degree come from one record per vertex, so every neighbour row and its
+// coefficient are requested at once after a single dependent load (further
+// neighbours, rare on these graphs, walk the incidence list).
 // The per-sample CG state lives in shared memory; after each CTA reduction one
 // thread per sample takes its decisions in FP64.
 //
@@ -35,7 +37,7 @@ namespace {
 constexpr int kBT = 256;          // threads per CTA
 constexpr int kSG = 8;            // samples per group: one 32-byte row per vertex
 constexpr int kVP = kBT / 2;      // vertices per half-step (two threads per vertex row)
-constexpr int kU = 2;             // vertices per thread per step
+constexpr int kU = 1;             // vertices per thread per step
 constexpr int kWarps = kBT / 32;
 constexpr int kChunk = 16;        // FP32 partial sums over this many vertices
 constexpr double kInnerRtol = 1e-5;
@@ -134,12 +136,46 @@ __device__ __forceinline__ float get(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// Bulk prefetch into L2 (TMA) of the vector rows of the vertices kPF steps
+// ahead: the rows of a step are contiguous ([nv][8] floats), so one thread
+// requests each vector's next block while the CTA works on the current one,
+// and the step's own-row loads then hit L2 instead of waiting on DRAM.
+constexpr int kPF = 4;
+__device__ __forceinline__ void prefetch_rows(const float* rows, int32_t v0, int32_t nv) {
+  const int32_t b = v0 + kPF * kVP;
+  if (b >= nv) return;
+  const int32_t n = nv - b < kVP ? nv - b : kVP;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(rows + (int64_t)b * kSG),
+               "r"((uint32_t)n * kSG * 4)
+               : "memory");
+}
+
+// The vertices' neighbour records of one step (vertices v0 + u kVP, u < kU):
+// their first four neighbours and (incidence-list start, degree); past the
+// end the records are empty.
+__device__ __forceinline__ void load_ell(const int4* __restrict__ ell, int32_t v0, int32_t nv,
+                                         int4 (&a)[kU], int2 (&b)[kU]) {
+  const int2* __restrict__ info = reinterpret_cast<const int2*>(ell + nv);
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    const int32_t v = v0 + u * kVP;
+    if (v < nv) {
+      a[u] = __ldg(ell + v);
+      b[u] = __ldg(info + v);
+    } else {
+      a[u] = make_int4(0, 0, 0, 0);
+      b[u] = make_int2(0, 0);
+    }
+  }
+}
+
 }  // namespace
 
 // gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out; xout also
 // holds the FP64 iterate). R, PA, PB, Dv: [L][ceil(S / 8)][nv][8] FP32 scratch.
 __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
-    DevGraph g, int32_t L, int64_t S, const double* __restrict__ diag,
+    DevGraph g, const int4* __restrict__ ell, int32_t L, int64_t S,
+    const double* __restrict__ diag,
     const double* __restrict__ offv, const float* __restrict__ dscale,
     const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
     float* __restrict__ R, float* __restrict__ PA, float* __restrict__ PB,
@@ -309,25 +345,37 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           Acc4<1> a;
           a.init();
           if (any) {
+            const float4 bf4 = make_float4(bf[0], bf[1], bf[2], bf[3]);
+            // p' of vertex w from its r and old p
+            auto pnext = [&](int64_t w, float4 rw) -> float4 {
+              return fst ? rw : sel4(fs, rw, fma4(bf4, ld4(pold + w), rw));
+            };
             for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
+              if (threadIdx.x == 0) {  // rows of r and p kPF steps ahead (hh = 0 here)
+                prefetch_rows(r, v0, nv);
+                if (!fst) prefetch_rows(pold, v0, nv);
+              }
+              int4 ea[kU];
+              int2 eb[kU];
+              load_ell(ell, v0, nv, ea, eb);  // the step's neighbour records
 #pragma unroll
               for (int u = 0; u < kU; ++u) {
                 const int32_t v = v0 + u * kVP;
                 if (v >= nv) break;
-                const int32_t k0 = vptr[v], k1 = vptr[v + 1];
-                const float4 rv = ld4(r + (int64_t)v * kSG);
-                float4 pv = rv;
-                if (!fst) pv = sel4(fs, rv, fma4(make_float4(bf[0], bf[1], bf[2], bf[3]),
-                                                 ld4(pold + (int64_t)v * kSG), rv));
+                const int32_t k0 = eb[u].x, deg = eb[u].y;
+                const int32_t wl[4] = {ea[u].x, ea[u].y, ea[u].z, ea[u].w};
+                const float4 pv = pnext((int64_t)v * kSG, ld4(r + (int64_t)v * kSG));
                 float4 q = pv;
-                for (int32_t k = k0; k < k1; ++k) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  if (i < deg) {
+                    const int64_t w = (int64_t)wl[i] * kSG;
+                    q = fma1(Ot[k0 + i], pnext(w, ld4(r + w)), q);
+                  }
+                }
+                for (int32_t k = k0 + 4; k < k0 + deg; ++k) {
                   const int64_t w = (int64_t)nbr[k] * kSG;
-                  const float o = Ot[k];
-                  const float4 rw = ld4(r + w);
-                  float4 pw = rw;
-                  if (!fst) pw = sel4(fs, rw, fma4(make_float4(bf[0], bf[1], bf[2], bf[3]),
-                                                   ld4(pold + w), rw));
-                  q = fma1(o, pw, q);
+                  q = fma1(Ot[k], pnext(w, ld4(r + w)), q);
                 }
                 st4(pnew + (int64_t)v * kSG, pv);
 #pragma unroll
@@ -374,15 +422,27 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           a.init();
           if (any) {
             for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
+              if (threadIdx.x == 0) {  // rows of p', d and r kPF steps ahead
+                prefetch_rows(pnew, v0, nv);
+                prefetch_rows(dv, v0, nv);
+                prefetch_rows(r, v0, nv);
+              }
+              int4 ea[kU];
+              int2 eb[kU];
+              load_ell(ell, v0, nv, ea, eb);  // the step's neighbour records
 #pragma unroll
               for (int u = 0; u < kU; ++u) {
                 const int32_t v = v0 + u * kVP;
                 if (v >= nv) break;
-                const int32_t k0 = vptr[v], k1 = vptr[v + 1];
+                const int32_t k0 = eb[u].x, deg = eb[u].y;
+                const int32_t wl[4] = {ea[u].x, ea[u].y, ea[u].z, ea[u].w};
                 const int64_t iv = (int64_t)v * kSG;
                 const float4 pv = ld4(pnew + iv);
                 float4 q = pv;
-                for (int32_t k = k0; k < k1; ++k)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                  if (i < deg) q = fma1(Ot[k0 + i], ld4(pnew + (int64_t)wl[i] * kSG), q);
+                for (int32_t k = k0 + 4; k < k0 + deg; ++k)
                   q = fma1(Ot[k], ld4(pnew + (int64_t)nbr[k] * kSG), q);
                 const float4 d0 = ld4(dv + iv);
                 const float4 r0 = ld4(r + iv);
@@ -477,7 +537,7 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
 // Vectors of the batched layout need [L][ceil(S / 8) * 8][nv] floats each.
 int64_t pcg_batch_padded_samples(int64_t S) { return (S + kSG - 1) / kSG * kSG; }
 
-void launch_pcg_batch(const DevGraph& g, int32_t L, int64_t S, const double* diag,
+void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,
                       const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
                       double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
@@ -485,7 +545,7 @@ void launch_pcg_batch(const DevGraph& g, int32_t L, int64_t S, const double* dia
   const int64_t items = (int64_t)L * ((S + kSG - 1) / kSG);
   if (items <= 0) return;
   const int blocks = (int)(items < (int64_t)1 << 30 ? items : (int64_t)1 << 30);
-  pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, L, S, diag, offv, dscale, offv_t, gvec, x, R, PA,
+  pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, ell, L, S, diag, offv, dscale, offv_t, gvec, x, R, PA,
                                            PB, Dv, rtol, max_iter, iters, status);
 }
 

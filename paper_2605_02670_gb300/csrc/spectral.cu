@@ -392,169 +392,6 @@ int grid_units(int64_t units) {
 // contract bhat with 1 / mu_jl, so one node (ends) or one mode (coefficients)
 // per thread and a shared-memory footprint of one edge's rows keep several
 // CTAs per SM.
-constexpr int kEndsThreads = 256;
-
-// End values of every node from the transformed rows: thread l accumulates
-// O_l (odd modes) and E_l (even modes) over the edge's modes, rows
-// phi_j bh_j staged once per (edge, sample group).
-constexpr int kEndsCta = 128;  // threads of the end-value kernel (two nodes each)
-
-template <int SG>
-__global__ void __launch_bounds__(kEndsCta, 4)
-    spec_ends_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
-                     int32_t n_edges, const float* __restrict__ bhat, double* __restrict__ gvec,
-                     int consistent) {
-  extern __shared__ __align__(16) float ends_sm[];
-  const int64_t nsg = (S + SG - 1) / SG;
-  const int64_t units = (int64_t)n_edges * nsg;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int32_t e = edges[u / nsg];
-    const int64_t s0 = (u % nsg) * SG;
-    const int32_t m = g.nel[e] - 1;
-    const int64_t off = g.ioff[e];
-    const int kv = (int)(S - s0 < SG ? S - s0 : SG);
-    float* bt = ends_sm;                  // [m][SG] phi_j bh_j
-    float* sig = bt + (size_t)m * SG;     // [m] 4 sin^2(pi j / (2 (m + 1)))
-    __syncthreads();  // the previous unit is done with the shared arrays
-    stage_rows<SG>(bhat + off * S + s0, S, kv, m, bt);
-    for (int32_t j = threadIdx.x; j < m; j += blockDim.x) {
-      const float sh = 2.f * sinpif((float)(j + 1) / (float)(2 * (m + 1)));
-      sig[j] = sh * sh;
-    }
-    __syncthreads();
-    const float scale = sqrtf(2.f / (float)(m + 1));
-    for (int32_t t = threadIdx.x; t < m * SG; t += blockDim.x)
-      bt[t] *= scale * sinpif((float)(t / SG + 1) / (float)(m + 1));
-    __syncthreads();
-    const double h = g.he[e];
-    const float h2f = (float)(h * h);
-    const int32_t va = g.eu[e], vb = g.ev[e];
-    // nodes l and l + ceil(L / 2) per thread: every staged row serves both
-    const int32_t half = (nd.L + 1) / 2;
-    for (int32_t l0 = threadIdx.x; l0 < half; l0 += blockDim.x) {
-      const int32_t l1 = l0 + half;
-      const bool two = l1 < nd.L;
-      const float dl0 = nd.shift[l0] * h2f;
-      const float dl1 = two ? nd.shift[l1] * h2f : 1.f;
-      // consistent mass: T' = tridiag(-1, 2 + delta', -1) with
-      // delta' = delta / eps, eps = 1 - delta / 6, so
-      // 1 / (delta' + sig) = eps / (delta + sig eps) (no pole: delta (1 - sig/6)
-      // + sig > 0 for sig <= 4); the lumped case is eps = 1
-      const float ep0 = consistent ? 1.f - dl0 * (1.f / 6.f) : 1.f;
-      const float ep1 = consistent ? 1.f - dl1 * (1.f / 6.f) : 1.f;
-      float od0[SG], ev0[SG], od1[SG], ev1[SG];
-#pragma unroll
-      for (int s = 0; s < SG; ++s) od0[s] = ev0[s] = od1[s] = ev1[s] = 0.f;
-      int32_t j = 0;
-      for (; j + 1 < m; j += 2) {  // odd mode j + 1 into od, even mode j + 2 into ev
-        const float sa = sig[j], sb = sig[j + 1];
-        spec_acc2<SG>(__fdividef(ep0, fmaf(sa, ep0, dl0)), __fdividef(ep1, fmaf(sa, ep1, dl1)),
-                      bt + (size_t)j * SG, od0, od1);
-        spec_acc2<SG>(__fdividef(ep0, fmaf(sb, ep0, dl0)), __fdividef(ep1, fmaf(sb, ep1, dl1)),
-                      bt + (size_t)(j + 1) * SG, ev0, ev1);
-      }
-      if (j < m)
-        spec_acc2<SG>(__fdividef(ep0, fmaf(sig[j], ep0, dl0)),
-                      __fdividef(ep1, fmaf(sig[j], ep1, dl1)), bt + (size_t)j * SG, od0, od1);
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (q == 1 && !two) break;
-        double* gl = gvec + ((int64_t)(q ? l1 : l0) * S + s0) * g.nv;
-#pragma unroll
-        for (int s = 0; s < SG; ++s) {
-          if (s < kv) {
-            const float o = q ? od1[s] : od0[s], v = q ? ev1[s] : ev0[s];
-            atomicAdd(gl + (int64_t)s * g.nv + va, (double)(o + v));
-            atomicAdd(gl + (int64_t)s * g.nv + vb, (double)(o - v));
-          }
-        }
-      }
-    }
-  }
-}
-
-// Sine-basis coefficients of the recovery, written over the edge's bhat rows:
-// c_j = D_j bh_j + phi_j sum_l (xa_l + (-1)^(j+1) xb_l) / mu_jl with
-// D_j = sum_l sc_l / mu_jl; thread j owns mode j, the nodes' weighted vertex
-// values (xa +- xb) and constants are staged once per (edge, sample group).
-template <int SG>
-__global__ void __launch_bounds__(kEndsThreads)
-    spec_coef_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
-                     int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw,
-                     int consistent) {
-  extern __shared__ __align__(16) float coef_sm[];
-  const int32_t L = nd.L;
-  float* xp = coef_sm;                     // [L][SG] xa + xb
-  float* xm = xp + (size_t)L * SG;         // [L][SG] xa - xb
-  float* dls = xm + (size_t)L * SG;        // [L] delta_l
-  float* scs = dls + L;                    // [L] sc_l
-  float* eps = scs + L;                    // [L] 1 - delta_l / 6 (consistent mass) or 1
-  const int64_t nsg = (S + SG - 1) / SG;
-  const int64_t units = (int64_t)n_edges * nsg;
-  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int32_t e = edges[u / nsg];
-    const int64_t s0 = (u % nsg) * SG;
-    const int32_t m = g.nel[e] - 1;
-    const int64_t off = g.ioff[e];
-    const int kv = (int)(S - s0 < SG ? S - s0 : SG);
-    const double h = g.he[e];
-    const float hf = (float)h, h2f = (float)(h * h);
-    const int32_t va = g.eu[e], vb = g.ev[e];
-    __syncthreads();
-    for (int32_t l = threadIdx.x; l < L; l += blockDim.x) {
-      dls[l] = nd.shift[l] * h2f;
-      scs[l] = nd.wgam[l] * hf;
-      eps[l] = consistent ? 1.f - dls[l] * (1.f / 6.f) : 1.f;
-    }
-    for (int32_t t = threadIdx.x; t < L * SG; t += blockDim.x) {
-      const int32_t l = t / SG, s = t - l * SG;
-      float a = 0.f, c = 0.f;
-      if (s < kv) {
-        a = xw[((int64_t)l * g.nv + va) * S + s0 + s];
-        c = xw[((int64_t)l * g.nv + vb) * S + s0 + s];
-      }
-      xp[t] = a + c;
-      xm[t] = a - c;
-    }
-    __syncthreads();
-    const float scale = sqrtf(2.f / (float)(m + 1));
-    // modes 4 b + p and 4 b + p + 2 (equal parity p) per thread: every staged
-    // row of (xa +- xb) serves both
-    for (int32_t t = threadIdx.x; 2 * t < m + 1; t += blockDim.x) {
-      const int32_t j0 = 4 * (t >> 1) + (t & 1), j1 = j0 + 2;
-      if (j0 >= m) continue;
-      const bool two = j1 < m;
-      float sh = 2.f * sinpif((float)(j0 + 1) / (float)(2 * (m + 1)));
-      const float s0f = sh * sh;
-      sh = 2.f * sinpif((float)(j1 + 1) / (float)(2 * (m + 1)));
-      const float s1f = two ? sh * sh : s0f;
-      const float* X = (j0 & 1) ? xm : xp;  // mode j + 1 odd <=> j even
-      float C0[SG], C1[SG], D0 = 0.f, D1 = 0.f;
-#pragma unroll
-      for (int s = 0; s < SG; ++s) C0[s] = C1[s] = 0.f;
-      // consistent mass: sc' / mu' = sc / (delta + sig eps) and the couplings'
-      // 1 / mu' = eps / (delta + sig eps) (eps = 1: lumped)
-      for (int32_t l = 0; l < L; ++l) {
-        const float dl = dls[l], sc = scs[l], ep = eps[l];
-        const float r0 = __fdividef(1.f, fmaf(s0f, ep, dl)), r1 = __fdividef(1.f, fmaf(s1f, ep, dl));
-        D0 = fmaf(sc, r0, D0);
-        D1 = fmaf(sc, r1, D1);
-        spec_acc2<SG>(r0 * ep, r1 * ep, X + (size_t)l * SG, C0, C1);
-      }
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (q == 1 && !two) break;
-        const int32_t j = q ? j1 : j0;
-        const float phi = scale * sinpif((float)(j + 1) / (float)(m + 1));
-        float* row = bhat + (off + j) * S + s0;
-#pragma unroll
-        for (int s = 0; s < SG; ++s)
-          if (s < kv) row[s] = fmaf(q ? D1 : D0, row[s], phi * (q ? C1[s] : C0[s]));
-      }
-    }
-  }
-}
-
 }  // namespace
 
 // Spectral bins: interior-node limit, threads per CTA and modes per thread
@@ -652,41 +489,5 @@ template int launch_spec_recover<float>(const DevGraph&, const DevNodes&, double
 template int launch_spec_recover<double>(const DevGraph&, const DevNodes&, double, int64_t,
                                          const int32_t*, const int32_t*, const float*,
                                          const float*, double*, cudaStream_t);
-
-int launch_spec_ends(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, const float* bhat,
-                     double* gvec, cudaStream_t st, bool consistent) {
-  (void)kappa2;
-  int32_t n = 0;
-  for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
-  if (n <= 0) return 0;
-  const int32_t mmax = g.max_m < kSpecBins[kNumSpecBins - 1].mmax ? g.max_m
-                                                                   : kSpecBins[kNumSpecBins - 1].mmax;
-  const size_t smem = ((size_t)mmax * kSpecSG + mmax) * sizeof(float);
-  cudaFuncSetAttribute(spec_ends_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  const int64_t cap = (int64_t)sm_count() * 16;
-  spec_ends_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsCta, smem, st>>>(
-      g, nd, S, bin_edges, n, bhat, gvec, consistent ? 1 : 0);
-  return 1;
-}
-
-int launch_spec_coef(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
-                     const int32_t* bin_edges, const int32_t* bin_count, float* bhat,
-                     const float* xw, cudaStream_t st, bool consistent) {
-  (void)kappa2;
-  int32_t n = 0;
-  for (int i = 0; i < kNumSpecBins; ++i) n += bin_count[i];
-  if (n <= 0) return 0;
-  const size_t smem = ((size_t)nd.L * (2 * kSpecSG + 3)) * sizeof(float);
-  cudaFuncSetAttribute(spec_coef_kernel<kSpecSG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)smem);
-  const int64_t units = (int64_t)n * ((S + kSpecSG - 1) / kSpecSG);
-  const int64_t cap = (int64_t)sm_count() * 8;
-  spec_coef_kernel<kSpecSG><<<(int)(units < cap ? units : cap), kEndsThreads, smem, st>>>(
-      g, nd, S, bin_edges, n, bhat, xw, consistent ? 1 : 0);
-  return 1;
-}
 
 }  // namespace grf
