@@ -241,6 +241,23 @@ int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint
                     int64_t n_samples, void* out_host, const grf_options* opts,
                     void* stream, grf_stats* stats);
 
+/* n_calls draws of grf_sample_host (seeds[c], n_samples each) into the host
+ * buffers out_host[c], pipelined: while call c computes on `stream`, the
+ * field of call c - 1 crosses to the host on a second stream of the handle.
+ * Each finished field is first copied device -> device into a second cached
+ * device buffer (so that the next call, whose replayed CUDA graph writes the
+ * first one, can start at once); every out_host[c] has the layout of
+ * grf_sample. The copies run in call order on one stream, so entries may
+ * repeat a buffer (the last call's field is what it holds). Pinned host
+ * memory keeps the copies asynchronous. The results equal n_calls separate
+ * grf_sample_host calls with the same seeds. Returns after the last copy;
+ * stats (may be NULL) sums the calls' iteration counts and keeps the worst
+ * status. Errors as grf_sample; GRF_EINVAL for n_calls < 0 or NULL arrays. */
+int grf_sample_host_stream(grf_graph* g, double kappa, double beta, double k_step,
+                           const uint64_t* seeds, int64_t n_calls, int64_t n_samples,
+                           void* const* out_host, const grf_options* opts, void* stream,
+                           grf_stats* stats);
+
 /* White noise only (Eq. wh_def with the lumped factor, Sec. 2.5):
  *   raw_words != 0: out is uint32 [n_samples][n_dofs], word j of sample s =
  *     word (j mod 4) of Philox4x32-10(key = (seed lo32, seed hi32),

@@ -39,7 +39,8 @@ GRF_TIMING_ONLY = 1 << 30
 
 C_SYMBOLS = ("grf_graph_create", "grf_graph_destroy", "grf_graph_info",
              "grf_graph_vertex_order", "grf_sample",
-             "grf_sample_host", "grf_noise", "grf_apply", "grf_schur", "grf_vertex_solve",
+             "grf_sample_host", "grf_sample_host_stream", "grf_noise", "grf_apply", "grf_schur",
+             "grf_vertex_solve",
              "grf_vertex_solve_noalloc", "grf_autotune", "grf_workspace_bytes",
              "grf_precond_init", "grf_precond_set", "grf_precond_get", "grf_precond_save",
              "grf_precond_load", "grf_precond_forward", "grf_precond_loss_grad",
@@ -104,6 +105,7 @@ def _load() -> ctypes.CDLL:
         "grf_graph_vertex_order": [P, P],
         "grf_sample": [P, D, D, D, U64, I64, P, P, P, P],
         "grf_sample_host": [P, D, D, D, U64, I64, P, P, P, P],
+        "grf_sample_host_stream": [P, D, D, D, P, I64, I64, P, P, P, P],
         "grf_noise": [P, U64, I64, P, I32, P],
         "grf_apply": [P, D, I64, P, P, P, I64, P, P, P, P, P],
         "grf_schur": [P, D, D, D, P, P, P],
@@ -237,6 +239,18 @@ def grf_sample_host(handle, kappa, beta, k_step, seed, n_samples, out: np.ndarra
     _check(_lib.grf_sample_host(handle, float(kappa), float(beta), float(k_step), int(seed),
                                 int(n_samples), _ptr(out), ctypes.byref(opts), _stream(stream),
                                 ctypes.byref(st)))
+    return st.as_dict()
+
+
+def grf_sample_host_stream(handle, kappa, beta, k_step, seeds, n_samples, outs,
+                           opts: grf_options, stream=None) -> dict:
+    """len(seeds) pipelined host draws into the host arrays outs (one per seed)."""
+    sd = np.ascontiguousarray(seeds, np.uint64)
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.ctypes.data for o in outs])
+    st = grf_stats()
+    _check(_lib.grf_sample_host_stream(handle, float(kappa), float(beta), float(k_step),
+                                       _ptr(sd), int(sd.shape[0]), int(n_samples), ptrs,
+                                       ctypes.byref(opts), _stream(stream), ctypes.byref(st)))
     return st.as_dict()
 
 
@@ -425,6 +439,18 @@ class Graph:
         stats = grf_sample_host(self.handle, kappa, beta, k_step, seed, n_samples, out, opts,
                                 stream)
         return out, stats
+
+    def sample_host_stream(self, kappa, beta, k_step, seeds, n_samples, precision="fp64",
+                           out_dtype=None, outs=None, stream=None, **knobs):
+        """One host array per seed, drawn back to back with the host copies of
+        one call overlapping the next call's compute."""
+        opts = make_options(precision, out_dtype, **knobs)
+        dt = np.float64 if opts.out_dtype == GRF_OUT_F64 else np.float32
+        if outs is None:
+            outs = [np.empty((n_samples, self.n_dofs), dtype=dt) for _ in seeds]
+        stats = grf_sample_host_stream(self.handle, kappa, beta, k_step, seeds, n_samples, outs,
+                                       opts, stream)
+        return outs, stats
 
     def autotune(self, kappa, beta, k_step, n_samples, precision="fp64", out_dtype=None,
                  rtol=0.0, max_iter=0, reps=2, stream=None, precond="jacobi"):

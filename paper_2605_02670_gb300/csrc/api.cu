@@ -181,6 +181,12 @@ struct grf_graph {
   // CUDA graph (which bakes the output pointer in) stays valid
   void* host_out = nullptr;
   size_t host_out_bytes = 0;
+  // grf_sample_host_stream: the second device buffer, the copy stream and its
+  // two events (the staged field, the finished host copy)
+  void* host_stage = nullptr;
+  size_t host_stage_bytes = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_staged = nullptr, ev_d2h = nullptr;
 
   void drop_graph() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -209,6 +215,10 @@ struct grf_graph {
       if (ws) cudaFree(ws);
       if (lm.blk) cudaFree(lm.blk);
       if (host_out) cudaFree(host_out);
+      if (host_stage) cudaFree(host_stage);
+      if (ev_staged) cudaEventDestroy(ev_staged);
+      if (ev_d2h) cudaEventDestroy(ev_d2h);
+      if (copy_stream) cudaStreamDestroy(copy_stream);
       if (dst.blk) cudaFree(dst.blk);
       if (cons.blk) cudaFree(cons.blk);
       cudaSetDevice(cur);
@@ -2101,6 +2111,23 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   return GRF_OK;
 }
 
+// The cached device output of the host entry points (grown when needed; a
+// captured graph that writes the old buffer is dropped first).
+static int ensure_host_out(grf_graph* g, size_t bytes, void* stream) {
+  if (g->host_out_bytes >= bytes) return GRF_OK;
+  CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  if (g->host_out) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    g->drop_graph();
+    CUDA_TRY(cudaFree(g->host_out));
+    g->host_out = nullptr;
+    g->host_out_bytes = 0;
+  }
+  CUDA_TRY(cudaMalloc(&g->host_out, bytes ? bytes : 1));
+  g->host_out_bytes = bytes ? bytes : 1;
+  return GRF_OK;
+}
+
 int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint64_t seed,
                     int64_t n_samples, void* out_host, const grf_options* opts, void* stream,
                     grf_stats* stats) {
@@ -2110,18 +2137,7 @@ int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint
   GRF_TRY(read_opts(opts, &o));
   GRF_TRY(ensure_device(g));
   const size_t bytes = (size_t)g->n * (size_t)n_samples * (o.out_dtype == GRF_OUT_F64 ? 8 : 4);
-  if (g->host_out_bytes < bytes) {  // grow the cached device output
-    CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    if (g->host_out) {
-      CUDA_TRY(cudaDeviceSynchronize());
-      g->drop_graph();  // a captured graph may write to the old buffer
-      CUDA_TRY(cudaFree(g->host_out));
-      g->host_out = nullptr;
-      g->host_out_bytes = 0;
-    }
-    CUDA_TRY(cudaMalloc(&g->host_out, bytes ? bytes : 1));
-    g->host_out_bytes = bytes ? bytes : 1;
-  }
+  GRF_TRY(ensure_host_out(g, bytes, stream));
   int r = grf_sample(g, kappa, beta, k_step, seed, n_samples, g->host_out, opts, stream, stats);
   if (r == GRF_OK || r == GRF_ENOCONV) {
     cudaError_t e = cudaMemcpyAsync(out_host, g->host_out, bytes, cudaMemcpyDeviceToHost,
@@ -2130,6 +2146,72 @@ int grf_sample_host(grf_graph* g, double kappa, double beta, double k_step, uint
     if (e != cudaSuccess) r = fail(GRF_ECUDA, "copy to host: %s", cudaGetErrorString(e));
   }
   return r;
+}
+
+int grf_sample_host_stream(grf_graph* g, double kappa, double beta, double k_step,
+                           const uint64_t* seeds, int64_t n_calls, int64_t n_samples,
+                           void* const* out_host, const grf_options* opts, void* stream,
+                           grf_stats* stats) {
+  GRF_TRY(check_graph(g));
+  if (n_calls < 0) return fail(GRF_EINVAL, "bad n_calls");
+  if (n_calls == 0) return finish(RunStats{}, g, stats);
+  if (!seeds || !out_host) return fail(GRF_EINVAL, "seeds or out_host is null");
+  for (int64_t c = 0; c < n_calls; ++c)
+    if (!out_host[c]) return fail(GRF_EINVAL, "out_host[%lld] is null", (long long)c);
+  Opts o;
+  GRF_TRY(read_opts(opts, &o));
+  if (n_samples < 0 || n_samples > (int64_t)1 << 24) return fail(GRF_EINVAL, "bad n_samples");
+  GRF_TRY(ensure_device(g));
+  const size_t bytes = (size_t)g->n * (size_t)n_samples * (o.out_dtype == GRF_OUT_F64 ? 8 : 4);
+  cudaStream_t st = (cudaStream_t)stream;
+  GRF_TRY(ensure_host_out(g, bytes, stream));
+  if (g->host_stage_bytes < bytes) {
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (g->host_stage) CUDA_TRY(cudaFree(g->host_stage));
+    g->host_stage = nullptr;
+    g->host_stage_bytes = 0;
+    CUDA_TRY(cudaMalloc(&g->host_stage, bytes ? bytes : 1));
+    g->host_stage_bytes = bytes ? bytes : 1;
+  }
+  if (!g->copy_stream) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaEventCreateWithFlags(&g->ev_staged, cudaEventDisableTiming));
+    CUDA_TRY(cudaEventCreateWithFlags(&g->ev_d2h, cudaEventDisableTiming));
+  }
+  grf_stats sum{};
+  int worst = GRF_OK;
+  for (int64_t c = 0; c < n_calls; ++c) {
+    grf_stats one{};
+    const int r = grf_sample(g, kappa, beta, k_step, seeds[c], n_samples, g->host_out, opts,
+                             stream, &one);
+    if (r != GRF_OK && r != GRF_ENOCONV) {
+      cudaStreamSynchronize(g->copy_stream);
+      return r;
+    }
+    if (r == GRF_ENOCONV) worst = r;
+    sum.n_dofs = one.n_dofs;
+    sum.n_nodes += one.n_nodes;
+    sum.n_systems += one.n_systems;
+    sum.pcg_iters_total += one.pcg_iters_total;
+    sum.pcg_iters_max = std::max(sum.pcg_iters_max, one.pcg_iters_max);
+    sum.n_unconverged += one.n_unconverged;
+    sum.numeric_flag |= one.numeric_flag;
+    sum.kernel_launches += one.kernel_launches;
+    sum.n_precond_fallback += one.n_precond_fallback;
+    for (int i = 0; i < 8; ++i) sum.phase_ms[i] += one.phase_ms[i];
+    // stage the field (after the previous host copy has left the stage), then
+    // copy it to the host on the copy stream while the next call computes
+    if (c > 0) CUDA_TRY(cudaStreamWaitEvent(st, g->ev_d2h, 0));
+    CUDA_TRY(cudaMemcpyAsync(g->host_stage, g->host_out, bytes, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaEventRecord(g->ev_staged, st));
+    CUDA_TRY(cudaStreamWaitEvent(g->copy_stream, g->ev_staged, 0));
+    CUDA_TRY(cudaMemcpyAsync(out_host[c], g->host_stage, bytes, cudaMemcpyDeviceToHost,
+                             g->copy_stream));
+    CUDA_TRY(cudaEventRecord(g->ev_d2h, g->copy_stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(g->copy_stream));
+  if (stats) *stats = sum;
+  return worst;
 }
 
 int grf_noise(grf_graph* g, uint64_t seed, int64_t n_samples, void* out, int32_t raw_words,

@@ -141,13 +141,24 @@ __device__ __forceinline__ float get(const float4& v, int i) {
 // requests each vector's next block while the CTA works on the current one,
 // and the step's own-row loads then hit L2 instead of waiting on DRAM.
 constexpr int kPF = 4;
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void prefetch_rows(const float* rows, int32_t v0, int32_t nv) {
   const int32_t b = v0 + kPF * kVP;
   if (b >= nv) return;
   const int32_t n = nv - b < kVP ? nv - b : kVP;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(rows + (int64_t)b * kSG),
-               "r"((uint32_t)n * kSG * 4)
-               : "memory");
+  prefetch_l2(rows + (int64_t)b * kSG, (uint32_t)n * kSG * 4);
+}
+// the same for one FP64 sample row of the ABI layout ([S][nv] per node):
+// the whole 16-byte chunks inside the block (a row may start 8 bytes off)
+__device__ __forceinline__ void prefetch_row64(const double* row, int32_t v0, int32_t nv) {
+  const int32_t b = v0 + kPF * kVP;
+  if (b >= nv) return;
+  const int32_t n = nv - b < kVP ? nv - b : kVP;
+  const uintptr_t lo = ((uintptr_t)(row + b) + 15) & ~(uintptr_t)15;
+  const uintptr_t hi = (uintptr_t)(row + b + n) & ~(uintptr_t)15;
+  if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
 }
 
 // The vertices' neighbour records of one step (vertices v0 + u kVP, u < kU):
@@ -188,7 +199,6 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
   const int64_t n_items = (int64_t)L * nsg;
   const int hh = threadIdx.x & 1;            // half row: samples 4 hh .. 4 hh + 3
   const int32_t vs = threadIdx.x >> 1;       // vertex lane
-  const int32_t* __restrict__ vptr = g.vptr;
   const int32_t* __restrict__ nbr = g.adj_nbr;
   const double rtol2 = rtol * rtol;
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -276,7 +286,19 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         Acc4<2> a;
         a.init();
         for (int32_t v = vs; v < nv; v += kVP) {
-          const int32_t k0 = vptr[v], k1 = vptr[v + 1];
+          if (threadIdx.x < 2) {  // this half row's x and g rows kPF steps ahead
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i)
+              if (LIVE(i) && !dn[i]) {
+                prefetch_row64(XS(i), v, nv);
+                prefetch_row64(GS(i), v, nv);
+              }
+          }
+          int4 ea[kU];
+          int2 eb[kU];
+          load_ell(ell, v, nv, ea, eb);
+          const int32_t k0 = eb[0].x, deg = eb[0].y;
+          const int32_t wl[4] = {ea[0].x, ea[0].y, ea[0].z, ea[0].w};
           const double dd = D[v];
           const float dsv = Ds[v];
           float sv4[4];
@@ -284,8 +306,12 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           for (int i = 0; i < 4; ++i) {
             sv4[i] = 0.f;
             if (dn[i]) continue;
-            double y = dd * XS(i)[v];
-            for (int32_t k = k0; k < k1; ++k) y = fma(O[k], XS(i)[nbr[k]], y);
+            const double* __restrict__ xs = XS(i);
+            double y = dd * xs[v];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              if (j < deg) y = fma(O[k0 + j], xs[wl[j]], y);
+            for (int32_t k = k0 + 4; k < k0 + deg; ++k) y = fma(O[k], xs[nbr[k]], y);
             const double rv = GS(i)[v] - y;
             const float rel = (float)(rv * ivg[i]);
             sv4[i] = (float)(rv * ir[i]) * dsv;

@@ -569,3 +569,19 @@ def test_neumann_neumann_vertex_solve():
         _, u_ref = sampler.vertex_condensation(m, ml, kmat, 0.05, rhs)
         err = np.linalg.norm(uv.cpu().numpy() - u_ref, axis=1) / np.linalg.norm(u_ref, axis=1)
         assert err.max() < tol, (precision, err)
+
+
+def test_sample_host_stream_equals_separate_host_calls():
+    g = gi.random_small_graph(12, 20, 3)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.05)
+    kw = dict(precision="mixed", out_dtype="f32", use_graph=True, interior="spectral_umma")
+    seeds = [5, 6, 7]
+    outs, st = G.sample_host_stream(2.0, 0.7, 0.4, seeds, 4, **kw)
+    assert st["n_unconverged"] == 0 and st["pcg_iters_total"] > 0
+    for sd, o in zip(seeds, outs):
+        ref, _ = G.sample_host(2.0, 0.7, 0.4, sd, 4, **kw)
+        np.testing.assert_array_equal(o, ref)
+    # one buffer reused for every call holds the last call's field
+    buf = np.empty_like(outs[0])
+    G.sample_host_stream(2.0, 0.7, 0.4, seeds, 4, outs=[buf, buf, buf], **kw)
+    np.testing.assert_array_equal(buf, outs[-1])
