@@ -200,7 +200,7 @@ def _wdict(w):
             "seed": w.seed, "n_samples": w.n_samples}
 
 
-def oracle_sample(w, graph, n_nodes_sample=8, parallel=False):
+def oracle_sample(w, graph, n_nodes_sample=32, parallel=False):
     """Time the FP64 oracle on a bounded sample of the workload: mesh, assembly
     and noise for all samples, then `n_nodes_sample` of the L quadrature nodes
     (spread over the range), each factorised once and solved for every sample;
@@ -243,8 +243,9 @@ def oracle_sample(w, graph, n_nodes_sample=8, parallel=False):
              f"size), scaled by the DOF ratio {scale:.1f}")
     return {"value": w.n_samples / total, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"{where}: mesh+assembly+noise for {w.n_samples} samples, then {how} "
-                       f"(SuperLU factorisation + {w.n_samples} solves each), extrapolated "
-                       f"linearly to all {L} nodes; measured {wall:.1f} s"),
+                       f"(SuperLU factorisation + {w.n_samples} solves each)"
+                       + ("" if parallel else f", extrapolated linearly to all {L} nodes")
+                       + f"; measured {wall:.1f} s"),
             "wall_s": wall}
 
 

@@ -328,11 +328,14 @@ int grf_vertex_solve_noalloc(grf_graph* g, double kappa, double alpha, double ga
 /* Launch-schedule autotuner (the paper has no counterpart; it picks GPU launch
  * knobs only and does not change the computed field beyond rounding): times
  * grf_sample with CUDA events on `stream`, after one warm-up call each and
- * `reps` timed calls each, in two passes: first the edge-interior solvers
+ * `reps` timed calls each, in three passes: first the edge-interior solvers
  * (mixed precision: THOMAS and SPECTRAL with recover_sg in {1, 2, 4} where
  * tridiagonal edges remain, SPECTRAL_TC, and SPECTRAL_UMMA for n_samples <= 256;
  * FP64: THOMAS) with the default PCG layout, then every PCG layout (PER_SYSTEM,
- * and in mixed precision STAGED, STAGED_PAIRS, BATCHED) with the fastest solver.
+ * and in mixed precision STAGED, STAGED_PAIRS, BATCHED) with the fastest solver,
+ * then, in mixed precision where FP32 tridiagonal edges remain, the sweep
+ * layouts SEGMENTS and NODES against base->sweep (the segment/node split by
+ * edge length).
  *   out: device buffer [n_samples][n_dofs] of base->out_dtype for the trials;
  *   base: options whose precision, out_dtype, rtol and max_iter are kept (NULL:
  *     defaults); best: receives base with the fastest knobs; best_ms: its mean

@@ -869,7 +869,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   rs->begin(2, st);
   if (sizeof(T) == 4) {
     // FP32: the tridiagonal edges (all of them, or those the spectral path
-    // leaves over), short ones by segments and long ones by nodes; then the
+    // leaves over), short ones by segments and long ones by nodes, and the
     // spectral bins
     const bool spec = o.spectral && w.bhat;
     const int p = spec ? 2 : 0;
@@ -879,7 +879,25 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     }
     const int32_t head = bins_before(g, p, node_bin0(g, p, o, L));
     const int32_t tail = bins_total(g, p) - head;
-    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head);
+    if (o.consistent && !(spec && umma_ready(g, o, S, L)))
+      return fail(GRF_ENOTSUP, "the consistent mass needs the tensor-core sine transforms");
+    const bool umma = spec && umma_ready(g, o, S, L);
+    // tensor-core path with the per-edge end-value buffer: its gather writes
+    // g = b_v + (end values) for every node and sample, so it runs first and
+    // the tridiagonal edges then add into it
+    const bool gather_init = umma && w.ends;
+    if (umma) {
+      rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
+                                                    w.status, g->n_sm, st);
+      if (!gather_init)
+        rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], 0);
+      rs->launches += launch_spec_ends_umma(g->d, nd, S, g->d_spec_edges, g->spec_count,
+                                            g->n_spec_bins, w.bhat, gvec, w.ends,
+                                            (const float*)b, o.consistent, w.status, g->n_sm,
+                                            st);
+    }
+    rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head,
+                                       !umma);
     if (tail > 0 && !prm)
       return fail(GRF_EINVAL, "node-parallel condensation of %d edges without sweep constants",
                   (int)tail);
@@ -887,18 +905,10 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
                                             g->d_bin_edges[p] + head, tail, gvec, st);
-    if (o.consistent && !(spec && umma_ready(g, o, S, L)))
-      return fail(GRF_ENOTSUP, "the consistent mass needs the tensor-core sine transforms");
-    if (spec && umma_ready(g, o, S, L)) {
-      rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
-                                                    w.status, g->n_sm, st);
-      rs->launches += launch_spec_ends_umma(g->d, nd, S, g->d_spec_edges, g->spec_count,
-                                            g->n_spec_bins, w.bhat, gvec, w.ends,
-                                            o.consistent, w.status, g->n_sm, st);
-    } else if (spec && o.spec_tc)
+    if (!umma && spec && o.spec_tc)
       rs->launches += launch_spec_condense_mma(g->d, nd, S, (const float*)b, g->d_spec_edges,
                                                g->spec_count, w.bhat, gvec, st);
-    else if (spec)
+    else if (!umma && spec)
       rs->launches += launch_spec_condense(g->d, nd, kappa2, S, (const float*)b, g->d_spec_edges,
                                            g->spec_count, w.bhat, gvec, st);
   } else {
@@ -2061,24 +2071,39 @@ int grf_autotune(grf_graph* g, double kappa, double beta, double k_step, int64_t
   double best_t = 1e300;
   grf_options best_o = b0;
   int rc = GRF_OK;
-  // two passes: the interior solvers with the default PCG layout, then the PCG
-  // layouts with the best interior solver (the two phases hardly interact)
-  std::vector<std::pair<int, std::pair<int, int>>> trials;
-  for (auto cand : cands) trials.push_back({GRF_PCG_STAGED, cand});
+  // three passes: the interior solvers with the default PCG layout, then the
+  // PCG layouts with the best interior solver (the two phases hardly
+  // interact), then, where FP32 tridiagonal edges remain, the layout of their
+  // sweeps (segments only, node-parallel only, or the built-in length split)
+  struct Trial {
+    int lay, interior, sg, sweep;
+  };
+  std::vector<Trial> trials;
+  for (auto cand : cands) trials.push_back({GRF_PCG_STAGED, cand.first, cand.second, b0.sweep});
   const size_t n_first = trials.size();
+  size_t n_second = 0;
   for (size_t ti = 0;; ++ti) {
-    if (ti == n_first)
+    if (ti == n_first) {
       for (int lay : layouts)
         if (lay != GRF_PCG_STAGED)
-          trials.push_back({lay, {best_o.interior, best_o.recover_sg}});
+          trials.push_back({lay, best_o.interior, best_o.recover_sg, b0.sweep});
+      n_second = trials.size();
+    }
+    if (n_second > 0 && ti == n_second && fp32) {
+      const bool tridiag = best_o.interior == GRF_INTERIOR_THOMAS || g->thomas_rest() > 0;
+      if (tridiag)
+        for (int sw : {GRF_SWEEP_SEGMENTS, GRF_SWEEP_NODES})
+          if (sw != b0.sweep)
+            trials.push_back({best_o.pcg_layout, best_o.interior, best_o.recover_sg, sw});
+    }
     if (ti >= trials.size()) break;
     {
-      const int lay = trials[ti].first;
-      const auto cand = trials[ti].second;
+      const Trial tr = trials[ti];
       grf_options c = b0;
-      c.pcg_layout = lay;
-      c.interior = cand.first;
-      c.recover_sg = cand.second;
+      c.pcg_layout = tr.lay;
+      c.interior = tr.interior;
+      c.recover_sg = tr.sg;
+      c.sweep = tr.sweep;
       rc = grf_sample(g, kappa, beta, k_step, 1, n_samples, out, &c, stream, nullptr);
       if (rc != GRF_OK && rc != GRF_ENOCONV) break;
       float ms = 0.f;

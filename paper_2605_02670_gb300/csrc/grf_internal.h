@@ -118,11 +118,12 @@ void launch_nn_coeffs(const DevGraph& g, int32_t L, const double* saa, const dou
 // ---- thomas.cu
 // rhs (sample-minor [n][S], T) -> condensed right-hand side gvec[l][s][v] (double):
 // gvec = b at the vertices plus the end values of the listed edges (edges null:
-// every edge). Returns the number of kernels launched.
+// every edge); init = false: gvec already holds b plus other edges' values and
+// only the listed edges are added. Returns the number of kernels launched.
 template <typename T>
 int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                     const T* b, double* gvec, cudaStream_t st, const int32_t* edges = nullptr,
-                    int32_t n_edges = 0);
+                    int32_t n_edges = 0, bool init = true);
 // Vertex accumulation out[s][v] = sum_l w_l x[l][s][v], and fused interior
 // recovery + quadrature sum for the interior DOFs: binned register-resident
 // kernels (recover.cu) for edges up to the largest bin, the sequential kernel
@@ -273,14 +274,15 @@ int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, in
 // Samples run in blocks of spec_umma_sample_block(S) (a multiple of 16, at
 // most 64; at most 32 for the coefficients); the shared memory of the
 // coefficient kernel grows with L (spec_umma_fits). ends: a scratch of
-// 2 E S L floats for the end values per edge, then added into gvec by a
-// gather over the vertices' incidences (null: FP64 atomics into gvec).
+// 2 E S L floats for the end values per edge, then gathered over the vertices'
+// incidences into gvec = b_v + (end values), b the sample-minor noise: this
+// initialises gvec (null ends: FP64 atomics into an initialised gvec).
 int32_t spec_umma_sample_block(int64_t S);
 bool spec_umma_fits(int32_t L);
 int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
-                          const float* bhat, double* gvec, float* ends, bool consistent,
-                          PcgStatus* status, int n_sm, cudaStream_t st);
+                          const float* bhat, double* gvec, float* ends, const float* b,
+                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st);
 int launch_spec_coef_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
                           float* bhat, const float* xw, bool consistent, PcgStatus* status,

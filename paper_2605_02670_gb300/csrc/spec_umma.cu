@@ -23,17 +23,18 @@
 //
 // Splitting the modes by parity makes each product a plain GEMM: the end-value
 // K runs over the even modes into one accumulator and then over the odd modes
-// into another; the coefficient rows are 128 even and 128 odd modes, each tile
-// against its own right-hand side (xa + xb or xa - xb).
+// into another; a coefficient unit takes 128 modes of one parity against that
+// parity's right-hand side (xa + xb or xa - xb).
 //
-// One CTA of 512 threads per SM walks (edge, sample block, row block) units.
-// A unit is a 256-row block of A (two UMMA tiles of M = 128) against a
-// 64-wide K stage at a time, double-buffered: threads t and t + 256 generate
-// the two halves of row t of A (32 reciprocals each, split into BF16 hi/lo,
-// stored in the 128-byte-swizzled K-major layout) from per-unit tables laid
-// out in K order, and the B tile of the next stage waits in registers while
-// one thread issues the 24 MMAs of the current stage (2 tiles x 4 K steps x 3
-// split products, FP32 accumulators in tensor memory, N = the sample block).
+// Two CTAs of 256 threads per SM walk (edge, sample block, row block[, parity])
+// units, so that one CTA's barriers and latencies overlap the other's work. A
+// unit is a 128-row tile of A (UMMA M = 128) against a 64-wide K stage at a
+// time, double-buffered: threads t and t + 128 generate the two halves of row
+// t of A (32 reciprocals each, split into BF16 hi/lo, stored in the
+// 128-byte-swizzled K-major layout) from per-unit tables laid out in K order,
+// and the B tile of the next stage waits in registers while one thread issues
+// the 12 MMAs of the current stage (4 K steps x 3 split products, FP32
+// accumulators in tensor memory, N = the sample block of at most 32).
 // Epilogues: the end values go to a per-edge buffer [e][end][s][l] (lanes on
 // consecutive nodes, plain coalesced stores) and a gather over each vertex's
 // incidences adds them into g, where FP64 atomics into the vertex-major g
@@ -51,21 +52,18 @@ namespace {
 
 using namespace umma;
 
-constexpr int kT = 512;                        // threads; t and t + 256 share row t of A
-constexpr int kRows = 256;                     // A rows per unit (two 128-row tiles)
+constexpr int kT = 256;                        // threads; t and t + 128 share row t of A
+constexpr int kRows = 128;                     // A rows per unit (one UMMA tile)
 constexpr int kK = 64;                         // K per stage
-constexpr int kMaxSB = 64;                     // samples per unit (UMMA N)
-constexpr uint32_t kATile = 128 * kK * 2;      // one 128-row tile, one BF16 plane: 16 KB
-constexpr uint32_t kAPlane = 2 * kATile;       // both tiles
-constexpr uint32_t kBPlane = kMaxSB * kK * 2;  // 8 KB
-constexpr uint32_t kStageEnds = 2 * kAPlane + 2 * kBPlane;  // A hi/lo, B hi/lo
-constexpr int kMaxSBC = 32;                    // samples per coefficient unit
-constexpr uint32_t kBPlaneC = kMaxSBC * kK * 2;  // 4 KB
-constexpr uint32_t kStageCoef = 2 * kAPlane + 4 * kBPlaneC;  // A hi/lo, B+ hi/lo, B- hi/lo
-constexpr uint32_t kBhTile = kRows * kMaxSBC * 4;  // the block's bh rows (FP32): 32 KB
+constexpr int kMaxSB = 32;                     // samples per unit (UMMA N)
+constexpr uint32_t kATile = kRows * kK * 2;    // one BF16 plane of A: 16 KB
+constexpr uint32_t kBPlane = kMaxSB * kK * 2;  // 4 KB
+constexpr uint32_t kStage = 2 * kATile + 2 * kBPlane;  // A hi/lo, B hi/lo
+constexpr uint32_t kBhTile = kRows * kMaxSB * 4;       // a coefficient unit's bh rows: 16 KB
 constexpr int kMaxM = 1024;                    // modes of the sine-basis path
 constexpr int kMaxKE = kMaxM + 2 * kK;         // K positions of the end values (both parities)
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kColsEnds = 64;             // two accumulators of SB columns
+constexpr uint32_t kColsCoef = 32;
 constexpr size_t kSmemLimit = 232448;          // 227 KB per CTA
 
 __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
@@ -83,6 +81,7 @@ __device__ __forceinline__ float mode_shift(int32_t j, int32_t m) {
 struct Pipe {
   uint64_t* mbar;
   uint32_t* tslot;
+  uint32_t cols;
   uint32_t uses0, uses1;  // commits to each stage's barrier so far
   bool failed;
 
@@ -93,9 +92,10 @@ struct Pipe {
     else
       ++uses0;
   }
-  __device__ void init(unsigned char* at) {
+  __device__ void init(unsigned char* at, uint32_t tmem_cols) {
     mbar = reinterpret_cast<uint64_t*>(at);
     tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    cols = tmem_cols;
     uses0 = uses1 = 0;
     failed = false;
     if (threadIdx.x == 0) {
@@ -103,7 +103,7 @@ struct Pipe {
       mbar_init(&mbar[1], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < 32) tmem_alloc(tslot, kTmemCols);
+    if (threadIdx.x < 32) tmem_alloc(tslot, cols);
     fence_before();
     __syncthreads();
     fence_after();
@@ -130,19 +130,17 @@ struct Pipe {
     }
     fence_before();
     __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(*tslot, kTmemCols);
+    if (threadIdx.x < 32) tmem_dealloc(*tslot, cols);
   }
 };
 
-// Row t of a 256-row A block, chunk c (8 values) of one stage: split and
-// stored into the tile of the row (rows 0..127 tile 0, 128..255 tile 1).
+// Chunk c (8 values) of row t of A in one stage: split and stored.
 __device__ __forceinline__ void store_a_row(unsigned char* a_hi, unsigned char* a_lo, int t,
                                             int c, const float (&x)[8]) {
   uint4 hi, lo;
   split8(x, hi, lo);
-  const uint32_t o = (uint32_t)(t >> 7) * kATile + swz(t & 127, c);
-  *reinterpret_cast<uint4*>(a_hi + o) = hi;
-  *reinterpret_cast<uint4*>(a_lo + o) = lo;
+  *reinterpret_cast<uint4*>(a_hi + swz(t, c)) = hi;
+  *reinterpret_cast<uint4*>(a_lo + swz(t, c)) = lo;
 }
 
 __device__ __forceinline__ void store_b_row(unsigned char* b_hi, unsigned char* b_lo, int n,
@@ -153,26 +151,19 @@ __device__ __forceinline__ void store_b_row(unsigned char* b_hi, unsigned char* 
   *reinterpret_cast<uint4*>(b_lo + swz(n, c)) = lo;
 }
 
-
-// MMAs of one stage: tile 0 always, tile 1 when it has rows; accumulator
-// columns col0 (tile 0) and col1 (tile 1).
-__device__ __forceinline__ void issue_stage(uint32_t tmem, unsigned char* a_hi, unsigned char* a_lo,
-                                            unsigned char* b0_hi, unsigned char* b0_lo,
-                                            unsigned char* b1_hi, unsigned char* b1_lo,
-                                            uint32_t col0, uint32_t col1, bool tile1,
-                                            uint32_t idesc, bool acc) {
+// The 12 MMAs of one stage into the accumulator at column col.
+__device__ __forceinline__ void issue_stage(uint32_t tmem, uint32_t col, unsigned char* a_hi,
+                                            unsigned char* a_lo, unsigned char* b_hi,
+                                            unsigned char* b_lo, uint32_t idesc, bool acc) {
   fence_after();
-  mma_split_stage(tmem + col0, sdesc(smem_u32(a_hi)), sdesc(smem_u32(a_lo)),
-                  sdesc(smem_u32(b0_hi)), sdesc(smem_u32(b0_lo)), idesc, acc);
-  if (tile1)
-    mma_split_stage(tmem + col1, sdesc(smem_u32(a_hi + kATile)), sdesc(smem_u32(a_lo + kATile)),
-                    sdesc(smem_u32(b1_hi)), sdesc(smem_u32(b1_lo)), idesc, acc);
+  mma_split_stage(tmem + col, sdesc(smem_u32(a_hi)), sdesc(smem_u32(a_lo)), sdesc(smem_u32(b_hi)),
+                  sdesc(smem_u32(b_lo)), idesc, acc);
 }
 
 // ---------------------------------------------------------------- end values
 
 template <bool kCons>
-__global__ void __launch_bounds__(kT, 1)
+__global__ void __launch_bounds__(kT, 2)
     spec_ends_umma_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
                           int32_t n_edges, const float* __restrict__ bhat,
                           double* __restrict__ gvec, float* __restrict__ ends, int32_t SB,
@@ -181,20 +172,20 @@ __global__ void __launch_bounds__(kT, 1)
   unsigned char* sm = align1024(se_raw);
   // per-unit tables in K order (the even modes, then the odd modes, each
   // padded to whole stages): mode shift, phi_j (0 on padding), mode (-1)
-  float* sigk = reinterpret_cast<float*>(sm + 2 * kStageEnds);
+  float* sigk = reinterpret_cast<float*>(sm + 2 * kStage);
   float* phik = sigk + kMaxKE;
   int32_t* modek = reinterpret_cast<int32_t*>(phik + kMaxKE);
   Pipe pp;
-  pp.init(reinterpret_cast<unsigned char*>(modek + kMaxKE));
+  pp.init(reinterpret_cast<unsigned char*>(modek + kMaxKE), kColsEnds);
   const uint32_t tmem = *pp.tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row = tid & (kRows - 1), half = tid >> 8;  // A row and which 32 of its 64 K
+  const int row = tid & (kRows - 1), half = tid >> 7;  // A row and which 32 of its 64 K
   const uint32_t idesc = idesc_bf16(128, SB);
   const int32_t L = nd.L;
   const int64_t nsb = (S + SB - 1) / SB;
   const int32_t nrb = (L + kRows - 1) / kRows;
   const int64_t units = (int64_t)n_edges * nsb * nrb;
-  // B tile item of this thread: sample bn, K chunk bc (SB x 8 items)
+  // B tile item of this thread: sample bn, K chunk bc (SB x 8 <= 256 items)
   const bool bitem = tid < SB * 8;
   const int bn = tid % SB, bc = tid / SB;
 
@@ -224,7 +215,6 @@ __global__ void __launch_bounds__(kT, 1)
     const int32_t l = rb * kRows + row;
     const float dl = l < L ? nd.shift[l] * h2f : 1.f;
     const float ep = kCons ? 1.f - dl * (1.f / 6.f) : 1.f;
-    const bool tile1 = rb * kRows + 128 < L;  // rows of tile 1 exist
     const float* bcol = bhat + off * S + s0 + bn;
     const bool bok = bitem && bn < kv;
     float xb[8];
@@ -244,9 +234,9 @@ __global__ void __launch_bounds__(kT, 1)
       float xn[8];
       if (t + 1 < nk) load_b(t + 1, xn);
       if (!pp.acquire(st)) break;
-      unsigned char* a_hi = sm + st * kStageEnds;
-      unsigned char* a_lo = a_hi + kAPlane;
-      unsigned char* b_hi = a_lo + kAPlane;
+      unsigned char* a_hi = sm + st * kStage;
+      unsigned char* a_lo = a_hi + kATile;
+      unsigned char* b_hi = a_lo + kATile;
       unsigned char* b_lo = b_hi + kBPlane;
       const float* sg = sigk + t * kK + half * 32;
 #pragma unroll
@@ -274,51 +264,49 @@ __global__ void __launch_bounds__(kT, 1)
       fence_proxy_async();
       __syncthreads();
       if (tid == 0) {
-        const int par = t >= ks_e ? 1 : 0;  // accumulator of the odd modes
-        issue_stage(tmem, a_hi, a_lo, b_hi, b_lo, b_hi, b_lo, (uint32_t)(2 * par * SB),
-                    (uint32_t)((2 * par + 1) * SB), tile1, idesc, t != 0 && t != ks_e);
+        // odd modes from stage ks_e on, into the second accumulator
+        issue_stage(tmem, t >= ks_e ? (uint32_t)SB : 0u, a_hi, a_lo, b_hi, b_lo, idesc,
+                    t != 0 && t != ks_e);
         commit(&pp.mbar[st]);
       }
       pp.bump(st);
     }
     if (pp.failed || !pp.drain(last)) break;
-    // epilogue: warp w reads tile (w / 4) % 2, lanes 32 (w % 4) .. + 31, the
-    // sample half w / 8 of both accumulators
-    const int q4 = warp & 3, tl = (warp >> 2) & 1, hs = warp >> 3;
-    if (tl == 0 || tile1) {
-      const int32_t lr = rb * kRows + 128 * tl + 32 * q4 + lane;
-      const uint32_t lanes = (uint32_t)(32 * q4) << 16;
-      const int hsb = SB / 2;
-      const int64_t dv = (int64_t)g.ev[e] - g.eu[e];
-      for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
-        float o[8], v[8];
-        tmem_ld8(tmem + lanes + (uint32_t)(tl * SB + cb), o);
-        if (ks_o > 0) {
-          tmem_ld8(tmem + lanes + (uint32_t)((2 + tl) * SB + cb), v);
-        } else {
+    // epilogue: warp w reads lanes 32 (w % 4) .. + 31, sample half w / 4, of
+    // both accumulators
+    const int q4 = warp & 3, hs = warp >> 2;
+    const int32_t lr = rb * kRows + 32 * q4 + lane;
+    const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+    const int hsb = SB / 2;
+    const int64_t dv = (int64_t)g.ev[e] - g.eu[e];
+    for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
+      float o[8], v[8];
+      tmem_ld8(tmem + lanes + (uint32_t)cb, o);
+      if (ks_o > 0) {
+        tmem_ld8(tmem + lanes + (uint32_t)(SB + cb), v);
+      } else {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) v[i] = 0.f;
-        }
-        if (lr < L && ends) {
-          // per-edge buffer [e][end][s][l]: lanes write consecutive nodes
-          float* pe = ends + ((int64_t)e * 2 * S + s0 + cb) * L + lr;
-          const int64_t side = S * (int64_t)L;
+        for (int i = 0; i < 8; ++i) v[i] = 0.f;
+      }
+      if (lr < L && ends) {
+        // per-edge buffer [e][end][s][l]: lanes write consecutive nodes
+        float* pe = ends + ((int64_t)e * 2 * S + s0 + cb) * L + lr;
+        const int64_t side = S * (int64_t)L;
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (cb + i < kv) {
-              pe[(int64_t)i * L] = o[i] + v[i];
-              pe[(int64_t)i * L + side] = o[i] - v[i];
-            }
-        } else if (lr < L) {
-          double* pa = gvec + ((int64_t)lr * S + s0 + cb) * g.nv + g.eu[e];
+        for (int i = 0; i < 8; ++i)
+          if (cb + i < kv) {
+            pe[(int64_t)i * L] = o[i] + v[i];
+            pe[(int64_t)i * L + side] = o[i] - v[i];
+          }
+      } else if (lr < L) {
+        double* pa = gvec + ((int64_t)lr * S + s0 + cb) * g.nv + g.eu[e];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (cb + i < kv) {
-              atomicAdd(pa, (double)(o[i] + v[i]));
-              atomicAdd(pa + dv, (double)(o[i] - v[i]));
-              pa += g.nv;
-            }
-        }
+        for (int i = 0; i < 8; ++i)
+          if (cb + i < kv) {
+            atomicAdd(pa, (double)(o[i] + v[i]));
+            atomicAdd(pa + dv, (double)(o[i] - v[i]));
+            pa += g.nv;
+          }
       }
     }
     fence_before();
@@ -328,14 +316,15 @@ __global__ void __launch_bounds__(kT, 1)
   pp.finish(status);
 }
 
-// g(l, s, v) += sum over the spectral edges at v of that end's value, from the
-// per-edge buffer [e][end][s][l]. A CTA takes 32 vertices x 32 nodes of one
-// sample: warp w gathers vertices 4w .. 4w + 3 with the lanes on consecutive
-// nodes, and after a transpose in shared memory writes 32 consecutive
-// vertices per node (FP32 sums over the incidences, added in FP64).
+// g(l, s, v) = b_v(s) + sum over the spectral edges at v of that end's value,
+// from the per-edge buffer [e][end][s][l] and the sample-minor noise b. A CTA
+// takes 32 vertices x 32 nodes of one sample: warp w gathers vertices
+// 4w .. 4w + 3 with the lanes on consecutive nodes, and after a transpose in
+// shared memory writes 32 consecutive vertices per node (FP32 sums over the
+// incidences, added to b_v in FP64).
 __global__ void __launch_bounds__(256)
     ends_gather_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ ends,
-                       double* __restrict__ gvec) {
+                       const float* __restrict__ b, double* __restrict__ gvec) {
   __shared__ float tile[32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t nvt = (g.nv + 31) / 32, nlt = (L + 31) / 32;
@@ -365,16 +354,19 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int32_t l = l0 + 4 * warp + q, v = v0 + lane;
-      if (l < L && v < g.nv) gvec[((int64_t)l * S + s) * g.nv + v] += (double)tile[lane][4 * warp + q];
+      if (l < L && v < g.nv)
+        gvec[((int64_t)l * S + s) * g.nv + v] =
+            (double)b[(int64_t)v * S + s] + (double)tile[lane][4 * warp + q];
     }
     __syncthreads();
   }
 }
 
+
 // -------------------------------------------------------------- coefficients
 
 template <bool kCons>
-__global__ void __launch_bounds__(kT, 1)
+__global__ void __launch_bounds__(kT, 2)
     spec_coef_umma_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
                           int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw,
                           int32_t SB, int32_t nrb, PcgStatus* __restrict__ status) {
@@ -383,45 +375,45 @@ __global__ void __launch_bounds__(kT, 1)
   const int32_t L = nd.L;
   const int nk = (L + kK - 1) / kK;
   const int LK = nk * kK;  // K positions: the nodes, padded to whole stages
+  float* bht = reinterpret_cast<float*>(sm + 2 * kStage);  // [kRows][SB] the unit's bh rows
   // per-unit node tables: delta_l (1 on padding), eps_l (1), sc_l (0)
-  float* bht = reinterpret_cast<float*>(sm + 2 * kStageCoef);  // [kRows][SB] bh rows
-  float* dls = bht + kRows * kMaxSBC;
+  float* dls = bht + kRows * kMaxSB;
   float* eps = dls + LK;
   float* scs = eps + LK;
   float* dpart = scs + LK;  // [kT] the two halves of each row's D_j
   Pipe pp;
-  pp.init(reinterpret_cast<unsigned char*>(dpart + kT));
+  pp.init(reinterpret_cast<unsigned char*>(dpart + kT), kColsCoef);
   const uint32_t tmem = *pp.tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row = tid & (kRows - 1), half = tid >> 8;
+  const int row = tid & (kRows - 1), half = tid >> 7;
   const uint32_t idesc = idesc_bf16(128, SB);
   const int64_t nsb = (S + SB - 1) / SB;
-  const int64_t units = (int64_t)n_edges * nsb * nrb;
+  const int64_t units = (int64_t)n_edges * nsb * nrb * 2;
   const bool bitem = tid < SB * 8;
   const int bn = tid % SB, bc = tid / SB;
   const int64_t xstride = (int64_t)g.nv * S;  // from node l to node l + 1 in xw
+  const bool async_bh = (S & 3) == 0;         // 16-byte row chunks
 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int32_t rb = (int32_t)(u % nrb);
-    const int64_t rest = u / nrb;
+    const int par = (int)(u & 1);  // 0: even modes (xa + xb), 1: odd modes (xa - xb)
+    const int32_t rb = (int32_t)((u >> 1) % nrb);
+    const int64_t rest = (u >> 1) / nrb;
     const int64_t s0 = (rest % nsb) * SB;
     const int32_t e = edges[rest / nsb];
     const int32_t m = g.nel[e] - 1;
-    if (m < 1 || 2 * 128 * rb >= m) continue;  // no mode in this row block
+    if (m < 1 || 2 * kRows * rb + par >= m) continue;  // no mode of this parity here
     const int kv = (int)(S - s0 < SB ? S - s0 : SB);
     const int64_t off = g.ioff[e];
     const double h = g.he[e];
     const float hf = (float)h, h2f = (float)(h * h);
     const int32_t va = g.eu[e], vb = g.ev[e];
-    // the block's bh rows, fetched asynchronously now and used by the epilogue
-    // (16-byte copies need S to be a multiple of 4; otherwise the epilogue
-    // reads them itself)
-    const bool async_bh = (S & 3) == 0;
+    // mode of row r: j = 2 (128 rb + r) + par
+    // the unit's bh rows, fetched asynchronously now and used by the epilogue
     if (async_bh) {
-      const int cpr = SB / 4;  // 16-byte chunks per row
+      const int cpr = SB / 4;
       for (int idx = tid; idx < kRows * cpr; idx += kT) {
         const int rr = idx / cpr, c4 = idx - rr * cpr;
-        const int32_t jr = 2 * (128 * rb + (rr & 127)) + (rr >> 7);
+        const int32_t jr = 2 * (kRows * rb + rr) + par;
         const int valid = jr < m ? (kv - 4 * c4 > 4 ? 4 : (kv - 4 * c4 > 0 ? kv - 4 * c4 : 0)) : 0;
         const float* src = bhat + (off + (jr < m ? jr : 0)) * S + s0 + (valid > 0 ? 4 * c4 : 0);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
@@ -439,10 +431,9 @@ __global__ void __launch_bounds__(kT, 1)
       scs[p] = ok ? nd.wgam[p] * hf : 0.f;
     }
     __syncthreads();
-    // this thread's row: tile row / 128 (0: even modes, 1: odd modes)
-    const int32_t j = 2 * (128 * rb + (row & 127)) + (row >> 7);
+    const int32_t j = 2 * (kRows * rb + row) + par;
     const float sg = j < m ? mode_shift(j, m) : 0.f;
-    const bool tile1 = 2 * 128 * rb + 1 < m;  // an odd mode exists in this block
+    const float sgn = par ? -1.f : 1.f;
     float D = 0.f;
     const bool bok = bitem && bn < kv;
     const float* pxa = xw + (int64_t)va * S + s0 + bn;
@@ -465,12 +456,10 @@ __global__ void __launch_bounds__(kT, 1)
       float na[8], nc[8];
       if (t + 1 < nk) load_b(t + 1, na, nc);
       if (!pp.acquire(st)) break;
-      unsigned char* a_hi = sm + st * kStageCoef;
-      unsigned char* a_lo = a_hi + kAPlane;
-      unsigned char* bp_hi = a_lo + kAPlane;
-      unsigned char* bp_lo = bp_hi + kBPlaneC;
-      unsigned char* bm_hi = bp_lo + kBPlaneC;
-      unsigned char* bm_lo = bm_hi + kBPlaneC;
+      unsigned char* a_hi = sm + st * kStage;
+      unsigned char* a_lo = a_hi + kATile;
+      unsigned char* b_hi = a_lo + kATile;
+      unsigned char* b_lo = b_hi + kBPlane;
       const int k0 = t * kK + half * 32;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -497,15 +486,13 @@ __global__ void __launch_bounds__(kT, 1)
         store_a_row(a_hi, a_lo, row, 4 * half + c, x);
       }
       if (bitem) {
-        float xp[8], xm[8];
+        float xx[8];
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
           const float ep = kCons ? eps[t * kK + bc * 8 + r] : 1.f;
-          xp[r] = ep * (xa[r] + xc[r]);
-          xm[r] = ep * (xa[r] - xc[r]);
+          xx[r] = ep * fmaf(sgn, xc[r], xa[r]);
         }
-        store_b_row(bp_hi, bp_lo, bn, bc, xp);
-        store_b_row(bm_hi, bm_lo, bn, bc, xm);
+        store_b_row(b_hi, b_lo, bn, bc, xx);
       }
       if (t + 1 < nk) {
 #pragma unroll
@@ -517,8 +504,7 @@ __global__ void __launch_bounds__(kT, 1)
       fence_proxy_async();
       __syncthreads();
       if (tid == 0) {
-        issue_stage(tmem, a_hi, a_lo, bp_hi, bp_lo, bm_hi, bm_lo, 0u, (uint32_t)SB, tile1, idesc,
-                    t != 0);
+        issue_stage(tmem, 0u, a_hi, a_lo, b_hi, b_lo, idesc, t != 0);
         commit(&pp.mbar[st]);
       }
       pp.bump(st);
@@ -527,24 +513,24 @@ __global__ void __launch_bounds__(kT, 1)
     dpart[tid] = D;
     if (!pp.drain(last)) break;
     // epilogue, two passes through shared memory (the stage buffers are free):
-    // (1) warp w reads tile (w / 4) % 2, lanes 32 (w % 4) .. + 31, sample half
-    //     w / 8, into a row-major tile of the block's rows (SB + 1 floats a row)
+    // (1) warp w reads lanes 32 (w % 4) .. + 31, sample half w / 4, into a
+    //     row-major tile (SB + 1 floats a row)
     float* ct = reinterpret_cast<float*>(sm);
     float* rowd = ct + kRows * (SB + 1);  // D_j of each row
     float* rowp = rowd + kRows;           // phi_j of each row
-    const int q4 = warp & 3, tl = (warp >> 2) & 1, hs = warp >> 3;
-    if (tl == 0 || tile1) {
-      const int rr = 128 * tl + 32 * q4 + lane;  // row within the block
+    const int q4 = warp & 3, hs = warp >> 2;
+    {
+      const int rr = 32 * q4 + lane;
       const uint32_t lanes = (uint32_t)(32 * q4) << 16;
       const int hsb = SB / 2;
       for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
         float cv[8];
-        tmem_ld8(tmem + lanes + (uint32_t)(tl * SB + cb), cv);
+        tmem_ld8(tmem + lanes + (uint32_t)cb, cv);
 #pragma unroll
         for (int i = 0; i < 8; ++i) ct[rr * (SB + 1) + cb + i] = cv[i];
       }
       if (hs == 0) {
-        const int32_t jr = 2 * (128 * rb + 32 * q4 + lane) + tl;
+        const int32_t jr = 2 * (kRows * rb + rr) + par;
         rowd[rr] = dpart[rr] + dpart[kRows + rr];
         rowp[rr] = sqrtf(2.f / (float)(m + 1)) * sinpif((float)(jr + 1) / (float)(m + 1));
       }
@@ -553,11 +539,10 @@ __global__ void __launch_bounds__(kT, 1)
     __syncthreads();
     // (2) c_j = D_j bh_j + phi_j C_j over whole rows: consecutive threads take
     //     consecutive samples of one mode, so every store is coalesced
-    const int nrow = tile1 ? kRows : 128;
 #pragma unroll 4
-    for (int idx = tid; idx < nrow * SB; idx += kT) {
+    for (int idx = tid; idx < kRows * SB; idx += kT) {
       const int rr = idx / SB, sc = idx - rr * SB;
-      const int32_t jr = 2 * (128 * rb + (rr & 127)) + (rr >> 7);
+      const int32_t jr = 2 * (kRows * rb + rr) + par;
       if (jr < m && sc < kv) {
         float* o = bhat + (off + jr) * S + s0 + sc;
         const float bh = async_bh ? bht[rr * SB + sc] : *o;
@@ -571,10 +556,10 @@ __global__ void __launch_bounds__(kT, 1)
   pp.finish(status);
 }
 
-size_t ends_smem() { return 1024 + 2 * (size_t)kStageEnds + 3 * (size_t)kMaxKE * 4 + 64; }
+size_t ends_smem() { return 1024 + 2 * (size_t)kStage + 3 * (size_t)kMaxKE * 4 + 64; }
 size_t coef_smem(int32_t L) {
   const size_t lk = (size_t)(L + kK - 1) / kK * kK;
-  return 1024 + 2 * (size_t)kStageCoef + kBhTile + (3 * lk + kT) * sizeof(float) + 64;
+  return 1024 + 2 * (size_t)kStage + kBhTile + (3 * lk + kT) * sizeof(float) + 64;
 }
 
 }  // namespace
@@ -591,8 +576,8 @@ bool spec_umma_fits(int32_t L) {
 
 int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
-                          const float* bhat, double* gvec, float* ends, bool consistent,
-                          PcgStatus* status, int n_sm, cudaStream_t st) {
+                          const float* bhat, double* gvec, float* ends, const float* b,
+                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st) {
   int32_t n = 0;
   for (int i = 0; i < n_bins; ++i) n += bin_count[i];
   if (n <= 0) return 0;
@@ -601,12 +586,14 @@ int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
   auto kern = consistent ? spec_ends_umma_kernel<true> : spec_ends_umma_kernel<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * ((nd.L + kRows - 1) / kRows);
-  const int grid = (int)(units < n_sm ? units : n_sm);
-  kern<<<grid, kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, gvec, ends, SB, status);
+  const int64_t cap = 2 * (int64_t)n_sm;  // two CTAs per SM
+  kern<<<(int)(units < cap ? units : cap), kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, gvec,
+                                                           ends, SB, status);
   if (!ends) return 1;
   const int64_t tiles = (int64_t)((g.nv + 31) / 32) * ((nd.L + 31) / 32) * S;
-  const int64_t cap = (int64_t)n_sm * 8;
-  ends_gather_kernel<<<(int)(tiles < cap ? tiles : cap), 256, 0, st>>>(g, nd.L, S, ends, gvec);
+  const int64_t gcap = (int64_t)n_sm * 8;
+  ends_gather_kernel<<<(int)(tiles < gcap ? tiles : gcap), 256, 0, st>>>(g, nd.L, S, ends, b,
+                                                                         gvec);
   return 2;
 }
 
@@ -617,15 +604,17 @@ int launch_spec_coef_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
   int32_t n = 0;
   for (int i = 0; i < n_bins; ++i) n += bin_count[i];
   if (n <= 0) return 0;
-  const int32_t SB = spec_umma_sample_block(S) < kMaxSBC ? spec_umma_sample_block(S) : kMaxSBC;
+  const int32_t SB = spec_umma_sample_block(S);
   const size_t smem = coef_smem(nd.L);
   auto kern = consistent ? spec_coef_umma_kernel<true> : spec_coef_umma_kernel<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int32_t mmax = g.max_m < kMaxM ? g.max_m : kMaxM;
-  const int32_t nrb = mmax > 0 ? (mmax + kRows - 1) / kRows : 1;  // 128 even + 128 odd modes
-  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * nrb;
-  const int grid = (int)(units < n_sm ? units : n_sm);
-  kern<<<grid, kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, xw, SB, nrb, status);
+  // row blocks of 128 modes of one parity
+  const int32_t nrb = mmax > 0 ? ((mmax + 1) / 2 + kRows - 1) / kRows : 1;
+  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * nrb * 2;
+  const int64_t cap = 2 * (int64_t)n_sm;
+  kern<<<(int)(units < cap ? units : cap), kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, xw, SB,
+                                                           nrb, status);
   return 1;
 }
 

@@ -178,50 +178,64 @@ __global__ void __launch_bounds__(256) condense_kernel(DevGraph g, DevNodes nd, 
 // U_v = sum_l w_l u_v^(l) in FP64; also leaves xw[l][v][s] = w_l u_v^(l) in the
 // sweep precision for the interior recovery (sample-minor: an edge end's
 // samples are one contiguous row).
-// One CTA per tile of 32 vertices and up to 64 samples: for each node l the
-// tile's FP64 solutions are read along the vertices ([l][s][v] rows) and the
-// weighted values written along the samples ([l][v][s] rows) through a
-// shared-memory transpose, so both sides stay coalesced; the FP64 node sum of
-// every (s, v) stays in the registers of its thread.
-constexpr int kAccTile = 32, kAccRows = 8, kAccS = 64;
+// One CTA per tile of 32 vertices and 32 samples: for each node l the tile's
+// FP64 solutions are read along the vertices ([l][s][v] rows) and the weighted
+// values written along the samples ([l][v][s] rows) through a shared-memory
+// transpose, so both sides stay coalesced; the FP64 node sum of every (s, v)
+// stays in the registers of its thread. kAccL nodes are loaded before each
+// transpose, so every thread has kAccL x 4 independent loads in flight.
+constexpr int kAccTile = 32, kAccRows = 8, kAccS = 32, kAccL = 4;
 
 template <typename T, typename OutT>
 __global__ void __launch_bounds__(kAccTile * kAccRows)
     vertex_accum_kernel(DevGraph g, DevNodes nd, int64_t S, const double* __restrict__ xv,
                         OutT* __restrict__ out, T* __restrict__ xw) {
-  __shared__ T tile[kAccS][kAccTile + 1];
+  __shared__ T tile[kAccL][kAccS][kAccTile + 1];
   const int tx = threadIdx.x % kAccTile, ty = threadIdx.x / kAccTile;
   const int64_t n_vt = (g.nv + kAccTile - 1) / kAccTile;
   const int64_t n_sc = (S + kAccS - 1) / kAccS;
+  constexpr int kQ = kAccS / kAccRows;
   for (int64_t b = blockIdx.x; b < n_vt * n_sc; b += gridDim.x) {
     const int64_t v0 = (b % n_vt) * kAccTile, s0 = (b / n_vt) * kAccS;
     const int vn = (int)(g.nv - v0 < kAccTile ? g.nv - v0 : kAccTile);
     const int sn = (int)(S - s0 < kAccS ? S - s0 : kAccS);
-    double acc[kAccS / kAccRows];
+    double acc[kQ];
 #pragma unroll
-    for (int q = 0; q < kAccS / kAccRows; ++q) acc[q] = 0.0;
-    for (int32_t l = 0; l < nd.L; ++l) {
-      const double wl = nd.weight[l];
+    for (int q = 0; q < kQ; ++q) acc[q] = 0.0;
+    for (int32_t l0 = 0; l0 < nd.L; l0 += kAccL) {
+      const int nl = nd.L - l0 < kAccL ? nd.L - l0 : kAccL;
+      double x[kAccL][kQ];
 #pragma unroll
-      for (int q = 0; q < kAccS / kAccRows; ++q) {
-        const int s = ty + q * kAccRows;
-        if (s < sn && tx < vn) {
-          const double wx = wl * xv[((int64_t)l * S + s0 + s) * g.nv + v0 + tx];
+      for (int u = 0; u < kAccL; ++u)
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const int s = ty + q * kAccRows;
+          x[u][q] = (u < nl && s < sn && tx < vn)
+                        ? xv[((int64_t)(l0 + u) * S + s0 + s) * g.nv + v0 + tx]
+                        : 0.0;
+        }
+#pragma unroll
+      for (int u = 0; u < kAccL; ++u) {
+        const double wl = u < nl ? nd.weight[l0 + u] : 0.0;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+          const double wx = wl * x[u][q];
           acc[q] += wx;
-          tile[s][tx] = (T)wx;
+          tile[u][ty + q * kAccRows][tx] = (T)wx;
         }
       }
       __syncthreads();
       // the tile's rows xw[l][v0 + j][s0 .. s0 + sn) follow each other when
       // sn == S; write them along the samples
-      for (int idx = threadIdx.x; idx < vn * sn; idx += blockDim.x) {
-        const int j = idx / sn, s = idx - j * sn;
-        xw[((int64_t)l * g.nv + v0 + j) * S + s0 + s] = tile[s][j];
+      for (int idx = threadIdx.x; idx < nl * vn * sn; idx += blockDim.x) {
+        const int u = idx / (vn * sn), r = idx - u * vn * sn;
+        const int j = r / sn, s = r - j * sn;
+        xw[((int64_t)(l0 + u) * g.nv + v0 + j) * S + s0 + s] = tile[u][s][j];
       }
       __syncthreads();
     }
 #pragma unroll
-    for (int q = 0; q < kAccS / kAccRows; ++q) {
+    for (int q = 0; q < kQ; ++q) {
       const int s = ty + q * kAccRows;
       if (s < sn && tx < vn) out[(s0 + s) * g.n + v0 + tx] = (OutT)acc[q];
     }
@@ -339,10 +353,13 @@ int recover_sample_group() { return kSG; }
 
 template <typename T>
 int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
-                    double* gvec, cudaStream_t st, const int32_t* edges, int32_t n_edges) {
-  gvec_init_kernel<T><<<grid_for((int64_t)nd.L * S * g.nv, 256), 256, 0, st>>>(g, nd.L, S, b, gvec);
+                    double* gvec, cudaStream_t st, const int32_t* edges, int32_t n_edges,
+                    bool init) {
+  if (init)
+    gvec_init_kernel<T><<<grid_for((int64_t)nd.L * S * g.nv, 256), 256, 0, st>>>(g, nd.L, S, b,
+                                                                                 gvec);
   if (!edges) n_edges = g.ne;
-  if (g.ni == 0 || n_edges == 0) return 1;
+  if (g.ni == 0 || n_edges == 0) return init ? 1 : 0;
   const int64_t nsg = (S + kSG - 1) / kSG;
   // one thread per node (rounded up to whole warps, at most 256 per pass)
   int threads = ((nd.L + 31) / 32) * 32;
@@ -357,7 +374,7 @@ int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_
   if (blocks > sm_count() * 64) blocks = sm_count() * 64;
   condense_kernel<T><<<(int)blocks, threads, smem, st>>>(g, nd, kappa2, S, b, gvec, stage_max,
                                                          edges, n_edges);
-  return 2;
+  return init ? 2 : 1;
 }
 
 template <typename T, typename OutT>
@@ -395,10 +412,10 @@ void launch_to_minor(const DevGraph& g, int64_t S, const double* src, T* dst, bo
 
 template int launch_condense<float>(const DevGraph&, const DevNodes&, double, int64_t,
                                     const float*, double*, cudaStream_t, const int32_t*,
-                                    int32_t);
+                                    int32_t, bool);
 template int launch_condense<double>(const DevGraph&, const DevNodes&, double, int64_t,
                                      const double*, double*, cudaStream_t, const int32_t*,
-                                     int32_t);
+                                     int32_t, bool);
 #define GRF_INST_RECOVER(T, O)                                                                 \
   template int launch_recover<T, O>(const DevGraph&, const DevNodes&, double, int64_t, const T*, \
                                     const double*, O*, const SweepParams<T>*, T*,                \
