@@ -260,6 +260,26 @@ def test_umma_transforms_sample_counts(S):
         assert rel_l2(u.double().cpu().numpy(), ref, ml) < TOL["mixed"]
 
 
+@pytest.mark.parametrize("S", [8, 33])
+def test_umma_with_edges_beyond_the_sine_basis(S):
+    """Edges longer than the sine-basis path (1199 and 2599 interior nodes, swept
+    node-parallel) beside tensor-core edges: the gathered end values initialise
+    the right-hand sides and the sweeps add theirs after; 33 samples also give a
+    ragged second sample block in the contractions."""
+    ne = [40, 300, 1200, 2600, 7, 513]
+    eu = np.array([0, 1, 2, 3, 0, 1])
+    ev = np.array([1, 2, 3, 0, 2, 3])
+    lengths = np.array(ne) * 1e-3 * np.linspace(0.95, 1.05, len(ne))
+    g = gi.Graph(4, eu, ev, lengths)
+    G = _graph(g, n_elems=ne)
+    kappa, beta, k, seed = 4.0, 0.7, 0.5, 13
+    ml, ref = _oracle(f"umma_long{S}", g, kappa, beta, k, seed, S, n_elems=ne)
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype="f64",
+                     interior="spectral_umma")
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    assert rel_l2(u.cpu().numpy(), ref, ml) < TOL["mixed"]
+
+
 def test_umma_transforms_graph_replay_and_apply():
     """The tensor-core path inside a captured CUDA graph (replayed twice with
     different seeds) and through the general right-hand-side entry point."""
