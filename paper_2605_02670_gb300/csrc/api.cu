@@ -426,6 +426,22 @@ struct HostNodes {
   int32_t L() const { return (int32_t)alpha.size(); }
 };
 
+// w_l A_l^{-1} = (w_l / s_l) (A_l / s_l)^{-1} for any s_l > 0: every node is
+// rescaled by s_l = max(alpha_l, gamma_l), exactly in FP64 on the host, so that
+// the shifted operator's coefficients and the weights that reach the FP32
+// kernels stay O(1) whatever the shift (e^{2y} passes the FP32 range for the
+// outer sinc nodes of small steps: 3.4e38 at y = 44.4).
+void normalize_nodes(HostNodes& h) {
+  for (size_t l = 0; l < h.alpha.size(); ++l) {
+    const double s = std::max(h.alpha[l], h.gamma[l]);
+    if (s > 0 && std::isfinite(s)) {
+      h.alpha[l] /= s;
+      h.gamma[l] /= s;
+      h.weight[l] /= s;
+    }
+  }
+}
+
 // Sinc quadrature nodes of Eq. 4 with the limits of Sec. 4.1, 0 < f < 1:
 // y_l = l k, l = -K^- .. K^+; A_l = M_L + t_l K with t_l = e^{2 y_l};
 // weight w_l = (2 k sin(pi f) / pi) e^{2 f y_l}.
@@ -441,6 +457,7 @@ HostNodes quadrature_nodes(double f, double k) {
     h.gamma.push_back(std::exp(2.0 * y));
     h.weight.push_back(c * std::exp(2.0 * f * y));
   }
+  normalize_nodes(h);
   return h;
 }
 
@@ -2289,6 +2306,7 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   hn.alpha.assign(alpha, alpha + n_nodes);
   hn.gamma.assign(gamma, gamma + n_nodes);
   hn.weight.assign(weight, weight + n_nodes);
+  normalize_nodes(hn);
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
   if (o.consistent && (g->thomas_rest() > 0 || dst_gemm_sample_pad(n_rhs) == 0))
