@@ -585,3 +585,24 @@ def test_sample_host_stream_equals_separate_host_calls():
     buf = np.empty_like(outs[0])
     G.sample_host_stream(2.0, 0.7, 0.4, seeds, 4, outs=[buf, buf, buf], **kw)
     np.testing.assert_array_equal(buf, outs[-1])
+
+
+@pytest.mark.parametrize("interior", ["thomas", "spectral", "spectral_umma"])
+def test_apply_extreme_shifts_mixed(interior):
+    """Shifts far outside the FP32 range (the outer sinc nodes of small steps
+    reach t = e^133): the nodes are rescaled to O(1) before the FP32 kernels."""
+    g = gi.random_small_graph(12, 20, 3)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.01)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.01)
+    kappa = 1.3
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = np.random.default_rng(8).standard_normal((3, m.n_dofs))
+    t = np.array([1e-45, 1e-12, 1.0, 1e25, 1e45, 6e57])
+    w = np.array([1e-30, 1e-6, 1.0, 1e15, 1e34, 3e43])
+    out, st = G.apply(kappa, np.ones_like(t), t, w, torch.tensor(rhs, device="cuda"),
+                      precision="mixed", out_dtype="f64", interior=interior)
+    assert st["numeric_flag"] == 0 and st["n_unconverged"] == 0
+    ref = sampler.shifted_sum(ml, kmat, rhs, t, w)
+    num = np.sqrt((ml[None, :] * (out.cpu().numpy() - ref) ** 2).sum(axis=1))
+    den = np.sqrt((ml[None, :] * ref ** 2).sum(axis=1))
+    assert (num / den).max() < 1e-5
