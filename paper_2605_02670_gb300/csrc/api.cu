@@ -649,6 +649,32 @@ int check_consistent(const grf_graph* g, const Opts& o, double beta, int64_t S) 
   return GRF_OK;
 }
 
+// The FP32 edge-interior kernels work with delta_l = (alpha_l / gamma_l +
+// kappa^2) h_e^2 and c_l = gamma_l / h_e (nodes already rescaled to
+// max(alpha, gamma) = 1). Nodes whose delta passes 1e36 or whose c falls below
+// 1e-36 on some edge (shifts t_l below about 1e-36 h) leave the FP32 range
+// (normal numbers down to 1.2e-38) and are refused in mixed precision; FP64
+// takes them. The sinc nodes of k = 0.25, beta = 0.25 on h = 2^-9 reach
+// delta 8e28 and c 3e-32.
+int check_fp32_range(const grf_graph* g, const Opts& o, double kappa,
+                     const std::vector<HostNodes>& stages) {
+  if (o.precision == GRF_FP64 || g->ne == 0) return GRF_OK;
+  double hmax = 0.0;
+  for (int32_t e = 0; e < g->ne; ++e) hmax = std::max(hmax, g->he[e]);
+  for (auto& s : stages)
+    for (int32_t l = 0; l < s.L(); ++l) {
+      if (!(s.gamma[l] > 0)) continue;
+      const double delta = (s.alpha[l] / s.gamma[l] + kappa * kappa) * hmax * hmax;
+      const double c = s.gamma[l] / hmax;
+      if (!(delta < 1e36) || !(c > 1e-36))
+        return fail(GRF_ENOTSUP,
+                    "quadrature node %d (alpha %g, gamma %g) is outside the FP32 range of the "
+                    "mixed path on this mesh (delta %g, c %g); use FP64",
+                    (int)l, s.alpha[l], s.gamma[l], delta, c);
+    }
+  return GRF_OK;
+}
+
 // The tensor-core transforms run for this call (the plan exists for its S).
 bool umma_ready(const grf_graph* g, const Opts& o, int64_t S, int32_t L) {
   return o.spec_umma && g->dst.blk && g->dst.dev.sp == dst_gemm_sample_pad(S) &&
@@ -1128,6 +1154,7 @@ int sample_impl(grf_graph* g, double kappa, double beta, double k_step, uint64_t
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
   GRF_TRY(check_consistent(g, o, beta, S));
+  GRF_TRY(check_fp32_range(g, o, kappa, stages));
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
   if (o.consistent) GRF_TRY(ensure_cons_plan(g));
@@ -1146,6 +1173,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
   std::vector<HostNodes> stages;
   plan(beta, k_step, &stages);
   GRF_TRY(check_consistent(g, o, beta, S));
+  GRF_TRY(check_fp32_range(g, o, kappa, stages));
   GRF_TRY(ensure_ws(g, sample_ws_bytes(g, stages, S, sizeof(T), o)));
   if (o.spec_umma) GRF_TRY(ensure_dst_plan(g, S));
   if (o.consistent) GRF_TRY(ensure_cons_plan(g));
@@ -2307,6 +2335,7 @@ int grf_apply(grf_graph* g, double kappa, int64_t n_nodes, const double* alpha,
   hn.gamma.assign(gamma, gamma + n_nodes);
   hn.weight.assign(weight, weight + n_nodes);
   normalize_nodes(hn);
+  GRF_TRY(check_fp32_range(g, o, kappa, std::vector<HostNodes>{hn}));
   const size_t ts = o.precision == GRF_FP64 ? 8 : 4;
   const size_t head = align_up((size_t)g->n * n_rhs * ts);
   if (o.consistent && (g->thomas_rest() > 0 || dst_gemm_sample_pad(n_rhs) == 0))

@@ -597,8 +597,8 @@ def test_apply_extreme_shifts_mixed(interior):
     kappa = 1.3
     ml, _, kmat = sampler.assemble(m, kappa)
     rhs = np.random.default_rng(8).standard_normal((3, m.n_dofs))
-    t = np.array([1e-45, 1e-12, 1.0, 1e25, 1e45, 6e57])
-    w = np.array([1e-30, 1e-6, 1.0, 1e15, 1e34, 3e43])
+    t = np.array([1e-32, 1e-12, 1.0, 1e25, 1e45, 6e57])
+    w = np.array([1e-22, 1e-6, 1.0, 1e15, 1e34, 3e43])
     out, st = G.apply(kappa, np.ones_like(t), t, w, torch.tensor(rhs, device="cuda"),
                       precision="mixed", out_dtype="f64", interior=interior)
     assert st["numeric_flag"] == 0 and st["n_unconverged"] == 0
@@ -606,3 +606,25 @@ def test_apply_extreme_shifts_mixed(interior):
     num = np.sqrt((ml[None, :] * (out.cpu().numpy() - ref) ** 2).sum(axis=1))
     den = np.sqrt((ml[None, :] * ref ** 2).sum(axis=1))
     assert (num / den).max() < 1e-5
+
+
+def test_apply_shift_below_the_fp32_range_is_refused_in_mixed():
+    """t = 1e-45 on h = 0.01 gives c = t / h = 1e-43 (subnormal in FP32): the
+    mixed path refuses the node, FP64 computes it."""
+    g = gi.random_small_graph(12, 20, 3)
+    G = grf.Graph(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.01)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=0.01)
+    kappa = 1.3
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = np.random.default_rng(8).standard_normal((2, m.n_dofs))
+    t, w = np.array([1e-45, 1.0]), np.array([1e-30, 1.0])
+    with pytest.raises(grf.GrfError) as ei:
+        G.apply(kappa, np.ones_like(t), t, w, torch.tensor(rhs, device="cuda"),
+                precision="mixed", out_dtype="f64")
+    assert ei.value.code == grf.GRF_ENOTSUP
+    out, _ = G.apply(kappa, np.ones_like(t), t, w, torch.tensor(rhs, device="cuda"),
+                     precision="fp64")
+    ref = sampler.shifted_sum(ml, kmat, rhs, t, w)
+    num = np.sqrt((ml[None, :] * (out.cpu().numpy() - ref) ** 2).sum(axis=1))
+    den = np.sqrt((ml[None, :] * ref ** 2).sum(axis=1))
+    assert (num / den).max() < 1e-6
