@@ -717,6 +717,8 @@ struct ApplyWs {
   int32_t lp_chunk;
   void* dscale;         // T [L][V]
   void* offv_t;         // float [L][2E] (mixed precision only)
+  float2 *dpair, *opair;  // FP64 blocks as FP32 pairs [L][V], [L][2E] (mixed only)
+  float *xh, *xl, *gh, *gl;  // batched PCG refinement vectors, shaped as r (mixed only)
   void *yscr, *rpscr;
   void* prm;  // SweepParams<T> [L][E]
   void* xw;   // T [L][V][S] (sample-minor)
@@ -753,6 +755,20 @@ void carve_lp_infer(Carve& c, const grf_graph* g, int32_t nodes, LpActs* a) {
   a->n = nullptr;
 }
 
+// The batched PCG's FP32-pair state (mixed precision): the blocks as pairs
+// and the iterate and scaled right-hand side, hi and lo, shaped as r.
+void carve_pairs(Carve& c, size_t Ls, size_t Sv, size_t V, size_t E, size_t tsize, ApplyWs* w) {
+  w->dpair = w->opair = nullptr;
+  w->xh = w->xl = w->gh = w->gl = nullptr;
+  if (tsize != 4) return;
+  w->dpair = c.take<float2>(Ls * V);
+  w->opair = c.take<float2>(Ls * 2 * E);
+  w->xh = c.take<float>(Ls * Sv * V);
+  w->xl = c.take<float>(Ls * Sv * V);
+  w->gh = c.take<float>(Ls * Sv * V);
+  w->gl = c.take<float>(Ls * Sv * V);
+}
+
 void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsize, ApplyWs* w,
                  int precond = GRF_PRECOND_JACOBI, bool spectral = false, bool umma = false) {
   const size_t Ls = (size_t)L, E = (size_t)g->ne, V = (size_t)g->nv, Ss = (size_t)S;
@@ -787,6 +803,7 @@ void carve_apply(Carve& c, const grf_graph* g, int32_t L, int64_t S, size_t tsiz
   }
   w->dscale = c.take<char>(Ls * V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(Ls * 2 * E * 4) : nullptr;
+  carve_pairs(c, Ls, Sv, V, E, tsize, w);
   // scratch of the sequential recovery, only for edges longer than every bin
   const size_t ni_long = g->long_edges(tsize == 8) > 0 ? (size_t)g->ni : 0;
   w->acc = c.take<double>(ni_long * Ss);
@@ -907,7 +924,8 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   SweepParams<T>* prm = (SweepParams<T>*)w.prm;
   if (sizeof(T) == 4 && o.spectral && w.bhat && g->thomas_rest() == 0) prm = nullptr;
   rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, prm,
-                                  (T*)w.dscale, (T*)w.offv_t, st, o.consistent);
+                                  (T*)w.dscale, (T*)w.offv_t, st, o.consistent, w.dpair,
+                                  w.opair);
   rs->end(1, st);
   rs->begin(2, st);
   if (sizeof(T) == 4) {
@@ -987,9 +1005,11 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   }
   rs->begin(3, st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
+  const PcgPairs pairs{w.dpair, w.opair, w.xh, w.xl, w.gh, w.gl};
   launch_pcg<T>(g->d, g->d_order, g->d_ell, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
-                (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st);
+                (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st,
+                w.dpair ? &pairs : nullptr);
   rs->end(3, st);
   rs->launches += 1;
   CUDA_TRY(cudaGetLastError());
@@ -1332,6 +1352,7 @@ void carve_vertex_solve(Carve& c, const grf_graph* g, int64_t S, size_t tsize, A
   w->pre_c = w->pre_n = nullptr;
   w->dscale = c.take<char>(V * tsize);
   w->offv_t = tsize == 4 ? c.take<char>(2 * E * 4) : nullptr;
+  carve_pairs(c, 1, Sv, V, E, tsize, w);
   w->iters = c.take<int32_t>(Ss);
   w->status = c.take<PcgStatus>(1);
   // sweep constants of the one node: launch_schur fills them and the

@@ -101,13 +101,16 @@ struct alignas(4 * sizeof(T)) SweepParams {
 //   offv[l][k] = sab[l][adj_edge[k]] in vertex-incidence order;
 //   prm[l][e] (if not null): the sweep constants above;
 //   dscale[l][v] (if not null): 1 / S_vv (T = double) or 1 / sqrt(S_vv) (T = float);
-//   offv_t (T = float, if not null): offv / sqrt(S_vv S_ww).
+//   offv_t (T = float, if not null): offv / sqrt(S_vv S_ww);
+//   dpair[l][v], opair[l][k] (if not null): diag and offv as FP32 pairs
+//   (hi = fl32(x), lo = fl32(x - hi)).
 // Returns the number of kernels launched.
 // consistent: blocks of the consistent-mass operator (no sweep constants).
 template <typename T>
 int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa,
                  double* sab, double* diag, double* offv, SweepParams<T>* prm, T* dscale,
-                 T* offv_t, cudaStream_t st, bool consistent = false);
+                 T* offv_t, cudaStream_t st, bool consistent = false, float2* dpair = nullptr,
+                 float2* opair = nullptr);
 
 // Neumann-Neumann preconditioner coefficients per node: pc[l][v] (diagonal) and
 // pn[l][k] (incidence k), for the Jacobi-scaled system (scaled) or S itself.
@@ -179,17 +182,27 @@ constexpr int kPreJacobi = 0, kPreNeumann = 1, kPreLearned = 2;
 // ell: nv int4 (each vertex's first four neighbours, padded with itself),
 // then nv int2 (incidence-list start, degree).
 int64_t pcg_batch_padded_samples(int64_t S);
+// Extra state of the batched layout's refinement, which runs in FP32-pair
+// arithmetic: the FP64 blocks as pairs (launch_schur's dpair [L][V], opair
+// [L][2E]) and four more vectors of the batched shape (iterate hi/lo and
+// scaled right-hand side hi/lo).
+struct PcgPairs {
+  const float2* dp;
+  const float2* op;
+  float *xh, *xl, *gh, *gl;
+};
 void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,
                       const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
-                      double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
-                      cudaStream_t st);
+                      const PcgPairs& pp, double rtol, int32_t max_iter, int32_t* iters,
+                      PcgStatus* status, cudaStream_t st);
+// pairs: required by the batched layout (FP32 only), ignored otherwise.
 template <typename VT>
 void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int32_t L, int64_t S,
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
-                cudaStream_t st);
+                cudaStream_t st, const PcgPairs* pairs);
 
 int recover_sample_group();
 

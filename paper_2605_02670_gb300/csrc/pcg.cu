@@ -1470,12 +1470,12 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int3
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,
                 const double* gvec, double* x, VT* d, VT* r, VT* p, VT* q, VT* y, double rtol,
                 int32_t max_iter, int32_t* iters, PcgStatus* status, int layout,
-                cudaStream_t st) {
+                cudaStream_t st, const PcgPairs* pairs) {
   const int64_t nsys = (int64_t)L * S;
   if constexpr (sizeof(VT) == 4) {
-    if (layout == 4 && pre == kPreJacobi) {
-      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
-                       max_iter, iters, status, st);
+    if (layout == 4 && pre == kPreJacobi && pairs) {
+      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, *pairs,
+                       rtol, max_iter, iters, status, st);
       return;
     }
     if ((layout == 2 || layout == 3) && pre == kPreJacobi && group_fits(g)) {
@@ -1519,9 +1519,9 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int3
   if constexpr (sizeof(VT) == 4) {
     // larger graphs: samples batched in rows of 8 (the vectors are carved with
     // the sample count padded to a multiple of 8)
-    if (layout != 1 && pre == kPreJacobi) {
-      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, rtol,
-                       max_iter, iters, status, st);
+    if (layout != 1 && pre == kPreJacobi && pairs) {
+      launch_pcg_batch(g, ell, L, S, diag, offv, dscale_t, offv_t, gvec, x, r, p, q, d, *pairs,
+                       rtol, max_iter, iters, status, st);
       return;
     }
   }
@@ -1551,7 +1551,7 @@ void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int3
                                const double*, const double*, const VT*, const VT*, int,      \
                                const VT*, const VT*, const double*, double*, VT*, VT*, VT*,  \
                                VT*, VT*, double, int32_t, int32_t*, PcgStatus*, int,         \
-                               cudaStream_t);
+                               cudaStream_t, const PcgPairs*);
 GRF_INST(float)
 GRF_INST(double)
 #undef GRF_INST

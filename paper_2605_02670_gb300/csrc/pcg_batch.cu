@@ -5,9 +5,16 @@
 // (incidence list, scaled block) serves the 8 samples and every vector access
 // is a whole sector.
 //
-// Mixed precision, as in the other layouts: FP32 CG on the Jacobi-scaled system
-// (D^-1/2 S D^-1/2) e = D^-1/2 r inside FP64 iterative refinement; the
-// refinement residual r = g - S x uses the FP64 blocks and the FP64 iterate.
+// Mixed precision: FP32 CG on the Jacobi-scaled system (D^-1/2 S D^-1/2) e =
+// D^-1/2 r inside iterative refinement on S x~ = g~, g~ = g / ||g||. The
+// refinement keeps its iterate x~ and right-hand side g~ as FP32 pairs
+// (hi + lo, 48 significant bits), reads the FP64 blocks as pairs too, and
+// forms r~ = g~ - S x~ as a compensated dot product (each product split exactly
+// by an FMA, each sum by TwoSum; Ogita, Rump and Oishi's Dot2), accurate to a
+// few units of 2^-48 of its terms, so no FP64 instruction runs in the
+// refinement loop: FP64 issues at a small fraction of the FP32 rate. FP64
+// remains in the norms of g, its split into pairs, the per-sample decisions
+// and the final x = ||g|| (x~hi + x~lo).
 // The dot products are accumulated in FP64 (FP32 partial sums over at most 16
 // vertices per thread, then FP64 across the vector and the CTA) and the CG
 // scalars alpha, beta are FP64; the vector updates are FP32.
@@ -45,10 +52,12 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Per-sample state of the group (one entry per sample, written by thread j).
 struct SampleState {
-  double rz, rz0, best, stop2, inner_e, rho, inv_g;
+  double rz, rz0, best, stop2, inner_e, rho, inv_g, gn;
   int32_t it, since;
   int32_t done, bad, cg, has_d, first;
-  float af, bf, ig;  // FP32 alpha, beta, 1 / rho for the vector passes
+  float af, bf;  // FP32 alpha, beta for the vector passes
+  float scl;     // ||g|| / rho: r~ to the inner solve's right-hand side
+  float xsc;     // rho / ||g||: the inner solution to the update of x~
 };
 
 struct BatchShared {
@@ -136,6 +145,34 @@ __device__ __forceinline__ float get(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// (s, c) -= (ah + al)(xh + xl), s + c a running sum with its error term: the
+// product ah xh = p + pe exactly (FMA), s - p = t + se exactly (TwoSum), the
+// cross terms ah xl + al xh (and the dropped al xl, below 2^-46 of the
+// product) need only FP32 accuracy. The _rn intrinsics keep the compiler from
+// fusing the error-free steps.
+__device__ __forceinline__ void ff_sub_prod(float& s, float& c, float ah, float al, float xh,
+                                            float xl) {
+  const float p = __fmul_rn(ah, xh);
+  const float pe = __fmaf_rn(ah, xh, -p);
+  const float mp = -p;
+  const float t = __fadd_rn(s, mp);
+  const float bv = __fsub_rn(t, s);
+  const float se = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(mp, bv));
+  s = t;
+  c += se - (pe + fmaf(ah, xl, al * xh));
+}
+// (h, l) += t with h + l renormalised (two TwoSums): the FP32-pair iterate.
+__device__ __forceinline__ void ff_add(float& h, float& l, float t) {
+  float s = __fadd_rn(h, t);
+  float bv = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(t, bv));
+  e = __fadd_rn(e, l);
+  const float s2 = __fadd_rn(s, e);
+  bv = __fsub_rn(s2, s);
+  l = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(e, bv));
+  h = s2;
+}
+
 // Bulk prefetch into L2 (TMA) of the vector rows of the vertices kPF steps
 // ahead: the rows of a step are contiguous ([nv][8] floats), so one thread
 // requests each vector's next block while the CTA works on the current one,
@@ -150,17 +187,6 @@ __device__ __forceinline__ void prefetch_rows(const float* rows, int32_t v0, int
   const int32_t n = nv - b < kVP ? nv - b : kVP;
   prefetch_l2(rows + (int64_t)b * kSG, (uint32_t)n * kSG * 4);
 }
-// the same for one FP64 sample row of the ABI layout ([S][nv] per node):
-// the whole 16-byte chunks inside the block (a row may start 8 bytes off)
-__device__ __forceinline__ void prefetch_row64(const double* row, int32_t v0, int32_t nv) {
-  const int32_t b = v0 + kPF * kVP;
-  if (b >= nv) return;
-  const int32_t n = nv - b < kVP ? nv - b : kVP;
-  const uintptr_t lo = ((uintptr_t)(row + b) + 15) & ~(uintptr_t)15;
-  const uintptr_t hi = (uintptr_t)(row + b + n) & ~(uintptr_t)15;
-  if (hi > lo) prefetch_l2(reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo));
-}
-
 // The vertices' neighbour records of one step (vertices v0 + u kVP, u < kU):
 // their first four neighbours and (incidence-list start, degree); past the
 // end the records are empty.
@@ -182,16 +208,18 @@ __device__ __forceinline__ void load_ell(const int4* __restrict__ ell, int32_t v
 
 }  // namespace
 
-// gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out; xout also
-// holds the FP64 iterate). R, PA, PB, Dv: [L][ceil(S / 8)][nv][8] FP32 scratch.
+// gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out).
+// DP, OP: the FP64 blocks as FP32 pairs, [L][nv] and [L][2E].
+// R, PA, PB, Dv, XH, XL, GH, GL: [L][ceil(S / 8)][nv][8] FP32 scratch.
 __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     DevGraph g, const int4* __restrict__ ell, int32_t L, int64_t S,
-    const double* __restrict__ diag,
-    const double* __restrict__ offv, const float* __restrict__ dscale,
+    const float2* __restrict__ DP, const float2* __restrict__ OP,
+    const float* __restrict__ dscale,
     const float* __restrict__ offv_t, const double* __restrict__ gvec, double* __restrict__ xout,
     float* __restrict__ R, float* __restrict__ PA, float* __restrict__ PB,
-    float* __restrict__ Dv, double rtol, int32_t max_iter, int32_t* __restrict__ iters,
-    PcgStatus* __restrict__ status) {
+    float* __restrict__ Dv, float* __restrict__ XH, float* __restrict__ XL,
+    float* __restrict__ GH, float* __restrict__ GL, double rtol, int32_t max_iter,
+    int32_t* __restrict__ iters, PcgStatus* __restrict__ status) {
   __shared__ BatchShared sh;
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
@@ -204,8 +232,8 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
   for (int64_t item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int64_t l = L - 1 - item / nsg;  // largest shifts first (longest solves)
     const int64_t s0 = (item % nsg) * kSG;
-    const double* __restrict__ D = diag + l * nv;
-    const double* __restrict__ O = offv + l * ne2;
+    const float2* __restrict__ Dp = DP + l * nv;
+    const float2* __restrict__ Op = OP + l * ne2;
     const float* __restrict__ Ds = dscale + l * nv;
     const float* __restrict__ Ot = offv_t + l * ne2;
     const int64_t base = (l * nsg + (item % nsg)) * (int64_t)nv * kSG + 4 * hh;
@@ -213,6 +241,10 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     float* __restrict__ pa = PA + base;
     float* __restrict__ pb = PB + base;
     float* __restrict__ dv = Dv + base;
+    float* __restrict__ xh = XH + base;
+    float* __restrict__ xl = XL + base;
+    float* __restrict__ gh = GH + base;
+    float* __restrict__ gl = GL + base;
     // this thread's 4 samples: FP64 rows of g and x (row i at + i nv; only
     // the first nlive exist)
     const int64_t sfirst = s0 + 4 * hh;
@@ -223,7 +255,7 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
 #define XS(i) (x0 + (int64_t)(i) * nv)
 #define LIVE(i) ((i) < nlive)
 
-    // ---- ||g||^2, ||D^-1/2 g||^2 (FP64); x = 0
+    // ---- ||g||^2, ||D^-1/2 g||^2 (FP64)
     {
       Acc4<2> a;
       a.init();
@@ -235,7 +267,6 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           const double sv = gv * dsv;
           a.d[i][0] = fma(gv, gv, a.d[i][0]);
           a.d[i][1] = fma(sv, sv, a.d[i][1]);
-          if (LIVE(i)) XS(i)[v] = 0.0;
         }
       }
       double out[2] = {0.0, 0.0};
@@ -245,81 +276,118 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         const bool lv = s0 + threadIdx.x < S;
         q.bad = lv && (!isfinite(out[0]) || !isfinite(out[1]));
         q.done = !lv || q.bad || !(out[0] > 0.0) || !(out[1] > 0.0);
-        q.inv_g = q.done ? 0.0 : 1.0 / sqrt(out[0]);
-        // the inner FP32 solve runs on r = D^-1/2 r64 / rho, O(1) whatever the
-        // node's scale: rho = ||D^-1/2 g|| first, then the estimate of the
+        q.gn = q.done ? 0.0 : sqrt(out[0]);
+        q.inv_g = q.done ? 0.0 : 1.0 / q.gn;
+        // the inner FP32 solve runs on r = D^-1/2 r~ ||g|| / rho, O(1) whatever
+        // the node's scale: rho = ||D^-1/2 g|| first, then the estimate of the
         // refinement residual's norm from the previous inner solve
         q.rho = q.done ? 1.0 : sqrt(out[1]);
         q.rz0 = q.done ? 0.0 : out[1] / (q.rho * q.rho);
+        q.scl = q.done ? 0.f : (float)(q.gn / q.rho);
         q.inner_e = kInnerRtol;
         q.it = 0;
-        q.ig = (float)(1.0 / q.rho);
         q.cg = 0;
       }
       __syncthreads();
+      // ---- g~ = g / ||g|| as FP32 pairs, x~ = 0, r = D^-1/2 g~ ||g|| / rho
       bool dn[4];
-      float ig[4];
+      double ivg[4];
+      float sc[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) dn[i] = sh.st[4 * hh + i].done, ig[i] = sh.st[4 * hh + i].ig;
+      for (int i = 0; i < 4; ++i) {
+        const SampleState& q = sh.st[4 * hh + i];
+        dn[i] = q.done;
+        ivg[i] = q.inv_g;
+        sc[i] = q.scl;
+      }
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int32_t v = vs; v < nv; v += kVP) {
         const float dsv = Ds[v];
-        float rv[4];
+        float hv[4], lv[4], rv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) rv[i] = dn[i] ? 0.f : ((float)GS(i)[v] * ig[i]) * dsv;
-        st4(r + (int64_t)v * kSG, make_float4(rv[0], rv[1], rv[2], rv[3]));
+        for (int i = 0; i < 4; ++i) {
+          const double gt = dn[i] ? 0.0 : GS(i)[v] * ivg[i];
+          hv[i] = __double2float_rn(gt);
+          lv[i] = __double2float_rn(gt - (double)hv[i]);
+          rv[i] = (hv[i] * sc[i]) * dsv;
+        }
+        const int64_t iv = (int64_t)v * kSG;
+        st4(gh + iv, make_float4(hv[0], hv[1], hv[2], hv[3]));
+        st4(gl + iv, make_float4(lv[0], lv[1], lv[2], lv[3]));
+        st4(xh + iv, z4);
+        st4(xl + iv, z4);
+        st4(r + iv, make_float4(rv[0], rv[1], rv[2], rv[3]));
       }
       __syncthreads();
     }
 
     for (int32_t round = 0; round <= max_iter; ++round) {
       if (round > 0) {
-        // ---- FP64 refinement residual r64 = g - S x; stored r = D^-1/2 r64 / rho
+        // ---- refinement residual r~ = g~ - S x~ in FP32-pair arithmetic;
+        // stored r = D^-1/2 r~ ||g|| / rho
         bool dn[4];
-        double ir[4], ivg[4];
+        float sc[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const SampleState& q = sh.st[4 * hh + i];
           dn[i] = q.done;
-          ir[i] = 1.0 / q.rho;
-          ivg[i] = q.inv_g;
+          sc[i] = q.scl;
         }
         Acc4<2> a;
         a.init();
         for (int32_t v = vs; v < nv; v += kVP) {
-          if (threadIdx.x < 2) {  // this half row's x and g rows kPF steps ahead
-#pragma unroll 1
-            for (int i = 0; i < 4; ++i)
-              if (LIVE(i) && !dn[i]) {
-                prefetch_row64(XS(i), v, nv);
-                prefetch_row64(GS(i), v, nv);
-              }
+          if (threadIdx.x == 0) {  // rows of x~ and g~ kPF steps ahead
+            prefetch_rows(xh, v, nv);
+            prefetch_rows(xl, v, nv);
+            prefetch_rows(gh, v, nv);
+            prefetch_rows(gl, v, nv);
           }
           int4 ea[kU];
           int2 eb[kU];
           load_ell(ell, v, nv, ea, eb);
           const int32_t k0 = eb[0].x, deg = eb[0].y;
           const int32_t wl[4] = {ea[0].x, ea[0].y, ea[0].z, ea[0].w};
-          const double dd = D[v];
+          const int64_t iv = (int64_t)v * kSG;
+          const float2 dp = Dp[v];
           const float dsv = Ds[v];
+          const float4 xh0 = ld4(xh + iv), xl0 = ld4(xl + iv);
+          const float4 g0h = ld4(gh + iv), g0l = ld4(gl + iv);
+          float s4[4], c4[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            s4[i] = get(g0h, i);
+            c4[i] = get(g0l, i);
+            ff_sub_prod(s4[i], c4[i], dp.x, dp.y, get(xh0, i), get(xl0, i));
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (j < deg) {
+              const float2 op = Op[k0 + j];
+              const int64_t w = (int64_t)wl[j] * kSG;
+              const float4 wh = ld4(xh + w), wlo = ld4(xl + w);
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                ff_sub_prod(s4[i], c4[i], op.x, op.y, get(wh, i), get(wlo, i));
+            }
+          }
+          for (int32_t k = k0 + 4; k < k0 + deg; ++k) {
+            const float2 op = Op[k];
+            const int64_t w = (int64_t)nbr[k] * kSG;
+            const float4 wh = ld4(xh + w), wlo = ld4(xl + w);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              ff_sub_prod(s4[i], c4[i], op.x, op.y, get(wh, i), get(wlo, i));
+          }
           float sv4[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            sv4[i] = 0.f;
-            if (dn[i]) continue;
-            const double* __restrict__ xs = XS(i);
-            double y = dd * xs[v];
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-              if (j < deg) y = fma(O[k0 + j], xs[wl[j]], y);
-            for (int32_t k = k0 + 4; k < k0 + deg; ++k) y = fma(O[k], xs[nbr[k]], y);
-            const double rv = GS(i)[v] - y;
-            const float rel = (float)(rv * ivg[i]);
-            sv4[i] = (float)(rv * ir[i]) * dsv;
+            const float rel = dn[i] ? 0.f : s4[i] + c4[i];
+            sv4[i] = (rel * sc[i]) * dsv;
             a.f[i][0] = fmaf(rel, rel, a.f[i][0]);
             a.f[i][1] = fmaf(sv4[i], sv4[i], a.f[i][1]);
           }
           a.tick();
-          st4(r + (int64_t)v * kSG, make_float4(sv4[0], sv4[1], sv4[2], sv4[3]));
+          st4(r + iv, make_float4(sv4[0], sv4[1], sv4[2], sv4[3]));
         }
         double out[2] = {0.0, 0.0};
         group_sum<2>(a, sh, out);
@@ -518,30 +586,55 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           if (!__syncthreads_or(cgj2)) break;
         }
       }
-      // ---- x += rho D^-1/2 d for the samples that ran a correction this round
+      // ---- x~ += (rho / ||g||) D^-1/2 d for the samples that ran a correction
+      // this round (FP32-pair update)
       {
-        bool up[4];
-        double rh[4];
+        bool up[4], any = false;
+        float xs[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const SampleState& q = sh.st[4 * hh + i];
           up[i] = q.has_d && !q.bad;
-          rh[i] = q.rho;
+          xs[i] = up[i] ? (float)(q.rho * q.inv_g) : 0.f;
+          any |= up[i];
         }
-        for (int32_t v = vs; v < nv; v += kVP) {
-          const float4 d4 = ld4(dv + (int64_t)v * kSG);
-          const double dsv = (double)Ds[v];
+        if (any) {
+          for (int32_t v = vs; v < nv; v += kVP) {
+            const int64_t iv = (int64_t)v * kSG;
+            const float4 d4 = ld4(dv + iv);
+            float4 h4 = ld4(xh + iv), l4 = ld4(xl + iv);
+            const float dsv = Ds[v];
+            float hv[4] = {h4.x, h4.y, h4.z, h4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            if (up[i]) XS(i)[v] = fma(rh[i] * dsv, (double)get(d4, i), XS(i)[v]);
+            for (int i = 0; i < 4; ++i)
+              if (up[i]) ff_add(hv[i], lv[i], (xs[i] * dsv) * get(d4, i));
+            st4(xh + iv, make_float4(hv[0], hv[1], hv[2], hv[3]));
+            st4(xl + iv, make_float4(lv[0], lv[1], lv[2], lv[3]));
+          }
         }
       }
-      __syncthreads();  // x complete, every thread done with the state
+      __syncthreads();  // x~ complete, every thread done with the state
       if (threadIdx.x < kSG) {
         SampleState& q = sh.st[threadIdx.x];
-        if (q.has_d && !q.bad) q.rho *= sqrt(fmax(q.rz, 1e-24 * q.rz0));
+        if (q.has_d && !q.bad) {
+          q.rho *= sqrt(fmax(q.rz, 1e-24 * q.rz0));
+          q.scl = (float)(q.gn / q.rho);
+        }
       }
       __syncthreads();
+    }
+    // ---- x = ||g|| (x~hi + x~lo) in FP64
+    {
+      double gn[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) gn[i] = sh.st[4 * hh + i].gn;
+      for (int32_t v = vs; v < nv; v += kVP) {
+        const int64_t iv = (int64_t)v * kSG;
+        const float4 h4 = ld4(xh + iv), l4 = ld4(xl + iv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (LIVE(i)) XS(i)[v] = gn[i] * ((double)get(h4, i) + (double)get(l4, i));
+      }
     }
     if (threadIdx.x < kSG && s0 + threadIdx.x < S) {
       const SampleState& q = sh.st[threadIdx.x];
@@ -563,16 +656,20 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
 // Vectors of the batched layout need [L][ceil(S / 8) * 8][nv] floats each.
 int64_t pcg_batch_padded_samples(int64_t S) { return (S + kSG - 1) / kSG * kSG; }
 
+// diag and offv (FP64) are read through their FP32-pair copies pp.dp, pp.op.
 void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,
                       const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
-                      double rtol, int32_t max_iter, int32_t* iters, PcgStatus* status,
-                      cudaStream_t st) {
+                      const PcgPairs& pp, double rtol, int32_t max_iter, int32_t* iters,
+                      PcgStatus* status, cudaStream_t st) {
+  (void)diag;
+  (void)offv;
   const int64_t items = (int64_t)L * ((S + kSG - 1) / kSG);
   if (items <= 0) return;
   const int blocks = (int)(items < (int64_t)1 << 30 ? items : (int64_t)1 << 30);
-  pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, ell, L, S, diag, offv, dscale, offv_t, gvec, x, R, PA,
-                                           PB, Dv, rtol, max_iter, iters, status);
+  pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, ell, L, S, pp.dp, pp.op, dscale, offv_t, gvec, x, R,
+                                           PA, PB, Dv, pp.xh, pp.xl, pp.gh, pp.gl, rtol, max_iter,
+                                           iters, status);
 }
 
 }  // namespace grf

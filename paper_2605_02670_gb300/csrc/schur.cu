@@ -83,10 +83,18 @@ __global__ void edge_blocks_kernel(DevGraph g, DevNodes nd, double kappa2, doubl
 
 // diag[l][v] = S_vv, offv in incidence order, and the PCG scaling in precision
 // T: 1 / S_vv for FP64 PCG, 1 / sqrt(S_vv) for the Jacobi-scaled FP32 solve.
+// x = hi + lo with hi = fl32(x) and lo = fl32(x - hi): 48 of x's 53 bits, the
+// form the batched PCG's refinement residual reads the FP64 blocks in.
+__device__ __forceinline__ float2 split_pair(double x) {
+  const float hi = __double2float_rn(x);
+  return make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
 template <typename T>
 __global__ void vertex_diag_kernel(DevGraph g, int32_t L, const double* __restrict__ saa,
                                    const double* __restrict__ sab, double* __restrict__ diag,
-                                   double* __restrict__ offv, T* __restrict__ dscale) {
+                                   double* __restrict__ offv, T* __restrict__ dscale,
+                                   float2* __restrict__ dpair, float2* __restrict__ opair) {
   const int64_t total = (int64_t)L * g.nv;
   const int64_t nadj = 2 * (int64_t)g.ne;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -98,8 +106,10 @@ __global__ void vertex_diag_kernel(DevGraph g, int32_t L, const double* __restri
       const int64_t i = l * g.ne + g.adj_edge[k];
       d += saa[i];
       offv[l * nadj + k] = sab[i];
+      if (opair) opair[l * nadj + k] = split_pair(sab[i]);
     }
     diag[t] = d;
+    if (dpair) dpair[t] = split_pair(d);
     if (dscale) dscale[t] = sizeof(T) == 8 ? (T)(1.0 / d) : (T)(1.0 / sqrt(d));
   }
 }
@@ -169,11 +179,11 @@ int grid_for(int64_t total, int threads) {
 template <typename T>
 int launch_schur(const DevGraph& g, const DevNodes& nd, double kappa2, double* saa, double* sab,
                  double* diag, double* offv, SweepParams<T>* prm, T* dscale, T* offv_t,
-                 cudaStream_t st, bool consistent) {
+                 cudaStream_t st, bool consistent, float2* dpair, float2* opair) {
   edge_blocks_kernel<T><<<grid_for((int64_t)nd.L * g.ne, 256), 256, 0, st>>>(
       g, nd, kappa2, saa, sab, consistent ? nullptr : prm, consistent ? 1 : 0);
-  vertex_diag_kernel<T><<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, saa, sab,
-                                                                             diag, offv, dscale);
+  vertex_diag_kernel<T><<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(
+      g, nd.L, saa, sab, diag, offv, dscale, dpair, opair);
   if constexpr (sizeof(T) == 4) {
     if (dscale && offv_t) {
       scaled_offdiag_kernel<<<grid_for((int64_t)nd.L * g.nv, 256), 256, 0, st>>>(g, nd.L, offv,
@@ -196,9 +206,9 @@ template void launch_nn_coeffs<double>(const DevGraph&, int32_t, const double*, 
 
 template int launch_schur<float>(const DevGraph&, const DevNodes&, double, double*, double*,
                                  double*, double*, SweepParams<float>*, float*, float*,
-                                 cudaStream_t, bool);
+                                 cudaStream_t, bool, float2*, float2*);
 template int launch_schur<double>(const DevGraph&, const DevNodes&, double, double*, double*,
                                   double*, double*, SweepParams<double>*, double*, double*,
-                                  cudaStream_t, bool);
+                                  cudaStream_t, bool, float2*, float2*);
 
 }  // namespace grf

@@ -224,6 +224,34 @@ def test_batched_pcg_vertex_solve_matches_oracle(S, gamma):
     assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
 
 
+@pytest.mark.parametrize("gamma", [1e-12, 3.0, 1e7])
+def test_batched_pcg_refinement_reaches_below_fp32(gamma):
+    """The batched layout's refinement forms its residual in FP32-pair
+    arithmetic: asked for rtol 1e-11, far below what an FP32 residual can
+    resolve, the vertex solution's residual against the oracle's dense FP64
+    Schur complement, for the GPU's own right-hand side, stays within a small
+    multiple of rtol."""
+    from oracle import noise
+    g = gi.random_small_graph(40, 70, 9)
+    h = 0.05
+    G = _graph(g, h=h)
+    m = fem.build_mesh(g.edge_u, g.edge_v, g.lengths, g.n_vertices, h=h)
+    kappa, S, rtol = 1.7, 11, 1e-11
+    ml, _, kmat = sampler.assemble(m, kappa)
+    rhs = noise.white_noise(ml, 5, S)
+    opts = grf.make_options("mixed", pcg_layout="batched", rtol=rtol)
+    gv = torch.empty((S, G.n_kept), dtype=torch.float64, device="cuda")
+    uv = torch.empty_like(gv)
+    rt = torch.tensor(rhs, device="cuda")
+    st = grf.grf_vertex_solve(G.handle, kappa, 1.0, gamma, S, rt.data_ptr(), gv.data_ptr(),
+                              uv.data_ptr(), opts, None)
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    s_dense = sampler.vertex_schur_dense(m, ml, kmat, gamma)
+    g_np, u_np = gv.cpu().numpy(), uv.cpu().numpy()
+    res = np.linalg.norm(g_np - u_np @ s_dense.T, axis=1) / np.linalg.norm(g_np, axis=1)
+    assert res.max() < 20 * rtol, res
+
+
 def test_batched_pcg_whole_sample_ragged_groups():
     g = gi.random_small_graph(40, 70, 9)
     h = 0.05

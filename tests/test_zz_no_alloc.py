@@ -39,14 +39,16 @@ def _scratch_bytes(n_dofs, n_kept, n_edges, n_rhs, ts):
     """The buffers the entry point carves from its static array, each rounded
     up to 256 bytes: the sample-minor right-hand side, the node constants, the
     Schur system, four PCG vectors per right-hand side, the Jacobi scaling, the
-    FP32 copy of the off-diagonals (mixed), iteration counts, the status words
-    and the per-edge sweep constants (4 values per edge) that the long FP32
-    edges' node-parallel condensation reads."""
+    FP32 copy of the off-diagonals (mixed), the FP32-pair copies of the Schur
+    blocks and the batched PCG's four pair vectors (mixed), iteration counts,
+    the status words and the per-edge sweep constants (4 values per edge) that
+    the long FP32 edges' node-parallel condensation reads."""
     up = lambda x: (x + 255) // 256 * 256
     E, V, S = n_edges, n_kept, n_rhs
     Sv = (S + 7) // 8 * 8 if ts == 4 else S  # FP32 PCG vectors: samples padded to 8
     parts = [n_dofs * S * ts, 8, 8, 8, 8 * E, 8 * E, 8 * V, 16 * E] + [Sv * V * ts] * 4
-    parts += [V * ts] + ([8 * E] if ts == 4 else []) + [4 * S, 24, 4 * ts * E]
+    parts += [V * ts] + ([8 * E, 8 * V, 16 * E] + [Sv * V * 4] * 4 if ts == 4 else [])
+    parts += [4 * S, 24, 4 * ts * E]
     return sum(up(x) for x in parts)
 
 
