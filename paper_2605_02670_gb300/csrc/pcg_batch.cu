@@ -15,9 +15,9 @@
 // refinement loop: FP64 issues at a small fraction of the FP32 rate. FP64
 // remains in the norms of g, its split into pairs, the per-sample decisions
 // and the final x = ||g|| (x~hi + x~lo).
-// The dot products are accumulated in FP64 (FP32 partial sums over at most 16
-// vertices per thread, then FP64 across the vector and the CTA) and the CG
-// scalars alpha, beta are FP64; the vector updates are FP32.
+// The dot products are FP32 partial sums over at most 16 vertices per thread,
+// accumulated as FP32 pairs and summed in FP64 across the CTA; the CG scalars
+// alpha, beta are FP64; the vector updates are FP32.
 //
 // A thread owns 4 of the group's samples (one 16-byte half row) of one vertex
 // per step. The vertex's first four neighbours and its incidence-list start
@@ -65,58 +65,63 @@ struct BatchShared {
   SampleState st[kSG];
 };
 
-// FP32 partial sums of 4 samples x N values, flushed into FP64 every kChunk
-// vertices.
+// (h, l) += t with h + l renormalised (two TwoSums): an FP32 pair.
+__device__ __forceinline__ void ff_add(float& h, float& l, float t) {
+  float s = __fadd_rn(h, t);
+  float bv = __fsub_rn(s, h);
+  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(t, bv));
+  e = __fadd_rn(e, l);
+  const float s2 = __fadd_rn(s, e);
+  bv = __fsub_rn(s2, s);
+  l = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(e, bv));
+  h = s2;
+}
+
+// FP32 partial sums of 4 samples x N values, flushed every kChunk vertices
+// into FP32 pairs (no FP64 instruction in the vertex loops).
 template <int N>
 struct Acc4 {
-  double d[4][N];
-  float f[4][N];
+  float f[4][N], h[4][N], l[4][N];
   int c;
   __device__ __forceinline__ void init() {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int k = 0; k < N; ++k) d[i][k] = 0.0, f[i][k] = 0.f;
+      for (int k = 0; k < N; ++k) f[i][k] = h[i][k] = l[i][k] = 0.f;
     c = 0;
   }
-  __device__ __forceinline__ void tick() {
-    if (++c == kChunk) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int k = 0; k < N; ++k) d[i][k] += (double)f[i][k], f[i][k] = 0.f;
-      c = 0;
-    }
-  }
-  __device__ __forceinline__ void finish() {
+  __device__ __forceinline__ void flush() {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int k = 0; k < N; ++k) d[i][k] += (double)f[i][k], f[i][k] = 0.f;
+      for (int k = 0; k < N; ++k) ff_add(h[i][k], l[i][k], f[i][k]), f[i][k] = 0.f;
+  }
+  __device__ __forceinline__ void tick() {
+    if (++c == kChunk) flush(), c = 0;
   }
 };
 
 // Per-sample CTA sums: lanes of equal parity share a half row (4 samples).
-// After the call thread j < 8 holds the sums of sample j in out[k].
+// The warp sums run on the pairs; one FP64 value per (warp, sample) then goes
+// through shared memory. After the call thread j < 8 holds the sums of sample
+// j in out[k].
 template <int N>
 __device__ __forceinline__ void group_sum(Acc4<N>& a, BatchShared& sh, double (&out)[N]) {
-  a.finish();
+  a.flush();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int k = 0; k < N; ++k) {
-      double v = a.d[i][k];
+      float h = a.h[i][k], l = a.l[i][k];
 #pragma unroll
-      for (int o = 2; o < 32; o <<= 1) v += __shfl_xor_sync(kFull, v, o);
-      a.d[i][k] = v;
+      for (int o = 2; o < 32; o <<= 1) {
+        const float oh = __shfl_xor_sync(kFull, h, o), ol = __shfl_xor_sync(kFull, l, o);
+        ff_add(h, l, oh);
+        l += ol;
+      }
+      if (lane < 2) sh.red[warp][4 * lane + i][k] = (double)h + (double)l;
     }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane < 2) {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < N; ++k) sh.red[warp][4 * lane + i][k] = a.d[i][k];
-  }
   __syncthreads();
   if (threadIdx.x < kSG) {
 #pragma unroll
@@ -161,18 +166,6 @@ __device__ __forceinline__ void ff_sub_prod(float& s, float& c, float ah, float 
   s = t;
   c += se - (pe + fmaf(ah, xl, al * xh));
 }
-// (h, l) += t with h + l renormalised (two TwoSums): the FP32-pair iterate.
-__device__ __forceinline__ void ff_add(float& h, float& l, float t) {
-  float s = __fadd_rn(h, t);
-  float bv = __fsub_rn(s, h);
-  float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(t, bv));
-  e = __fadd_rn(e, l);
-  const float s2 = __fadd_rn(s, e);
-  bv = __fsub_rn(s2, s);
-  l = __fadd_rn(__fsub_rn(s, __fsub_rn(s2, bv)), __fsub_rn(e, bv));
-  h = s2;
-}
-
 // Bulk prefetch into L2 (TMA) of the vector rows of the vertices kPF steps
 // ahead: the rows of a step are contiguous ([nv][8] floats), so one thread
 // requests each vector's next block while the CTA works on the current one,
@@ -257,20 +250,38 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
 
     // ---- ||g||^2, ||D^-1/2 g||^2 (FP64)
     {
-      Acc4<2> a;
-      a.init();
+      double a[4][2] = {};
       for (int32_t v = vs; v < nv; v += kVP) {
         const double dsv = (double)Ds[v];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const double gv = LIVE(i) ? GS(i)[v] : 0.0;
           const double sv = gv * dsv;
-          a.d[i][0] = fma(gv, gv, a.d[i][0]);
-          a.d[i][1] = fma(sv, sv, a.d[i][1]);
+          a[i][0] = fma(gv, gv, a[i][0]);
+          a[i][1] = fma(sv, sv, a[i][1]);
         }
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int o = 2; o < 32; o <<= 1) a[i][k] += __shfl_xor_sync(kFull, a[i][k], o);
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      if (lane < 2) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int k = 0; k < 2; ++k) sh.red[warp][4 * lane + i][k] = a[i][k];
+      }
+      __syncthreads();
       double out[2] = {0.0, 0.0};
-      group_sum<2>(a, sh, out);
+      if (threadIdx.x < kSG) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int w = 0; w < kWarps; ++w) out[k] += sh.red[w][threadIdx.x][k];
+      }
       if (threadIdx.x < kSG) {
         SampleState& q = sh.st[threadIdx.x];
         const bool lv = s0 + threadIdx.x < S;
@@ -335,6 +346,9 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         }
         Acc4<2> a;
         a.init();
+        int4 ea_n[kU];
+        int2 eb_n[kU];
+        load_ell(ell, vs, nv, ea_n, eb_n);
         for (int32_t v = vs; v < nv; v += kVP) {
           if (threadIdx.x == 0) {  // rows of x~ and g~ kPF steps ahead
             prefetch_rows(xh, v, nv);
@@ -344,7 +358,9 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           }
           int4 ea[kU];
           int2 eb[kU];
-          load_ell(ell, v, nv, ea, eb);
+          ea[0] = ea_n[0];
+          eb[0] = eb_n[0];
+          load_ell(ell, v + kVP, nv, ea_n, eb_n);  // the next step's records
           const int32_t k0 = eb[0].x, deg = eb[0].y;
           const int32_t wl[4] = {ea[0].x, ea[0].y, ea[0].z, ea[0].w};
           const int64_t iv = (int64_t)v * kSG;
@@ -444,14 +460,21 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
             auto pnext = [&](int64_t w, float4 rw) -> float4 {
               return fst ? rw : sel4(fs, rw, fma4(bf4, ld4(pold + w), rw));
             };
+            int4 ea_n[kU];
+            int2 eb_n[kU];
+            load_ell(ell, vs, nv, ea_n, eb_n);
             for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
               if (threadIdx.x == 0) {  // rows of r and p kPF steps ahead (hh = 0 here)
                 prefetch_rows(r, v0, nv);
                 if (!fst) prefetch_rows(pold, v0, nv);
               }
+              // this step's neighbour records, loaded one step earlier; the
+              // next step's requested now
               int4 ea[kU];
               int2 eb[kU];
-              load_ell(ell, v0, nv, ea, eb);  // the step's neighbour records
+#pragma unroll
+              for (int u = 0; u < kU; ++u) ea[u] = ea_n[u], eb[u] = eb_n[u];
+              load_ell(ell, v0 + kU * kVP, nv, ea_n, eb_n);
 #pragma unroll
               for (int u = 0; u < kU; ++u) {
                 const int32_t v = v0 + u * kVP;
@@ -515,6 +538,9 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           Acc4<1> a;
           a.init();
           if (any) {
+            int4 ea_n[kU];
+            int2 eb_n[kU];
+            load_ell(ell, vs, nv, ea_n, eb_n);
             for (int32_t v0 = vs; v0 < nv; v0 += kU * kVP) {
               if (threadIdx.x == 0) {  // rows of p', d and r kPF steps ahead
                 prefetch_rows(pnew, v0, nv);
@@ -523,7 +549,9 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
               }
               int4 ea[kU];
               int2 eb[kU];
-              load_ell(ell, v0, nv, ea, eb);  // the step's neighbour records
+#pragma unroll
+              for (int u = 0; u < kU; ++u) ea[u] = ea_n[u], eb[u] = eb_n[u];
+              load_ell(ell, v0 + kU * kVP, nv, ea_n, eb_n);
 #pragma unroll
               for (int u = 0; u < kU; ++u) {
                 const int32_t v = v0 + u * kVP;
