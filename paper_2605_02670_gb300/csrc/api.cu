@@ -187,6 +187,9 @@ struct grf_graph {
   size_t host_stage_bytes = 0;
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_staged = nullptr, ev_d2h = nullptr;
+  // the Schur blocks' side stream and its fork and join events
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   void drop_graph() {
     if (gc.exec) cudaGraphExecDestroy(gc.exec);
@@ -219,6 +222,9 @@ struct grf_graph {
       if (ev_staged) cudaEventDestroy(ev_staged);
       if (ev_d2h) cudaEventDestroy(ev_d2h);
       if (copy_stream) cudaStreamDestroy(copy_stream);
+      if (ev_fork) cudaEventDestroy(ev_fork);
+      if (ev_join) cudaEventDestroy(ev_join);
+      if (side_stream) cudaStreamDestroy(side_stream);
       if (dst.blk) cudaFree(dst.blk);
       if (cons.blk) cudaFree(cons.blk);
       cudaSetDevice(cur);
@@ -912,6 +918,15 @@ int collect(const ApplyWs& w, cudaStream_t st, int32_t L, int64_t S, RunStats* r
   return GRF_OK;
 }
 
+// The side stream on which the Schur blocks run beside the condensation.
+int ensure_side(grf_graph* g) {
+  if (g->side_stream) return GRF_OK;
+  CUDA_TRY(cudaStreamCreateWithFlags(&g->side_stream, cudaStreamNonBlocking));
+  CUDA_TRY(cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+  return GRF_OK;
+}
+
 // Schur blocks + condensation + PCG for the nodes already uploaded to w.
 template <typename T>
 int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64_t S,
@@ -919,14 +934,25 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                  RunStats* rs) {
   const DevNodes nd = dev_nodes(w, L);
   CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
-  rs->begin(1, st);
   // the Thomas sweep constants are needed only where an edge is left to Thomas
   SweepParams<T>* prm = (SweepParams<T>*)w.prm;
   if (sizeof(T) == 4 && o.spectral && w.bhat && g->thomas_rest() == 0) prm = nullptr;
+  // Without sweep constants nothing before the PCG reads the Schur blocks:
+  // they run on a side stream beside the condensation (FP64-bound kernels
+  // beside tensor-core and streaming ones) and the PCG waits for them.
+  if (!prm && !rs->capturing) GRF_TRY(ensure_side(g));
+  const bool side = !prm && g->side_stream;
+  cudaStream_t sst = side ? g->side_stream : st;
+  if (side) {
+    CUDA_TRY(cudaEventRecord(g->ev_fork, st));
+    CUDA_TRY(cudaStreamWaitEvent(sst, g->ev_fork, 0));
+  }
+  rs->begin(1, sst);
   rs->launches += launch_schur<T>(g->d, nd, kappa2, w.saa, w.sab, w.diag, w.offv, prm,
-                                  (T*)w.dscale, (T*)w.offv_t, st, o.consistent, w.dpair,
+                                  (T*)w.dscale, (T*)w.offv_t, sst, o.consistent, w.dpair,
                                   w.opair);
-  rs->end(1, st);
+  rs->end(1, sst);
+  if (side) CUDA_TRY(cudaEventRecord(g->ev_join, sst));
   rs->begin(2, st);
   if (sizeof(T) == 4) {
     // FP32: the tridiagonal edges (all of them, or those the spectral path
@@ -940,8 +966,10 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     }
     const int32_t head = bins_before(g, p, node_bin0(g, p, o, L));
     const int32_t tail = bins_total(g, p) - head;
-    if (o.consistent && !(spec && umma_ready(g, o, S, L)))
+    if (o.consistent && !(spec && umma_ready(g, o, S, L))) {
+      if (side) cudaStreamWaitEvent(st, g->ev_join, 0);
       return fail(GRF_ENOTSUP, "the consistent mass needs the tensor-core sine transforms");
+    }
     const bool umma = spec && umma_ready(g, o, S, L);
     // tensor-core path with the per-edge end-value buffer: its gather writes
     // g = b_v + (end values) for every node and sample, so it runs first and
@@ -959,9 +987,11 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     }
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head,
                                        !umma);
-    if (tail > 0 && !prm)
+    if (tail > 0 && !prm) {
+      if (side) cudaStreamWaitEvent(st, g->ev_join, 0);
       return fail(GRF_EINVAL, "node-parallel condensation of %d edges without sweep constants",
                   (int)tail);
+    }
     if (tail > 0)
       rs->launches += launch_condense_nodes(g->d, L, S, (const float*)b,
                                             (const SweepParams<float>*)prm,
@@ -976,6 +1006,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st);
   }
   rs->end(2, st);
+  if (side) CUDA_TRY(cudaStreamWaitEvent(st, g->ev_join, 0));
   // FP64 PCG uses the FP64 blocks; the FP32 solve their scaled FP32 copy
   const T* offv_t = sizeof(T) == 8 ? (const T*)w.offv : (const T*)w.offv_t;
   const bool learned = sizeof(T) == 4 && o.precond == GRF_PRECOND_LEARNED;
@@ -1233,6 +1264,7 @@ int sample_graph_impl(grf_graph* g, double kappa, double beta, double k_step, ui
       gc.h_status_cap = (int)stages.size();
     }
     if (!g->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
+    GRF_TRY(ensure_side(g));
     RunStats cap;
     cap.capturing = true;
     cap.timing = o.timing;
