@@ -271,6 +271,7 @@ int ensure_device(grf_graph* g) {
   c.take<int32_t>(V); c.take<int32_t>(V + 1); c.take<int32_t>(2 * E); c.take<int32_t>(2 * E);
   c.take<float>((size_t)g->n);
   c.take<int4>(2 * V);
+  c.take<int4>(V); c.take<int32_t>(V);
   void* blk = nullptr;
   CUDA_TRY(cudaMalloc(&blk, c.off));
   g->device = dev;
@@ -345,6 +346,26 @@ int ensure_device(grf_graph* g) {
     }
     CUDA_TRY(cudaMemcpy(ell, h.data(), 2 * V * sizeof(int4), cudaMemcpyHostToDevice));
     g->d_ell = ell;
+    // the end-value gather's records: incidences on sine-basis edges
+    int4* sinc = k.take<int4>(V);
+    int32_t* scnt = k.take<int32_t>(V);
+    std::vector<int4> hs(V);
+    std::vector<int32_t> hc(V);
+    for (size_t v = 0; v < V; ++v) {
+      int32_t w[4] = {-1, -1, -1, -1}, c = 0;
+      for (int32_t kk = g->vptr[v]; kk < g->vptr[v + 1]; ++kk) {
+        const int32_t e = g->adj_edge[kk], m = g->nel[e] - 1;
+        if (m < 1 || m > kSpecMaxM) continue;
+        if (c < 4) w[c] = 2 * e + (g->eu[e] == (int64_t)v ? 0 : 1);
+        ++c;
+      }
+      hs[v] = make_int4(w[0], w[1], w[2], w[3]);
+      hc[v] = c;
+    }
+    CUDA_TRY(cudaMemcpy(sinc, hs.data(), V * sizeof(int4), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(scnt, hc.data(), V * sizeof(int32_t), cudaMemcpyHostToDevice));
+    d.spec_inc = sinc;
+    d.spec_cnt = scnt;
   }
   sqrt_ml_kernel<<<(int)blocks, 256>>>(d, mlv, sml, smlf);
   CUDA_TRY(cudaGetLastError());

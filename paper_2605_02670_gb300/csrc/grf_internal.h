@@ -25,6 +25,8 @@ inline int sm_count() {
 }
 
 // Device copy of the mesh (Sec. 3, Phase 1). Vertex ids are kept ids.
+constexpr int32_t kSpecMaxM = 1024;  // interior nodes of the longest sine-basis edge
+
 struct DevGraph {
   int32_t nv;        // kept vertices
   int32_t ne;        // edges
@@ -41,6 +43,10 @@ struct DevGraph {
   const int32_t* adj_nbr;   // [2 ne] vertex at the other end
   const int32_t* adj_rev;   // [2 ne] index of the same edge in the other end's list
   const double* sqrt_ml;    // [n] sqrt of the lumped mass per DOF
+  // per vertex its first four incidences on sine-basis edges (1 <= m <= 1024)
+  // as 2 e + end (end 0 at x = 0), -1 past them, and how many it has in all
+  const int4* spec_inc;     // [nv]: edges with m <= kSpecMaxM count
+  const int32_t* spec_cnt;  // [nv]
 };
 
 // A renumbering of the vertices into slots (reverse Cuthill-McKee order,

@@ -60,7 +60,7 @@ constexpr uint32_t kATile = kRows * kK * 2;    // one BF16 plane of A: 16 KB
 constexpr uint32_t kBPlane = kMaxSB * kK * 2;  // 4 KB
 constexpr uint32_t kStage = 2 * kATile + 2 * kBPlane;  // A hi/lo, B hi/lo
 constexpr uint32_t kBhTile = kRows * kMaxSB * 4;       // a coefficient unit's bh rows: 16 KB
-constexpr int kMaxM = 1024;                    // modes of the sine-basis path
+constexpr int kMaxM = kSpecMaxM;               // modes of the sine-basis path
 constexpr int kMaxKE = kMaxM + 2 * kK;         // K positions of the end values (both parities)
 constexpr uint32_t kColsEnds = 64;             // two accumulators of SB columns
 constexpr uint32_t kColsCoef = 32;
@@ -239,16 +239,20 @@ __global__ void __launch_bounds__(kT, 2)
       unsigned char* b_hi = a_lo + kATile;
       unsigned char* b_lo = b_hi + kBPlane;
       const float* sg = sigk + t * kK + half * 32;
+      // rows past the last node are left as they are: a GEMM row depends on
+      // its own A row only, and the epilogue stores none of them
+      if (l < L) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const float4 s4a = *reinterpret_cast<const float4*>(sg + 8 * c);
-        const float4 s4b = *reinterpret_cast<const float4*>(sg + 8 * c + 4);
-        const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
-        float x[8];
+        for (int c = 0; c < 4; ++c) {
+          const float4 s4a = *reinterpret_cast<const float4*>(sg + 8 * c);
+          const float4 s4b = *reinterpret_cast<const float4*>(sg + 8 * c + 4);
+          const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
+          float x[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r)
-          x[r] = kCons ? ep * rcp_approx(fmaf(sv[r], ep, dl)) : rcp_approx(sv[r] + dl);
-        store_a_row(a_hi, a_lo, row, 4 * half + c, x);
+          for (int r = 0; r < 8; ++r)
+            x[r] = kCons ? ep * rcp_approx(fmaf(sv[r], ep, dl)) : rcp_approx(sv[r] + dl);
+          store_a_row(a_hi, a_lo, row, 4 * half + c, x);
+        }
       }
       if (bitem) {
         const float* pk = phik + t * kK + bc * 8;
@@ -321,7 +325,10 @@ __global__ void __launch_bounds__(kT, 2)
 // takes 32 vertices x 32 nodes of one sample: warp w gathers vertices
 // 4w .. 4w + 3 with the lanes on consecutive nodes, and after a transpose in
 // shared memory writes 32 consecutive vertices per node (FP32 sums over the
-// incidences, added to b_v in FP64).
+// incidences, added to b_v in FP64). Each vertex's first four sine-basis
+// incidences come from one record (g.spec_inc), so the end values of all four
+// vertices of a warp are requested together; the rare further incidences walk
+// the incidence list.
 __global__ void __launch_bounds__(256)
     ends_gather_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ ends,
                        const float* __restrict__ b, double* __restrict__ gvec) {
@@ -329,23 +336,42 @@ __global__ void __launch_bounds__(256)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int32_t nvt = (g.nv + 31) / 32, nlt = (L + 31) / 32;
   const int64_t tiles = (int64_t)nvt * nlt * S;
+  const int64_t SL = S * (int64_t)L;  // from one (edge, end) to the next in ends
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int32_t vt = (int32_t)(t % nvt);
     const int64_t r2 = t / nvt;
     const int32_t l0 = (int32_t)(r2 % nlt) * 32;
     const int64_t s = r2 / nlt;
     const int32_t v0 = vt * 32;
+    const int32_t l = l0 + lane;
+    const float* __restrict__ es = ends + s * L + l;  // + (2 e + end) SL
+    int4 rec[4];
+    int32_t cnt[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int32_t v = v0 + 4 * warp + q, l = l0 + lane;
+      const int32_t v = v0 + 4 * warp + q;
+      const bool ok = v < g.nv && l < L;
+      rec[q] = ok ? __ldg(g.spec_inc + v) : make_int4(-1, -1, -1, -1);
+      cnt[q] = ok ? __ldg(g.spec_cnt + v) : 0;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int4 r = rec[q];
       float acc = 0.f;
-      if (v < g.nv && l < L) {
+      if (r.x >= 0) acc += __ldg(es + r.x * SL);
+      if (r.y >= 0) acc += __ldg(es + r.y * SL);
+      if (r.z >= 0) acc += __ldg(es + r.z * SL);
+      if (r.w >= 0) acc += __ldg(es + r.w * SL);
+      if (cnt[q] > 4) {  // the incidences after the fourth sine-basis one
+        const int32_t v = v0 + 4 * warp + q;
+        int32_t c = 0;
         for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
           const int32_t e = g.adj_edge[k];
           const int32_t m = g.nel[e] - 1;
           if (m < 1 || m > kMaxM) continue;  // no interior, or not a sine-basis edge
+          if (c++ < 4) continue;
           const int64_t end = g.eu[e] == v ? 0 : 1;
-          acc += ends[((int64_t)e * 2 * S + end * S + s) * L + l];
+          acc += es[(2 * (int64_t)e + end) * SL];
         }
       }
       tile[4 * warp + q][lane] = acc;
@@ -353,15 +379,14 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int32_t l = l0 + 4 * warp + q, v = v0 + lane;
-      if (l < L && v < g.nv)
-        gvec[((int64_t)l * S + s) * g.nv + v] =
+      const int32_t lq = l0 + 4 * warp + q, v = v0 + lane;
+      if (lq < L && v < g.nv)
+        gvec[((int64_t)lq * S + s) * g.nv + v] =
             (double)b[(int64_t)v * S + s] + (double)tile[lane][4 * warp + q];
     }
     __syncthreads();
   }
 }
-
 
 // -------------------------------------------------------------- coefficients
 
@@ -461,8 +486,11 @@ __global__ void __launch_bounds__(kT, 2)
       unsigned char* b_hi = a_lo + kATile;
       unsigned char* b_lo = b_hi + kBPlane;
       const int k0 = t * kK + half * 32;
+      // rows of modes past m are left as they are (their rows of the
+      // accumulator are never stored)
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
+        if (j >= m) break;
         const float4 d4a = *reinterpret_cast<const float4*>(dls + k0 + 8 * c);
         const float4 d4b = *reinterpret_cast<const float4*>(dls + k0 + 8 * c + 4);
         const float4 s4a = *reinterpret_cast<const float4*>(scs + k0 + 8 * c);
