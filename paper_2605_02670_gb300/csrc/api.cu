@@ -974,6 +974,10 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
                                   w.opair);
   rs->end(1, sst);
   if (side) CUDA_TRY(cudaEventRecord(g->ev_join, sst));
+  const int pre_kind = (sizeof(T) == 4 && o.precond == GRF_PRECOND_LEARNED)
+                           ? kPreLearned
+                           : (o.precond == GRF_PRECOND_NEUMANN ? kPreNeumann : kPreJacobi);
+  bool g32 = false;  // g given to the PCG in FP32 (see below)
   rs->begin(2, st);
   if (sizeof(T) == 4) {
     // FP32: the tridiagonal edges (all of them, or those the spectral path
@@ -996,6 +1000,11 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
     // g = b_v + (end values) for every node and sample, so it runs first and
     // the tridiagonal edges then add into it
     const bool gather_init = umma && w.ends;
+    // When every edge with interior nodes is on the tensor-core path and the
+    // batched PCG will run, the gather writes g in FP32 straight into that
+    // PCG's layout (the end values and the noise are FP32 already)
+    g32 = gather_init && head == 0 && tail == 0 && w.gh &&
+          pcg_batch_selected(g->d, o.pcg_layout, pre_kind);
     if (umma) {
       rs->launches += launch_dst_gemm<false, float>(g->d, g->dst.dev, S, (const float*)b, w.bhat,
                                                     w.status, g->n_sm, st);
@@ -1004,7 +1013,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
       rs->launches += launch_spec_ends_umma(g->d, nd, S, g->d_spec_edges, g->spec_count,
                                             g->n_spec_bins, w.bhat, gvec, w.ends,
                                             (const float*)b, o.consistent, w.status, g->n_sm,
-                                            st);
+                                            st, g32 ? w.gh : nullptr);
     }
     rs->launches += launch_condense<T>(g->d, nd, kappa2, S, b, gvec, st, g->d_bin_edges[p], head,
                                        !umma);
@@ -1057,7 +1066,7 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   }
   rs->begin(3, st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
-  const PcgPairs pairs{w.dpair, w.opair, w.xh, w.xl, w.gh, w.gl};
+  const PcgPairs pairs{w.dpair, w.opair, w.xh, w.xl, w.gh, w.gl, g32};
   launch_pcg<T>(g->d, g->d_order, g->d_ell, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
                 (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st,

@@ -196,12 +196,17 @@ struct PcgPairs {
   const float2* dp;
   const float2* op;
   float *xh, *xl, *gh, *gl;
+  // true: gh already holds g in FP32 (launch_spec_ends_umma's g32) and the
+  // FP64 gvec is not read
+  bool g32;
 };
 void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,
                       const double* gvec, double* x, float* R, float* PA, float* PB, float* Dv,
                       const PcgPairs& pp, double rtol, int32_t max_iter, int32_t* iters,
                       PcgStatus* status, cudaStream_t st);
+// Whether launch_pcg<float> with pairs takes the batched layout.
+bool pcg_batch_selected(const DevGraph& g, int layout, int pre);
 // pairs: required by the batched layout (FP32 only), ignored otherwise.
 template <typename VT>
 void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int32_t L, int64_t S,
@@ -295,13 +300,16 @@ int launch_spec_recover(const DevGraph& g, const DevNodes& nd, double kappa2, in
 // coefficient kernel grows with L (spec_umma_fits). ends: a scratch of
 // 2 E S L floats for the end values per edge, then gathered over the vertices'
 // incidences into gvec = b_v + (end values), b the sample-minor noise: this
-// initialises gvec (null ends: FP64 atomics into an initialised gvec).
+// initialises gvec (null ends: FP64 atomics into an initialised gvec). With
+// g32 (and ends) the sums go in FP32 to g32 in the batched PCG's layout
+// [L][ceil(S / 8)][nv][8] instead, and gvec is not touched.
 int32_t spec_umma_sample_block(int64_t S);
 bool spec_umma_fits(int32_t L);
 int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
                           const float* bhat, double* gvec, float* ends, const float* b,
-                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st);
+                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st,
+                          float* g32 = nullptr);
 int launch_spec_coef_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
                           float* bhat, const float* xw, bool consistent, PcgStatus* status,

@@ -1465,6 +1465,13 @@ bool group_fits(const DevGraph& g) {
 
 }  // namespace
 
+bool pcg_batch_selected(const DevGraph& g, int layout, int pre) {
+  if (pre != kPreJacobi) return false;
+  if (layout == 4) return true;
+  if ((layout == 2 || layout == 3) && group_fits(g)) return false;
+  return layout != 1;
+}
+
 template <typename VT>
 void launch_pcg(const DevGraph& g, const VertexOrder& ord, const int4* ell, int32_t L, int64_t S,
                 const double* diag, const double* offv, const VT* dscale_t, const VT* offv_t, int pre, const VT* pc, const VT* pn,

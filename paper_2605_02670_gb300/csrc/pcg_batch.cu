@@ -201,7 +201,9 @@ __device__ __forceinline__ void load_ell(const int4* __restrict__ ell, int32_t v
 
 }  // namespace
 
-// gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out).
+// gvec, xout: [L][S][nv] FP64 (right-hand sides in, solutions out); with
+// g32 the right-hand sides come in FP32 in GH (same layout as the vectors) and
+// gvec is not read.
 // DP, OP: the FP64 blocks as FP32 pairs, [L][nv] and [L][2E].
 // R, PA, PB, Dv, XH, XL, GH, GL: [L][ceil(S / 8)][nv][8] FP32 scratch.
 __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     float* __restrict__ R, float* __restrict__ PA, float* __restrict__ PB,
     float* __restrict__ Dv, float* __restrict__ XH, float* __restrict__ XL,
     float* __restrict__ GH, float* __restrict__ GL, double rtol, int32_t max_iter,
-    int32_t* __restrict__ iters, PcgStatus* __restrict__ status) {
+    int32_t* __restrict__ iters, PcgStatus* __restrict__ status, int g32) {
   __shared__ BatchShared sh;
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
@@ -242,14 +244,31 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     // the first nlive exist)
     const int64_t sfirst = s0 + 4 * hh;
     const int nlive = (int)(S - sfirst < 0 ? 0 : (S - sfirst > 4 ? 4 : S - sfirst));
-    const double* __restrict__ g0 = gvec + (l * S + (nlive > 0 ? sfirst : 0)) * nv;
+    const double* __restrict__ g0 = g32 ? nullptr : gvec + (l * S + (nlive > 0 ? sfirst : 0)) * nv;
     double* __restrict__ x0 = xout + (l * S + (nlive > 0 ? sfirst : 0)) * nv;
 #define GS(i) (g0 + (int64_t)(i) * nv)
 #define XS(i) (x0 + (int64_t)(i) * nv)
 #define LIVE(i) ((i) < nlive)
 
-    // ---- ||g||^2, ||D^-1/2 g||^2 (FP64)
+    // ---- ||g||^2, ||D^-1/2 g||^2 (FP64; from the FP32 g in gh: FP32 pair sums)
     {
+      double out[2] = {0.0, 0.0};
+      if (g32) {
+        Acc4<2> a2;
+        a2.init();
+        for (int32_t v = vs; v < nv; v += kVP) {
+          const float dsv = Ds[v];
+          const float4 g4 = ld4(gh + (int64_t)v * kSG);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float gv = LIVE(i) ? get(g4, i) : 0.f, sv = gv * dsv;
+            a2.f[i][0] = fmaf(gv, gv, a2.f[i][0]);
+            a2.f[i][1] = fmaf(sv, sv, a2.f[i][1]);
+          }
+          a2.tick();
+        }
+        group_sum<2>(a2, sh, out);
+      } else {
       double a[4][2] = {};
       for (int32_t v = vs; v < nv; v += kVP) {
         const double dsv = (double)Ds[v];
@@ -275,12 +294,12 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
           for (int k = 0; k < 2; ++k) sh.red[warp][4 * lane + i][k] = a[i][k];
       }
       __syncthreads();
-      double out[2] = {0.0, 0.0};
       if (threadIdx.x < kSG) {
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
           for (int w = 0; w < kWarps; ++w) out[k] += sh.red[w][threadIdx.x][k];
+      }
       }
       if (threadIdx.x < kSG) {
         SampleState& q = sh.st[threadIdx.x];
@@ -289,6 +308,17 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
         q.done = !lv || q.bad || !(out[0] > 0.0) || !(out[1] > 0.0);
         q.gn = q.done ? 0.0 : sqrt(out[0]);
         q.inv_g = q.done ? 0.0 : 1.0 / q.gn;
+        if (g32 && !q.done) {
+          // g~ = g fl32(1 / ||g||) exactly as a pair; ||g|| the exact inverse
+          // of that factor, so that x = ||g|| x~ solves S x = g
+          const float ivf = (float)q.inv_g;
+          if (!(ivf >= 1.17549435e-38f) || !isfinite(ivf)) {
+            q.bad = q.done = 1;
+          } else {
+            q.inv_g = (double)ivf;
+            q.gn = 1.0 / (double)ivf;
+          }
+        }
         // the inner FP32 solve runs on r = D^-1/2 r~ ||g|| / rho, O(1) whatever
         // the node's scale: rho = ||D^-1/2 g|| first, then the estimate of the
         // refinement residual's norm from the previous inner solve
@@ -315,14 +345,25 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
       for (int32_t v = vs; v < nv; v += kVP) {
         const float dsv = Ds[v];
         float hv[4], lv[4], rv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const double gt = dn[i] ? 0.0 : GS(i)[v] * ivg[i];
-          hv[i] = __double2float_rn(gt);
-          lv[i] = __double2float_rn(gt - (double)hv[i]);
-          rv[i] = (hv[i] * sc[i]) * dsv;
-        }
         const int64_t iv = (int64_t)v * kSG;
+        if (g32) {
+          const float4 g4 = ld4(gh + iv);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float gv = dn[i] ? 0.f : get(g4, i), ivf = (float)ivg[i];
+            hv[i] = gv * ivf;
+            lv[i] = fmaf(gv, ivf, -hv[i]);  // g ivf = hv + lv exactly
+            rv[i] = (hv[i] * sc[i]) * dsv;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const double gt = dn[i] ? 0.0 : GS(i)[v] * ivg[i];
+            hv[i] = __double2float_rn(gt);
+            lv[i] = __double2float_rn(gt - (double)hv[i]);
+            rv[i] = (hv[i] * sc[i]) * dsv;
+          }
+        }
         st4(gh + iv, make_float4(hv[0], hv[1], hv[2], hv[3]));
         st4(gl + iv, make_float4(lv[0], lv[1], lv[2], lv[3]));
         st4(xh + iv, z4);
@@ -697,7 +738,7 @@ void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, 
   const int blocks = (int)(items < (int64_t)1 << 30 ? items : (int64_t)1 << 30);
   pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, ell, L, S, pp.dp, pp.op, dscale, offv_t, gvec, x, R,
                                            PA, PB, Dv, pp.xh, pp.xl, pp.gh, pp.gl, rtol, max_iter,
-                                           iters, status);
+                                           iters, status, pp.g32 ? 1 : 0);
 }
 
 }  // namespace grf

@@ -388,6 +388,84 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same sums in FP32 straight into the batched vertex PCG's layout
+// g32[l][s / 8][v][s % 8] (the end values and the noise are FP32, so g carries
+// their rounding already; samples past S are written as 0). A CTA takes 32
+// vertices x 32 nodes x 8 samples: warp w gathers vertices 4w .. 4w + 3 with
+// the lanes on consecutive nodes, and after a transpose in shared memory each
+// node's 32 x 8 block is one contiguous kilobyte.
+__global__ void __launch_bounds__(256)
+    ends_gather32_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ ends,
+                         const float* __restrict__ b, float* __restrict__ g32) {
+  constexpr int kRow = 257;  // 32 vertices x 8 samples per node, padded
+  __shared__ float tile[32 * kRow];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t nvt = (g.nv + 31) / 32, nlt = (L + 31) / 32;
+  const int64_t nsg = (S + 7) / 8;
+  const int64_t tiles = (int64_t)nvt * nlt * nsg;
+  const int64_t SL = S * (int64_t)L;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int32_t vt = (int32_t)(t % nvt);
+    const int64_t r2 = t / nvt;
+    const int32_t l0 = (int32_t)(r2 % nlt) * 32;
+    const int64_t sg = r2 / nlt;
+    const int32_t v0 = vt * 32;
+    const int32_t l = l0 + lane;
+    int4 rec[4];
+    int32_t cnt[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int32_t v = v0 + 4 * warp + q;
+      const bool ok = v < g.nv && l < L;
+      rec[q] = ok ? __ldg(g.spec_inc + v) : make_int4(-1, -1, -1, -1);
+      cnt[q] = ok ? __ldg(g.spec_cnt + v) : 0;
+    }
+#pragma unroll 1
+    for (int j = 0; j < 8; ++j) {
+      const int64_t s = sg * 8 + j;
+      const bool sok = s < S;
+      const float* __restrict__ es = ends + (sok ? s : 0) * L + l;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int4 r = rec[q];
+        float acc = 0.f;
+        if (sok) {
+          if (r.x >= 0) acc += __ldg(es + r.x * SL);
+          if (r.y >= 0) acc += __ldg(es + r.y * SL);
+          if (r.z >= 0) acc += __ldg(es + r.z * SL);
+          if (r.w >= 0) acc += __ldg(es + r.w * SL);
+          if (cnt[q] > 4) {  // the incidences after the fourth sine-basis one
+            const int32_t v = v0 + 4 * warp + q;
+            int32_t c = 0;
+            for (int32_t k = g.vptr[v]; k < g.vptr[v + 1]; ++k) {
+              const int32_t e = g.adj_edge[k];
+              const int32_t m = g.nel[e] - 1;
+              if (m < 1 || m > kMaxM) continue;
+              if (c++ < 4) continue;
+              const int64_t end = g.eu[e] == v ? 0 : 1;
+              acc += es[(2 * (int64_t)e + end) * SL];
+            }
+          }
+        }
+        tile[lane * kRow + (4 * warp + q) * 8 + j] = acc;
+      }
+    }
+    __syncthreads();
+    // thread t: vertex v0 + t / 8, sample 8 sg + t % 8 of every node
+    const int32_t v = v0 + (int32_t)(threadIdx.x >> 3);
+    const int64_t s = sg * 8 + (threadIdx.x & 7);
+    const float bv = (v < g.nv && s < S) ? b[(int64_t)v * S + s] : 0.f;
+    for (int i = 0; i < 32; ++i) {
+      const int32_t li = l0 + i;
+      if (li >= L) break;
+      if (v < g.nv)
+        g32[(((int64_t)li * nsg + sg) * g.nv + v) * 8 + (threadIdx.x & 7)] =
+            s < S ? bv + tile[i * kRow + threadIdx.x] : 0.f;
+    }
+    __syncthreads();
+  }
+}
+
 // -------------------------------------------------------------- coefficients
 
 template <bool kCons>
@@ -605,7 +683,8 @@ bool spec_umma_fits(int32_t L) {
 int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
                           const int32_t* bin_edges, const int32_t* bin_count, int n_bins,
                           const float* bhat, double* gvec, float* ends, const float* b,
-                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st) {
+                          bool consistent, PcgStatus* status, int n_sm, cudaStream_t st,
+                          float* g32) {
   int32_t n = 0;
   for (int i = 0; i < n_bins; ++i) n += bin_count[i];
   if (n <= 0) return 0;
@@ -618,8 +697,14 @@ int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
   kern<<<(int)(units < cap ? units : cap), kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, gvec,
                                                            ends, SB, status);
   if (!ends) return 1;
-  const int64_t tiles = (int64_t)((g.nv + 31) / 32) * ((nd.L + 31) / 32) * S;
   const int64_t gcap = (int64_t)n_sm * 8;
+  if (g32) {
+    const int64_t tiles = (int64_t)((g.nv + 31) / 32) * ((nd.L + 31) / 32) * ((S + 7) / 8);
+    ends_gather32_kernel<<<(int)(tiles < gcap ? tiles : gcap), 256, 0, st>>>(g, nd.L, S, ends, b,
+                                                                             g32);
+    return 2;
+  }
+  const int64_t tiles = (int64_t)((g.nv + 31) / 32) * ((nd.L + 31) / 32) * S;
   ends_gather_kernel<<<(int)(tiles < gcap ? tiles : gcap), 256, 0, st>>>(g, nd.L, S, ends, b,
                                                                          gvec);
   return 2;
