@@ -63,7 +63,8 @@ constexpr uint32_t kBhTile = kRows * kMaxSB * 4;       // a coefficient unit's b
 constexpr int kMaxM = kSpecMaxM;               // modes of the sine-basis path
 constexpr int kMaxKE = kMaxM + 2 * kK;         // K positions of the end values (both parities)
 constexpr uint32_t kColsEnds = 64;             // two accumulators of SB columns
-constexpr uint32_t kColsCoef = 32;
+constexpr int kMaxRB = (kMaxM / 2 + 127) / 128;  // row blocks of one parity's modes
+constexpr uint32_t kColsCoef = kMaxRB * kMaxSB;   // one accumulator per row block
 constexpr size_t kSmemLimit = 232448;          // 227 KB per CTA
 
 __device__ __forceinline__ unsigned char* align1024(unsigned char* p) {
@@ -472,26 +473,32 @@ template <bool kCons>
 __global__ void __launch_bounds__(kT, 2)
     spec_coef_umma_kernel(DevGraph g, DevNodes nd, int64_t S, const int32_t* __restrict__ edges,
                           int32_t n_edges, float* __restrict__ bhat, const float* __restrict__ xw,
-                          int32_t SB, int32_t nrb, PcgStatus* __restrict__ status) {
+                          int32_t SB, PcgStatus* __restrict__ status) {
   extern __shared__ unsigned char sc_raw[];
   unsigned char* sm = align1024(sc_raw);
   const int32_t L = nd.L;
   const int nk = (L + kK - 1) / kK;
   const int LK = nk * kK;  // K positions: the nodes, padded to whole stages
-  float* bht = reinterpret_cast<float*>(sm + 2 * kStage);  // [kRows][SB] the unit's bh rows
-  // per-unit node tables: delta_l (1 on padding), eps_l (1), sc_l (0)
+  // two A buffers (hi and lo planes) for the row blocks in turn, then two B
+  // buffers for the K stages in turn
+  unsigned char* const abuf = sm;
+  unsigned char* const bbuf = sm + 4 * kATile;
+  float* bht = reinterpret_cast<float*>(sm + 2 * kStage);  // [kRows][SB] one row block's bh
+  // per-unit node tables: delta_l (1 on padding), eps_l (1), sc_l (0); the
+  // mode shift of each row of each row block; the partial D_j of each thread
   float* dls = bht + kRows * kMaxSB;
   float* eps = dls + LK;
   float* scs = eps + LK;
-  float* dpart = scs + LK;  // [kT] the two halves of each row's D_j
+  float* sigr = scs + LK;             // [kMaxRB][kRows]
+  float* dsum = sigr + kMaxRB * kRows;  // [kMaxRB][kT]
   Pipe pp;
-  pp.init(reinterpret_cast<unsigned char*>(dpart + kT), kColsCoef);
+  pp.init(reinterpret_cast<unsigned char*>(dsum + kMaxRB * kT), kColsCoef);
   const uint32_t tmem = *pp.tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = tid & (kRows - 1), half = tid >> 7;
   const uint32_t idesc = idesc_bf16(128, SB);
   const int64_t nsb = (S + SB - 1) / SB;
-  const int64_t units = (int64_t)n_edges * nsb * nrb * 2;
+  const int64_t units = (int64_t)n_edges * nsb * 2;
   const bool bitem = tid < SB * 8;
   const int bn = tid % SB, bc = tid / SB;
   const int64_t xstride = (int64_t)g.nv * S;  // from node l to node l + 1 in xw
@@ -499,20 +506,22 @@ __global__ void __launch_bounds__(kT, 2)
 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const int par = (int)(u & 1);  // 0: even modes (xa + xb), 1: odd modes (xa - xb)
-    const int32_t rb = (int32_t)((u >> 1) % nrb);
-    const int64_t rest = (u >> 1) / nrb;
+    const int64_t rest = u >> 1;
     const int64_t s0 = (rest % nsb) * SB;
     const int32_t e = edges[rest / nsb];
     const int32_t m = g.nel[e] - 1;
-    if (m < 1 || 2 * kRows * rb + par >= m) continue;  // no mode of this parity here
+    const int32_t npar = par ? m / 2 : (m + 1) / 2;  // modes of this parity
+    if (m < 1 || npar < 1) continue;
+    const int nrbe = (npar + kRows - 1) / kRows;  // row blocks of 128 modes (<= kMaxRB)
     const int kv = (int)(S - s0 < SB ? S - s0 : SB);
     const int64_t off = g.ioff[e];
     const double h = g.he[e];
     const float hf = (float)h, h2f = (float)(h * h);
     const int32_t va = g.eu[e], vb = g.ev[e];
-    // mode of row r: j = 2 (128 rb + r) + par
-    // the unit's bh rows, fetched asynchronously now and used by the epilogue
-    if (async_bh) {
+    // mode of row r of row block rb: j = 2 (128 rb + r) + par
+    // the bh rows of row block rb, fetched asynchronously and used by its epilogue
+    auto fetch_bh = [&](int rb) {
+      if (!async_bh) return;
       const int cpr = SB / 4;
       for (int idx = tid; idx < kRows * cpr; idx += kT) {
         const int rr = idx / cpr, c4 = idx - rr * cpr;
@@ -525,7 +534,8 @@ __global__ void __launch_bounds__(kT, 2)
                      : "memory");
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
-    }
+    };
+    fetch_bh(0);
     for (int32_t p = tid; p < LK; p += kT) {
       const bool ok = p < L;
       const float d = ok ? nd.shift[p] * h2f : 1.f;
@@ -533,11 +543,15 @@ __global__ void __launch_bounds__(kT, 2)
       eps[p] = (kCons && ok) ? 1.f - d * (1.f / 6.f) : 1.f;
       scs[p] = ok ? nd.wgam[p] * hf : 0.f;
     }
+    for (int rb = 0; rb < nrbe; ++rb) {
+      if (tid < kRows) {
+        const int32_t j = 2 * (kRows * rb + tid) + par;
+        sigr[rb * kRows + tid] = j < m ? mode_shift(j, m) : 0.f;
+      }
+      dsum[rb * kT + tid] = 0.f;
+    }
     __syncthreads();
-    const int32_t j = 2 * (kRows * rb + row) + par;
-    const float sg = j < m ? mode_shift(j, m) : 0.f;
     const float sgn = par ? -1.f : 1.f;
-    float D = 0.f;
     const bool bok = bitem && bn < kv;
     const float* pxa = xw + (int64_t)va * S + s0 + bn;
     const float* pxb = xw + (int64_t)vb * S + s0 + bn;
@@ -553,52 +567,68 @@ __global__ void __launch_bounds__(kT, 2)
     };
     load_b(0, xa, xc);
     int last = 0;
-    for (int t = 0; t < nk; ++t) {
-      const int st = t & 1;
-      last = st;
+    for (int t = 0; t < nk && !pp.failed; ++t) {
       float na[8], nc[8];
       if (t + 1 < nk) load_b(t + 1, na, nc);
-      if (!pp.acquire(st)) break;
-      unsigned char* a_hi = sm + st * kStage;
-      unsigned char* a_lo = a_hi + kATile;
-      unsigned char* b_hi = a_lo + kATile;
+      unsigned char* b_hi = bbuf + (t & 1) * 2 * kBPlane;
       unsigned char* b_lo = b_hi + kBPlane;
       const int k0 = t * kK + half * 32;
-      // rows of modes past m are left as they are (their rows of the
-      // accumulator are never stored)
+      for (int rb = 0; rb < nrbe; ++rb) {
+        // sub-stage (t, rb) in A buffer st; acquiring it (its MMAs of two
+        // sub-stages ago are done) also frees the B buffer of stage t - 2
+        const int st = (t * nrbe + rb) & 1;
+        last = st;
+        if (!pp.acquire(st)) break;
+        unsigned char* a_hi = abuf + st * 2 * kATile;
+        unsigned char* a_lo = a_hi + kATile;
+        if (rb == 0 && bitem) {
+          float xx[8];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (j >= m) break;
-        const float4 d4a = *reinterpret_cast<const float4*>(dls + k0 + 8 * c);
-        const float4 d4b = *reinterpret_cast<const float4*>(dls + k0 + 8 * c + 4);
-        const float4 s4a = *reinterpret_cast<const float4*>(scs + k0 + 8 * c);
-        const float4 s4b = *reinterpret_cast<const float4*>(scs + k0 + 8 * c + 4);
-        const float dv[8] = {d4a.x, d4a.y, d4a.z, d4a.w, d4b.x, d4b.y, d4b.z, d4b.w};
-        const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
-        float ev[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
-        if (kCons) {
-          const float4 e4a = *reinterpret_cast<const float4*>(eps + k0 + 8 * c);
-          const float4 e4b = *reinterpret_cast<const float4*>(eps + k0 + 8 * c + 4);
-          ev[0] = e4a.x, ev[1] = e4a.y, ev[2] = e4a.z, ev[3] = e4a.w;
-          ev[4] = e4b.x, ev[5] = e4b.y, ev[6] = e4b.z, ev[7] = e4b.w;
+          for (int r = 0; r < 8; ++r) {
+            const float ep = kCons ? eps[t * kK + bc * 8 + r] : 1.f;
+            xx[r] = ep * fmaf(sgn, xc[r], xa[r]);
+          }
+          store_b_row(b_hi, b_lo, bn, bc, xx);
         }
-        float x[8];
+        // rows of modes past m are left as they are (their rows of the
+        // accumulator are never stored)
+        const int32_t j = 2 * (kRows * rb + row) + par;
+        if (j < m) {
+          const float sg = sigr[rb * kRows + row];
+          float D = 0.f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float a = rcp_approx(kCons ? fmaf(sg, ev[r], dv[r]) : sg + dv[r]);
-          D = fmaf(sv[r], a, D);
-          x[r] = a;
-        }
-        store_a_row(a_hi, a_lo, row, 4 * half + c, x);
-      }
-      if (bitem) {
-        float xx[8];
+          for (int c = 0; c < 4; ++c) {
+            const float4 d4a = *reinterpret_cast<const float4*>(dls + k0 + 8 * c);
+            const float4 d4b = *reinterpret_cast<const float4*>(dls + k0 + 8 * c + 4);
+            const float4 s4a = *reinterpret_cast<const float4*>(scs + k0 + 8 * c);
+            const float4 s4b = *reinterpret_cast<const float4*>(scs + k0 + 8 * c + 4);
+            const float dv[8] = {d4a.x, d4a.y, d4a.z, d4a.w, d4b.x, d4b.y, d4b.z, d4b.w};
+            const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
+            float ev[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+            if (kCons) {
+              const float4 e4a = *reinterpret_cast<const float4*>(eps + k0 + 8 * c);
+              const float4 e4b = *reinterpret_cast<const float4*>(eps + k0 + 8 * c + 4);
+              ev[0] = e4a.x, ev[1] = e4a.y, ev[2] = e4a.z, ev[3] = e4a.w;
+              ev[4] = e4b.x, ev[5] = e4b.y, ev[6] = e4b.z, ev[7] = e4b.w;
+            }
+            float x[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float ep = kCons ? eps[t * kK + bc * 8 + r] : 1.f;
-          xx[r] = ep * fmaf(sgn, xc[r], xa[r]);
+            for (int r = 0; r < 8; ++r) {
+              const float a = rcp_approx(kCons ? fmaf(sg, ev[r], dv[r]) : sg + dv[r]);
+              D = fmaf(sv[r], a, D);
+              x[r] = a;
+            }
+            store_a_row(a_hi, a_lo, row, 4 * half + c, x);
+          }
+          dsum[rb * kT + tid] += D;
         }
-        store_b_row(b_hi, b_lo, bn, bc, xx);
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          issue_stage(tmem, (uint32_t)(rb * SB), a_hi, a_lo, b_hi, b_lo, idesc, t != 0);
+          commit(&pp.mbar[st]);
+        }
+        pp.bump(st);
       }
       if (t + 1 < nk) {
 #pragma unroll
@@ -607,53 +637,49 @@ __global__ void __launch_bounds__(kT, 2)
           xc[r] = nc[r];
         }
       }
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        issue_stage(tmem, 0u, a_hi, a_lo, b_hi, b_lo, idesc, t != 0);
-        commit(&pp.mbar[st]);
-      }
-      pp.bump(st);
     }
-    if (pp.failed) break;
-    dpart[tid] = D;
-    if (!pp.drain(last)) break;
-    // epilogue, two passes through shared memory (the stage buffers are free):
-    // (1) warp w reads lanes 32 (w % 4) .. + 31, sample half w / 4, into a
-    //     row-major tile (SB + 1 floats a row)
+    if (pp.failed || !pp.drain(last)) break;
+    // epilogue of each row block, two passes through shared memory (the A
+    // buffers are free):
+    // (1) warp w reads lanes 32 (w % 4) .. + 31, sample half w / 4, of the row
+    //     block's accumulator into a row-major tile (SB + 1 floats a row)
     float* ct = reinterpret_cast<float*>(sm);
     float* rowd = ct + kRows * (SB + 1);  // D_j of each row
     float* rowp = rowd + kRows;           // phi_j of each row
     const int q4 = warp & 3, hs = warp >> 2;
-    {
-      const int rr = 32 * q4 + lane;
-      const uint32_t lanes = (uint32_t)(32 * q4) << 16;
-      const int hsb = SB / 2;
-      for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
-        float cv[8];
-        tmem_ld8(tmem + lanes + (uint32_t)cb, cv);
+    for (int rb = 0; rb < nrbe; ++rb) {
+      {
+        const int rr = 32 * q4 + lane;
+        const uint32_t lanes = (uint32_t)(32 * q4) << 16;
+        const int hsb = SB / 2;
+        for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
+          float cv[8];
+          tmem_ld8(tmem + lanes + (uint32_t)(rb * SB + cb), cv);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) ct[rr * (SB + 1) + cb + i] = cv[i];
+          for (int i = 0; i < 8; ++i) ct[rr * (SB + 1) + cb + i] = cv[i];
+        }
+        if (hs == 0) {
+          const int32_t jr = 2 * (kRows * rb + rr) + par;
+          rowd[rr] = dsum[rb * kT + rr] + dsum[rb * kT + kRows + rr];
+          rowp[rr] = sqrtf(2.f / (float)(m + 1)) * sinpif((float)(jr + 1) / (float)(m + 1));
+        }
       }
-      if (hs == 0) {
-        const int32_t jr = 2 * (kRows * rb + rr) + par;
-        rowd[rr] = dpart[rr] + dpart[kRows + rr];
-        rowp[rr] = sqrtf(2.f / (float)(m + 1)) * sinpif((float)(jr + 1) / (float)(m + 1));
-      }
-    }
-    if (async_bh) asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    // (2) c_j = D_j bh_j + phi_j C_j over whole rows: consecutive threads take
-    //     consecutive samples of one mode, so every store is coalesced
+      if (async_bh) asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      // (2) c_j = D_j bh_j + phi_j C_j over whole rows: consecutive threads take
+      //     consecutive samples of one mode, so every store is coalesced
 #pragma unroll 4
-    for (int idx = tid; idx < kRows * SB; idx += kT) {
-      const int rr = idx / SB, sc = idx - rr * SB;
-      const int32_t jr = 2 * (kRows * rb + rr) + par;
-      if (jr < m && sc < kv) {
-        float* o = bhat + (off + jr) * S + s0 + sc;
-        const float bh = async_bh ? bht[rr * SB + sc] : *o;
-        *o = fmaf(rowd[rr], bh, rowp[rr] * ct[rr * (SB + 1) + sc]);
+      for (int idx = tid; idx < kRows * SB; idx += kT) {
+        const int rr = idx / SB, sc = idx - rr * SB;
+        const int32_t jr = 2 * (kRows * rb + rr) + par;
+        if (jr < m && sc < kv) {
+          float* o = bhat + (off + jr) * S + s0 + sc;
+          const float bh = async_bh ? bht[rr * SB + sc] : *o;
+          *o = fmaf(rowd[rr], bh, rowp[rr] * ct[rr * (SB + 1) + sc]);
+        }
       }
+      __syncthreads();  // the tile and bh rows read: the next row block's may land
+      if (rb + 1 < nrbe) fetch_bh(rb + 1);
     }
     fence_before();
     __syncthreads();  // accumulators, tables and shared tiles read before the next unit
@@ -665,7 +691,8 @@ __global__ void __launch_bounds__(kT, 2)
 size_t ends_smem() { return 1024 + 2 * (size_t)kStage + 3 * (size_t)kMaxKE * 4 + 64; }
 size_t coef_smem(int32_t L) {
   const size_t lk = (size_t)(L + kK - 1) / kK * kK;
-  return 1024 + 2 * (size_t)kStage + kBhTile + (3 * lk + kT) * sizeof(float) + 64;
+  return 1024 + 2 * (size_t)kStage + kBhTile +
+         (3 * lk + (size_t)kMaxRB * (kRows + kT)) * sizeof(float) + 64;
 }
 
 }  // namespace
@@ -721,13 +748,11 @@ int launch_spec_coef_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
   const size_t smem = coef_smem(nd.L);
   auto kern = consistent ? spec_coef_umma_kernel<true> : spec_coef_umma_kernel<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int32_t mmax = g.max_m < kMaxM ? g.max_m : kMaxM;
-  // row blocks of 128 modes of one parity
-  const int32_t nrb = mmax > 0 ? ((mmax + 1) / 2 + kRows - 1) / kRows : 1;
-  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * nrb * 2;
+  // one unit per (edge, sample block, parity), all its row blocks of modes
+  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * 2;
   const int64_t cap = 2 * (int64_t)n_sm;
   kern<<<(int)(units < cap ? units : cap), kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, xw, SB,
-                                                           nrb, status);
+                                                           status);
   return 1;
 }
 
