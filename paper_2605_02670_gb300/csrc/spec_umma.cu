@@ -62,7 +62,8 @@ constexpr uint32_t kStage = 2 * kATile + 2 * kBPlane;  // A hi/lo, B hi/lo
 constexpr uint32_t kBhTile = kRows * kMaxSB * 4;       // a coefficient unit's bh rows: 16 KB
 constexpr int kMaxM = kSpecMaxM;               // modes of the sine-basis path
 constexpr int kMaxKE = kMaxM + 2 * kK;         // K positions of the end values (both parities)
-constexpr uint32_t kColsEnds = 64;             // two accumulators of SB columns
+constexpr int kEndsRB = 2;                     // row blocks of 128 nodes per end-value unit
+constexpr uint32_t kColsEnds = 2 * kEndsRB * 32;  // two accumulators of SB columns per block
 constexpr int kMaxRB = (kMaxM / 2 + 127) / 128;  // row blocks of one parity's modes
 constexpr uint32_t kColsCoef = kMaxRB * kMaxSB;   // one accumulator per row block
 constexpr size_t kSmemLimit = 232448;          // 227 KB per CTA
@@ -171,6 +172,10 @@ __global__ void __launch_bounds__(kT, 2)
                           PcgStatus* __restrict__ status) {
   extern __shared__ unsigned char se_raw[];
   unsigned char* sm = align1024(se_raw);
+  // two A buffers (hi and lo planes) for the row blocks in turn, then two B
+  // buffers for the K stages in turn
+  unsigned char* const abuf = sm;
+  unsigned char* const bbuf = sm + 4 * kATile;
   // per-unit tables in K order (the even modes, then the odd modes, each
   // padded to whole stages): mode shift, phi_j (0 on padding), mode (-1)
   float* sigk = reinterpret_cast<float*>(sm + 2 * kStage);
@@ -185,18 +190,21 @@ __global__ void __launch_bounds__(kT, 2)
   const int32_t L = nd.L;
   const int64_t nsb = (S + SB - 1) / SB;
   const int32_t nrb = (L + kRows - 1) / kRows;
-  const int64_t units = (int64_t)n_edges * nsb * nrb;
+  const int32_t ngr = (nrb + kEndsRB - 1) / kEndsRB;  // groups of kEndsRB row blocks
+  const int64_t units = (int64_t)n_edges * nsb * ngr;
   // B tile item of this thread: sample bn, K chunk bc (SB x 8 <= 256 items)
   const bool bitem = tid < SB * 8;
   const int bn = tid % SB, bc = tid / SB;
 
   for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
-    const int32_t rb = (int32_t)(u % nrb);
-    const int64_t rest = u / nrb;
+    const int32_t gr = (int32_t)(u % ngr);
+    const int64_t rest = u / ngr;
     const int64_t s0 = (rest % nsb) * SB;
     const int32_t e = edges[rest / nsb];
     const int32_t m = g.nel[e] - 1;
     if (m < 1) continue;
+    const int32_t rb0 = gr * kEndsRB;
+    const int nrbe = nrb - rb0 < kEndsRB ? nrb - rb0 : kEndsRB;  // row blocks of this unit
     const int kv = (int)(S - s0 < SB ? S - s0 : SB);
     const int64_t off = g.ioff[e];
     const float h2f = (float)(g.he[e] * g.he[e]);
@@ -213,9 +221,6 @@ __global__ void __launch_bounds__(kT, 2)
       modek[p] = j;
     }
     __syncthreads();
-    const int32_t l = rb * kRows + row;
-    const float dl = l < L ? nd.shift[l] * h2f : 1.f;
-    const float ep = kCons ? 1.f - dl * (1.f / 6.f) : 1.f;
     const float* bcol = bhat + off * S + s0 + bn;
     const bool bok = bitem && bn < kv;
     float xb[8];
@@ -229,89 +234,99 @@ __global__ void __launch_bounds__(kT, 2)
     };
     load_b(0, xb);
     int last = 0;
-    for (int t = 0; t < nk; ++t) {
-      const int st = t & 1;
-      last = st;
+    for (int t = 0; t < nk && !pp.failed; ++t) {
       float xn[8];
       if (t + 1 < nk) load_b(t + 1, xn);
-      if (!pp.acquire(st)) break;
-      unsigned char* a_hi = sm + st * kStage;
-      unsigned char* a_lo = a_hi + kATile;
-      unsigned char* b_hi = a_lo + kATile;
+      unsigned char* b_hi = bbuf + (t & 1) * 2 * kBPlane;
       unsigned char* b_lo = b_hi + kBPlane;
       const float* sg = sigk + t * kK + half * 32;
-      // rows past the last node are left as they are: a GEMM row depends on
-      // its own A row only, and the epilogue stores none of them
-      if (l < L) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const float4 s4a = *reinterpret_cast<const float4*>(sg + 8 * c);
-          const float4 s4b = *reinterpret_cast<const float4*>(sg + 8 * c + 4);
-          const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
+      for (int rb = 0; rb < nrbe; ++rb) {
+        // sub-stage (t, rb) in A buffer st; acquiring it (its MMAs of two
+        // sub-stages ago are done) also frees the B buffer of stage t - 2
+        const int st = (t * nrbe + rb) & 1;
+        last = st;
+        if (!pp.acquire(st)) break;
+        unsigned char* a_hi = abuf + st * 2 * kATile;
+        unsigned char* a_lo = a_hi + kATile;
+        if (rb == 0 && bitem) {
+          const float* pk = phik + t * kK + bc * 8;
           float x[8];
 #pragma unroll
-          for (int r = 0; r < 8; ++r)
-            x[r] = kCons ? ep * rcp_approx(fmaf(sv[r], ep, dl)) : rcp_approx(sv[r] + dl);
-          store_a_row(a_hi, a_lo, row, 4 * half + c, x);
+          for (int r = 0; r < 8; ++r) x[r] = pk[r] * xb[r];
+          store_b_row(b_hi, b_lo, bn, bc, x);
         }
-      }
-      if (bitem) {
-        const float* pk = phik + t * kK + bc * 8;
-        float x[8];
+        // rows past the last node are left as they are: a GEMM row depends on
+        // its own A row only, and the epilogue stores none of them
+        const int32_t l = (rb0 + rb) * kRows + row;
+        if (l < L) {
+          const float dl = nd.shift[l] * h2f;
+          const float ep = kCons ? 1.f - dl * (1.f / 6.f) : 1.f;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) x[r] = pk[r] * xb[r];
-        store_b_row(b_hi, b_lo, bn, bc, x);
+          for (int c = 0; c < 4; ++c) {
+            const float4 s4a = *reinterpret_cast<const float4*>(sg + 8 * c);
+            const float4 s4b = *reinterpret_cast<const float4*>(sg + 8 * c + 4);
+            const float sv[8] = {s4a.x, s4a.y, s4a.z, s4a.w, s4b.x, s4b.y, s4b.z, s4b.w};
+            float x[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+              x[r] = kCons ? ep * rcp_approx(fmaf(sv[r], ep, dl)) : rcp_approx(sv[r] + dl);
+            store_a_row(a_hi, a_lo, row, 4 * half + c, x);
+          }
+        }
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          // odd modes from stage ks_e on, into each row block's second accumulator
+          issue_stage(tmem, (uint32_t)((2 * rb + (t >= ks_e ? 1 : 0)) * SB), a_hi, a_lo, b_hi,
+                      b_lo, idesc, t != 0 && t != ks_e);
+          commit(&pp.mbar[st]);
+        }
+        pp.bump(st);
       }
       if (t + 1 < nk) {
 #pragma unroll
         for (int r = 0; r < 8; ++r) xb[r] = xn[r];
       }
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        // odd modes from stage ks_e on, into the second accumulator
-        issue_stage(tmem, t >= ks_e ? (uint32_t)SB : 0u, a_hi, a_lo, b_hi, b_lo, idesc,
-                    t != 0 && t != ks_e);
-        commit(&pp.mbar[st]);
-      }
-      pp.bump(st);
     }
     if (pp.failed || !pp.drain(last)) break;
     // epilogue: warp w reads lanes 32 (w % 4) .. + 31, sample half w / 4, of
-    // both accumulators
+    // both accumulators of each row block
     const int q4 = warp & 3, hs = warp >> 2;
-    const int32_t lr = rb * kRows + 32 * q4 + lane;
     const uint32_t lanes = (uint32_t)(32 * q4) << 16;
     const int hsb = SB / 2;
     const int64_t dv = (int64_t)g.ev[e] - g.eu[e];
-    for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
-      float o[8], v[8];
-      tmem_ld8(tmem + lanes + (uint32_t)cb, o);
-      if (ks_o > 0) {
-        tmem_ld8(tmem + lanes + (uint32_t)(SB + cb), v);
-      } else {
+    for (int rb = 0; rb < nrbe; ++rb) {
+      const int32_t lr = (rb0 + rb) * kRows + 32 * q4 + lane;
+      const uint32_t c0 = (uint32_t)(2 * rb * SB);
+      for (int cb = hs * hsb; cb < (hs + 1) * hsb; cb += 8) {
+        float o[8], v[8];
+        tmem_ld8(tmem + lanes + c0 + (uint32_t)cb, o);
+        if (ks_o > 0) {
+          tmem_ld8(tmem + lanes + c0 + (uint32_t)(SB + cb), v);
+        } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = 0.f;
-      }
-      if (lr < L && ends) {
-        // per-edge buffer [e][end][s][l]: lanes write consecutive nodes
-        float* pe = ends + ((int64_t)e * 2 * S + s0 + cb) * L + lr;
-        const int64_t side = S * (int64_t)L;
+          for (int i = 0; i < 8; ++i) v[i] = 0.f;
+        }
+        if (lr < L && ends) {
+          // per-edge buffer [e][end][s][l]: lanes write consecutive nodes
+          float* pe = ends + ((int64_t)e * 2 * S + s0 + cb) * L + lr;
+          const int64_t side = S * (int64_t)L;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (cb + i < kv) {
-            pe[(int64_t)i * L] = o[i] + v[i];
-            pe[(int64_t)i * L + side] = o[i] - v[i];
-          }
-      } else if (lr < L) {
-        double* pa = gvec + ((int64_t)lr * S + s0 + cb) * g.nv + g.eu[e];
+          for (int i = 0; i < 8; ++i)
+            if (cb + i < kv) {
+              pe[(int64_t)i * L] = o[i] + v[i];
+              pe[(int64_t)i * L + side] = o[i] - v[i];
+            }
+        } else if (lr < L) {
+          double* pa = gvec + ((int64_t)lr * S + s0 + cb) * g.nv + g.eu[e];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if (cb + i < kv) {
-            atomicAdd(pa, (double)(o[i] + v[i]));
-            atomicAdd(pa + dv, (double)(o[i] - v[i]));
-            pa += g.nv;
-          }
+          for (int i = 0; i < 8; ++i)
+            if (cb + i < kv) {
+              atomicAdd(pa, (double)(o[i] + v[i]));
+              atomicAdd(pa + dv, (double)(o[i] - v[i]));
+              pa += g.nv;
+            }
+        }
       }
     }
     fence_before();
@@ -719,7 +734,8 @@ int launch_spec_ends_umma(const DevGraph& g, const DevNodes& nd, int64_t S,
   const size_t smem = ends_smem();
   auto kern = consistent ? spec_ends_umma_kernel<true> : spec_ends_umma_kernel<false>;
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * ((nd.L + kRows - 1) / kRows);
+  const int64_t nrb = (nd.L + kRows - 1) / kRows;
+  const int64_t units = (int64_t)n * ((S + SB - 1) / SB) * ((nrb + kEndsRB - 1) / kEndsRB);
   const int64_t cap = 2 * (int64_t)n_sm;  // two CTAs per SM
   kern<<<(int)(units < cap ? units : cap), kT, smem, st>>>(g, nd, S, bin_edges, n, bhat, gvec,
                                                            ends, SB, status);
