@@ -952,7 +952,7 @@ int ensure_side(grf_graph* g) {
 template <typename T>
 int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64_t S,
                  const T* b, double* gvec, double* xv, const Opts& o, cudaStream_t st,
-                 RunStats* rs) {
+                 RunStats* rs, bool* xw_ready = nullptr) {
   const DevNodes nd = dev_nodes(w, L);
   CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(PcgStatus), st));
   // the Thomas sweep constants are needed only where an edge is left to Thomas
@@ -1066,13 +1066,18 @@ int vertex_phase(grf_graph* g, const ApplyWs& w, int32_t L, double kappa2, int64
   }
   rs->begin(3, st);
   const int pre = learned ? kPreLearned : (neumann ? kPreNeumann : kPreJacobi);
-  const PcgPairs pairs{w.dpair, w.opair, w.xh, w.xl, w.gh, w.gl, g32};
+  // with g in FP32 (the tensor-core sampler path) the PCG also hands the
+  // recovery its weighted values w_l u^(l) directly
+  const bool xw_out = g32 && w.xw && xw_ready;
+  const PcgPairs pairs{w.dpair, w.opair, w.xh, w.xl, w.gh, w.gl, g32,
+                       xw_out ? (float*)w.xw : nullptr, w.weight, xv};
+  if (xw_ready) *xw_ready = xw_out;
   launch_pcg<T>(g->d, g->d_order, g->d_ell, L, S, w.diag, w.offv, (const T*)w.dscale, offv_t, pre,
                 (const T*)w.pre_c, (const T*)w.pre_n, gvec, xv, (T*)w.d, (T*)w.r, (T*)w.p,
                 (T*)w.q, (T*)w.y, o.rtol, o.max_iter, w.iters, w.status, o.pcg_layout, st,
                 w.dpair ? &pairs : nullptr);
   rs->end(3, st);
-  rs->launches += 1;
+  rs->launches += xw_out ? 2 : 1;  // the PCG (and its weighted-output pass)
   CUDA_TRY(cudaGetLastError());
   return GRF_OK;
 }
@@ -1094,7 +1099,8 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   } else {
     GRF_TRY(upload_nodes(hn, w, st));
   }
-  GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs));
+  bool xw_ready = false;  // the PCG wrote the recovery's weighted values
+  GRF_TRY(vertex_phase<T>(g, w, hn.L(), k2, S, b, w.gvec, w.x, o, st, rs, &xw_ready));
   const bool spec = sizeof(T) == 4 && o.spectral;
   const int p = sizeof(T) == 8 ? 1 : (spec ? 2 : 0);
   // FP32: bins from i0 on (and the edges beyond every bin) by the node sweeps
@@ -1106,7 +1112,7 @@ int dd_apply(grf_graph* g, const HostNodes& hn, double kappa, int64_t S, const T
   rs->launches += launch_recover<T, OutT>(g->d, dev_nodes(w, hn.L()), k2, S, b, w.x, out,
                                           (const SweepParams<T>*)w.prm, (T*)w.xw,
                                           g->d_bin_edges[p], counts, g->n_bins[p], w.acc,
-                                          (T*)w.yscr, (T*)w.rpscr, o.recover_sg, st);
+                                          (T*)w.yscr, (T*)w.rpscr, o.recover_sg, st, xw_ready);
   if (sizeof(T) == 4 && tail > 0)
     rs->launches += launch_recover_nodes<OutT>(
         g->d, hn.L(), S, (const float*)b, (const SweepParams<float>*)w.prm, (const float*)w.xw,

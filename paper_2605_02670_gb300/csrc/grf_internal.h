@@ -140,12 +140,15 @@ int launch_condense(const DevGraph& g, const DevNodes& nd, double kappa2, int64_
 // need acc/yscr/rpscr, sized [n_interior][S]). bin_count is a host array.
 // Returns the number of kernels launched.
 // prm: sweep constants from launch_schur; xw: [L][nv][S] scratch that receives
-// w_l u_v^(l) in precision T (sample-minor).
+// w_l u_v^(l) in precision T (sample-minor). xw_ready: xw already holds them
+// (FP32, written by the batched PCG) and xv is not read: the vertex values are
+// their sums over the nodes.
 template <typename T, typename OutT>
 int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S,
                    const T* b, const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins,
-                   double* acc, T* yscr, T* rpscr, int sg, cudaStream_t st);
+                   double* acc, T* yscr, T* rpscr, int sg, cudaStream_t st,
+                   bool xw_ready = false);
 // ---- sweep.cu (FP32 interiors)
 // Node-parallel sweeps: one warp per (edge, 4 samples), each lane a set of
 // quadrature nodes (at most kNodeSweepMaxNL per lane, so L <= 32 kNodeSweepMaxNL).
@@ -199,6 +202,12 @@ struct PcgPairs {
   // true: gh already holds g in FP32 (launch_spec_ends_umma's g32) and the
   // FP64 gvec is not read
   bool g32;
+  // not null: the solutions leave as the recovery's weighted values
+  // xw[l][v][s] = w_l u_v^(l) (FP32, weight = the node weights w_l) instead of
+  // the FP64 x
+  float* xw;
+  const double* weight;
+  double* gn;  // [L][S] scratch for ||g|| of each system (with xw)
 };
 void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, const double* diag,
                       const double* offv, const float* dscale, const float* offv_t,

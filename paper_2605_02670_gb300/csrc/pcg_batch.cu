@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
     float* __restrict__ R, float* __restrict__ PA, float* __restrict__ PB,
     float* __restrict__ Dv, float* __restrict__ XH, float* __restrict__ XL,
     float* __restrict__ GH, float* __restrict__ GL, double rtol, int32_t max_iter,
-    int32_t* __restrict__ iters, PcgStatus* __restrict__ status, int g32) {
+    int32_t* __restrict__ iters, PcgStatus* __restrict__ status, int g32,
+    double* __restrict__ gnout) {
   __shared__ BatchShared sh;
   const int32_t nv = g.nv;
   const int64_t ne2 = 2 * (int64_t)g.ne;
@@ -692,8 +693,12 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
       }
       __syncthreads();
     }
-    // ---- x = ||g|| (x~hi + x~lo) in FP64
-    {
+    // ---- x = ||g|| (x~hi + x~lo) in FP64; or only ||g|| per system, from
+    // which pcg_batch_out_kernel forms the recovery's weighted values
+    if (gnout) {
+      if (threadIdx.x < kSG && s0 + threadIdx.x < S)
+        gnout[l * S + s0 + threadIdx.x] = sh.st[threadIdx.x].gn;
+    } else {
       double gn[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) gn[i] = sh.st[4 * hh + i].gn;
@@ -722,6 +727,31 @@ __global__ void __launch_bounds__(kBT, 3) pcg_batch_kernel(
 #undef XS
 #undef LIVE
 
+// xw[l][v][s] = w_l ||g||_ls (x~hi + x~lo)[l][s / 8][v][s % 8] in FP32: thread
+// per (l, v, four samples), consecutive threads on consecutive samples, so the
+// writes are coalesced and the reads whole 16-byte pieces of the sample rows.
+__global__ void __launch_bounds__(256)
+    pcg_batch_out_kernel(int32_t nv, int32_t L, int64_t S, const float* __restrict__ XH,
+                         const float* __restrict__ XL, const double* __restrict__ gn,
+                         const double* __restrict__ weight, float* __restrict__ xw) {
+  const int64_t nq = (S + 3) / 4, nsg = (S + kSG - 1) / kSG;
+  const int64_t n = (int64_t)L * nv * nq;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = t % nq, lv = t / nq;
+    const int64_t v = lv % nv, l = lv / nv;
+    const int64_t s = 4 * q;
+    const int64_t src = ((l * nsg + s / kSG) * nv + v) * kSG + (s % kSG);
+    const float4 h = ld4(XH + src), lo = ld4(XL + src);
+    const double w = weight[l];
+    const float y[4] = {h.x + lo.x, h.y + lo.y, h.z + lo.z, h.w + lo.w};
+    float* o = xw + lv * S + s;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (s + i < S) o[i] = (float)(w * gn[l * S + s + i]) * y[i];
+  }
+}
+
 // Vectors of the batched layout need [L][ceil(S / 8) * 8][nv] floats each.
 int64_t pcg_batch_padded_samples(int64_t S) { return (S + kSG - 1) / kSG * kSG; }
 
@@ -738,7 +768,15 @@ void launch_pcg_batch(const DevGraph& g, const int4* ell, int32_t L, int64_t S, 
   const int blocks = (int)(items < (int64_t)1 << 30 ? items : (int64_t)1 << 30);
   pcg_batch_kernel<<<blocks, kBT, 0, st>>>(g, ell, L, S, pp.dp, pp.op, dscale, offv_t, gvec, x, R,
                                            PA, PB, Dv, pp.xh, pp.xl, pp.gh, pp.gl, rtol, max_iter,
-                                           iters, status, pp.g32 ? 1 : 0);
+                                           iters, status, pp.g32 ? 1 : 0,
+                                           pp.xw ? pp.gn : nullptr);
+  if (pp.xw) {
+    const int64_t n = (int64_t)L * g.nv * ((S + 3) / 4);
+    const int64_t blocks = (n + 255) / 256 < (int64_t)sm_count() * 32 ? (n + 255) / 256
+                                                                        : (int64_t)sm_count() * 32;
+    pcg_batch_out_kernel<<<(int)blocks, 256, 0, st>>>(g.nv, L, S, pp.xh, pp.xl, pp.gn, pp.weight,
+                                                      pp.xw);
+  }
 }
 
 }  // namespace grf

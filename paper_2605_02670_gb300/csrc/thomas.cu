@@ -242,6 +242,78 @@ __global__ void __launch_bounds__(kAccTile * kAccRows)
   }
 }
 
+// The vertex values from weighted values the batched PCG wrote already
+// (xw[l][v][s] = w_l u_v^(l), FP32): out(s, v) = sum over l, accumulated as an
+// FP32 pair per value (about 48 bits, no FP64 instruction). One CTA per tile of
+// 32 vertices x 32 samples: the lanes read along the samples, four rows of
+// vertices per thread, and a transpose in shared memory writes along the
+// vertices.
+__device__ __forceinline__ void pair_add(float& h, float& l, float t) {
+  const float s = __fadd_rn(h, t);
+  const float bv = __fsub_rn(s, h);
+  l = __fadd_rn(l, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bv)), __fsub_rn(t, bv)));
+  h = s;
+}
+
+template <typename OutT>
+__global__ void __launch_bounds__(kAccTile * kAccRows)
+    vertex_sum_kernel(DevGraph g, int32_t L, int64_t S, const float* __restrict__ xw,
+                      OutT* __restrict__ out) {
+  __shared__ float tile[kAccS][kAccTile + 1];
+  const int tx = threadIdx.x % kAccTile, ty = threadIdx.x / kAccTile;
+  const int64_t n_vt = (g.nv + kAccTile - 1) / kAccTile;
+  const int64_t n_sc = (S + kAccS - 1) / kAccS;
+  constexpr int kQ = kAccTile / kAccRows;
+  const int64_t lstride = (int64_t)g.nv * S;
+  for (int64_t b = blockIdx.x; b < n_vt * n_sc; b += gridDim.x) {
+    const int64_t v0 = (b % n_vt) * kAccTile, s0 = (b / n_vt) * kAccS;
+    const int vn = (int)(g.nv - v0 < kAccTile ? g.nv - v0 : kAccTile);
+    const int sn = (int)(S - s0 < kAccS ? S - s0 : kAccS);
+    float h[kQ], lo[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) h[q] = lo[q] = 0.f;
+    const float* p = xw + (v0 + ty) * S + s0 + tx;
+    if (tx < sn) {
+      int32_t l = 0;
+      for (; l + 4 <= L; l += 4) {
+        float x[4][kQ];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < kQ; ++q)
+            x[u][q] = ty + q * kAccRows < vn ? __ldg(p + (l + u) * lstride + q * kAccRows * S)
+                                             : 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) pair_add(h[q], lo[q], x[u][q]);
+      }
+      for (; l < L; ++l)
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+          if (ty + q * kAccRows < vn) pair_add(h[q], lo[q], __ldg(p + l * lstride + q * kAccRows * S));
+    }
+    if (sizeof(OutT) == 8) {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int j = ty + q * kAccRows;
+        if (tx < sn && j < vn) out[(s0 + tx) * g.n + v0 + j] = (OutT)((double)h[q] + (double)lo[q]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) tile[tx][ty + q * kAccRows] = h[q] + lo[q];
+      __syncthreads();
+      // thread (tx, ty): vertex v0 + tx of samples ty, ty + 8, ...
+#pragma unroll
+      for (int q = 0; q < kAccS / kAccRows; ++q) {
+        const int s = ty + q * kAccRows;
+        if (s < sn && tx < vn) out[(s0 + s) * g.n + v0 + tx] = (OutT)tile[s][tx];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // thread -> (e, sample group); loops over all nodes l, keeping the FP64 sum
 // of w_l x^(l) in acc. yscr / rpscr hold the forward sweep for the back sweep.
 template <typename T, typename OutT>
@@ -381,11 +453,15 @@ template <typename T, typename OutT>
 int launch_recover(const DevGraph& g, const DevNodes& nd, double kappa2, int64_t S, const T* b,
                    const double* xv, OutT* out, const SweepParams<T>* prm, T* xw,
                    const int32_t* bin_edges, const int32_t* bin_count, int32_t n_bins, double* acc,
-                   T* yscr, T* rpscr, int sg, cudaStream_t st) {
+                   T* yscr, T* rpscr, int sg, cudaStream_t st, bool xw_ready) {
   {
     const int64_t tiles = ((g.nv + kAccTile - 1) / kAccTile) * ((S + kAccS - 1) / kAccS);
-    vertex_accum_kernel<T, OutT><<<grid_for(tiles * 256, 256), kAccTile * kAccRows, 0, st>>>(
-        g, nd, S, xv, out, xw);
+    if (xw_ready && sizeof(T) == 4)
+      vertex_sum_kernel<OutT><<<grid_for(tiles * 256, 256), kAccTile * kAccRows, 0, st>>>(
+          g, nd.L, S, (const float*)xw, out);
+    else
+      vertex_accum_kernel<T, OutT><<<grid_for(tiles * 256, 256), kAccTile * kAccRows, 0, st>>>(
+          g, nd, S, xv, out, xw);
   }
   int launches = 1;
   if (g.ni == 0) return launches;
@@ -420,7 +496,7 @@ template int launch_condense<double>(const DevGraph&, const DevNodes&, double, i
   template int launch_recover<T, O>(const DevGraph&, const DevNodes&, double, int64_t, const T*, \
                                     const double*, O*, const SweepParams<T>*, T*,                \
                                     const int32_t*, const int32_t*, int32_t, double*, T*, T*,    \
-                                    int, cudaStream_t);
+                                    int, cudaStream_t, bool);
 GRF_INST_RECOVER(float, float)
 GRF_INST_RECOVER(float, double)
 GRF_INST_RECOVER(double, double)
