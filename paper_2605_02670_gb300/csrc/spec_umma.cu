@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256)
       rec[q] = ok ? __ldg(g.spec_inc + v) : make_int4(-1, -1, -1, -1);
       cnt[q] = ok ? __ldg(g.spec_cnt + v) : 0;
     }
-#pragma unroll 1
+#pragma unroll 2
     for (int j = 0; j < 8; ++j) {
       const int64_t s = sg * 8 + j;
       const bool sok = s < S;
