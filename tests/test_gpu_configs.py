@@ -308,6 +308,29 @@ def test_umma_with_edges_beyond_the_sine_basis(S):
     assert rel_l2(u.cpu().numpy(), ref, ml) < TOL["mixed"]
 
 
+@pytest.mark.parametrize("S", [8, 11])
+@pytest.mark.parametrize("out_dtype", ["f32", "f64"])
+def test_umma_with_batched_pcg_fp32_rhs_and_weighted_output(S, out_dtype):
+    """Every edge on the tensor-core path with the batched vertex PCG: the
+    end-value gather writes g in FP32 into the PCG's sample rows, the PCG hands
+    the recovery its weighted values in FP32 and the vertex values are FP32-pair
+    sums of them. 11 samples give a ragged sample group (padded samples written
+    as zero, scalar stores of the weighted values). Against the oracle, and
+    against the same call with the per-system PCG (FP64 solutions, FP64 vertex
+    sums)."""
+    g = small_lattice()
+    G = _graph(g, h=H9)
+    kappa, beta, k, seed = 2.0, 0.75, 0.25, 6
+    ml, ref = _oracle("lattice6", g, kappa, beta, k, seed, S, h=H9)
+    u, st = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype=out_dtype,
+                     interior="spectral_umma", pcg_layout="batched")
+    assert st["n_unconverged"] == 0 and st["numeric_flag"] == 0
+    assert rel_l2(u.double().cpu().numpy(), ref, ml) < TOL["mixed"]
+    u2, _ = G.sample(kappa, beta, k, seed, S, precision="mixed", out_dtype=out_dtype,
+                     interior="spectral_umma", pcg_layout="per_system")
+    assert rel_l2(u.double().cpu().numpy(), u2.double().cpu().numpy(), ml) < 1e-5
+
+
 def test_umma_transforms_graph_replay_and_apply():
     """The tensor-core path inside a captured CUDA graph (replayed twice with
     different seeds) and through the general right-hand-side entry point."""
