@@ -313,8 +313,10 @@ int grf_vertex_solve(grf_graph* g, double kappa, double alpha, double gamma, int
  *   graph on that device before; otherwise GRF_EINVAL, with no device work.
  *   Sizes whose scratch (about 8 n_dofs n_rhs bytes in FP64, 4 in mixed
  *   precision, plus the Schur system, the per-edge sweep constants and four
- *   PCG vectors per right-hand side) exceeds 16 MiB are rejected with
- *   GRF_EINVAL and a message naming the limit and the bytes needed.
+ *   PCG vectors per right-hand side; in mixed precision also the Schur system
+ *   as FP32 pairs and four more vectors for the batched PCG's refinement)
+ *   exceeds 16 MiB are rejected with GRF_EINVAL and a message naming the
+ *   limit and the bytes needed.
  *   The first call on a device looks up the device address of the static array
  *   (once per device, with that device current); make that first call before
  *   any stream capture. All calls share the one array and it keeps the last
